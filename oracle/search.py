@@ -1,0 +1,163 @@
+"""Discrete-search oracle -- TEST INFRASTRUCTURE ONLY (plain Python).
+
+Follows Sec. III-B of the paper:
+  * Eq. mode_selection: full enumeration picks argmin of the merit over the
+    evaluated orders (feasible first; ties go to the lower enumeration index);
+  * Eq. search_merit:   M_hat = J_hat + mu * max(v_hat - eps_feas, 0);
+  * "Neighborhood expansion": N_1(m) = one insertion, deletion or
+    substitution of a mode segment;
+  * Algorithm 1: walk the evaluated set V in increasing merit and admit unseen
+    neighbours (not in V or the next batch) until the batch holds B orders.
+
+Readings where the paper is silent (listed in the design notes):
+  * enumeration order of a neighbourhood: substitutions (position, then mode
+    ascending), then insertions (position 0..L, mode ascending), then
+    deletions (position ascending); lengths outside [1, L_max] are skipped;
+  * only the k best orders of V are walked (beam k);
+  * rank key (M_hat, code) -- the u64 mode code breaks ties;
+  * mode code: code = L + sum_i (m_i + 1) (M + 1)^(i + 1).
+"""
+from __future__ import annotations
+
+from typing import Iterable, Sequence
+
+
+def encode(seq: Sequence[int], n_modes: int) -> int:
+    """u64 mode code of a sequence (length in the lowest digit)."""
+    base = n_modes + 1
+    code = len(seq)
+    p = base
+    for m in seq:
+        code += (int(m) + 1) * p
+        p *= base
+    assert code < 2 ** 64
+    return code
+
+
+def decode(code: int, n_modes: int) -> tuple[int, ...]:
+    base = n_modes + 1
+    L = code % base
+    code //= base
+    out = []
+    for _ in range(L):
+        out.append(code % base - 1)
+        code //= base
+    return tuple(out)
+
+
+def merit(cost: float, viol: float, eps_feas: float = 1e-5, mu: float = 100.0) -> float:
+    """Eq. search_merit."""
+    return cost + mu * max(viol - eps_feas, 0.0)
+
+
+def enumeration_argmin(costs, viols, eps_feas: float = 1e-5, mu: float = 100.0) -> int:
+    """Eq. mode_selection over an enumerated list: the feasible order of least
+    merit (lowest index on ties); if none is feasible, the least merit."""
+    best, best_key = -1, None
+    for i, (c, v) in enumerate(zip(costs, viols)):
+        key = (0 if v <= eps_feas else 1, merit(c, v, eps_feas, mu), i)
+        if best_key is None or key < best_key:
+            best, best_key = i, key
+    return best
+
+
+def neighbours(seq: Sequence[int], n_modes: int, l_max: int) -> list[tuple[int, ...]]:
+    """N_1(m) in the enumeration order stated in the module docstring
+    (duplicates kept; the caller skips orders already seen)."""
+    s = tuple(int(m) for m in seq)
+    L = len(s)
+    out: list[tuple[int, ...]] = []
+    for i in range(L):                       # substitutions
+        for m in range(n_modes):
+            if m != s[i]:
+                out.append(s[:i] + (m,) + s[i + 1:])
+    if L + 1 <= l_max:                       # insertions
+        for i in range(L + 1):
+            for m in range(n_modes):
+                out.append(s[:i] + (m,) + s[i:])
+    if L - 1 >= 1:                           # deletions
+        for i in range(L):
+            out.append(s[:i] + s[i + 1:])
+    return out
+
+
+def neighbour_slots(n_modes: int, l_max: int) -> int:
+    """Upper bound on |N_1(m)| for any m of length <= l_max: the number of
+    neighbour slots per parent used to order candidates."""
+    L = l_max
+    return L * (n_modes - 1) + (L + 1) * n_modes + L
+
+
+def expand(evaluated: dict, k: int, batch: int, n_modes: int, l_max: int) -> list[tuple[int, ...]]:
+    """One round of Algorithm 1 (lines 5-10) on the evaluated set
+    V = {code: (merit, seq)}: walk the k best orders by (merit, code) and
+    admit unseen neighbours until `batch` orders are collected."""
+    ranked = sorted(evaluated.items(), key=lambda kv: (kv[1][0], kv[0]))[:k]
+    seen = set(evaluated)
+    out: list[tuple[int, ...]] = []
+    for _, (_, seq) in ranked:
+        for nb in neighbours(seq, n_modes, l_max):
+            c = encode(nb, n_modes)
+            if c in seen:
+                continue
+            seen.add(c)
+            out.append(nb)
+            if len(out) == batch:
+                return out
+    return out
+
+
+def run_expansion(evaluate, seed_batch: Iterable[Sequence[int]], k: int, batch: int, n_modes: int,
+                  l_max: int, rounds: int, budget: int | None = None):
+    """Algorithm 1's loop: evaluate F_s, add to V, expand; stops after
+    `rounds` expansions, when no unseen neighbour remains, or at the budget
+    (the last batch is truncated to fit).  evaluate(list_of_seqs) returns a
+    list of merits.  Returns V = {code: (merit, seq)} and the batch sizes."""
+    V: dict = {}
+    frontier = [tuple(int(m) for m in s) for s in seed_batch]
+    sizes = []
+    s = 0
+    while frontier and s <= rounds:
+        if budget is not None:
+            frontier = frontier[: max(0, budget - len(V))]
+            if not frontier:
+                break
+        merits = evaluate(frontier)
+        for seq, mval in zip(frontier, merits):
+            V[encode(seq, n_modes)] = (float(mval), seq)
+        sizes.append(len(frontier))
+        frontier = expand(V, k, batch, n_modes, l_max)
+        s += 1
+    return V, sizes
+
+
+# ---------------------------------------------------------------- grammar
+
+def count_admissible_push(n_faces: int, cap: int) -> int:
+    """Number of admissible pushing orders of at most `cap` segments over the
+    alphabet {free} + faces (Sec. III-A: no two consecutive segments share a
+    mode; a contact changes faces through free motion).  Reading fixed by the
+    counts the paper prints (Sec. IV-A): orders start in free, and a direct
+    contact-to-contact switch is allowed only between adjacent faces of the
+    cyclic face list.  Counted by brute-force dynamic programming over the
+    last mode."""
+    FREE = n_faces
+
+    def ok(a, b):
+        if a == b:
+            return False
+        if a == FREE or b == FREE:
+            return True
+        return (a - b) % n_faces in (1, n_faces - 1)
+
+    counts = {FREE: 1}   # sequences of length 1 that start in free
+    total = 1
+    for _ in range(2, cap + 1):
+        nxt: dict = {}
+        for last, c in counts.items():
+            for m in range(n_faces + 1):
+                if ok(last, m):
+                    nxt[m] = nxt.get(m, 0) + c
+        counts = nxt
+        total += sum(counts.values())
+    return total

@@ -1,0 +1,110 @@
+"""Pins of the discrete-search oracle (no GPU): mode code, neighbourhood,
+Algorithm 1 invariants, and the admissible-order counts the paper prints
+(Sec. III-A transition rules, Sec. III-B, Sec. IV-A)."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import search as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_admissible_counts_match_paper():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "admissible_counts.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 4
+    for f, cap, count in rows:
+        assert S.count_admissible_push(int(f), int(cap)) == int(count)
+
+
+def test_admissible_count_brute_force_small():
+    # the DP equals explicit enumeration on a small alphabet
+    F, cap = 4, 5
+    FREE = F
+
+    def ok(s):
+        if s[0] != FREE:
+            return False
+        for a, b in zip(s, s[1:]):
+            if a == b:
+                return False
+            if a != FREE and b != FREE and (a - b) % F not in (1, F - 1):
+                return False
+        return True
+
+    n = sum(ok(s) for L in range(1, cap + 1) for s in itertools.product(range(F + 1), repeat=L))
+    assert n == S.count_admissible_push(F, cap)
+
+
+def test_code_roundtrip_and_injective():
+    seen = set()
+    for L in range(1, 4):
+        for s in itertools.product(range(12), repeat=L):
+            c = S.encode(s, 12)
+            assert S.decode(c, 12) == s
+            seen.add(c)
+    assert len(seen) == 12 + 144 + 1728
+    assert S.encode([11] * 16, 12) < 2 ** 64
+
+
+def test_neighbourhood_counts_and_order():
+    M, Lmax = 12, 6
+    s = (3, 7, 1)
+    nb = S.neighbours(s, M, Lmax)
+    assert len(nb) == 3 * 11 + 4 * 12 + 3
+    assert nb[0] == (0, 7, 1) and nb[10] == (11, 7, 1)           # substitutions first
+    assert nb[33] == (0, 3, 7, 1)                                 # then insertions
+    assert nb[-3:] == [(7, 1), (3, 1), (3, 7)]                    # then deletions
+    assert all(len(x) <= Lmax for x in nb)
+    assert S.neighbours((5,), M, 1) == [(m,) for m in range(12) if m != 5]   # no insert/delete
+    assert S.neighbour_slots(M, Lmax) >= max(len(S.neighbours(s, M, Lmax)) for s in [(0,) * 6, (1, 2)])
+
+
+def test_expand_invariants():
+    rng = np.random.default_rng(0)
+    M, Lmax = 12, 4
+    V = {}
+    for s in itertools.product(range(M), repeat=2):
+        V[S.encode(s, M)] = (float(rng.uniform()), s)
+    out = S.expand(V, k=8, batch=500, n_modes=M, l_max=Lmax)
+    codes = [S.encode(s, M) for s in out]
+    assert len(out) <= 500 and len(set(codes)) == len(codes)
+    assert not set(codes) & set(V)
+    # walked in merit order: the first admitted orders are neighbours of the best one
+    best = min(V.items(), key=lambda kv: (kv[1][0], kv[0]))[1][1]
+    first = list(dict.fromkeys(x for x in S.neighbours(best, M, Lmax) if S.encode(x, M) not in V))
+    assert out[: len(first)] == first
+
+
+def test_expansion_recovers_enumeration_argmin_unlimited_budget():
+    # Algorithm 1 invariant: with an unlimited budget (and a merit whose best
+    # order is reachable by single edits) expansion finds enumeration's best
+    M, Lmax = 5, 3
+    allseq = [s for L in range(1, Lmax + 1) for s in itertools.product(range(M), repeat=L)]
+    target = (4, 1, 3)
+
+    def f(batch):
+        return [sum(a != b for a, b in itertools.zip_longest(s, target, fillvalue=-1)) + 0.01 * len(s)
+                for s in batch]
+
+    V, sizes = S.run_expansion(f, [(m,) for m in range(M)], k=4, batch=20, n_modes=M, l_max=Lmax, rounds=100)
+    best_enum = allseq[int(np.argmin(f(allseq)))]
+    best_exp = min(V.values(), key=lambda v: v[0])[1]
+    assert best_exp == best_enum == target
+    assert all(sz <= 20 for sz in sizes[1:])
+    assert len(V) == sum(sizes)                    # no order evaluated twice
+
+
+def test_budget_truncates_last_batch():
+    M, Lmax = 4, 3
+    V, sizes = S.run_expansion(lambda b: [float(sum(s)) for s in b], [(m,) for m in range(M)], k=2, batch=10,
+                               n_modes=M, l_max=Lmax, rounds=50, budget=23)
+    assert sum(sizes) == 23 and len(V) == 23
+
+
+def test_enumeration_argmin_prefers_feasible_then_index():
+    costs = [1.0, 0.5, 0.5, 0.1]
+    viols = [0.0, 0.0, 0.0, 1e-3]
+    assert S.enumeration_argmin(costs, viols) == 1
