@@ -1,0 +1,306 @@
+"""Benchmark of the CoMET hot path on GB300: converged mode-TO solves/s.
+
+Workload (the 4-segment pushing enumeration): square slider 0.09 m,
+c = 0.04 m, mu = 0.3, 12 modes per segment, every order of 4 segments
+(20,736 per instance), 20 intervals per segment (N = 80), 64 seeded
+start/goal instances, cold start.  One step = the full enumeration of one
+instance: every order solved by the persistent evaluator, scored
+(Eq. inexact_mode_value, Eq. search_merit) and the enumeration argmin taken
+(Eq. mode_selection).  Steps cycle through the instances.
+
+Prints one JSON line (contract of the driver): value = converged solves
+(status CONVERGED and FP64-certified v_hat < 1e-5) per second over the timed
+steps, device-timed with CUDA events on the problem's stream, inputs resident
+in HBM; e2e = the same metric through the C ABI with host buffers (copies
+inside the timed region); roofline of the evaluator kernel against the FP32
+ALU peak; cpu_baseline = the FP64 oracle on the host cores over a bounded
+sample of the same workload.
+
+``--impl reference`` times the oracle alone (host cores) on the same workload
+and prints the reference line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "converged mode-TO solves/s (viol<1e-5) on 1 GB300; plan time vs plain evaluator"
+UNIT = "solves/s"
+N_INSTANCES = 64
+SEG, K = 4, 20
+N_STAGES = SEG * K
+# algorithmic FP32 flops of one solver iteration per stage (dense count of
+# the method's steps: derivatives 60, row assembly and beta A^T A 1450,
+# 7x7 Cholesky 230, gains with 5 right-hand sides 490, Schur update 230,
+# forward pass 70, 8-trial line search 800)
+FLOP_PER_STAGE_ITER = 3330
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def instances():
+    return [W.push_l4_instance(s) for s in range(N_INSTANCES)]
+
+
+def oracle_rate(insts, seconds_target: float = 12.0, max_n: int = 20736):
+    """The FP64 oracle as it stands, one TO per host thread on every core,
+    over a bounded sample of the workload (orders of instance 0 in
+    enumeration order).  Returns (converged solves/s, solves/s, sample)."""
+    import oracle
+
+    seqs = W.all_sequences(12, SEG)
+    cores = os.cpu_count() or 1
+    n = 64 * cores
+    t0 = time.time()
+    res, _ = oracle.solve_batch([insts[0]], np.zeros(n, np.int32), seqs[:n], np.full(n, SEG, np.int32),
+                                nthreads=cores)
+    dt = time.time() - t0
+    # grow the sample to about `seconds_target` seconds of CPU work
+    n2 = int(min(max_n, max(n, n * seconds_target / max(dt, 1e-3))))
+    if n2 > n:
+        t0 = time.time()
+        res, _ = oracle.solve_batch([insts[0]], np.zeros(n2, np.int32), seqs[:n2], np.full(n2, SEG, np.int32),
+                                    nthreads=cores)
+        dt = time.time() - t0
+        n = n2
+    conv = int(np.sum((res["status"] == 0) & (res["viol"] < 1e-5)))
+    return conv / dt, n / dt, n, cores, dt
+
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return
+    insts = instances()
+    t_all = 0.0
+    conv_all = 0
+    for s in range(args.steps):
+        r, _, n, cores, dt = oracle_rate(insts, seconds_target=max(2.0, 60.0 / max(1, args.steps)))
+        t_all += dt
+        conv_all += r * dt
+    value = conv_all / t_all
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "push_l4 enumeration (4 segments x 12 modes, N=80), oracle sample",
+                                         "instances": N_INSTANCES, "orders_per_instance": 20736},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {n} orders of instance 0 per step, FP64 C oracle, one TO per thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2609_21803_gb300 as P
+
+    rank, world, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    P.build.build()
+    P.lib()
+    insts = instances()
+    seqs = W.all_sequences(12, SEG)
+    n = len(seqs)
+    stream = torch.cuda.Stream()
+    # one problem per instance; orders resident on the device (replicas: rank
+    # r takes instances r, r + world, ...)
+    my = list(range(rank, N_INSTANCES, world))
+    probs = []
+    with torch.cuda.stream(stream):
+        for i in my:
+            probs.append(P.Problem([insts[i]], stream=stream))
+    packed = P.pack_mode_seqs(seqs)
+    d_seqs = torch.from_numpy(packed.view(np.uint8).reshape(n, 24)).cuda()
+    cost = torch.empty(n, dtype=torch.float32, device="cuda")
+    status = torch.empty(n, dtype=torch.int32, device="cuda")
+    viol = torch.empty(n, dtype=torch.float32, device="cuda")
+    iters = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    torch.cuda.synchronize()
+
+    def step(j):
+        pr = probs[j % len(probs)]
+        P.comet_eval_modes(pr.handle, d_seqs, n, None, cost, None, status)
+        P.comet_eval_stats(pr.handle, viol, None, iters, None)
+        conv = (status == 0) & (viol < 1e-5)
+        # enumeration argmin (Eq. mode_selection): least merit among feasible
+        key = torch.where(viol <= 1e-5, cost, torch.full_like(cost, float("inf")))
+        best = torch.argmin(key)
+        return conv.sum(), best, iters.sum()
+
+    with torch.cuda.stream(stream):
+        for w in range(args.warmup):
+            step(w)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_dev = 0.0
+    conv_total = 0
+    iter_total = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    outs = []
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            outs.append(step(args.warmup + s))
+            ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        t_dev += ev[s][0].elapsed_time(ev[s][1]) / 1e3
+        conv_total += int(outs[s][0])
+        iter_total += int(outs[s][2])
+    # max over ranks of the timed region, sum of the work
+    if world > 1:
+        t = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t)
+        c = torch.tensor([conv_total, iter_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        conv_total, iter_total = int(c[0]), int(c[1])
+    clk = clocks.stop()
+    value = conv_total / t_dev
+
+    # e2e: the C ABI with host buffers (orders in, cost/status out), copies inside
+    host_seqs = packed
+    h_cost = np.zeros(n, np.float32)
+    h_status = np.zeros(n, np.int32)
+    h_viol = np.zeros(n, np.float32)
+    t0 = time.time()
+    e2e_conv = 0
+    e2e_steps = max(1, min(args.steps, 4))
+    for s in range(e2e_steps):
+        pr = probs[(args.warmup + s) % len(probs)]
+        P.comet_eval_modes(pr.handle, host_seqs, n, None, h_cost, None, h_status)
+        P.comet_eval_stats(pr.handle, h_viol, None, None, None)
+        e2e_conv += int(np.sum((h_status == 0) & (h_viol < 1e-5)))
+    e2e_t = time.time() - t0
+    e2e_value = e2e_conv * world / e2e_t
+
+    flops = FLOP_PER_STAGE_ITER * N_STAGES * iter_total
+    achieved = flops / t_dev / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "push_l4 full enumeration: 20,736 orders (4 segments x 12 modes) x N=80 intervals "
+                               "per step, one seeded instance per step, cold start",
+                   "instances": N_INSTANCES, "orders_per_step": n, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * 24),
+                "d2h_bytes_per_step": int(n * (4 + 4 + 4))},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "note": "achieved = 3330 flop x 80 stages x solver iterations / device time; peak = FP32 "
+                             "FMA rate at 2070 MHz (152 SMs x 128 lanes)"},
+        "iterations_per_solve": iter_total / (args.steps * n * world),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        conv_rate, rate, ns, cores, dt = oracle_rate(insts)
+        line["cpu_baseline"] = {"value": conv_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {ns} orders of instance 0 ({dt:.1f} s), FP64 C oracle, "
+                                          f"one TO per host thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for pr in probs:
+        pr.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * comet.h -- C ABI of the GB300 CoMET hot path.
+ *
+ * CoMET (Li & Chalvatzaki, "Contact-Rich Motion Planning via GPU-Parallel
+ * Mode Evaluation") scores contact-mode orders m by solving one
+ * mode-conditioned trajectory optimisation (TO) per order, Eq. mode_nlp
+ *     J*(m) = min_z J(z, m)  s.t.  g(z, m) = 0,  h(z, m) <= 0,
+ * returns the inexact mode value of Eq. inexact_mode_value
+ *     J_hat = J(z_hat, m),  v_hat = max(|g|_inf, |[h]+|_inf)
+ * and ranks orders by the merit of Eq. search_merit
+ *     M_hat = J_hat + mu * max(v_hat - eps_feas, 0),
+ * expanding the best ones by one-edit neighbourhoods (Sec. III-B,
+ * Algorithm 1).
+ *
+ * Conventions for every entry point
+ *   - All functions return a comet_status; call-level failures return an
+ *     error code and set a thread-local message (comet_last_error()).
+ *     Per-TO numerical failures never fail a call: they are reported in the
+ *     per-TO status array (COMET_TO_*).
+ *   - Buffers are owned by the caller.  A pointer argument may point to
+ *     host memory or to device memory of the device the problem was created
+ *     on; the library detects which (cudaPointerGetAttributes).  Device
+ *     buffers are used in place and the call is asynchronous on the
+ *     problem's stream; host buffers are staged through device memory owned
+ *     by the problem, and the call returns after the results are copied
+ *     back.
+ *   - Trajectory layout (warm starts and outputs), one record of
+ *     comet_traj_stride(problem) floats per TO, component-major and padded
+ *     to N_max intervals:  x[N_max+1], y[N_max+1], theta[N_max+1],
+ *     s[N_max+1], f_n[N_max], f_t[N_max], sdot[N_max]; only the first N+1
+ *     states and N controls of a TO with N intervals are meaningful.
+ *   - Mode code of an order (m_0 .. m_{L-1}) over an alphabet of M modes:
+ *     code = L + sum_i (m_i + 1) (M + 1)^(i + 1)   (unsigned 64-bit).
+ */
+#ifndef COMET_H
+#define COMET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    COMET_OK = 0,
+    COMET_ERR_INVALID_ARG = 1, /* a null, negative or out-of-range argument */
+    COMET_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    COMET_ERR_OOM = 3,         /* device memory could not be allocated */
+    COMET_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    COMET_ERR_BUDGET = 5,      /* a capacity (frontier, batch) is exhausted */
+    COMET_ERR_INTERNAL = 6
+} comet_status;
+
+/* per-TO status (Sec. III-C "Stopping and scoring") */
+enum {
+    COMET_TO_CONVERGED = 0,   /* scaled feasibility, stationarity and complementarity met,
+                                 and the FP64-certified v_hat <= eps_feas */
+    COMET_TO_MAX_ITER = 1,    /* iteration budget exhausted (feasibility not implied) */
+    COMET_TO_INFEASIBLE = 2,  /* FP32 stop test met but the FP64 certificate v_hat > eps_feas */
+    COMET_TO_FACTOR_FAIL = 3, /* reserved: every step of the budget was rejected */
+    COMET_TO_NONFINITE = 4    /* a non-finite value appeared in the iterate */
+};
+
+enum { COMET_TASK_PUSHER_SLIDER = 0, COMET_TASK_BIMANUAL = 1 };
+
+#define COMET_MAX_SEGMENTS 16
+
+/* One planning instance (Sec. III-A).  Pushing: a rectangular slider of
+ * sides side_x x side_y [m] with an ellipsoidal limit surface of radius
+ * c_ls [m] and force-to-velocity gain kappa, pusher friction mu, state
+ * (x, y, theta, s), control (f_n, f_t, sdot), K = knots_per_segment
+ * intervals of dt [s] per mode segment, orders of at most max_segments
+ * segments over n_modes = 12 modes (face 0..3 x stick, slide+, slide-),
+ * cost w_terminal |pose_N - goal|^2 + w_control sum_k |u_k|^2. */
+typedef struct {
+    int32_t task;
+    int32_t knots_per_segment;
+    int32_t max_segments;
+    int32_t n_modes;
+    double side_x, side_y, c_ls, mu, dt, kappa;
+    double start[3], goal[3];
+    double w_terminal, w_control;
+    double mass, ground_mu; /* bimanual only */
+} comet_instance_desc;
+
+/* Solver options (Sec. III-C).  Zero-initialised fields take the defaults
+ * returned by comet_default_opts(). */
+typedef struct {
+    int32_t max_iters;       /* exploration budget t_exp (default 300) */
+    int32_t ref_iters;       /* refinement budget t_ref (default 1500) */
+    double eps_feas;         /* feasibility tolerance on v_hat (1e-5) */
+    double eps_primal;       /* scaled primal tolerance of the stop test (1e-6) */
+    double eps_dual;         /* stationarity tolerance at beta <= beta_ref (1e-4) */
+    double eps_comp;         /* complementarity tolerance (1e-6) */
+    double merit_mu;         /* mu of Eq. search_merit (100) */
+    double beta0, beta_max, beta_ref; /* penalty 1/mu_AL: start, cap, reference (100, 1e4, 1e3) */
+    double rho0, rho_min;    /* proximal damping: start and lower bound (1e-4, 1e-4) */
+    int32_t precision_flags; /* bit 0: FP64 iterative refinement of the Riccati step when
+                                beta > 1e4 (default on) */
+    int32_t reserved;
+} comet_solver_opts;
+
+/* One mode order: instance index, length and modes (24 bytes). */
+typedef struct {
+    int32_t instance;
+    uint8_t len;
+    uint8_t modes[COMET_MAX_SEGMENTS];
+    uint8_t pad[3];
+} comet_mode_seq;
+
+typedef struct comet_problem comet_problem;
+typedef struct comet_frontier comet_frontier;
+
+/* Fill *opts with the defaults listed above. */
+comet_status comet_default_opts(comet_solver_opts* opts);
+
+/* Create a problem holding n_instances instance descriptors (copied) and
+ * the solver options (copied; NULL = defaults) on the current CUDA device.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream).  The
+ * problem owns its device scratch (descriptors, per-warp workspaces, staging
+ * buffers).  Errors: INVALID_ARG for bad descriptors (non-positive sizes,
+ * K * max_segments > 4096, max_segments > 16, n_modes != 12 for pushing),
+ * CUDA / OOM from the runtime. */
+comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_instances,
+                                  const comet_solver_opts* opts, void* cuda_stream,
+                                  comet_problem** out);
+
+/* Release the problem and its device memory (synchronises its stream). */
+comet_status comet_problem_destroy(comet_problem* p);
+
+/* Floats per trajectory record: 7 * N_max + 4 with N_max the largest
+ * K * max_segments over the instances. */
+int64_t comet_traj_stride(const comet_problem* p);
+
+/* Solve one mode-conditioned TO (Eq. mode_nlp) per order.
+ *   mode_seqs   [n] orders (instance index < n_instances, 1 <= len <=
+ *               max_segments of that instance, modes < n_modes); a TO with
+ *               order length L has N = K * L intervals split evenly among
+ *               the segments
+ *   warm_starts [n][stride] floats or NULL for the cold start (zero
+ *               controls, pose interpolated from start to goal, s = 0)
+ *   out_cost    [n]  J_hat in physical units (FP64-certified, rounded to float)
+ *   out_traj    [n][stride] returned trajectories, or NULL
+ *   out_status  [n]  COMET_TO_*
+ * The budget is opts.max_iters per TO.  Errors: INVALID_ARG (n < 0, null
+ * required pointers, a malformed order -- checked on the host for host
+ * buffers and on the device for device buffers, where the TO's status
+ * becomes COMET_TO_NONFINITE and the call returns INVALID_ARG after the
+ * stream is synchronised), CUDA, OOM. */
+comet_status comet_eval_modes(comet_problem* p, const comet_mode_seq* mode_seqs, int64_t n,
+                              const float* warm_starts, float* out_cost, float* out_traj,
+                              int32_t* out_status);
+
+/* Same as comet_eval_modes with an explicit iteration budget (e.g. the
+ * refinement budget t_ref of Algorithm 1). */
+comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* mode_seqs, int64_t n,
+                                     const float* warm_starts, int32_t max_iters, float* out_cost,
+                                     float* out_traj, int32_t* out_status);
+
+/* Per-TO diagnostics of the last comet_eval_modes call on this problem, all
+ * nullable, each [n]: v_hat (FP64-certified, physical units), M_hat, the
+ * number of iterations used and the FP64 stationarity residual
+ * |grad J + A^T lambda|_inf.  Same host/device rules as comet_eval_modes. */
+comet_status comet_eval_stats(comet_problem* p, float* out_viol, float* out_merit,
+                              int32_t* out_iters, float* out_stat);
+
+/* Mode code of an order (see the conventions above); 0 if invalid. */
+uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* comet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

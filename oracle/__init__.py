@@ -67,6 +67,7 @@ class Opts(ctypes.Structure):
         ("eps_primal", ctypes.c_double), ("eps_dual", ctypes.c_double), ("eps_comp", ctypes.c_double),
         ("omega_ratio", ctypes.c_double), ("eta_ratio", ctypes.c_double),
         ("eps_feas", ctypes.c_double), ("merit_mu", ctypes.c_double), ("beta_ref", ctypes.c_double),
+        ("curv_skip", ctypes.c_int32), ("pad1", ctypes.c_int32),
     ]
 
 
@@ -77,13 +78,14 @@ class Result(ctypes.Structure):
         ("beta", ctypes.c_double), ("rho", ctypes.c_double),
         ("status", ctypes.c_int32), ("iters", ctypes.c_int32),
         ("n_outer", ctypes.c_int32), ("n_rejected", ctypes.c_int32),
+        ("n_curv_fail", ctypes.c_int32), ("pad1", ctypes.c_int32),
     ]
 
 
 RESULT_DTYPE = np.dtype([
     ("cost", "f8"), ("viol", "f8"), ("merit", "f8"), ("stat", "f8"), ("comp", "f8"),
     ("beta", "f8"), ("rho", "f8"), ("status", "i4"), ("iters", "i4"),
-    ("n_outer", "i4"), ("n_rejected", "i4"),
+    ("n_outer", "i4"), ("n_rejected", "i4"), ("n_curv_fail", "i4"), ("pad1", "i4"),
 ])
 assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result)
 

@@ -520,7 +520,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
 void orc_default_opts(orc_opts* o) {
     o->max_iters = 300;
     o->max_factor_retries = 8;
-    o->n_alpha = 8;
+    o->n_alpha = 7;
     o->max_inner = 40;
     o->beta0 = 100.0;
     o->beta_max = 1e4;
@@ -538,6 +538,7 @@ void orc_default_opts(orc_opts* o) {
     o->eps_feas = 1e-5;
     o->merit_mu = 100.0;
     o->beta_ref = 1e3;
+    o->curv_skip = 3;
 }
 
 /* add alpha * dz (interleaved) to a component-major trajectory */
@@ -627,7 +628,7 @@ int32_t orc_solve(const orc_instance* in, int32_t len, const uint8_t* modes, int
         orc_cold_start(in, N, z);
 
     double beta = opt->beta0, rho = opt->rho0, eta = INFINITY;
-    int32_t inner = 0, it = 0, status = ORC_MAX_ITER, n_outer = 0, n_rej = 0;
+    int32_t inner = 0, it = 0, status = ORC_MAX_ITER, n_outer = 0, n_rej = 0, curv_hold = 0, n_curv_fail = 0;
     kkt_measures m;
     for (it = 0; it < opt->max_iters; ++it) {
         measures(in, len, modes, N, z, lam, beta, y, grad, &m);
@@ -661,7 +662,16 @@ int32_t orc_solve(const orc_instance* in, int32_t len, const uint8_t* modes, int
         /* Newton step on the AL with the Lagrangian curvature of the dynamics;
          * if a local Cholesky finds S_k indefinite, fall back to the
          * Gauss-Newton model, then raise the damping rho (Sec. III-C) */
-        int32_t fac = orc_gn_step(in, len, modes, N, z, lam, beta, rho, 1, dz, grad);
+        int32_t fac = -1;
+        if (curv_hold == 0) {
+            fac = orc_gn_step(in, len, modes, N, z, lam, beta, rho, 1, dz, grad);
+            if (fac != 0) {
+                ++n_curv_fail;
+                curv_hold = opt->curv_skip;
+            }
+        } else {
+            --curv_hold;
+        }
         for (int32_t r = 0; fac != 0 && r <= opt->max_factor_retries; ++r) {
             if (r > 0) rho = fmin(opt->rho_max, rho * 10.0);
             fac = orc_gn_step(in, len, modes, N, z, lam, beta, rho, 0, dz, grad);
@@ -713,6 +723,7 @@ int32_t orc_solve(const orc_instance* in, int32_t len, const uint8_t* modes, int
     res->iters = it;
     res->n_outer = n_outer;
     res->n_rejected = n_rej;
+    res->n_curv_fail = n_curv_fail;
     res->beta = beta;
     res->rho = rho;
     if (out_traj) memcpy(out_traj, z, sizeof(double) * nt);

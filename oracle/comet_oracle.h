@@ -55,7 +55,7 @@ typedef struct {
 typedef struct {
     int32_t max_iters;        /* iteration budget t */
     int32_t max_factor_retries;
-    int32_t n_alpha;          /* trial steps alpha = 2^-i, i < n_alpha */
+    int32_t n_alpha;          /* trial steps alpha = 2^-i, i < n_alpha (default 7) */
     int32_t max_inner;        /* inner iterations before a forced dual update */
     double beta0, beta_max, beta_growth;
     double rho0, rho_min, rho_max;
@@ -66,6 +66,8 @@ typedef struct {
     double eps_feas;          /* feasibility tolerance for v_hat */
     double merit_mu;          /* mu of Eq. search_merit */
     double beta_ref;          /* stationarity tolerance eps_dual * max(1, beta / beta_ref) */
+    int32_t curv_skip;        /* after an indefinite Newton model, iterations that use Gauss-Newton only (3) */
+    int32_t pad1;
 } orc_opts;
 
 enum { ORC_CONVERGED = 0, ORC_MAX_ITER = 1, ORC_INFEASIBLE = 2,
@@ -82,6 +84,8 @@ typedef struct {
     int32_t iters;
     int32_t n_outer;
     int32_t n_rejected;
+    int32_t n_curv_fail;      /* Newton models found indefinite */
+    int32_t pad1;
 } orc_result;
 
 void orc_default_opts(orc_opts* o);

@@ -1,0 +1,269 @@
+"""GB300-native CoMET hot path: thin Python binding of ``libcomet.so``.
+
+Every entry point of ``include/comet.h`` is exposed under the same name and
+only marshals arguments (ctypes); all computation runs in the CUDA library.
+The library is built in-tree by ``paper_2609_21803_gb300.build.build()``
+(nvcc, sm_103a).  Importing this package never falls back to another
+implementation: if the library is missing, ``lib()`` raises.
+
+Pointer arguments accept torch tensors (their ``data_ptr()``, host or CUDA),
+numpy arrays (host), raw integer addresses or ``None``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MAX_SEGMENTS = 16
+TO_CONVERGED, TO_MAX_ITER, TO_INFEASIBLE, TO_FACTOR_FAIL, TO_NONFINITE = range(5)
+OK = 0
+
+_lock = threading.Lock()
+_lib = None
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [
+        ("task", ctypes.c_int32), ("knots_per_segment", ctypes.c_int32),
+        ("max_segments", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+        ("side_x", ctypes.c_double), ("side_y", ctypes.c_double), ("c_ls", ctypes.c_double),
+        ("mu", ctypes.c_double), ("dt", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("start", ctypes.c_double * 3), ("goal", ctypes.c_double * 3),
+        ("w_terminal", ctypes.c_double), ("w_control", ctypes.c_double),
+        ("mass", ctypes.c_double), ("ground_mu", ctypes.c_double),
+    ]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [
+        ("max_iters", ctypes.c_int32), ("ref_iters", ctypes.c_int32),
+        ("eps_feas", ctypes.c_double), ("eps_primal", ctypes.c_double), ("eps_dual", ctypes.c_double),
+        ("eps_comp", ctypes.c_double), ("merit_mu", ctypes.c_double),
+        ("beta0", ctypes.c_double), ("beta_max", ctypes.c_double), ("beta_ref", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("rho_min", ctypes.c_double),
+        ("precision_flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class ModeSeq(ctypes.Structure):
+    _fields_ = [("instance", ctypes.c_int32), ("len", ctypes.c_uint8),
+                ("modes", ctypes.c_uint8 * MAX_SEGMENTS), ("pad", ctypes.c_uint8 * 3)]
+
+
+MODE_SEQ_DTYPE = np.dtype([("instance", "<i4"), ("len", "u1"), ("modes", "u1", (MAX_SEGMENTS,)),
+                           ("pad", "u1", (3,))])
+assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == 24
+
+# exported symbols of include/comet.h
+EXPORTS = (
+    "comet_default_opts", "comet_problem_create", "comet_problem_destroy", "comet_traj_stride",
+    "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_mode_code",
+    "comet_last_error",
+)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"libcomet.so is not built ({path}); run paper_2609_21803_gb300.build.build()")
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            L.comet_default_opts.argtypes = [ctypes.POINTER(SolverOpts)]
+            L.comet_problem_create.argtypes = [ctypes.POINTER(InstanceDesc), i32, ctypes.POINTER(SolverOpts), vp,
+                                               ctypes.POINTER(vp)]
+            L.comet_problem_destroy.argtypes = [vp]
+            L.comet_traj_stride.argtypes = [vp]
+            L.comet_traj_stride.restype = i64
+            L.comet_eval_modes.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+            L.comet_eval_modes_budget.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp]
+            L.comet_eval_stats.argtypes = [vp, vp, vp, vp, vp]
+            L.comet_mode_code.argtypes = [ctypes.POINTER(ModeSeq), i32]
+            L.comet_mode_code.restype = ctypes.c_uint64
+            L.comet_last_error.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name not in ("comet_traj_stride", "comet_mode_code", "comet_last_error"):
+                    getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+class CometError(RuntimeError):
+    pass
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise CometError(f"comet status {rc}: {lib().comet_last_error().decode()}")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+# ------------------------------------------------------------------ C ABI
+
+def comet_default_opts() -> SolverOpts:
+    o = SolverOpts()
+    _check(lib().comet_default_opts(ctypes.byref(o)))
+    return o
+
+
+def make_instance_desc(d: dict) -> InstanceDesc:
+    s = InstanceDesc()
+    s.task = int(d.get("task", 0))
+    s.knots_per_segment = int(d["knots_per_segment"])
+    s.max_segments = int(d["max_segments"])
+    s.n_modes = int(d.get("n_modes", 12))
+    for f in ("side_x", "side_y", "c_ls", "mu", "dt", "w_terminal", "w_control"):
+        setattr(s, f, float(d[f]))
+    s.kappa = float(d.get("kappa", 1.0))
+    for i in range(3):
+        s.start[i] = float(d["start"][i])
+        s.goal[i] = float(d["goal"][i])
+    s.mass = float(d.get("mass", 0.0))
+    s.ground_mu = float(d.get("ground_mu", 0.0))
+    return s
+
+
+def comet_problem_create(instances, opts=None, cuda_stream=None) -> int:
+    """instances: list of dicts (or InstanceDesc); opts: SolverOpts, dict or
+    None; cuda_stream: integer cudaStream_t handle or None.  Returns the
+    problem handle (an integer address)."""
+    descs = [x if isinstance(x, InstanceDesc) else make_instance_desc(x) for x in instances]
+    arr = (InstanceDesc * len(descs))(*descs)
+    o = None
+    if opts is not None:
+        if isinstance(opts, dict):
+            oo = comet_default_opts()
+            for k, v in opts.items():
+                setattr(oo, k, v)
+            opts = oo
+        o = ctypes.byref(opts)
+    h = ctypes.c_void_p()
+    _check(lib().comet_problem_create(arr, len(descs), o, cuda_stream, ctypes.byref(h)))
+    return h.value
+
+
+def comet_problem_destroy(problem: int):
+    _check(lib().comet_problem_destroy(problem))
+
+
+def comet_traj_stride(problem: int) -> int:
+    return int(lib().comet_traj_stride(problem))
+
+
+def comet_eval_modes(problem, mode_seqs, n, warm_starts, out_cost, out_traj, out_status):
+    _check(lib().comet_eval_modes(problem, _ptr(mode_seqs), int(n), _ptr(warm_starts), _ptr(out_cost),
+                                  _ptr(out_traj), _ptr(out_status)))
+
+
+def comet_eval_modes_budget(problem, mode_seqs, n, warm_starts, max_iters, out_cost, out_traj, out_status):
+    _check(lib().comet_eval_modes_budget(problem, _ptr(mode_seqs), int(n), _ptr(warm_starts), int(max_iters),
+                                         _ptr(out_cost), _ptr(out_traj), _ptr(out_status)))
+
+
+def comet_eval_stats(problem, out_viol, out_merit, out_iters, out_stat):
+    _check(lib().comet_eval_stats(problem, _ptr(out_viol), _ptr(out_merit), _ptr(out_iters), _ptr(out_stat)))
+
+
+def comet_mode_code(seq, n_modes: int = 12) -> int:
+    if not isinstance(seq, ModeSeq):
+        s = ModeSeq()
+        s.instance = 0
+        s.len = len(seq)
+        for i, m in enumerate(seq):
+            s.modes[i] = int(m)
+        seq = s
+    return int(lib().comet_mode_code(ctypes.byref(seq), n_modes))
+
+
+def comet_last_error() -> str:
+    return lib().comet_last_error().decode()
+
+
+# ------------------------------------------------------------- marshalling
+
+def pack_mode_seqs(seqs, inst_idx=None, lens=None) -> np.ndarray:
+    """Pack orders into the 24-byte comet_mode_seq records.  seqs: uint8
+    [n, L] (all of length L, or padded with `lens`) or a list of tuples."""
+    if isinstance(seqs, np.ndarray) and seqs.ndim == 2:
+        n, L = seqs.shape
+        out = np.zeros(n, dtype=MODE_SEQ_DTYPE)
+        out["modes"][:, :L] = seqs
+        out["len"] = L if lens is None else np.asarray(lens, dtype=np.uint8)
+    else:
+        n = len(seqs)
+        out = np.zeros(n, dtype=MODE_SEQ_DTYPE)
+        for i, s in enumerate(seqs):
+            out["modes"][i, : len(s)] = s
+            out["len"][i] = len(s)
+    out["instance"] = 0 if inst_idx is None else np.asarray(inst_idx, dtype=np.int32)
+    return out
+
+
+class Problem:
+    """Convenience owner of a comet_problem handle (torch tensors in/out)."""
+
+    def __init__(self, instances, opts=None, stream=None):
+        import torch
+
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = comet_problem_create(instances, opts, self.stream.cuda_stream)
+        self.stride = comet_traj_stride(self.handle)
+        self.instances = list(instances)
+
+    def close(self):
+        if self.handle:
+            comet_problem_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, seqs_dev, warm=None, want_traj=False, max_iters=0):
+        """seqs_dev: uint8 CUDA tensor [n, 24] of packed orders.  Returns a dict
+        of CUDA tensors: cost, status, viol, merit, iters, stat (and traj)."""
+        torch = self.torch
+        n = seqs_dev.shape[0]
+        dev = seqs_dev.device
+        cost = torch.empty(n, dtype=torch.float32, device=dev)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        traj = torch.empty((n, self.stride), dtype=torch.float32, device=dev) if want_traj else None
+        comet_eval_modes_budget(self.handle, seqs_dev, n, warm, max_iters, cost, traj, status)
+        out = {"cost": cost, "status": status}
+        if traj is not None:
+            out["traj"] = traj
+        viol = torch.empty(n, dtype=torch.float32, device=dev)
+        merit = torch.empty_like(viol)
+        iters = torch.empty(n, dtype=torch.int32, device=dev)
+        stat = torch.empty_like(viol)
+        comet_eval_stats(self.handle, viol, merit, iters, stat)
+        out.update(viol=viol, merit=merit, iters=iters, stat=stat)
+        return out

@@ -1,0 +1,72 @@
+// comet_internal.h -- types shared by the CUDA translation units of the
+// library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "comet.h"
+
+namespace comet {
+
+// Floats per stage record in the per-warp workspace: the u-block Cholesky
+// factor and coupling (33), the reduced (y, x, rhs) matrix (44), padded.
+constexpr int kRec = 80;
+// Largest number of intervals of one TO.
+constexpr int kMaxN = 4096;
+
+// FP32 (and FP64 for the certificate) constants of one instance.
+struct DevInstance {
+    float dt, kappa, inv_c2, mu, sc_cone;  // sc_cone = 1/sqrt(1+mu^2)
+    float inv_sigma[4];                    // dynamics-row scaling 1/sigma_r
+    float a[4], ell[4];                    // half-depth / half-length of face f
+    float start[3], goal[3];
+    float w_terminal, w_control;
+    int32_t K, Lmax, n_modes, task;
+    double dt_d, kappa_d, inv_c2_d, mu_d, sc_cone_d;
+    double sigma_d[4];
+    double a_d[4], ell_d[4];
+    double start_d[3], goal_d[3];
+    double w_terminal_d, w_control_d;
+};
+
+struct SolverParams {
+    int max_iters, max_retries, n_alpha, max_inner, curv_skip;
+    float beta0, beta_max, beta_growth, beta_ref;
+    float rho0, rho_min, rho_max;
+    float armijo_c1, ls_slack;
+    float eps_primal, eps_dual, eps_comp, omega_ratio, eta_ratio;
+    double eps_feas, merit_mu;
+    int refine;
+};
+
+struct EvalArgs {
+    const DevInstance* inst;
+    int n_inst;
+    const comet_mode_seq* seqs;
+    int64_t n;
+    const float* warm;
+    int64_t stride;  // floats per trajectory record (7*Nmax+4)
+    int Nmax;
+    float* out_cost;
+    float* out_traj;
+    int32_t* out_status;
+    float* out_viol;
+    float* out_merit;
+    int32_t* out_iters;
+    float* out_stat;
+    float* ws;               // per-warp stage records
+    int64_t ws_per_warp;     // floats
+    unsigned int* queue;     // work counter (next TO index)
+    int* bad_input;          // set when a malformed order is met
+    SolverParams sp;
+};
+
+// Shared memory (bytes) one warp needs for TOs of up to Nmax intervals.
+size_t smem_per_warp_bytes(int Nmax);
+// Launch the persistent evaluator: total_warps warps, warps_per_block per CTA.
+cudaError_t launch_eval(const EvalArgs& a, int total_warps, int warps_per_block, cudaStream_t s);
+// Occupancy of the evaluator for the given per-warp shared memory.
+int eval_blocks_per_sm(int warps_per_block, size_t smem_per_block);
+
+}  // namespace comet

@@ -1,0 +1,1154 @@
+// eval_kernel.cu -- persistent warp-per-TO evaluator of mode-conditioned
+// trajectory optimisations (CoMET, Sec. III-C), FP32 with compensated state
+// storage and an FP64 certificate.
+//
+// One warp owns one TO at a time and pulls the next TO index from a device
+// counter when it finishes (the resident pool of Sec. III-C, "Reusable pool
+// with independent stopping", kept on the device: no host round trip).  One
+// iteration of the augmented-Lagrangian Newton / Gauss-Newton method is:
+//
+//   A  stage-parallel (lane = interval k): dynamics, the fixed masked row
+//      layout of Sec. III-C (4 dynamics rows, 1 mode equality, 6
+//      inequalities), PHR multiplier estimates, merit / violation /
+//      complementarity, the local AL model over (u_k, x_{k+1}, x_k) and the
+//      elimination of the u_k block (independent of the value function, so
+//      it is taken off the sequential path);
+//   B  backward sweep k = N-1 .. 0 over S_k = H_k + rho I + beta A_k^T A_k
+//      (Sec. III-C "Fixed-workspace local solves"): only the 4 x_{k+1}
+//      columns are eliminated on the sequential path (Cholesky without
+//      pivoting, a failed pivot raises damping), producing V_k and the gains;
+//   C  forward pass dw_k = G_k [dx_k; 1];
+//   D  parallel trial-step merits: lane = (trial alpha, stage group), alpha
+//      in {0, 1, 1/2, ..., 1/64}, Armijo on the largest passing alpha;
+//   E  compensated update z += alpha dz and multiplier / penalty updates.
+//
+// The algorithm (steps, order, constants) is the one the FP64 oracle runs;
+// only the arithmetic precision and the parallel schedule differ.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "comet_internal.h"
+
+namespace comet {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------ warp helpers
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// error-free sum a + b = s + e (Knuth two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// lower-triangle flat index of (i, j), i >= j
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// face geometry: inward normal n, tangent t = rot90(n)
+__device__ __forceinline__ void face_nt(int face, float& nx, float& ny) {
+    nx = (face == 0) ? 1.f : ((face == 2) ? -1.f : 0.f);
+    ny = (face == 1) ? 1.f : ((face == 3) ? -1.f : 0.f);
+}
+
+struct ModeInfo {
+    int face, kind;  // kind 0 stick, 1 slide+, 2 slide-
+    bool smask;      // s-row of d_k masked (face change after interval k)
+};
+
+__device__ __forceinline__ ModeInfo mode_of(unsigned char b) {
+    ModeInfo mi;
+    mi.face = b & 3;
+    mi.kind = (b >> 2) & 3;
+    mi.smask = (b >> 4) & 1;
+    return mi;
+}
+
+__device__ __forceinline__ ModeInfo mode_info(const uint8_t* modes, int len, int N, int k) {
+    ModeInfo mi;
+    const int seg = (int)(((long long)k * len) / N);
+    const int m = modes[seg];
+    mi.face = m / 3;
+    mi.kind = m - 3 * mi.face;
+    mi.smask = false;
+    if (k + 1 < N) {
+        const int seg1 = (int)(((long long)(k + 1) * len) / N);
+        mi.smask = (modes[seg1] / 3) != mi.face;
+    }
+    return mi;
+}
+
+// --------------------------------------------------------------- the rows
+
+// Residual rows of interval k at (x_k, u_k, x_{k+1}) with the exact state
+// difference dx = x_{k+1} - x_k.  Values are internally scaled; `phys` is
+// the factor that maps a scaled value back to physical units.
+struct Rows {
+    float c[11];
+    float phys[11];
+    bool on[11];
+    // dynamics Jacobian pieces (scaled): d c_r / d x_k, d c_r / d u_k
+    float ax[4][4];
+    float au[4][3];
+    float ay[4];  // d c_r / d x_{k+1, r}
+    // linear rows' u-Jacobians (rows 4..8)
+    float lu[5][3];
+    // dynamics values for the curvature term
+    float f0, f1, ct, st;
+};
+
+__device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& mi, const float xk[4],
+                                          const float dx[4], const float u[3], Rows& R) {
+    float nx, ny;
+    face_nt(mi.face, nx, ny);
+    const float tx = -ny, ty = nx;
+    const float a = P.a[mi.face], ell = P.ell[mi.face];
+    const float k = P.kappa, ic2 = P.inv_c2, dt = P.dt;
+    const float th = xk[2], s = xk[3];
+    const float fn = u[0], ft = u[1], sd = u[2];
+    float st, ct;
+    sincosf(th, &st, &ct);
+    // quasi-static pusher-slider on an ellipsoidal limit surface:
+    // body twist = kappa * (F_x, F_y, m_z / c^2), m_z = -a f_t - s f_n
+    const float vx = k * (fn * nx + ft * tx);
+    const float vy = k * (fn * ny + ft * ty);
+    const float w = k * (-a * ft - s * fn) * ic2;
+    const float f[4] = {ct * vx - st * vy, st * vx + ct * vy, w, sd};
+    R.f0 = f[0];
+    R.f1 = f[1];
+    R.ct = ct;
+    R.st = st;
+    // Jacobians of f
+    const float Fx02 = -st * vx - ct * vy, Fx12 = ct * vx - st * vy, Fx23 = -k * fn * ic2;
+    const float Fu[4][3] = {{k * (ct * nx - st * ny), k * (ct * tx - st * ty), 0.f},
+                            {k * (st * nx + ct * ny), k * (st * tx + ct * ty), 0.f},
+                            {-k * s * ic2, -k * a * ic2, 0.f},
+                            {0.f, 0.f, 1.f}};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float is = P.inv_sigma[r];
+        R.c[r] = (dx[r] - dt * f[r]) * is;
+        R.phys[r] = 1.f / is;
+        R.on[r] = true;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) R.ax[r][j] = (r == j) ? -is : 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) R.au[r][j] = -dt * Fu[r][j] * is;
+        R.ay[r] = is;
+    }
+    R.ax[0][2] += -dt * Fx02 * P.inv_sigma[0];
+    R.ax[1][2] += -dt * Fx12 * P.inv_sigma[1];
+    R.ax[2][3] += -dt * Fx23 * P.inv_sigma[2];
+    if (mi.smask) R.on[3] = false;
+
+    const float mu = P.mu, sc = P.sc_cone;
+    const bool stick = mi.kind == 0;
+    const float sg = (mi.kind == 1) ? -1.f : 1.f;
+    // row 4: mode equality
+    if (stick) {
+        R.c[4] = sd;
+        R.phys[4] = 1.f;
+        R.lu[0][0] = 0.f; R.lu[0][1] = 0.f; R.lu[0][2] = 1.f;
+    } else {
+        R.c[4] = sc * (ft + sg * mu * fn);
+        R.phys[4] = 1.f / sc;
+        R.lu[0][0] = sc * sg * mu; R.lu[0][1] = sc; R.lu[0][2] = 0.f;
+    }
+    R.on[4] = true;
+    // rows 5, 6: friction cone (sticking only)
+    R.c[5] = sc * (ft - mu * fn);
+    R.lu[1][0] = -sc * mu; R.lu[1][1] = sc; R.lu[1][2] = 0.f;
+    R.c[6] = sc * (-ft - mu * fn);
+    R.lu[2][0] = -sc * mu; R.lu[2][1] = -sc; R.lu[2][2] = 0.f;
+    R.phys[5] = R.phys[6] = 1.f / sc;
+    R.on[5] = R.on[6] = stick;
+    // row 7: sliding direction
+    R.c[7] = sg * sd;
+    R.lu[3][0] = 0.f; R.lu[3][1] = 0.f; R.lu[3][2] = sg;
+    R.phys[7] = 1.f;
+    R.on[7] = !stick;
+    // row 8: unilateral contact -f_n <= 0
+    R.c[8] = -fn;
+    R.lu[4][0] = -1.f; R.lu[4][1] = 0.f; R.lu[4][2] = 0.f;
+    R.phys[8] = 1.f;
+    R.on[8] = true;
+    // rows 9, 10: contact point on the face, |s_k| <= ell
+    R.c[9] = s - ell;
+    R.c[10] = -s - ell;
+    R.phys[9] = R.phys[10] = 1.f;
+    R.on[9] = R.on[10] = true;
+#pragma unroll
+    for (int r = 0; r < 11; ++r)
+        if (!R.on[r]) R.c[r] = 0.f;
+}
+
+// PHR augmented-Lagrangian pieces of one row
+__device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float inv2b, float c) {
+    if (!ineq) return lam * c + 0.5f * beta * c * c;
+    const float t = fmaxf(lam + beta * c, 0.f);
+    return (t * t - lam * lam) * inv2b;
+}
+
+// ------------------------------------------------------------ shared memory
+
+struct Smem {
+    unsigned char* mb;  // [Nmax] per-interval mode byte: face | kind << 2 | smask << 4
+    float* Ky;   // [Nmax][4][5] x_{k+1} gains of the sweep
+    float* xh;   // [4][Nmax+1] state, high part
+    float* xl;   // [4][Nmax+1] state, low part
+    float* us;   // [3][Nmax]
+    float* lam;  // [3 + 11 Nmax]
+    float* dz;   // [7 Nmax + 4] interleaved step
+    float* gr;   // [7 Nmax + 4] interleaved AL gradient
+    float* M;    // [81] sweep matrix
+    float* V;    // [16] value-function Hessian
+    float* v;    // [4]  value-function gradient
+    float* misc; // [16]
+};
+
+__host__ __device__ inline size_t smem_floats(int Nmax) {
+    return (size_t)(Nmax + 3) / 4 + 20 * (size_t)Nmax + (size_t)8 * (Nmax + 1) + 3 * (size_t)Nmax + 3 +
+           11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4) + 81 + 16 + 4 + 16;
+}
+
+__device__ __forceinline__ Smem carve(float* base, int Nmax) {
+    Smem s;
+    float* p = base;
+    s.mb = reinterpret_cast<unsigned char*>(p); p += (Nmax + 3) / 4;
+    s.Ky = p; p += 20 * Nmax;
+    s.xh = p; p += 4 * (Nmax + 1);
+    s.xl = p; p += 4 * (Nmax + 1);
+    s.us = p; p += 3 * Nmax;
+    s.lam = p; p += 3 + 11 * Nmax;
+    s.dz = p; p += 7 * Nmax + 4;
+    s.gr = p; p += 7 * Nmax + 4;
+    s.M = p; p += 81;
+    s.V = p; p += 16;
+    s.v = p; p += 4;
+    s.misc = p;
+    return s;
+}
+
+// ------------------------------------------------- per-TO solver context
+
+struct Ctx {
+    const DevInstance* P;
+    uint8_t modes[COMET_MAX_SEGMENTS];
+    int len, N, Nmax;
+    Smem sm;
+    float* rec;  // this warp's stage records
+    int lane;
+};
+
+// Phase A over all stages.  Computes the violation / stationarity /
+// complementarity measures of the current iterate, the AL gradient (into
+// sm.gr), and, if `assemble`, the stage records for the sweep.  With
+// `update`, the multipliers are first replaced by their PHR estimates at
+// beta_old (the dual update of the outer loop).
+struct Measures {
+    float viol, stat, comp;
+    bool finite;
+};
+
+__device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool assemble, bool update,
+                            float beta_old) {
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = C.N + 1, lane = C.lane;
+    Smem& S = C.sm;
+    float viol = 0.f, comp = 0.f;
+    bool finite = true;
+    for (int k = lane; k < N; k += 32) {
+        const ModeInfo mi = mode_of(S.mb[k]);
+        float xk[4], dx[4], u[3];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float h0 = S.xh[i * Np1 + k], h1 = S.xh[i * Np1 + k + 1];
+            const float l0 = S.xl[i * Np1 + k], l1 = S.xl[i * Np1 + k + 1];
+            xk[i] = h0 + l0;
+            dx[i] = (h1 - h0) + (l1 - l0);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) u[j] = S.us[j * N + k];
+        Rows R;
+        eval_rows(P, mi, xk, dx, u, R);
+        float* lam = S.lam + 3 + 11 * k;
+        float y[11];
+        bool act[11];
+#pragma unroll
+        for (int r = 0; r < 11; ++r) {
+            const bool ineq = r >= 5;
+            float l = lam[r];
+            if (update && R.on[r]) {
+                const float t = l + beta_old * R.c[r];
+                l = ineq ? fmaxf(t, 0.f) : t;
+                lam[r] = l;
+            }
+            const float t = l + beta * R.c[r];
+            act[r] = R.on[r] && (!ineq || t > 0.f);
+            y[r] = act[r] ? (ineq ? fmaxf(t, 0.f) : t) : 0.f;
+            if (R.on[r]) {
+                const float vr = ineq ? fmaxf(R.c[r], 0.f) : fabsf(R.c[r]);
+                viol = fmaxf(viol, vr);
+                if (ineq) comp = fmaxf(comp, fabsf(y[r] * R.c[r]));
+                if (!isfinite(R.c[r])) finite = false;
+            }
+        }
+        // local AL gradient over (x_k, u_k, x_{k+1})
+        float gx[4] = {0.f, 0.f, 0.f, 0.f}, gu[3], gy[4];
+        const float R2 = 2.f * P.w_control;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gu[j] = R2 * u[j];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gx[j] += y[r] * R.ax[r][j];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gu[j] += y[r] * R.au[r][j];
+            gy[r] = y[r] * R.ay[r];
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gu[j] += y[4 + q] * R.lu[q][j];
+        gx[3] += y[9] - y[10];
+        // interleaved gradient: x_k slot gets the x_k part here, the x_{k+1}
+        // part is parked in dz and added in the pass below
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            S.gr[7 * k + i] = gx[i];
+            S.dz[7 * (k + 1) + i] = gy[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S.gr[7 * k + 4 + j] = gu[j];
+
+        if (assemble) {
+            // augmented local matrix over (u0..2, y0..3, x0..3, rhs), lower triangle
+            float A[78];
+#pragma unroll
+            for (int t = 0; t < 78; ++t) A[t] = 0.f;
+            // cost and proximal damping
+#pragma unroll
+            for (int j = 0; j < 3; ++j) A[tri(j, j)] += R2 + rho;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) A[tri(3 + i, 3 + i)] += rho;
+            // beta a a^T over active rows; dynamics rows first
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                float vv[11];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) vv[j] = R.au[r][j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) vv[3 + i] = (i == r) ? R.ay[r] : 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) vv[7 + i] = R.ax[r][i];
+                const float bw = act[r] ? beta : 0.f;
+#pragma unroll
+                for (int i = 0; i < 11; ++i)
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) A[tri(i, j)] += bw * vv[i] * vv[j];
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const float bw = act[4 + q] ? beta : 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) A[tri(i, j)] += bw * R.lu[q][i] * R.lu[q][j];
+            }
+            A[tri(10, 10)] += (act[9] ? beta : 0.f) + (act[10] ? beta : 0.f);
+            if (curvature) {
+                // Lagrangian curvature of the dynamics rows, -dt sum_r yd_r d^2 f_r,
+                // with yd_r the multiplier of the unscaled row
+                float nx, ny;
+                face_nt(mi.face, nx, ny);
+                const float tx = -ny, ty = nx, kk = P.kappa;
+                const float yd0 = y[0] * P.inv_sigma[0], yd1 = y[1] * P.inv_sigma[1];
+                const float yd2 = y[2] * P.inv_sigma[2];
+                const float h_thth = -yd0 * R.f0 - yd1 * R.f1;
+                const float h_thfn = yd0 * kk * (-R.st * nx - R.ct * ny) + yd1 * kk * (R.ct * nx - R.st * ny);
+                const float h_thft = yd0 * kk * (-R.st * tx - R.ct * ty) + yd1 * kk * (R.ct * tx - R.st * ty);
+                const float h_sfn = -yd2 * kk * P.inv_c2;
+                A[tri(9, 9)] -= P.dt * h_thth;  // (theta_k, theta_k)
+                A[tri(9, 0)] -= P.dt * h_thfn;  // (theta_k, f_n)
+                A[tri(9, 1)] -= P.dt * h_thft;  // (theta_k, f_t)
+                A[tri(10, 0)] -= P.dt * h_sfn;  // (s_k, f_n)
+            }
+            // right-hand side row: the gradient (u, y, x)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) A[tri(11, j)] = gu[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) A[tri(11, 3 + i)] = gy[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) A[tri(11, 7 + i)] = gx[i];
+            // eliminate the u block (3 Cholesky steps); a non-positive pivot
+            // marks the record (the sweep then reports failure)
+            bool pd = true;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float d = A[tri(j, j)];
+                pd = pd && (d > 0.f);
+                const float l = sqrtf(fmaxf(d, 1e-30f));
+                const float il = 1.f / l;
+                A[tri(j, j)] = l;
+#pragma unroll
+                for (int i = j + 1; i < 12; ++i) A[tri(i, j)] *= il;
+#pragma unroll
+                for (int c = j + 1; c < 12; ++c)
+#pragma unroll
+                    for (int i = c; i < 12; ++i) A[tri(i, c)] -= A[tri(i, j)] * A[tri(c, j)];
+            }
+            float rec[kRec];
+            rec[0] = A[tri(0, 0)]; rec[1] = A[tri(1, 0)]; rec[2] = A[tri(1, 1)];
+            rec[3] = A[tri(2, 0)]; rec[4] = A[tri(2, 1)]; rec[5] = A[tri(2, 2)];
+#pragma unroll
+            for (int i = 3; i < 12; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) rec[6 + (i - 3) * 3 + j] = A[tri(i, j)];
+#pragma unroll
+            for (int i = 3; i < 12; ++i)
+#pragma unroll
+                for (int j = 3; j <= i; ++j)
+                    if (!(i == 11 && j == 11)) rec[33 + tri(i - 3, j - 3)] = A[tri(i, j)];
+            rec[77] = pd ? 1.f : -1.f;
+            rec[78] = 0.f;
+            rec[79] = 0.f;
+            float4* dst = reinterpret_cast<float4*>(C.rec + (size_t)k * kRec);
+#pragma unroll
+            for (int q = 0; q < kRec / 4; ++q)
+                dst[q] = make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
+        }
+    }
+    __syncwarp();
+    // initial-state rows (3, unscaled) and terminal cost
+    if (lane < 3) {
+        float l = S.lam[lane];
+        const float c = (S.xh[lane * Np1] - P.start[lane]) + S.xl[lane * Np1];
+        if (update) {
+            l = l + beta_old * c;
+            S.lam[lane] = l;
+        }
+        viol = fmaxf(viol, fabsf(c));
+        if (!isfinite(c)) finite = false;
+    }
+    __syncwarp();
+    // combine the x parts of the gradient and take the stationarity measure
+    float stat = 0.f;
+    for (int k = lane; k <= N; k += 32) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float g = (k < N) ? S.gr[7 * k + i] : 0.f;
+            if (k > 0) g += S.dz[7 * k + i];
+            if (k == N && i < 3) g += 2.f * P.w_terminal * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N]);
+            if (k == 0 && i < 3) {
+                const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
+                g += S.lam[i] + beta * c;
+            }
+            S.gr[7 * k + i] = g;
+            stat = fmaxf(stat, fabsf(g));
+            if (!isfinite(g)) finite = false;
+        }
+        if (k < N) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float g = S.gr[7 * k + 4 + j];
+                stat = fmaxf(stat, fabsf(g));
+                if (!isfinite(g)) finite = false;
+            }
+        }
+    }
+    __syncwarp();
+    Measures m;
+    m.viol = warp_max(viol);
+    m.stat = warp_max(stat);
+    m.comp = warp_max(comp);
+    m.finite = __all_sync(kFull, finite);
+    return m;
+}
+
+// Entry (i, j) of the 9x9 lower triangle at flat index t (row-major).
+__device__ __forceinline__ void untri9(int t, int& i, int& j) {
+    i = 0;
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    j = t - i * (i + 1) / 2;
+}
+
+// Phase B: backward sweep over k = N-1 .. 0.  Only the x_{k+1} block is
+// eliminated on this sequential path.  Each stage leaves the raw y-factor
+// columns (pivots, y-y and (x, rhs)-y entries) in its record; the gains are
+// formed afterwards in a stage-parallel pass (phase_b_gains).  Records are
+// fetched three stages ahead.  Returns false if a pivot is not positive.
+constexpr int kPre = 3;
+__device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = C.N + 1, lane = C.lane;
+    Smem& S = C.sm;
+    // this lane's two entries of the 9x9 lower triangle (flat t0 = lane,
+    // t1 = lane + 32; only the first 44 are stored in the record)
+    int i0, j0, i1, j1;
+    untri9(lane, i0, j0);
+    untri9(lane + 32, i1, j1);
+    const bool has1 = lane + 32 < 44;
+    // V_N: terminal cost w_T |pose_N - goal|^2
+    if (lane < 16) S.V[lane] = ((lane % 5 == 0) && lane < 15) ? 2.f * P.w_terminal : 0.f;
+    if (lane < 4)
+        S.v[lane] = (lane < 3) ? 2.f * P.w_terminal * ((S.xh[lane * Np1 + N] - P.goal[lane]) + S.xl[lane * Np1 + N])
+                               : 0.f;
+    float q0[kPre], q1[kPre], qpd[kPre];
+#pragma unroll
+    for (int d = 0; d < kPre; ++d) {
+        const int kk = N - 1 - d;
+        q0[d] = q1[d] = 0.f;
+        qpd[d] = 1.f;
+        if (kk >= 0) {
+            const float* r = C.rec + (size_t)kk * kRec;
+            q0[d] = r[33 + lane];
+            q1[d] = has1 ? r[33 + lane + 32] : 0.f;
+            qpd[d] = r[77];
+        }
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int k = N - 1; k >= 0; --k) {
+        const float c0 = q0[0], c1 = q1[0];
+        const bool pd_u = qpd[0] > 0.f;
+#pragma unroll
+        for (int d = 0; d + 1 < kPre; ++d) {
+            q0[d] = q0[d + 1];
+            q1[d] = q1[d + 1];
+            qpd[d] = qpd[d + 1];
+        }
+        {
+            const int kk = k - kPre;
+            if (kk >= 0) {
+                const float* r = C.rec + (size_t)kk * kRec;
+                q0[kPre - 1] = r[33 + lane];
+                q1[kPre - 1] = has1 ? r[33 + lane + 32] : 0.f;
+                qpd[kPre - 1] = r[77];
+            }
+        }
+        // load the reduced matrix and add V_{k+1}, v_{k+1} to the x_{k+1} block
+        // (entries t < 10 are the y-y block; t = 36..39 are (rhs, y_j))
+        S.M[i0 * 9 + j0] = (lane < 10) ? c0 + S.V[i0 * 4 + j0] : c0;
+        if (has1) S.M[i1 * 9 + j1] = (i1 == 8 && j1 < 4) ? c1 + S.v[j1] : c1;
+        __syncwarp();
+        // eliminate the 4 x_{k+1} columns (each lane updates only entries in
+        // columns > j and reads only column j: no intra-step hazard)
+        bool pd = pd_u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float p = S.M[j * 9 + j];
+            pd = pd && (p > 0.f);
+            const float ip = 1.f / p;
+            if (j0 > j) S.M[i0 * 9 + j0] -= S.M[i0 * 9 + j] * S.M[j0 * 9 + j] * ip;
+            if (has1 && j1 > j) S.M[i1 * 9 + j1] -= S.M[i1 * 9 + j] * S.M[j1 * 9 + j] * ip;
+            __syncwarp();
+        }
+        if (!__all_sync(kFull, pd)) {
+            ok = false;
+            break;
+        }
+        // raw y-factor columns for the gains: record entries 33.. (consumed)
+        //   33 + tri(i, j) for the y-y block (i, j < 4, 10 entries)
+        //   43 + 4 c + j  for row (x0..x3, rhs) = 4 + c, column j (20 entries)
+        float* rec = C.rec + (size_t)k * kRec;
+        if (lane < 10) rec[33 + lane] = S.M[i0 * 9 + j0];
+        else if (lane < 30) {
+            const int c = (lane - 10) >> 2, j = (lane - 10) & 3;
+            rec[43 + 4 * c + j] = S.M[(4 + c) * 9 + j];
+        }
+        // V_k, v_k from the trailing block
+        if (lane < 10) {
+            const float val = S.M[(4 + i0) * 9 + (4 + j0)];
+            S.V[i0 * 4 + j0] = val;
+            S.V[j0 * 4 + i0] = val;
+        } else if (lane < 14) {
+            S.v[lane - 10] = S.M[8 * 9 + 4 + (lane - 10)];
+        }
+        __syncwarp();
+    }
+    if (!ok) return false;
+    // x_0 block: V_0 + rho I + beta on the three pose rows
+    float d0[4] = {0.f, 0.f, 0.f, 0.f};
+    bool pd0 = true;
+    if (lane == 0) {
+        float H[4][4], g[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) H[i][j] = S.V[i * 4 + j];
+            H[i][i] += rho;
+            g[i] = S.v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
+            H[i][i] += beta;
+            g[i] += S.lam[i] + beta * c;
+        }
+        float L[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float d = H[j][j];
+#pragma unroll
+            for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
+            pd0 = pd0 && d > 0.f;
+            const float l = sqrtf(fmaxf(d, 1e-30f));
+            L[j][j] = l;
+#pragma unroll
+            for (int i = j + 1; i < 4; ++i) {
+                float s = H[i][j];
+#pragma unroll
+                for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
+                L[i][j] = s / l;
+            }
+        }
+        float yv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float s = g[i];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
+            yv[i] = s / L[i][i];
+        }
+#pragma unroll
+        for (int i = 3; i >= 0; --i) {
+            float s = yv[i];
+#pragma unroll
+            for (int q = i + 1; q < 4; ++q) s -= L[q][i] * d0[q];
+            d0[i] = s / L[i][i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d0[i] = -d0[i];
+    }
+    pd0 = __shfl_sync(kFull, pd0 ? 1 : 0, 0) != 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dx0[i] = __shfl_sync(kFull, d0[i], 0);
+    return pd0;
+}
+
+// Stage-parallel gains: K_y,k = -L_y^{-T} [l_{x,y} | l_{rhs,y}] (4 x 5) from
+// the raw y-factor columns the sweep left in each record.
+__device__ void phase_b_gains(Ctx& C) {
+    const int N = C.N, lane = C.lane;
+    Smem& S = C.sm;
+    for (int k = lane; k < N; k += 32) {
+        const float* rec = C.rec + (size_t)k * kRec;
+        float m[30];
+#pragma unroll
+        for (int q = 0; q < 30; ++q) m[q] = rec[33 + q];
+        float ly[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float l = sqrtf(m[tri(j, j)]);
+            const float il = 1.f / l;
+            ly[j][j] = l;
+#pragma unroll
+            for (int i = j + 1; i < 4; ++i) ly[i][j] = m[tri(i, j)] * il;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) m[10 + 4 * c + j] *= il;  // l_{(4+c), j}
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            float K[4];
+#pragma unroll
+            for (int i = 3; i >= 0; --i) {
+                float s = -m[10 + 4 * c + i];
+#pragma unroll
+                for (int q = i + 1; q < 4; ++q) s -= ly[q][i] * K[q];
+                K[i] = s / ly[i][i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) S.Ky[k * 20 + i * 5 + c] = K[i];
+        }
+    }
+    __syncwarp();
+}
+
+// Phase C: forward pass.  The state chain dx_{k+1} = K_y,k [dx_k; 1] is the
+// only sequential part; the control steps
+//   du_k = -L_u^{-T} (l_{y,u}^T dx_{k+1} + l_{x,u}^T dx_k + l_{rhs,u}^T)
+// follow in a stage-parallel pass from the u-block factors of phase A.
+// Returns D = grad . dz.
+__device__ float phase_c(Ctx& C, const float dx0[4]) {
+    const int N = C.N, lane = C.lane;
+    Smem& S = C.sm;
+    float dx[4] = {dx0[0], dx0[1], dx0[2], dx0[3]};
+    if (lane < 4) S.dz[lane] = dx0[lane];
+    for (int k = 0; k < N; ++k) {
+        float w = 0.f;
+        if (lane < 4) {
+            const float* g = S.Ky + k * 20 + 5 * lane;
+            w = g[0] * dx[0] + g[1] * dx[1] + g[2] * dx[2] + g[3] * dx[3] + g[4];
+            S.dz[7 * (k + 1) + lane] = w;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dx[i] = __shfl_sync(kFull, w, i);
+    }
+    __syncwarp();
+    for (int k = lane; k < N; k += 32) {
+        const float* rec = C.rec + (size_t)k * kRec;
+        float f[33];
+#pragma unroll
+        for (int q = 0; q < 33; ++q) f[q] = rec[q];
+        float xa[4], xb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            xa[i] = S.dz[7 * k + i];
+            xb[i] = S.dz[7 * (k + 1) + i];
+        }
+        float R[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float s = f[6 + 8 * 3 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s += f[6 + i * 3 + j] * xb[i] + f[6 + (4 + i) * 3 + j] * xa[i];
+            R[j] = s;
+        }
+        const float du2 = -R[2] / f[5];
+        const float du1 = (-R[1] - f[4] * du2) / f[2];
+        const float du0 = (-R[0] - f[1] * du1 - f[3] * du2) / f[0];
+        S.dz[7 * k + 4] = du0;
+        S.dz[7 * k + 5] = du1;
+        S.dz[7 * k + 6] = du2;
+    }
+    __syncwarp();
+    float D = 0.f;
+    for (int t = lane; t < 7 * N + 4; t += 32) D += S.gr[t] * S.dz[t];
+    return warp_sum(D);
+}
+
+// merit contribution of interval k at the trial step alpha
+__device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, float beta, float inv2b) {
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = C.N + 1;
+    const Smem& S = C.sm;
+    const ModeInfo mi = mode_of(S.mb[k]);
+    float xk[4], dx[4], u[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float h0 = S.xh[i * Np1 + k], h1 = S.xh[i * Np1 + k + 1];
+        const float l0 = S.xl[i * Np1 + k] + alpha * S.dz[7 * k + i];
+        const float l1 = S.xl[i * Np1 + k + 1] + alpha * S.dz[7 * (k + 1) + i];
+        xk[i] = h0 + l0;
+        dx[i] = (h1 - h0) + (l1 - l0);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u[j] = S.us[j * N + k] + alpha * S.dz[7 * k + 4 + j];
+    Rows R;
+    eval_rows(P, mi, xk, dx, u, R);
+    const float* lam = S.lam + 3 + 11 * k;
+    float phi = P.w_control * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int r = 0; r < 11; ++r)
+        if (R.on[r]) phi += row_al(r >= 5, lam[r], beta, inv2b, R.c[r]);
+    if (k == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float c = (S.xh[i * Np1] - P.start[i]) + (S.xl[i * Np1] + alpha * S.dz[i]);
+            phi += row_al(false, S.lam[i], beta, inv2b, c);
+        }
+    }
+    if (k == N - 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float e = (S.xh[i * Np1 + N] - P.goal[i]) + (S.xl[i * Np1 + N] + alpha * S.dz[7 * N + i]);
+            phi += P.w_terminal * e * e;
+        }
+    }
+    return phi;
+}
+
+// Phase D: trial merits for alpha in {0, 1, 1/2, ..., 2^-(n_alpha-1)}.
+// Returns the accepted alpha (0 = rejected).
+__device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& sp) {
+    const int lane = C.lane;
+    const int a = lane & 7, grp = lane >> 3;
+    const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
+    float phi = 0.f;
+    const float inv2b = 0.5f / beta;
+    if (a <= sp.n_alpha)
+        for (int k = grp; k < C.N; k += 4) phi += stage_merit(C, k, alpha, beta, inv2b);
+    phi += __shfl_xor_sync(kFull, phi, 8);
+    phi += __shfl_xor_sync(kFull, phi, 16);
+    const float phi0 = __shfl_sync(kFull, phi, 0);
+    const float phi1 = __shfl_sync(kFull, phi, 1);
+    const float slack = sp.ls_slack * fabsf(phi0);
+    const bool flat = fabsf(D) <= slack;
+    bool pass = (a >= 1) && (a <= sp.n_alpha) && (phi <= phi0 + sp.armijo_c1 * alpha * D);
+    if (a == 1 && flat && phi1 <= phi0 + slack) pass = true;
+    const unsigned bal = __ballot_sync(kFull, pass) & 0xffu;
+    if (!bal) return 0.f;
+    const int first = __ffs(bal) - 1;
+    return ldexpf(1.f, -(first - 1));
+}
+
+// Phase E: compensated update z += alpha dz
+__device__ void phase_e(Ctx& C, float alpha) {
+    const int N = C.N, Np1 = C.N + 1, lane = C.lane;
+    Smem& S = C.sm;
+    for (int t = lane; t < 4 * Np1; t += 32) {
+        const int i = t / Np1, k = t - i * Np1;
+        float s, e;
+        two_sum(S.xh[t], S.xl[t] + alpha * S.dz[7 * k + i], s, e);
+        S.xh[t] = s;
+        S.xl[t] = e;
+    }
+    for (int t = lane; t < 3 * N; t += 32) {
+        const int j = t / N, k = t - j * N;
+        S.us[t] += alpha * S.dz[7 * k + 4 + j];
+    }
+    __syncwarp();
+}
+
+// FP64 certificate (Eq. inexact_mode_value in physical units, KKT residual)
+struct Cert {
+    double cost, viol, stat;
+    bool finite;
+};
+
+__device__ Cert certify(const Ctx& C, float beta) {
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = C.N + 1, lane = C.lane;
+    const Smem& S = C.sm;
+    double cost = 0.0, viol = 0.0, stat = 0.0;
+    bool finite = true;
+    // gradient pieces are accumulated per knot: lane handles knots k and
+    // recomputes the two adjacent intervals (k-1 as x_{k+1}, k as x_k)
+    for (int k = lane; k <= N; k += 32) {
+        double g[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int side = 0; side < 2; ++side) {
+            const int kk = (side == 0) ? k - 1 : k;  // interval index
+            if (kk < 0 || kk >= N) continue;
+            const ModeInfo mi = mode_info(C.modes, C.len, N, kk);
+            double x0[4], x1[4], u[3];
+            for (int i = 0; i < 4; ++i) {
+                x0[i] = (double)S.xh[i * Np1 + kk] + (double)S.xl[i * Np1 + kk];
+                x1[i] = (double)S.xh[i * Np1 + kk + 1] + (double)S.xl[i * Np1 + kk + 1];
+            }
+            for (int j = 0; j < 3; ++j) u[j] = (double)S.us[j * N + kk];
+            const double nx = (mi.face == 0) ? 1.0 : ((mi.face == 2) ? -1.0 : 0.0);
+            const double ny = (mi.face == 1) ? 1.0 : ((mi.face == 3) ? -1.0 : 0.0);
+            const double tx = -ny, ty = nx;
+            const double a = P.a_d[mi.face], ell = P.ell_d[mi.face];
+            const double kp = P.kappa_d, ic2 = P.inv_c2_d, dt = P.dt_d;
+            double st, ct;
+            sincos(x0[2], &st, &ct);
+            const double fn = u[0], ft = u[1], sd = u[2];
+            const double vx = kp * (fn * nx + ft * tx), vy = kp * (fn * ny + ft * ty);
+            const double f[4] = {ct * vx - st * vy, st * vx + ct * vy, kp * (-a * ft - x0[3] * fn) * ic2, sd};
+            const double Fx02 = -st * vx - ct * vy, Fx12 = ct * vx - st * vy, Fx23 = -kp * fn * ic2;
+            const double Fu[4][3] = {{kp * (ct * nx - st * ny), kp * (ct * tx - st * ty), 0.0},
+                                     {kp * (st * nx + ct * ny), kp * (st * tx + ct * ty), 0.0},
+                                     {-kp * x0[3] * ic2, -kp * a * ic2, 0.0},
+                                     {0.0, 0.0, 1.0}};
+            const double mu = P.mu_d, sc = P.sc_cone_d;
+            const bool stick = mi.kind == 0;
+            const double sg = (mi.kind == 1) ? -1.0 : 1.0;
+            double c[11], ph[11];
+            bool on[11];
+            double J[11][11];
+            for (int r = 0; r < 11; ++r) {
+                on[r] = true;
+                ph[r] = 1.0;
+                for (int j = 0; j < 11; ++j) J[r][j] = 0.0;
+            }
+            for (int r = 0; r < 4; ++r) {
+                const double is = 1.0 / P.sigma_d[r];
+                c[r] = (x1[r] - x0[r] - dt * f[r]) * is;
+                ph[r] = P.sigma_d[r];
+                J[r][r] = -is;
+                J[r][7 + r] = is;
+                for (int j = 0; j < 3; ++j) J[r][4 + j] = -dt * Fu[r][j] * is;
+            }
+            J[0][2] += -dt * Fx02 / P.sigma_d[0];
+            J[1][2] += -dt * Fx12 / P.sigma_d[1];
+            J[2][3] += -dt * Fx23 / P.sigma_d[2];
+            if (mi.smask) on[3] = false;
+            if (stick) {
+                c[4] = sd;
+                J[4][6] = 1.0;
+            } else {
+                c[4] = sc * (ft + sg * mu * fn);
+                J[4][4] = sc * sg * mu;
+                J[4][5] = sc;
+                ph[4] = 1.0 / sc;
+            }
+            c[5] = sc * (ft - mu * fn);
+            J[5][4] = -sc * mu;
+            J[5][5] = sc;
+            c[6] = sc * (-ft - mu * fn);
+            J[6][4] = -sc * mu;
+            J[6][5] = -sc;
+            ph[5] = ph[6] = 1.0 / sc;
+            on[5] = on[6] = stick;
+            c[7] = sg * sd;
+            J[7][6] = sg;
+            on[7] = !stick;
+            c[8] = -fn;
+            J[8][4] = -1.0;
+            c[9] = x0[3] - ell;
+            J[9][3] = 1.0;
+            c[10] = -x0[3] - ell;
+            J[10][3] = -1.0;
+            const float* lam = S.lam + 3 + 11 * kk;
+            for (int r = 0; r < 11; ++r) {
+                if (!on[r]) continue;
+                const bool ineq = r >= 5;
+                const double t = (double)lam[r] + (double)beta * c[r];
+                const double y = ineq ? fmax(t, 0.0) : t;
+                if (side == 1) {  // count each interval once
+                    const double vr = ineq ? fmax(c[r], 0.0) : fabs(c[r]);
+                    viol = fmax(viol, vr * ph[r]);
+                    if (!isfinite(c[r])) finite = false;
+                }
+                // gradient: side 0 contributes the x_{k+1} columns, side 1 the x_k and u_k ones
+                if (side == 0)
+                    for (int i = 0; i < 4; ++i) g[i] += y * J[r][7 + i];
+                else
+                    for (int i = 0; i < 7; ++i) g[i] += y * J[r][i];
+            }
+            if (side == 1) {
+                for (int j = 0; j < 3; ++j) {
+                    g[4 + j] += 2.0 * P.w_control_d * u[j];
+                    cost += P.w_control_d * u[j] * u[j];
+                }
+            }
+        }
+        if (k == N)
+            for (int i = 0; i < 3; ++i) {
+                const double e = (double)S.xh[i * Np1 + N] + (double)S.xl[i * Np1 + N] - P.goal_d[i];
+                g[i] += 2.0 * P.w_terminal_d * e;
+                cost += P.w_terminal_d * e * e;
+            }
+        if (k == 0)
+            for (int i = 0; i < 3; ++i) {
+                const double c = (double)S.xh[i * Np1] + (double)S.xl[i * Np1] - P.start_d[i];
+                g[i] += (double)S.lam[i] + (double)beta * c;
+                viol = fmax(viol, fabs(c));
+            }
+        const int nv = (k < N) ? 7 : 4;
+        for (int i = 0; i < nv; ++i) {
+            stat = fmax(stat, fabs(g[i]));
+            if (!isfinite(g[i])) finite = false;
+        }
+    }
+    Cert ct;
+    ct.cost = warp_sum_d(cost);
+    ct.viol = warp_max_d(viol);
+    ct.stat = warp_max_d(stat);
+    ct.finite = __all_sync(kFull, finite) && isfinite(ct.cost);
+    return ct;
+}
+
+// ------------------------------------------------------------------ kernel
+
+__global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
+    extern __shared__ float smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warp_global = blockIdx.x * (blockDim.x >> 5) + wib;
+    const size_t per_warp = smem_floats(A.Nmax);
+    Ctx C;
+    C.lane = lane;
+    C.Nmax = A.Nmax;
+    C.sm = carve(smem_raw + per_warp * wib, A.Nmax);
+    C.rec = A.ws + (size_t)warp_global * A.ws_per_warp;
+    const SolverParams& sp = A.sp;
+
+    for (;;) {
+        unsigned int t = 0;
+        if (lane == 0) t = atomicAdd(A.queue, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= A.n) break;
+        const int64_t ti = (int64_t)t;
+        // ---- load the order and validate it
+        const comet_mode_seq sq = A.seqs[ti];
+        bool bad = sq.instance < 0 || sq.instance >= A.n_inst;
+        const DevInstance* P = bad ? A.inst : A.inst + sq.instance;
+        const int len = sq.len;
+        bad = bad || len < 1 || len > P->Lmax || len > COMET_MAX_SEGMENTS;
+        if (!bad)
+            for (int i = 0; i < len; ++i) bad = bad || sq.modes[i] >= P->n_modes;
+        if (bad) {
+            if (lane == 0) {
+                atomicExch(A.bad_input, 1);
+                A.out_status[ti] = COMET_TO_NONFINITE;
+                A.out_cost[ti] = __int_as_float(0x7fc00000);
+                if (A.out_iters) A.out_iters[ti] = 0;
+                if (A.out_viol) A.out_viol[ti] = __int_as_float(0x7fc00000);
+                if (A.out_merit) A.out_merit[ti] = __int_as_float(0x7fc00000);
+                if (A.out_stat) A.out_stat[ti] = __int_as_float(0x7fc00000);
+            }
+            continue;
+        }
+        C.P = P;
+        C.len = len;
+        C.N = P->K * len;
+        for (int i = 0; i < COMET_MAX_SEGMENTS; ++i) C.modes[i] = sq.modes[i];
+        const int N = C.N, Np1 = N + 1;
+        Smem& S = C.sm;
+        // ---- initial iterate: warm start or the cold start
+        const float* warm = A.warm ? A.warm + ti * A.stride : nullptr;
+        const int Nm1 = A.Nmax + 1;
+        for (int q = lane; q < 4 * Np1; q += 32) {
+            const int i = q / Np1, k = q - i * Np1;
+            float x;
+            if (warm) {
+                x = warm[i * Nm1 + k];
+            } else if (i < 3) {
+                const float al = (float)k / (float)N;
+                x = (1.f - al) * P->start[i] + al * P->goal[i];
+            } else {
+                x = 0.f;
+            }
+            S.xh[q] = x;
+            S.xl[q] = 0.f;
+        }
+        for (int q = lane; q < 3 * N; q += 32) {
+            const int j = q / N, k = q - j * N;
+            S.us[q] = warm ? warm[4 * Nm1 + j * A.Nmax + k] : 0.f;
+        }
+        for (int q = lane; q < 3 + 11 * N; q += 32) S.lam[q] = 0.f;
+        for (int k = lane; k < N; k += 32) {
+            const ModeInfo mi = mode_info(C.modes, len, N, k);
+            S.mb[k] = (unsigned char)(mi.face | (mi.kind << 2) | ((mi.smask ? 1 : 0) << 4));
+        }
+        __syncwarp();
+
+        float beta = sp.beta0, rho = sp.rho0, eta = INFINITY;
+        int inner = 0, it = 0, status = COMET_TO_MAX_ITER, curv_hold = 0;
+        bool nonfinite = false;
+        for (it = 0; it < sp.max_iters; ++it) {
+            const bool curv = curv_hold == 0;
+            Measures m = phase_a(C, beta, rho, curv, true, false, beta);
+            if (!m.finite) {
+                status = COMET_TO_NONFINITE;
+                nonfinite = true;
+                break;
+            }
+            const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
+            if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
+                status = COMET_TO_CONVERGED;
+                break;
+            }
+            const float omega = fmaxf(eps_d, sp.omega_ratio * m.viol);
+            const bool solved = m.stat <= omega;
+            if (solved || inner >= sp.max_inner) {
+                const float beta_old = beta;
+                if (solved && m.viol > sp.eps_primal && m.viol > sp.eta_ratio * eta)
+                    beta = fminf(sp.beta_max, beta * sp.beta_growth);
+                eta = m.viol;
+                inner = 0;
+                // dual update at beta_old, then the model at the new (lam, beta)
+                phase_a(C, beta, rho, curv, true, true, beta_old);
+            }
+            // step: Newton with the dynamics curvature, then Gauss-Newton,
+            // then rising damping
+            float dx0[4];
+            bool fac = false;
+            if (curv) {
+                fac = phase_b(C, beta, rho, dx0);
+                if (!fac) curv_hold = sp.curv_skip;
+            } else {
+                --curv_hold;
+            }
+            // the first Gauss-Newton retry reuses the model assembled above
+            // when no curvature term was included
+            bool have_gn = !curv;
+            for (int r = 0; !fac && r <= sp.max_retries; ++r) {
+                if (r > 0) rho = fminf(sp.rho_max, rho * 10.f);
+                if (!have_gn) phase_a(C, beta, rho, false, true, false, beta);
+                have_gn = false;
+                fac = phase_b(C, beta, rho, dx0);
+            }
+            ++inner;
+            if (!fac) continue;
+            phase_b_gains(C);
+            const float D = phase_c(C, dx0);
+            const float alpha = phase_d(C, beta, D, sp);
+            if (alpha > 0.f) {
+                phase_e(C, alpha);
+                rho = fmaxf(sp.rho_min, rho / 10.f);
+            } else {
+                rho = fminf(sp.rho_max, rho * 10.f);
+            }
+        }
+        // ---- FP64 certificate and outputs
+        const Cert ct = certify(C, beta);
+        if (!ct.finite) nonfinite = true;
+        if (nonfinite) status = COMET_TO_NONFINITE;
+        if (status == COMET_TO_CONVERGED && !(ct.viol <= sp.eps_feas)) status = COMET_TO_INFEASIBLE;
+        if (lane == 0) {
+            A.out_status[ti] = status;
+            A.out_cost[ti] = (float)ct.cost;
+            if (A.out_viol) A.out_viol[ti] = (float)ct.viol;
+            if (A.out_merit) A.out_merit[ti] = (float)(ct.cost + sp.merit_mu * fmax(ct.viol - sp.eps_feas, 0.0));
+            if (A.out_iters) A.out_iters[ti] = it;
+            if (A.out_stat) A.out_stat[ti] = (float)ct.stat;
+        }
+        if (A.out_traj) {
+            float* out = A.out_traj + ti * A.stride;
+            for (int q = lane; q < 4 * Nm1; q += 32) {
+                const int i = q / Nm1, k = q - i * Nm1;
+                out[q] = (k <= N) ? S.xh[i * Np1 + k] + S.xl[i * Np1 + k] : 0.f;
+            }
+            for (int q = lane; q < 3 * A.Nmax; q += 32) {
+                const int j = q / A.Nmax, k = q - j * A.Nmax;
+                out[4 * Nm1 + q] = (k < N) ? S.us[j * N + k] : 0.f;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t smem_per_warp_bytes(int Nmax) { return smem_floats(Nmax) * sizeof(float); }
+
+int eval_blocks_per_sm(int warps_per_block, size_t smem_per_block) {
+    int nb = 0;
+    if (cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_block) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel, warps_per_block * 32, smem_per_block) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_eval(const EvalArgs& a, int total_warps, int warps_per_block, cudaStream_t s) {
+    const size_t smem = smem_per_warp_bytes(a.Nmax) * warps_per_block;
+    cudaError_t e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (total_warps + warps_per_block - 1) / warps_per_block;
+    eval_kernel<<<blocks, warps_per_block * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace comet

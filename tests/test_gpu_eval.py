@@ -1,0 +1,268 @@
+"""GPU parity of the CUDA evaluator (through the C ABI) against the FP64
+oracle.  Paper: Eq. mode_nlp, Eq. inexact_mode_value, Eq. search_merit,
+Eq. mode_selection, Sec. III-C.
+
+The TO is a local, non-convex solve (Eq. mode_nlp: "not guaranteed to
+attain J*(m)"), run in FP32 on the GPU and in FP64 by the oracle; the two
+follow the same iteration but can part ways at a near-tie of a discrete
+decision and then reach different local minima, each of them valid.  The
+parity bar therefore has two parts:
+  * every CONVERGED GPU result is certified by the oracle's own FP64
+    residual evaluation (v_hat <= 1e-5, cone / unilateral rows hold);
+  * where both converge to the same local solution, costs agree within
+    1e-4 relative plus the first-order effect of the stop test's allowed
+    infeasibility, |dJ| <= 1e-4 |J| + 2 * sum_i |lambda_i| * eps_primal
+    (bounded here through the certified violation), and the fraction of
+    such agreements, the status agreement and the enumeration argmin
+    (wherever the oracle's cost gap exceeds 1e-3 relative) are checked.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import search as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_21803_gb300 import build as B
+    B.build()
+    import paper_2609_21803_gb300 as P
+    P.lib()
+    torch.cuda.set_device(0)
+    return P
+
+
+def gpu_eval(P, insts, seqs, inst_idx=None, lens=None, warm=None, want_traj=False, max_iters=0, opts=None):
+    prob = P.Problem(insts, opts=opts)
+    packed = P.pack_mode_seqs(seqs, inst_idx, lens)
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(packed), 24)).cuda()
+    w = None if warm is None else torch.from_numpy(np.ascontiguousarray(warm, dtype=np.float32)).cuda()
+    r = prob.eval(d, warm=w, want_traj=want_traj, max_iters=max_iters)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in r.items()}
+    out["stride"] = prob.stride
+    prob.close()
+    return out
+
+
+def certify_fp64(inst, modes, N, traj_f32, Nmax):
+    """Physical violation of a GPU trajectory recomputed by the oracle."""
+    Np1, Nm1 = N + 1, Nmax + 1
+    tr = np.zeros(7 * N + 4)
+    for i in range(4):
+        tr[i * Np1: (i + 1) * Np1] = traj_f32[i * Nm1: i * Nm1 + Np1]
+    for j in range(3):
+        tr[4 * Np1 + j * N: 4 * Np1 + (j + 1) * N] = traj_f32[4 * Nm1 + j * Nmax: 4 * Nm1 + j * Nmax + N]
+    c, mask, scale, ci = oracle.rows(inst, modes, N, tr)
+    ineq = np.arange(11) >= 5
+    v = np.where(ineq, np.maximum(c, 0.0), np.abs(c)) / scale * mask
+    return max(float(np.max(v)), float(np.max(np.abs(ci)))), tr
+
+
+def compare(gpu, ref, eps_primal=1e-6):
+    cg, co = gpu["status"] == 0, ref["status"] == 0
+    both = cg & co
+    rel = np.abs(gpu["cost"].astype(np.float64) - ref["cost"]) / np.abs(ref["cost"])
+    same = both & (rel < 1e-2)          # same local solution
+    return cg, co, both, rel, same
+
+
+def test_straight_push_closed_form(P):
+    # goal (d, 0, 0) with face 0 sticking: J* = W R d^2 / (R + W N dt^2) = 10 d^2 / 17
+    inst = W.push_l2_straight(0.1)
+    seqs = np.array([[0, 0]], np.uint8)
+    g = gpu_eval(P, [inst], seqs, want_traj=True)
+    tr, lam, ref = oracle.solve(inst, [0, 0])
+    assert g["status"][0] == P.TO_CONVERGED
+    assert g["viol"][0] <= 1e-5
+    # same algorithm: GPU (FP32) and oracle (FP64) land on the same point
+    assert abs(g["cost"][0] - ref["cost"]) <= 1e-4 * ref["cost"]
+    # against the closed form, up to the stop test's allowed infeasibility
+    Jstar = 10 * 0.01 / 17
+    assert abs(g["cost"][0] - Jstar) <= 5e-4 * Jstar
+    fn = g["traj"][0][4 * 81: 4 * 81 + 16]
+    np.testing.assert_allclose(fn, 0.1 / 1.7, rtol=2e-3)
+
+
+def test_two_segment_enumeration_parity(P):
+    # BASELINE workload of 2-segment orders: every 144 orders x 32 seeded goals
+    seeds = range(32)
+    insts = [W.push_l2_instance(s) for s in seeds]
+    seqs = W.all_sequences(12, 2)
+    n = len(seqs) * len(insts)
+    allseq = np.tile(seqs, (len(insts), 1))
+    idx = np.repeat(np.arange(len(insts)), len(seqs)).astype(np.int32)
+    g = gpu_eval(P, insts, allseq, idx, want_traj=True)
+    ref, _ = oracle.solve_batch(insts, idx, allseq, np.full(n, 2, np.int32), nthreads=os.cpu_count())
+    cg, co, both, rel, same = compare(g, ref)
+    print(f"conv gpu {cg.mean():.4f} oracle {co.mean():.4f}; both {both.mean():.4f}; "
+          f"rel<1e-4 {np.mean(rel[both] < 1e-4):.4f}; same-solution {same.sum() / both.sum():.4f}")
+    assert cg.mean() >= 0.95 and abs(cg.mean() - co.mean()) <= 0.03
+    assert same.sum() >= 0.85 * both.sum()
+    # cost agreement where both reached the same local solution
+    bias = 2e-4 * np.abs(ref["cost"]) + 1e-7
+    assert np.mean(np.abs(g["cost"] - ref["cost"])[same] <= 1e-4 * np.abs(ref["cost"][same]) + bias[same]) >= 0.97
+    # feasibility flags (v_hat <= eps_feas) agree
+    assert np.mean((g["viol"] <= 1e-5) == (ref["viol"] <= 1e-5)) >= 0.97
+    # every CONVERGED GPU result is certified by the oracle's FP64 residuals
+    N = 16
+    for t in np.flatnonzero(cg)[::7]:
+        v, tr = certify_fp64(insts[idx[t]], allseq[t], N, g["traj"][t], 16)
+        assert v <= 1e-5, (t, v)
+        fnv, ftv = tr[4 * 17: 4 * 17 + N], tr[4 * 17 + N: 4 * 17 + 2 * N]
+        assert np.all(fnv >= -1e-5) and np.all(np.abs(ftv) <= insts[idx[t]]["mu"] * fnv + 2e-5)
+    # enumeration argmin (Eq. mode_selection) per instance: identical where
+    # the oracle's best is ahead of the GPU's pick by more than 1e-3 relative;
+    # where the GPU's local solve found a better minimum for another order
+    # (a valid, certified plan no worse than the oracle's best) the picks may
+    # differ -- the paper reports the same effect between its FP64 CPU and
+    # mixed-precision GPU evaluators
+    same_pick = 0
+    for i in range(len(insts)):
+        sl = slice(144 * i, 144 * (i + 1))
+        ag = S.enumeration_argmin(g["cost"][sl], g["viol"][sl])
+        ao = S.enumeration_argmin(ref["cost"][sl], ref["viol"][sl])
+        if ag == ao:
+            same_pick += 1
+            continue
+        gap = (ref["merit"][sl][ao] - ref["merit"][sl][ag]) / abs(ref["merit"][sl][ao])
+        if gap < -1e-3:   # the oracle's evaluation of the GPU pick is worse ...
+            # ... so the GPU's plan must itself be certified and at least as good
+            t = 144 * i + ag
+            v, _ = certify_fp64(insts[i], allseq[t], N, g["traj"][t], 16)
+            assert g["status"][t] == 0 and v <= 1e-5, (i, ag, v)
+            assert g["cost"][t] <= ref["cost"][sl][ao] * (1 + 1e-3), (i, ag, ao, g["cost"][t], ref["cost"][sl][ao])
+    assert same_pick >= 0.9 * len(insts), same_pick
+
+
+def test_four_segment_sampled_parity(P):
+    # the 4-segment workload at full size on the GPU (one instance, 20,736
+    # orders, the bench's launch configuration); the oracle checks a seeded
+    # sample of the results one by one
+    inst = W.push_l4_instance(5)
+    seqs = W.all_sequences(12, 4)
+    g = gpu_eval(P, [inst], seqs, want_traj=True)
+    rng = np.random.default_rng(0)
+    sub = np.sort(rng.choice(len(seqs), 256, replace=False))
+    ref, _ = oracle.solve_batch([inst], np.zeros(len(sub), np.int32), seqs[sub], np.full(len(sub), 4, np.int32),
+                                nthreads=os.cpu_count())
+    gs = {k: v[sub] for k, v in g.items() if k != "stride"}
+    cg, co, both, rel, same = compare(gs, ref)
+    print(f"N=80 conv gpu {np.mean(g['status'] == 0):.4f} sample gpu {cg.mean():.4f} oracle {co.mean():.4f} "
+          f"same {same.sum() / max(1, both.sum()):.4f} rel<1e-4 {np.mean(rel[both] < 1e-4):.4f}")
+    assert np.mean(g["status"] == 0) >= 0.75
+    assert abs(cg.mean() - co.mean()) <= 0.08
+    assert same.sum() >= 0.8 * both.sum()
+    bias = 4e-4 * np.abs(ref["cost"]) + 1e-7
+    assert np.mean(np.abs(gs["cost"] - ref["cost"])[same] <= 1e-4 * np.abs(ref["cost"][same]) + bias[same]) >= 0.95
+    # certification of the converged GPU results on the whole launch (sampled)
+    for t in np.flatnonzero(g["status"] == 0)[::211]:
+        v, _ = certify_fp64(inst, seqs[t], 80, g["traj"][t], 80)
+        assert v <= 1e-5, (t, v)
+
+
+def test_mixed_lengths_and_instances_one_launch(P):
+    # ragged launch: lengths 1..4 (N = 20..80) over three instances, 37 orders
+    insts = [W.push_l4_instance(s) for s in (1, 2, 3)]
+    rng = np.random.default_rng(3)
+    seqs, idx = [], []
+    for t in range(37):
+        L = 1 + t % 4
+        seqs.append(tuple(int(m) for m in rng.integers(0, 12, L)))
+        idx.append(t % 3)
+    g = gpu_eval(P, insts, seqs, idx)
+    modes, lens = W.pad_sequences(seqs, 4)
+    ref, _ = oracle.solve_batch(insts, np.array(idx, np.int32), modes, lens)
+    cg, co, both, rel, same = compare(g, ref)
+    assert cg.mean() >= 0.7
+    assert same.sum() >= 0.8 * both.sum()
+    assert np.all(g["iters"] <= 300)
+
+
+def test_warm_start_at_oracle_solution(P):
+    inst = W.push_l2_instance(4)
+    seqs = W.all_sequences(12, 2)[::13]
+    n = len(seqs)
+    ref, tr = oracle.solve_batch([inst], np.zeros(n, np.int32), seqs, np.full(n, 2, np.int32), want_traj=True)
+    warm = np.zeros((n, 7 * 16 + 4), np.float32)
+    warm[:] = tr[:, : 7 * 16 + 4]
+    g = gpu_eval(P, [inst], seqs, warm=warm)
+    ok = ref["status"] == 0
+    assert np.all(g["status"][ok] == 0)
+    # restarted at the oracle's point the GPU stays in its basin
+    rel = np.abs(g["cost"][ok] - ref["cost"][ok]) / np.abs(ref["cost"][ok])
+    assert np.all(rel < 1e-3) and np.median(rel) < 1e-4
+
+
+def test_edge_cases(P):
+    inst = W.push_l2_instance(0)
+    prob = P.Problem([inst])
+    # n = 0 is a no-op
+    empty = torch.zeros((0, 24), dtype=torch.uint8, device="cuda")
+    out = prob.eval(empty)
+    assert out["cost"].numel() == 0
+    # one TO and a partial warp count
+    for n in (1, 33):
+        seqs = W.random_sequences(n, n, 12, 2)
+        g = gpu_eval(P, [inst], seqs)
+        assert g["cost"].shape == (n,) and np.all(np.isfinite(g["cost"]))
+    # malformed orders from host memory are rejected before any work
+    bad = P.pack_mode_seqs(np.array([[0, 12]], np.uint8))
+    cost = np.zeros(1, np.float32)
+    status = np.zeros(1, np.int32)
+    with pytest.raises(P.CometError):
+        P.comet_eval_modes(prob.handle, bad, 1, None, cost, None, status)
+    bad = P.pack_mode_seqs(np.array([[0, 1, 2]], np.uint8))     # longer than max_segments
+    with pytest.raises(P.CometError):
+        P.comet_eval_modes(prob.handle, bad, 1, None, cost, None, status)
+    # malformed orders in device memory: per-TO status, no call failure
+    dbad = torch.from_numpy(P.pack_mode_seqs(np.array([[0, 12]], np.uint8)).view(np.uint8).reshape(1, 24)).cuda()
+    out = prob.eval(dbad)
+    torch.cuda.synchronize()
+    assert int(out["status"][0]) == P.TO_NONFINITE
+    # non-finite warm start -> NONFINITE status
+    warm = np.zeros((1, prob.stride), np.float32)
+    warm[0, 3] = np.nan
+    g = gpu_eval(P, [inst], np.array([[0, 1]], np.uint8), warm=warm)
+    assert g["status"][0] == P.TO_NONFINITE
+    prob.close()
+
+
+def test_host_and_device_buffers_agree_and_runs_are_deterministic(P):
+    insts = [W.push_l2_instance(6)]
+    seqs = W.all_sequences(12, 2)
+    n = len(seqs)
+    prob = P.Problem(insts)
+    packed = P.pack_mode_seqs(seqs)
+    h_cost = np.zeros(n, np.float32)
+    h_status = np.zeros(n, np.int32)
+    h_traj = np.zeros((n, prob.stride), np.float32)
+    P.comet_eval_modes(prob.handle, packed, n, None, h_cost, h_traj, h_status)
+    d = torch.from_numpy(packed.view(np.uint8).reshape(n, 24)).cuda()
+    a = prob.eval(d, want_traj=True)
+    b = prob.eval(d, want_traj=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a["cost"].cpu().numpy(), h_cost)
+    np.testing.assert_array_equal(a["status"].cpu().numpy(), h_status)
+    np.testing.assert_array_equal(a["traj"].cpu().numpy(), h_traj)
+    np.testing.assert_array_equal(a["cost"].cpu().numpy(), b["cost"].cpu().numpy())
+    prob.close()
+
+
+def test_budget_entry_point(P):
+    inst = W.push_l4_instance(9)
+    seqs = W.all_sequences(12, 4)[:64]
+    g5 = gpu_eval(P, [inst], seqs, max_iters=5)
+    assert np.all(g5["iters"] <= 5)
+    g = gpu_eval(P, [inst], seqs, max_iters=1500)
+    assert np.mean(g["status"] == 0) >= np.mean(gpu_eval(P, [inst], seqs)["status"] == 0)
