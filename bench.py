@@ -176,6 +176,8 @@ def run_gpu(args):
     P.lib()
     insts = instances()
     seqs = W.all_sequences(12, SEG)
+    if args.orders:
+        seqs = seqs[: args.orders]  # profiling runs only: a prefix of the enumeration
     n = len(seqs)
     stream = torch.cuda.Stream()
     # one problem per instance; orders resident on the device (replicas: rank
@@ -295,6 +297,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--orders", type=int, default=0, help="profiling only: solve this prefix of each enumeration")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
