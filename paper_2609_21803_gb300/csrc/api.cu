@@ -82,6 +82,108 @@ void dynamics_row_scales(const comet_instance_desc& d, double sigma[4]) {
 
 }  // namespace
 
+namespace comet {
+
+// FP32 / FP64 device constants of one instance descriptor.
+void make_dev_instance(const comet_instance_desc& d, DevInstance* out) {
+    DevInstance& q = *out;
+    memset(&q, 0, sizeof(q));
+    double sigma[4];
+    dynamics_row_scales(d, sigma);
+    q.dt_d = d.dt;
+    q.kappa_d = d.kappa;
+    q.inv_c2_d = 1.0 / (d.c_ls * d.c_ls);
+    q.mu_d = d.mu;
+    q.sc_cone_d = 1.0 / sqrt(1.0 + d.mu * d.mu);
+    for (int f = 0; f < 4; ++f) {
+        q.a_d[f] = (f % 2 == 0) ? 0.5 * d.side_x : 0.5 * d.side_y;
+        q.ell_d[f] = (f % 2 == 0) ? 0.5 * d.side_y : 0.5 * d.side_x;
+        q.a[f] = (float)q.a_d[f];
+        q.ell[f] = (float)q.ell_d[f];
+    }
+    for (int r = 0; r < 4; ++r) {
+        q.sigma_d[r] = sigma[r];
+        q.inv_sigma[r] = (float)(1.0 / sigma[r]);
+    }
+    for (int j = 0; j < 3; ++j) {
+        q.start_d[j] = d.start[j];
+        q.goal_d[j] = d.goal[j];
+        q.start[j] = (float)d.start[j];
+        q.goal[j] = (float)d.goal[j];
+    }
+    q.w_terminal_d = d.w_terminal;
+    q.w_control_d = d.w_control;
+    q.w_terminal = (float)d.w_terminal;
+    q.w_control = (float)d.w_control;
+    q.dt = (float)d.dt;
+    q.kappa = (float)d.kappa;
+    q.inv_c2 = (float)q.inv_c2_d;
+    q.mu = (float)d.mu;
+    q.sc_cone = (float)q.sc_cone_d;
+    q.K = d.knots_per_segment;
+    q.Lmax = d.max_segments;
+    q.n_modes = d.n_modes;
+    q.task = d.task;
+}
+
+// Solver parameters of a call from the options and an iteration budget
+// (max_iters <= 0 keeps opts.max_iters).
+SolverParams make_params(const comet_solver_opts& o, int max_iters) {
+    SolverParams sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.max_iters = max_iters > 0 ? max_iters : o.max_iters;
+    sp.max_retries = 8;
+    sp.n_alpha = 7;
+    sp.max_inner = 40;
+    sp.curv_skip = 3;
+    sp.beta0 = (float)o.beta0;
+    sp.beta_max = (float)o.beta_max;
+    sp.beta_growth = 10.f;
+    sp.beta_ref = (float)o.beta_ref;
+    sp.rho0 = (float)o.rho0;
+    sp.rho_min = (float)o.rho_min;
+    sp.rho_max = 1e6f;
+    sp.armijo_c1 = 1e-4f;
+    sp.ls_slack = 1e-6f;
+    sp.eps_primal = (float)o.eps_primal;
+    sp.eps_dual = (float)o.eps_dual;
+    sp.eps_comp = (float)o.eps_comp;
+    sp.omega_ratio = 1.f;
+    sp.eta_ratio = 0.25f;
+    sp.eps_feas = o.eps_feas;
+    sp.merit_mu = o.merit_mu;
+    sp.refine = o.precision_flags & 1;
+    return sp;
+}
+
+// Validate the instance descriptors; returns COMET_OK and N_max.
+comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out);
+
+}  // namespace comet
+
+namespace comet {
+// Options of a call: the defaults, overridden by every positive field of
+// `opts` (NULL = defaults); precision_flags is taken as given.
+void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out) {
+    comet_default_opts(out);
+    if (!opts) return;
+    const comet_solver_opts& o = *opts;
+    if (o.max_iters > 0) out->max_iters = o.max_iters;
+    if (o.ref_iters > 0) out->ref_iters = o.ref_iters;
+    if (o.eps_feas > 0) out->eps_feas = o.eps_feas;
+    if (o.eps_primal > 0) out->eps_primal = o.eps_primal;
+    if (o.eps_dual > 0) out->eps_dual = o.eps_dual;
+    if (o.eps_comp > 0) out->eps_comp = o.eps_comp;
+    if (o.merit_mu > 0) out->merit_mu = o.merit_mu;
+    if (o.beta0 > 0) out->beta0 = o.beta0;
+    if (o.beta_max > 0) out->beta_max = o.beta_max;
+    if (o.beta_ref > 0) out->beta_ref = o.beta_ref;
+    if (o.rho0 > 0) out->rho0 = o.rho0;
+    if (o.rho_min > 0) out->rho_min = o.rho_min;
+    out->precision_flags = o.precision_flags;
+}
+}  // namespace comet
+
 struct comet_problem {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -108,6 +210,26 @@ struct comet_problem {
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
 };
+
+namespace comet {
+comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out) {
+    int Nmax = 0;
+    for (int i = 0; i < n_instances; ++i) {
+        const comet_instance_desc& d = inst[i];
+        if (d.task != COMET_TASK_PUSHER_SLIDER)
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: task %d is not built", i, d.task);
+        if (d.n_modes != 12) return fail(COMET_ERR_INVALID_ARG, "instance %d: pushing needs n_modes = 12", i);
+        if (d.knots_per_segment < 1 || d.max_segments < 1 || d.max_segments > COMET_MAX_SEGMENTS ||
+            (int64_t)d.knots_per_segment * d.max_segments > comet::kMaxN)
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: bad knots_per_segment / max_segments", i);
+        if (!(d.side_x > 0 && d.side_y > 0 && d.c_ls > 0 && d.dt > 0 && d.mu >= 0 && d.kappa > 0))
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: non-positive geometry or dt", i);
+        Nmax = std::max(Nmax, d.knots_per_segment * d.max_segments);
+    }
+    *Nmax_out = Nmax;
+    return COMET_OK;
+}
+}  // namespace comet
 
 extern "C" {
 
@@ -153,38 +275,13 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
     *out = nullptr;
     if (!inst || n_instances < 1) return fail(COMET_ERR_INVALID_ARG, "need at least one instance");
     int Nmax = 0;
-    for (int i = 0; i < n_instances; ++i) {
-        const comet_instance_desc& d = inst[i];
-        if (d.task != COMET_TASK_PUSHER_SLIDER)
-            return fail(COMET_ERR_INVALID_ARG, "instance %d: task %d is not built", i, d.task);
-        if (d.n_modes != 12) return fail(COMET_ERR_INVALID_ARG, "instance %d: pushing needs n_modes = 12", i);
-        if (d.knots_per_segment < 1 || d.max_segments < 1 || d.max_segments > COMET_MAX_SEGMENTS ||
-            (int64_t)d.knots_per_segment * d.max_segments > comet::kMaxN)
-            return fail(COMET_ERR_INVALID_ARG, "instance %d: bad knots_per_segment / max_segments", i);
-        if (!(d.side_x > 0 && d.side_y > 0 && d.c_ls > 0 && d.dt > 0 && d.mu >= 0 && d.kappa > 0))
-            return fail(COMET_ERR_INVALID_ARG, "instance %d: non-positive geometry or dt", i);
-        Nmax = std::max(Nmax, d.knots_per_segment * d.max_segments);
+    {
+        const comet_status st = comet::check_instances(inst, n_instances, &Nmax);
+        if (st != COMET_OK) return st;
     }
     comet_problem* p = new (std::nothrow) comet_problem();
     if (!p) return fail(COMET_ERR_OOM, "host allocation failed");
-    comet_default_opts(&p->opts);
-    if (opts) {
-        // zero fields keep their defaults
-        const comet_solver_opts& o = *opts;
-        if (o.max_iters > 0) p->opts.max_iters = o.max_iters;
-        if (o.ref_iters > 0) p->opts.ref_iters = o.ref_iters;
-        if (o.eps_feas > 0) p->opts.eps_feas = o.eps_feas;
-        if (o.eps_primal > 0) p->opts.eps_primal = o.eps_primal;
-        if (o.eps_dual > 0) p->opts.eps_dual = o.eps_dual;
-        if (o.eps_comp > 0) p->opts.eps_comp = o.eps_comp;
-        if (o.merit_mu > 0) p->opts.merit_mu = o.merit_mu;
-        if (o.beta0 > 0) p->opts.beta0 = o.beta0;
-        if (o.beta_max > 0) p->opts.beta_max = o.beta_max;
-        if (o.beta_ref > 0) p->opts.beta_ref = o.beta_ref;
-        if (o.rho0 > 0) p->opts.rho0 = o.rho0;
-        if (o.rho_min > 0) p->opts.rho_min = o.rho_min;
-        p->opts.precision_flags = o.precision_flags;
-    }
+    comet::merge_opts(opts, &p->opts);
     p->inst.assign(inst, inst + n_instances);
     p->stream = (cudaStream_t)cuda_stream;
     p->Nmax = Nmax;
@@ -196,47 +293,7 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
         return cuda_fail(e, "device query");
     }
     std::vector<comet::DevInstance> h(n_instances);
-    for (int i = 0; i < n_instances; ++i) {
-        const comet_instance_desc& d = inst[i];
-        comet::DevInstance& q = h[i];
-        memset(&q, 0, sizeof(q));
-        double sigma[4];
-        dynamics_row_scales(d, sigma);
-        q.dt_d = d.dt;
-        q.kappa_d = d.kappa;
-        q.inv_c2_d = 1.0 / (d.c_ls * d.c_ls);
-        q.mu_d = d.mu;
-        q.sc_cone_d = 1.0 / sqrt(1.0 + d.mu * d.mu);
-        for (int f = 0; f < 4; ++f) {
-            q.a_d[f] = (f % 2 == 0) ? 0.5 * d.side_x : 0.5 * d.side_y;
-            q.ell_d[f] = (f % 2 == 0) ? 0.5 * d.side_y : 0.5 * d.side_x;
-            q.a[f] = (float)q.a_d[f];
-            q.ell[f] = (float)q.ell_d[f];
-        }
-        for (int r = 0; r < 4; ++r) {
-            q.sigma_d[r] = sigma[r];
-            q.inv_sigma[r] = (float)(1.0 / sigma[r]);
-        }
-        for (int j = 0; j < 3; ++j) {
-            q.start_d[j] = d.start[j];
-            q.goal_d[j] = d.goal[j];
-            q.start[j] = (float)d.start[j];
-            q.goal[j] = (float)d.goal[j];
-        }
-        q.w_terminal_d = d.w_terminal;
-        q.w_control_d = d.w_control;
-        q.w_terminal = (float)d.w_terminal;
-        q.w_control = (float)d.w_control;
-        q.dt = (float)d.dt;
-        q.kappa = (float)d.kappa;
-        q.inv_c2 = (float)q.inv_c2_d;
-        q.mu = (float)d.mu;
-        q.sc_cone = (float)q.sc_cone_d;
-        q.K = d.knots_per_segment;
-        q.Lmax = d.max_segments;
-        q.n_modes = d.n_modes;
-        q.task = d.task;
-    }
+    for (int i = 0; i < n_instances; ++i) comet::make_dev_instance(inst[i], &h[i]);
     e = cudaMalloc(&p->d_inst, sizeof(comet::DevInstance) * n_instances);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_inst, h.data(), sizeof(comet::DevInstance) * n_instances,
                                          cudaMemcpyHostToDevice);
@@ -401,30 +458,7 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* seq
     a.ws_per_warp = (int64_t)comet::kRec * p->Nmax;
     a.queue = p->d_queue;
     a.bad_input = p->d_bad;
-    const comet_solver_opts& o = p->opts;
-    comet::SolverParams& sp = a.sp;
-    sp.max_iters = max_iters > 0 ? max_iters : o.max_iters;
-    sp.max_retries = 8;
-    sp.n_alpha = 7;
-    sp.max_inner = 40;
-    sp.curv_skip = 3;
-    sp.beta0 = (float)o.beta0;
-    sp.beta_max = (float)o.beta_max;
-    sp.beta_growth = 10.f;
-    sp.beta_ref = (float)o.beta_ref;
-    sp.rho0 = (float)o.rho0;
-    sp.rho_min = (float)o.rho_min;
-    sp.rho_max = 1e6f;
-    sp.armijo_c1 = 1e-4f;
-    sp.ls_slack = 1e-6f;
-    sp.eps_primal = (float)o.eps_primal;
-    sp.eps_dual = (float)o.eps_dual;
-    sp.eps_comp = (float)o.eps_comp;
-    sp.omega_ratio = 1.f;
-    sp.eta_ratio = 0.25f;
-    sp.eps_feas = o.eps_feas;
-    sp.merit_mu = o.merit_mu;
-    sp.refine = o.precision_flags & 1;
+    a.sp = comet::make_params(p->opts, max_iters);
     CUDA_TRY(comet::launch_eval(a, (int)warps, p->warps_per_block, s), "evaluator launch");
 
     if (!dev_cost) CUDA_TRY(cudaMemcpyAsync(out_cost, d_cost, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy cost");

@@ -62,6 +62,12 @@ struct EvalArgs {
     SolverParams sp;
 };
 
+// Host-side conversions shared by the entry points (api.cu).
+void make_dev_instance(const comet_instance_desc& d, DevInstance* out);
+SolverParams make_params(const comet_solver_opts& o, int max_iters);
+comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out);
+void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out);
+
 // Shared memory (bytes) one warp needs for TOs of up to Nmax intervals.
 size_t smem_per_warp_bytes(int Nmax);
 // Launch the persistent evaluator: total_warps warps, warps_per_block per CTA.
