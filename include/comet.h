@@ -164,6 +164,40 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* mod
 comet_status comet_eval_stats(comet_problem* p, float* out_viol, float* out_merit,
                               int32_t* out_iters, float* out_stat);
 
+/* Solve one mode-conditioned TO per order without allocating any memory.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * For callers that cannot allocate device memory: code running inside a
+ * memory pool or arena that owns all device memory of the process, real-time
+ * loops where an allocation (and the synchronisation cudaMalloc / cudaFree
+ * can imply) is not allowed after start-up, or hosts that forbid the CUDA
+ * allocator.  No problem object is needed and nothing is allocated or freed:
+ * the evaluator's scratch lives in one fixed 32 MiB device array inside the
+ * library, which every device that loads the library holds until the
+ * process exits.
+ *   inst, n_instances  host descriptors, 1 <= n_instances <= 64 (more is
+ *                      rejected with COMET_ERR_INVALID_ARG)
+ *   opts               host options or NULL (defaults)
+ *   cuda_stream        cudaStream_t of the launch (NULL = legacy stream)
+ *   mode_seqs, warm_starts, out_cost, out_traj, out_status: as in
+ *                      comet_eval_modes, but every array must be DEVICE
+ *                      memory (nothing is staged; host pointers are rejected
+ *                      with COMET_ERR_INVALID_ARG); the trajectory stride is
+ *                      7 * N_max + 4 with N_max = max K * max_segments.
+ * Asynchronous on cuda_stream.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents (the work counter and error
+ * flag are cleared by each call); calls whose kernels overlap on the GPU --
+ * two streams or two host threads at once -- race on it and must be
+ * serialised by the caller.  Orders too long for the array (N_max such that
+ * four warps' stage records exceed it) are rejected with INVALID_ARG.
+ * Per-TO diagnostics (comet_eval_stats) are not produced. */
+comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst, int32_t n_instances,
+                                      const comet_solver_opts* opts, void* cuda_stream,
+                                      const comet_mode_seq* mode_seqs, int64_t n, const float* warm_starts,
+                                      float* out_cost, float* out_traj, int32_t* out_status);
+
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 

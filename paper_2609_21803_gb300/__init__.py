@@ -63,7 +63,7 @@ assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == 24
 EXPORTS = (
     "comet_default_opts", "comet_problem_create", "comet_problem_destroy", "comet_traj_stride",
     "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_mode_code",
-    "comet_last_error",
+    "comet_last_error", "comet_eval_modes_noalloc",
 )
 
 
@@ -92,6 +92,8 @@ def lib(build_if_missing: bool = False):
             L.comet_eval_modes.argtypes = [vp, vp, i64, vp, vp, vp, vp]
             L.comet_eval_modes_budget.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp]
             L.comet_eval_stats.argtypes = [vp, vp, vp, vp, vp]
+            L.comet_eval_modes_noalloc.argtypes = [ctypes.POINTER(InstanceDesc), i32, ctypes.POINTER(SolverOpts), vp,
+                                                   vp, i64, vp, vp, vp, vp]
             L.comet_mode_code.argtypes = [ctypes.POINTER(ModeSeq), i32]
             L.comet_mode_code.restype = ctypes.c_uint64
             L.comet_last_error.restype = ctypes.c_char_p
@@ -187,6 +189,24 @@ def comet_eval_modes_budget(problem, mode_seqs, n, warm_starts, max_iters, out_c
 
 def comet_eval_stats(problem, out_viol, out_merit, out_iters, out_stat):
     _check(lib().comet_eval_stats(problem, _ptr(out_viol), _ptr(out_merit), _ptr(out_iters), _ptr(out_stat)))
+
+
+def comet_eval_modes_noalloc(instances, opts, cuda_stream, mode_seqs, n, warm_starts, out_cost, out_traj,
+                             out_status):
+    """The allocation-free entry point: descriptors from the host, every
+    array in device memory (see include/comet.h)."""
+    descs = [x if isinstance(x, InstanceDesc) else make_instance_desc(x) for x in instances]
+    arr = (InstanceDesc * len(descs))(*descs)
+    o = None
+    if opts is not None:
+        if isinstance(opts, dict):
+            oo = comet_default_opts()
+            for k, v in opts.items():
+                setattr(oo, k, v)
+            opts = oo
+        o = ctypes.byref(opts)
+    _check(lib().comet_eval_modes_noalloc(arr, len(descs), o, cuda_stream, _ptr(mode_seqs), int(n),
+                                          _ptr(warm_starts), _ptr(out_cost), _ptr(out_traj), _ptr(out_status)))
 
 
 def comet_mode_code(seq, n_modes: int = 12) -> int:

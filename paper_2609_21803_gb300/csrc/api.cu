@@ -162,6 +162,11 @@ comet_status check_instances(const comet_instance_desc* inst, int32_t n_instance
 }  // namespace comet
 
 namespace comet {
+// Record a call-level error message for comet_last_error().
+void set_error(const char* msg) { g_err = msg; }
+}  // namespace comet
+
+namespace comet {
 // Options of a call: the defaults, overridden by every positive field of
 // `opts` (NULL = defaults); precision_flags is taken as given.
 void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out) {

@@ -67,6 +67,7 @@ void make_dev_instance(const comet_instance_desc& d, DevInstance* out);
 SolverParams make_params(const comet_solver_opts& o, int max_iters);
 comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out);
 void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out);
+void set_error(const char* msg);
 
 // Shared memory (bytes) one warp needs for TOs of up to Nmax intervals.
 size_t smem_per_warp_bytes(int Nmax);
