@@ -198,6 +198,50 @@ comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst, int32_t n
                                       const comet_mode_seq* mode_seqs, int64_t n, const float* warm_starts,
                                       float* out_cost, float* out_traj, int32_t* out_status);
 
+/* ---- greedy local mode expansion (Sec. III-B, Algorithm 1) ----------- */
+
+/* Create a frontier for one instance: the evaluated set V (up to capacity
+ * orders, with their merits M_hat of Eq. search_merit) and the next batch
+ * F_{s+1} (up to `batch` orders).  k_max bounds the beam k of comet_expand
+ * (1 <= k_max <= 4096).  Owns device memory; errors INVALID_ARG, OOM. */
+comet_status comet_frontier_create(comet_problem* p, int32_t instance, int64_t capacity, int32_t batch,
+                                   int32_t k_max, comet_frontier** out);
+
+comet_status comet_frontier_destroy(comet_frontier* f);
+
+/* Add n evaluated orders to V with their J_hat (cost) and v_hat (viol); the
+ * merit M_hat = J_hat + mu max(v_hat - eps_feas, 0) uses the problem's
+ * options.  An order already in V is not added twice.  Host or device
+ * arrays.  Errors: INVALID_ARG (an order of another instance, from host
+ * memory), BUDGET (more than the capacity); device-side overflow or
+ * malformed orders set the flags read by comet_frontier_size. */
+comet_status comet_frontier_add(comet_frontier* f, const comet_mode_seq* seqs, int64_t n, const float* cost,
+                                const float* viol);
+
+/* One expansion round (Algorithm 1, lines 5-10): rank V by (M_hat, mode
+ * code), walk the k best orders in that order and admit their unseen one-edit
+ * neighbours (substitutions, then insertions, then deletions; positions and
+ * modes ascending; orders in V or already admitted are skipped) until the
+ * batch holds `batch` orders.  Asynchronous on the problem's stream; the
+ * batch stays on the device (comet_frontier_next). */
+comet_status comet_expand(comet_problem* p, comet_frontier* frontier, int32_t k);
+
+/* Device pointer to the next batch F_{s+1} (valid until the next
+ * comet_expand) and its size; synchronises the problem's stream. */
+comet_status comet_frontier_next(comet_frontier* f, const comet_mode_seq** seqs, int64_t* n);
+
+/* Copy the next batch into out (host or device, room for cap orders) and
+ * return its size in *n; BUDGET if cap is too small; synchronises. */
+comet_status comet_frontier_copy_next(comet_frontier* f, comet_mode_seq* out, int64_t cap, int64_t* n);
+
+/* |V| and the device-side error flags (bit 0 malformed order, bit 1 value 2
+ * capacity exceeded); synchronises. */
+comet_status comet_frontier_size(comet_frontier* f, int64_t* n_evaluated, int32_t* error_flags);
+
+/* The k best orders of V by (M_hat, code): host arrays of mode codes (0 past
+ * |V|) and merits; synchronises. */
+comet_status comet_frontier_best(comet_frontier* f, int32_t k, uint64_t* out_codes, float* out_merit);
+
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 

@@ -64,6 +64,8 @@ EXPORTS = (
     "comet_default_opts", "comet_problem_create", "comet_problem_destroy", "comet_traj_stride",
     "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_mode_code",
     "comet_last_error", "comet_eval_modes_noalloc",
+    "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
+    "comet_frontier_next", "comet_frontier_size", "comet_frontier_best", "comet_frontier_copy_next",
 )
 
 
@@ -94,6 +96,14 @@ def lib(build_if_missing: bool = False):
             L.comet_eval_stats.argtypes = [vp, vp, vp, vp, vp]
             L.comet_eval_modes_noalloc.argtypes = [ctypes.POINTER(InstanceDesc), i32, ctypes.POINTER(SolverOpts), vp,
                                                    vp, i64, vp, vp, vp, vp]
+            L.comet_frontier_create.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(vp)]
+            L.comet_frontier_destroy.argtypes = [vp]
+            L.comet_frontier_add.argtypes = [vp, vp, i64, vp, vp]
+            L.comet_expand.argtypes = [vp, vp, i32]
+            L.comet_frontier_next.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i64)]
+            L.comet_frontier_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+            L.comet_frontier_copy_next.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+            L.comet_frontier_best.argtypes = [vp, i32, vp, vp]
             L.comet_mode_code.argtypes = [ctypes.POINTER(ModeSeq), i32]
             L.comet_mode_code.restype = ctypes.c_uint64
             L.comet_last_error.restype = ctypes.c_char_p
@@ -207,6 +217,70 @@ def comet_eval_modes_noalloc(instances, opts, cuda_stream, mode_seqs, n, warm_st
         o = ctypes.byref(opts)
     _check(lib().comet_eval_modes_noalloc(arr, len(descs), o, cuda_stream, _ptr(mode_seqs), int(n),
                                           _ptr(warm_starts), _ptr(out_cost), _ptr(out_traj), _ptr(out_status)))
+
+
+def comet_frontier_create(problem, instance: int, capacity: int, batch: int, k_max: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().comet_frontier_create(problem, instance, capacity, batch, k_max, ctypes.byref(h)))
+    return h.value
+
+
+def comet_frontier_destroy(frontier):
+    _check(lib().comet_frontier_destroy(frontier))
+
+
+def comet_frontier_add(frontier, seqs, n, cost, viol):
+    _check(lib().comet_frontier_add(frontier, _ptr(seqs), int(n), _ptr(cost), _ptr(viol)))
+
+
+def comet_expand(problem, frontier, k: int):
+    _check(lib().comet_expand(problem, frontier, int(k)))
+
+
+def comet_frontier_next(frontier):
+    """(device address of the next batch, its size)."""
+    p = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    _check(lib().comet_frontier_next(frontier, ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
+
+
+def comet_frontier_copy_next(frontier, out, cap: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().comet_frontier_copy_next(frontier, _ptr(out), int(cap), ctypes.byref(n)))
+    return n.value
+
+
+def frontier_next_orders(frontier, cap: int):
+    """The next batch as a list of mode tuples (host copy)."""
+    buf = np.zeros(cap, dtype=MODE_SEQ_DTYPE)
+    n = comet_frontier_copy_next(frontier, buf, cap)
+    return [tuple(int(m) for m in r["modes"][: r["len"]]) for r in buf[:n]]
+
+
+def comet_frontier_size(frontier):
+    n = ctypes.c_int64()
+    e = ctypes.c_int32()
+    _check(lib().comet_frontier_size(frontier, ctypes.byref(n), ctypes.byref(e)))
+    return n.value, e.value
+
+
+def comet_frontier_best(frontier, k: int):
+    codes = np.zeros(k, dtype=np.uint64)
+    merit = np.zeros(k, dtype=np.float32)
+    _check(lib().comet_frontier_best(frontier, int(k), codes.ctypes.data, merit.ctypes.data))
+    return codes, merit
+
+
+def decode_code(code: int, n_modes: int = 12):
+    base = n_modes + 1
+    L = code % base
+    code //= base
+    out = []
+    for _ in range(L):
+        out.append(code % base - 1)
+        code //= base
+    return tuple(out)
 
 
 def comet_mode_code(seq, n_modes: int = 12) -> int:

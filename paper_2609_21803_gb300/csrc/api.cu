@@ -14,6 +14,7 @@
 
 #include "comet.h"
 #include "comet_internal.h"
+#include "problem_internal.h"
 
 namespace {
 
@@ -189,32 +190,7 @@ void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out) {
 }
 }  // namespace comet
 
-struct comet_problem {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::vector<comet_instance_desc> inst;
-    comet::DevInstance* d_inst = nullptr;
-    comet_solver_opts opts;
-    int Nmax = 0;
-    int64_t stride = 0;
-    int num_sms = 0;
-    int warps_per_block = 4;
-    int blocks_per_sm = 0;
-    float* d_ws = nullptr;
-    int64_t ws_warps = 0;
-    unsigned int* d_queue = nullptr;
-    int* d_bad = nullptr;
-    // per-TO diagnostics of the last call
-    float* d_viol = nullptr;
-    float* d_merit = nullptr;
-    int32_t* d_iters = nullptr;
-    float* d_stat = nullptr;
-    int64_t stats_cap = 0;
-    int64_t last_n = 0;
-    // staging for host buffers
-    void* d_stage = nullptr;
-    size_t stage_bytes = 0;
-};
+
 
 namespace comet {
 comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out) {
@@ -234,6 +210,76 @@ comet_status check_instances(const comet_instance_desc* inst, int32_t n_instance
     *Nmax_out = Nmax;
     return COMET_OK;
 }
+}  // namespace comet
+
+namespace comet {
+
+static int64_t resident_warps(const comet_problem* p, int64_t n) {
+    // resident warps: every SM filled, never more warps than TOs; the grid is
+    // whole CTAs and any warp may pick any TO, so the workspace covers them all
+    const int64_t resident = (int64_t)p->num_sms * p->blocks_per_sm * p->warps_per_block;
+    return ((std::min<int64_t>(resident, std::max<int64_t>(n, 1)) + p->warps_per_block - 1) / p->warps_per_block) *
+           p->warps_per_block;
+}
+
+comet_status reserve_eval(comet_problem* p, int64_t n) {
+    if (p->stats_cap < n) {
+        cudaFree(p->d_viol); cudaFree(p->d_merit); cudaFree(p->d_iters); cudaFree(p->d_stat);
+        p->d_viol = p->d_merit = p->d_stat = nullptr;
+        p->d_iters = nullptr;
+        p->stats_cap = 0;
+        const int64_t cap = std::max<int64_t>(n, 1024);
+        CUDA_TRY(cudaMalloc(&p->d_viol, sizeof(float) * cap), "stats");
+        CUDA_TRY(cudaMalloc(&p->d_merit, sizeof(float) * cap), "stats");
+        CUDA_TRY(cudaMalloc(&p->d_iters, sizeof(int32_t) * cap), "stats");
+        CUDA_TRY(cudaMalloc(&p->d_stat, sizeof(float) * cap), "stats");
+        p->stats_cap = cap;
+    }
+    const int64_t warps = resident_warps(p, n);
+    if (p->ws_warps < warps) {
+        cudaFree(p->d_ws);
+        p->d_ws = nullptr;
+        p->ws_warps = 0;
+        CUDA_TRY(cudaMalloc(&p->d_ws, sizeof(float) * (size_t)kRec * p->Nmax * warps), "workspace");
+        p->ws_warps = warps;
+    }
+    return COMET_OK;
+}
+
+comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, int64_t n_max, const int64_t* d_n,
+                                const float* d_warm, int32_t max_iters, float* d_cost, float* d_traj,
+                                int32_t* d_status) {
+    cudaStream_t s = p->stream;
+    const int64_t warps = resident_warps(p, n_max);
+    if (p->ws_warps < warps || p->stats_cap < n_max) return fail(COMET_ERR_INTERNAL, "evaluator not reserved");
+    CUDA_TRY(cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned int), s), "queue reset");
+    CUDA_TRY(cudaMemsetAsync(p->d_bad, 0, sizeof(int), s), "flag reset");
+    EvalArgs a;
+    memset(&a, 0, sizeof(a));
+    a.inst = p->d_inst;
+    a.n_inst = (int)p->inst.size();
+    a.seqs = d_seqs;
+    a.n = n_max;
+    a.d_n = d_n;
+    a.warm = d_warm;
+    a.stride = p->stride;
+    a.Nmax = p->Nmax;
+    a.out_cost = d_cost;
+    a.out_traj = d_traj;
+    a.out_status = d_status;
+    a.out_viol = p->d_viol;
+    a.out_merit = p->d_merit;
+    a.out_iters = p->d_iters;
+    a.out_stat = p->d_stat;
+    a.ws = p->d_ws;
+    a.ws_per_warp = (int64_t)kRec * p->Nmax;
+    a.queue = p->d_queue;
+    a.bad_input = p->d_bad;
+    a.sp = make_params(p->opts, max_iters);
+    CUDA_TRY(launch_eval(a, (int)warps, p->warps_per_block, s), "evaluator launch");
+    return COMET_OK;
+}
+
 }  // namespace comet
 
 extern "C" {
@@ -356,18 +402,9 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* seq
     if (n > 0xffffffffLL) return fail(COMET_ERR_INVALID_ARG, "n too large");
     CUDA_TRY(cudaSetDevice(p->device), "cudaSetDevice");
     cudaStream_t s = p->stream;
-    // per-TO diagnostics buffers
-    if (p->stats_cap < n) {
-        cudaFree(p->d_viol); cudaFree(p->d_merit); cudaFree(p->d_iters); cudaFree(p->d_stat);
-        p->d_viol = p->d_merit = p->d_stat = nullptr;
-        p->d_iters = nullptr;
-        p->stats_cap = 0;
-        const int64_t cap = std::max<int64_t>(n, 1024);
-        CUDA_TRY(cudaMalloc(&p->d_viol, sizeof(float) * cap), "stats");
-        CUDA_TRY(cudaMalloc(&p->d_merit, sizeof(float) * cap), "stats");
-        CUDA_TRY(cudaMalloc(&p->d_iters, sizeof(int32_t) * cap), "stats");
-        CUDA_TRY(cudaMalloc(&p->d_stat, sizeof(float) * cap), "stats");
-        p->stats_cap = cap;
+    {
+        const comet_status st = comet::reserve_eval(p, n);
+        if (st != COMET_OK) return st;
     }
     p->last_n = n;
     if (n == 0) return COMET_OK;
@@ -427,44 +464,11 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* seq
     if (!dev_status) d_status = (int32_t*)(stage + o_status);
     if (!dev_traj) d_traj = (float*)(stage + o_traj);
 
-    // resident warps: every SM filled, never more warps than TOs
-    const int64_t resident = (int64_t)p->num_sms * p->blocks_per_sm * p->warps_per_block;
-    // the grid is whole CTAs, and any warp may pick any TO: the workspace
-    // covers every warp of the grid
-    const int64_t warps = ((std::min<int64_t>(resident, n) + p->warps_per_block - 1) / p->warps_per_block) *
-                          p->warps_per_block;
-    if (p->ws_warps < warps) {
-        cudaFree(p->d_ws);
-        p->d_ws = nullptr;
-        p->ws_warps = 0;
-        CUDA_TRY(cudaMalloc(&p->d_ws, sizeof(float) * (size_t)comet::kRec * p->Nmax * warps), "workspace");
-        p->ws_warps = warps;
+    {
+        const comet_status st =
+            comet::launch_eval_device(p, d_seqs, n, nullptr, d_warm, max_iters, d_cost, d_traj, d_status);
+        if (st != COMET_OK) return st;
     }
-    CUDA_TRY(cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned int), s), "queue reset");
-    CUDA_TRY(cudaMemsetAsync(p->d_bad, 0, sizeof(int), s), "flag reset");
-
-    comet::EvalArgs a;
-    memset(&a, 0, sizeof(a));
-    a.inst = p->d_inst;
-    a.n_inst = (int)p->inst.size();
-    a.seqs = d_seqs;
-    a.n = n;
-    a.warm = d_warm;
-    a.stride = p->stride;
-    a.Nmax = p->Nmax;
-    a.out_cost = d_cost;
-    a.out_traj = d_traj;
-    a.out_status = d_status;
-    a.out_viol = p->d_viol;
-    a.out_merit = p->d_merit;
-    a.out_iters = p->d_iters;
-    a.out_stat = p->d_stat;
-    a.ws = p->d_ws;
-    a.ws_per_warp = (int64_t)comet::kRec * p->Nmax;
-    a.queue = p->d_queue;
-    a.bad_input = p->d_bad;
-    a.sp = comet::make_params(p->opts, max_iters);
-    CUDA_TRY(comet::launch_eval(a, (int)warps, p->warps_per_block, s), "evaluator launch");
 
     if (!dev_cost) CUDA_TRY(cudaMemcpyAsync(out_cost, d_cost, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy cost");
     if (!dev_status)

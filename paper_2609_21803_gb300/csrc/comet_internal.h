@@ -44,7 +44,8 @@ struct EvalArgs {
     const DevInstance* inst;
     int n_inst;
     const comet_mode_seq* seqs;
-    int64_t n;
+    int64_t n;               // number of TOs (upper bound when d_n is set)
+    const int64_t* d_n;      // optional device-resident TO count
     const float* warm;
     int64_t stride;  // floats per trajectory record (7*Nmax+4)
     int Nmax;

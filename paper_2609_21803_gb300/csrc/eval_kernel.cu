@@ -978,12 +978,13 @@ __global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
     C.sm = carve(smem_raw + per_warp * wib, A.Nmax);
     C.rec = A.ws + (size_t)warp_global * A.ws_per_warp;
     const SolverParams& sp = A.sp;
+    const int64_t n_tos = A.d_n ? min(*A.d_n, A.n) : A.n;
 
     for (;;) {
         unsigned int t = 0;
         if (lane == 0) t = atomicAdd(A.queue, 1u);
         t = __shfl_sync(kFull, t, 0);
-        if ((int64_t)t >= A.n) break;
+        if ((int64_t)t >= n_tos) break;
         const int64_t ti = (int64_t)t;
         // ---- load the order and validate it
         const comet_mode_seq sq = A.seqs[ti];

@@ -1,0 +1,272 @@
+// frontier.cu -- host side of the greedy local mode expansion (Sec. III-B,
+// Algorithm 1): frontier lifetime, adding evaluated orders to V, one
+// expansion round, and the planner that runs Algorithm 1 on the device with
+// each round captured once as a CUDA graph and replayed.
+
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "comet.h"
+#include "comet_internal.h"
+#include "expand_internal.h"
+#include "problem_internal.h"
+
+struct comet_frontier {
+    comet_problem* p = nullptr;
+    comet::FrontierDev d;
+    int32_t batch = 0;
+    int32_t k_max = 0;
+    void* blob = nullptr;  // one allocation for all device arrays
+};
+
+namespace {
+
+comet_status ffail(comet_status st, const char* msg) {
+    comet::set_error(msg);
+    return st;
+}
+
+comet_status fcuda(cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return ffail(e == cudaErrorMemoryAllocation ? COMET_ERR_OOM : COMET_ERR_CUDA, buf);
+}
+
+#define FTRY(call, what)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return fcuda(e_, what);    \
+    } while (0)
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+bool dev_ptr(const void* ptr) {
+    cudaPointerAttributes at;
+    if (!ptr || cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+comet_status comet_frontier_create(comet_problem* p, int32_t instance, int64_t capacity, int32_t batch,
+                                   int32_t k_max, comet_frontier** out) {
+    if (!p || !out) return ffail(COMET_ERR_INVALID_ARG, "problem and out are required");
+    *out = nullptr;
+    if (instance < 0 || instance >= (int)p->inst.size()) return ffail(COMET_ERR_INVALID_ARG, "instance out of range");
+    if (capacity < 1 || batch < 1 || k_max < 1 || k_max > comet::kChunk || batch > capacity)
+        return ffail(COMET_ERR_INVALID_ARG, "need 1 <= batch <= capacity and 1 <= k_max <= 4096");
+    const comet_instance_desc& d = p->inst[instance];
+    comet_frontier* f = new comet_frontier();
+    f->p = p;
+    f->batch = batch;
+    f->k_max = k_max;
+    comet::FrontierDev& F = f->d;
+    memset(&F, 0, sizeof(F));
+    F.instance = instance;
+    F.n_modes = d.n_modes;
+    F.lmax = d.max_segments;
+    F.slots = F.lmax * (F.n_modes - 1) + (F.lmax + 1) * F.n_modes + F.lmax;
+    F.capacity = capacity;
+    F.batch_cap = std::max<int64_t>(batch, 1);
+    const uint64_t set_cap = pow2_at_least((uint64_t)capacity * 2);
+    const int64_t total = (int64_t)k_max * F.slots;
+    const uint64_t cand_cap = pow2_at_least((uint64_t)total * 2);
+    const int64_t chunks = (capacity + comet::kChunk - 1) / comet::kChunk;
+    const int64_t top_n = std::max<int64_t>(chunks * k_max, comet::kChunk);
+    // carve one allocation
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_codes = take(sizeof(unsigned long long) * capacity);
+    const size_t o_merit = take(sizeof(float) * capacity);
+    const size_t o_nV = take(sizeof(unsigned long long));
+    const size_t o_set = take(sizeof(unsigned long long) * set_cap);
+    const size_t o_ta = take(sizeof(comet::TopKey) * top_n);
+    const size_t o_tb = take(sizeof(comet::TopKey) * top_n);
+    const size_t o_cc = take(sizeof(unsigned long long) * total);
+    const size_t o_fl = take(sizeof(int) * total);
+    const size_t o_ck = take(sizeof(unsigned long long) * cand_cap);
+    const size_t o_co = take(sizeof(unsigned int) * cand_cap);
+    const size_t o_nx = take(sizeof(comet_mode_seq) * batch);
+    const size_t o_nn = take(sizeof(int64_t));
+    const size_t o_er = take(sizeof(int));
+    cudaError_t e = cudaMalloc(&f->blob, off);
+    if (e != cudaSuccess) {
+        delete f;
+        return fcuda(e, "frontier allocation");
+    }
+    char* b = (char*)f->blob;
+    F.codes = (unsigned long long*)(b + o_codes);
+    F.merit = (float*)(b + o_merit);
+    F.nV = (unsigned long long*)(b + o_nV);
+    F.set = (unsigned long long*)(b + o_set);
+    F.set_mask = set_cap - 1;
+    F.top_a = (comet::TopKey*)(b + o_ta);
+    F.top_b = (comet::TopKey*)(b + o_tb);
+    F.cand_code = (unsigned long long*)(b + o_cc);
+    F.flag = (int*)(b + o_fl);
+    F.cand_keys = (unsigned long long*)(b + o_ck);
+    F.cand_ord = (unsigned int*)(b + o_co);
+    F.cand_mask = cand_cap - 1;
+    F.next = (comet_mode_seq*)(b + o_nx);
+    F.n_next = (int64_t*)(b + o_nn);
+    F.error = (int*)(b + o_er);
+    e = cudaMemsetAsync(f->blob, 0, off, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        cudaFree(f->blob);
+        delete f;
+        return fcuda(e, "frontier init");
+    }
+    *out = f;
+    return COMET_OK;
+}
+
+comet_status comet_frontier_destroy(comet_frontier* f) {
+    if (!f) return COMET_OK;
+    if (f->p && f->p->stream) cudaStreamSynchronize(f->p->stream); else cudaDeviceSynchronize();
+    cudaFree(f->blob);
+    delete f;
+    return COMET_OK;
+}
+
+comet_status comet_frontier_add(comet_frontier* f, const comet_mode_seq* seqs, int64_t n, const float* cost,
+                                const float* viol) {
+    if (!f) return ffail(COMET_ERR_INVALID_ARG, "frontier is NULL");
+    if (n < 0) return ffail(COMET_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return COMET_OK;
+    if (!seqs || !cost || !viol) return ffail(COMET_ERR_INVALID_ARG, "seqs, cost and viol are required");
+    if (n > f->d.capacity) return ffail(COMET_ERR_BUDGET, "more orders than the frontier capacity");
+    comet_problem* p = f->p;
+    cudaStream_t s = p->stream;
+    // stage host arrays (validated first) through one temporary device block
+    const bool ds = dev_ptr(seqs), dc = dev_ptr(cost), dv = dev_ptr(viol);
+    void* tmp = nullptr;
+    const comet_mode_seq* d_seqs = seqs;
+    const float* d_cost = cost;
+    const float* d_viol = viol;
+    if (!(ds && dc && dv)) {
+        if (!ds)
+            for (int64_t i = 0; i < n; ++i)
+                if (seqs[i].instance != f->d.instance || seqs[i].len < 1 || seqs[i].len > f->d.lmax)
+                    return ffail(COMET_ERR_INVALID_ARG, "an order does not belong to this frontier's instance");
+        const size_t bs = sizeof(comet_mode_seq) * n, bf = sizeof(float) * n;
+        FTRY(cudaMalloc(&tmp, bs + 2 * bf + 512), "staging");
+        char* t = (char*)tmp;
+        if (!ds) {
+            FTRY(cudaMemcpyAsync(t, seqs, bs, cudaMemcpyHostToDevice, s), "copy orders");
+            d_seqs = (const comet_mode_seq*)t;
+        }
+        if (!dc) {
+            FTRY(cudaMemcpyAsync(t + bs + 256, cost, bf, cudaMemcpyHostToDevice, s), "copy cost");
+            d_cost = (const float*)(t + bs + 256);
+        }
+        if (!dv) {
+            FTRY(cudaMemcpyAsync(t + bs + bf + 512 - 256, viol, bf, cudaMemcpyHostToDevice, s), "copy viol");
+            d_viol = (const float*)(t + bs + bf + 512 - 256);
+        }
+    }
+    comet::FrontierDev F = f->d;
+    F.batch_cap = n;
+    const cudaError_t e = comet::launch_frontier_add(F, d_seqs, n, nullptr, d_cost, d_viol, (float)p->opts.eps_feas,
+                                                     (float)p->opts.merit_mu, s);
+    if (tmp) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return fcuda(e, "frontier add");
+    return COMET_OK;
+}
+
+comet_status comet_expand(comet_problem* p, comet_frontier* f, int32_t k) {
+    if (!p || !f || f->p != p) return ffail(COMET_ERR_INVALID_ARG, "problem / frontier mismatch");
+    if (k < 1 || k > f->k_max) return ffail(COMET_ERR_INVALID_ARG, "k out of [1, k_max]");
+    const cudaError_t e = comet::launch_expand(f->d, k, f->batch, 0, p->stream);
+    if (e != cudaSuccess) return fcuda(e, "expand");
+    return COMET_OK;
+}
+
+comet_status comet_frontier_next(comet_frontier* f, const comet_mode_seq** seqs, int64_t* n) {
+    if (!f || !seqs || !n) return ffail(COMET_ERR_INVALID_ARG, "arguments are required");
+    cudaStream_t s = f->p->stream;
+    int64_t nn = 0;
+    FTRY(cudaMemcpyAsync(&nn, f->d.n_next, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read count");
+    FTRY(cudaStreamSynchronize(s), "synchronise");
+    *seqs = f->d.next;
+    *n = nn;
+    return COMET_OK;
+}
+
+comet_status comet_frontier_copy_next(comet_frontier* f, comet_mode_seq* out, int64_t cap, int64_t* n) {
+    if (!f || !n || (cap > 0 && !out)) return ffail(COMET_ERR_INVALID_ARG, "arguments are required");
+    const comet_mode_seq* d = nullptr;
+    int64_t nn = 0;
+    const comet_status st = comet_frontier_next(f, &d, &nn);
+    if (st != COMET_OK) return st;
+    if (nn > cap) return ffail(COMET_ERR_BUDGET, "output buffer smaller than the next batch");
+    if (nn > 0) {
+        FTRY(cudaMemcpyAsync(out, d, sizeof(comet_mode_seq) * nn, cudaMemcpyDefault, f->p->stream), "copy batch");
+        FTRY(cudaStreamSynchronize(f->p->stream), "synchronise");
+    }
+    *n = nn;
+    return COMET_OK;
+}
+
+comet_status comet_frontier_size(comet_frontier* f, int64_t* n_evaluated, int32_t* error_flags) {
+    if (!f || !n_evaluated) return ffail(COMET_ERR_INVALID_ARG, "arguments are required");
+    cudaStream_t s = f->p->stream;
+    unsigned long long nv = 0;
+    int err = 0;
+    FTRY(cudaMemcpyAsync(&nv, f->d.nV, sizeof(nv), cudaMemcpyDeviceToHost, s), "read size");
+    FTRY(cudaMemcpyAsync(&err, f->d.error, sizeof(err), cudaMemcpyDeviceToHost, s), "read flags");
+    FTRY(cudaStreamSynchronize(s), "synchronise");
+    *n_evaluated = (int64_t)std::min<unsigned long long>(nv, (unsigned long long)f->d.capacity);
+    if (error_flags) *error_flags = err;
+    return COMET_OK;
+}
+
+comet_status comet_frontier_best(comet_frontier* f, int32_t k, uint64_t* out_codes, float* out_merit) {
+    if (!f || !out_codes || k < 1 || k > f->k_max) return ffail(COMET_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = f->p->stream;
+    // the top-k passes of an expansion round, without generating neighbours
+    comet::FrontierDev F = f->d;
+    cudaError_t e = cudaSuccess;
+    const comet::TopKey* top = comet::launch_topk(F, k, s, &e);
+    if (!top) return fcuda(e, "top-k");
+    std::vector<comet::TopKey> h(k);
+    FTRY(cudaMemcpyAsync(h.data(), top, sizeof(comet::TopKey) * k, cudaMemcpyDeviceToHost, s), "read top-k");
+    FTRY(cudaStreamSynchronize(s), "synchronise");
+    unsigned long long nv = 0;
+    FTRY(cudaMemcpy(&nv, F.nV, sizeof(nv), cudaMemcpyDeviceToHost), "read size");
+    for (int i = 0; i < k; ++i) {
+        const bool valid = (unsigned long long)i < nv;
+        out_codes[i] = valid ? h[i].code : 0;
+        if (out_merit) {
+            // invert the order-preserving key
+            const uint32_t mk = h[i].mk;
+            const uint32_t bits = (mk & 0x80000000u) ? (mk & 0x7fffffffu) : ~mk;
+            float m;
+            memcpy(&m, &bits, 4);
+            out_merit[i] = valid ? m : __builtin_inff();
+        }
+    }
+    return COMET_OK;
+}
+
+}  // extern "C"
