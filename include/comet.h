@@ -242,6 +242,44 @@ comet_status comet_frontier_size(comet_frontier* f, int64_t* n_evaluated, int32_
  * |V|) and merits; synchronises. */
 comet_status comet_frontier_best(comet_frontier* f, int32_t k, uint64_t* out_codes, float* out_merit);
 
+/* ---- the planner: Algorithm 1 on the device ---------------------------- */
+
+typedef struct {
+    int32_t k;          /* beam: expand the k best orders of V each round (64) */
+    int32_t batch;      /* batch width B (4096) */
+    int32_t rounds;     /* expansion rounds s_max (3) */
+    int32_t k_ref;      /* refinement count K_ref (256) */
+    int64_t budget;     /* evaluation budget, 0 = none; the last batch is truncated to fit */
+    int32_t ref_iters;  /* refinement budget t_ref, 0 = the problem's ref_iters */
+    int32_t use_graph;  /* capture one round (expand, evaluate, add) as a CUDA graph and replay it (1) */
+} comet_plan_opts;
+
+typedef struct {
+    comet_mode_seq best;  /* best refined feasible order (len 0 if none) */
+    float best_cost;      /* its J_hat after refinement */
+    float best_viol;      /* its v_hat */
+    int32_t best_status;
+    int32_t rounds_run;
+    int64_t evaluations;  /* |V| after exploration */
+    float explore_ms;     /* seed batch + rounds, device time */
+    float refine_ms;      /* top-K_ref re-solve, device time */
+} comet_plan_result;
+
+comet_status comet_default_plan_opts(comet_plan_opts* po);
+
+/* CoMET (Algorithm 1) for one instance: evaluate the seed batch F_0 with
+ * budget t_exp, add it to V, then run `rounds` rounds of {expand the k best
+ * orders of V into F_{s+1} (<= batch orders, <= budget evaluations in total),
+ * evaluate F_{s+1}, add it to V} entirely on the device -- batch sizes never
+ * return to the host, and with use_graph the round is one CUDA graph replayed
+ * `rounds` times (an empty round is a no-op).  Then re-solve the K_ref best
+ * orders of V with budget t_ref and return the best refined feasible order
+ * (status CONVERGED, v_hat <= eps_feas).  seeds: host or device orders of
+ * this instance; out_traj (nullable, host or device, comet_traj_stride
+ * floats) receives the winner's trajectory.  Synchronises the stream. */
+comet_status comet_plan(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
+                        const comet_plan_opts* opts, comet_plan_result* out, float* out_traj);
+
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 

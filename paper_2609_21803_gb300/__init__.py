@@ -50,9 +50,21 @@ class SolverOpts(ctypes.Structure):
     ]
 
 
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("batch", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("k_ref", ctypes.c_int32), ("budget", ctypes.c_int64), ("ref_iters", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
 class ModeSeq(ctypes.Structure):
     _fields_ = [("instance", ctypes.c_int32), ("len", ctypes.c_uint8),
                 ("modes", ctypes.c_uint8 * MAX_SEGMENTS), ("pad", ctypes.c_uint8 * 3)]
+
+
+class PlanResult(ctypes.Structure):
+    _fields_ = [("best", ModeSeq), ("best_cost", ctypes.c_float), ("best_viol", ctypes.c_float),
+                ("best_status", ctypes.c_int32), ("rounds_run", ctypes.c_int32), ("evaluations", ctypes.c_int64),
+                ("explore_ms", ctypes.c_float), ("refine_ms", ctypes.c_float)]
 
 
 MODE_SEQ_DTYPE = np.dtype([("instance", "<i4"), ("len", "u1"), ("modes", "u1", (MAX_SEGMENTS,)),
@@ -66,6 +78,7 @@ EXPORTS = (
     "comet_last_error", "comet_eval_modes_noalloc",
     "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
     "comet_frontier_next", "comet_frontier_size", "comet_frontier_best", "comet_frontier_copy_next",
+    "comet_default_plan_opts", "comet_plan",
 )
 
 
@@ -104,6 +117,8 @@ def lib(build_if_missing: bool = False):
             L.comet_frontier_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
             L.comet_frontier_copy_next.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
             L.comet_frontier_best.argtypes = [vp, i32, vp, vp]
+            L.comet_default_plan_opts.argtypes = [ctypes.POINTER(PlanOpts)]
+            L.comet_plan.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), ctypes.POINTER(PlanResult), vp]
             L.comet_mode_code.argtypes = [ctypes.POINTER(ModeSeq), i32]
             L.comet_mode_code.restype = ctypes.c_uint64
             L.comet_last_error.restype = ctypes.c_char_p
@@ -270,6 +285,29 @@ def comet_frontier_best(frontier, k: int):
     merit = np.zeros(k, dtype=np.float32)
     _check(lib().comet_frontier_best(frontier, int(k), codes.ctypes.data, merit.ctypes.data))
     return codes, merit
+
+
+def comet_default_plan_opts() -> PlanOpts:
+    o = PlanOpts()
+    _check(lib().comet_default_plan_opts(ctypes.byref(o)))
+    return o
+
+
+def comet_plan(problem, instance: int, seeds, n_seeds: int, opts=None, out_traj=None) -> dict:
+    """Algorithm 1 on the device (see include/comet.h); opts: PlanOpts, dict
+    or None.  Returns the result as a dict."""
+    if opts is None or isinstance(opts, dict):
+        o = comet_default_plan_opts()
+        for k, v in (opts or {}).items():
+            setattr(o, k, v)
+        opts = o
+    r = PlanResult()
+    _check(lib().comet_plan(problem, int(instance), _ptr(seeds), int(n_seeds), ctypes.byref(opts), ctypes.byref(r),
+                            _ptr(out_traj)))
+    best = tuple(int(r.best.modes[i]) for i in range(r.best.len))
+    return {"best": best, "best_cost": r.best_cost, "best_viol": r.best_viol, "best_status": r.best_status,
+            "rounds_run": r.rounds_run, "evaluations": r.evaluations, "explore_ms": r.explore_ms,
+            "refine_ms": r.refine_ms}
 
 
 def decode_code(code: int, n_modes: int = 12):

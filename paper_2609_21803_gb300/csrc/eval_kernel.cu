@@ -1145,8 +1145,18 @@ int eval_blocks_per_sm(int warps_per_block, size_t smem_per_block) {
 
 cudaError_t launch_eval(const EvalArgs& a, int total_warps, int warps_per_block, cudaStream_t s) {
     const size_t smem = smem_per_warp_bytes(a.Nmax) * warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the attribute is raised to the largest size seen on this device; it is
+    // not a stream operation, so raising it outside of a capture keeps
+    // launches capturable (problem creation raises it first)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    static size_t raised[64] = {};
+    if (dev < 64 && raised[dev] < smem) {
+        e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        raised[dev] = smem;
+    }
     const int blocks = (total_warps + warps_per_block - 1) / warps_per_block;
     eval_kernel<<<blocks, warps_per_block * 32, smem, s>>>(a);
     return cudaGetLastError();

@@ -325,9 +325,21 @@ cudaError_t launch_frontier_add(const FrontierDev& F, const comet_mode_seq* seqs
     return cudaGetLastError();
 }
 
+cudaError_t prepare_expand() {
+    // shared-memory attribute of the top-k kernel, once per device (not a
+    // stream operation: called at frontier creation, outside any capture)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static bool done[64] = {};
+    if (dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(topk_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)topk_smem_bytes());
+    if (e == cudaSuccess && dev < 64) done[dev] = true;
+    return e;
+}
+
 const TopKey* launch_topk(const FrontierDev& F, int k, cudaStream_t s, cudaError_t* err) {
-    cudaError_t e = cudaFuncSetAttribute(topk_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)topk_smem_bytes());
+    cudaError_t e = prepare_expand();
     *err = e;
     if (e != cudaSuccess) return nullptr;
     // chunk passes until one chunk remains; the first pass reads V directly

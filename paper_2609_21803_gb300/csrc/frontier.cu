@@ -69,6 +69,10 @@ comet_status comet_frontier_create(comet_problem* p, int32_t instance, int64_t c
     if (capacity < 1 || batch < 1 || k_max < 1 || k_max > comet::kChunk || batch > capacity)
         return ffail(COMET_ERR_INVALID_ARG, "need 1 <= batch <= capacity and 1 <= k_max <= 4096");
     const comet_instance_desc& d = p->inst[instance];
+    {
+        const cudaError_t pe = comet::prepare_expand();
+        if (pe != cudaSuccess) return fcuda(pe, "expand kernels");
+    }
     comet_frontier* f = new comet_frontier();
     f->p = p;
     f->batch = batch;
@@ -270,3 +274,230 @@ comet_status comet_frontier_best(comet_frontier* f, int32_t k, uint64_t* out_cod
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- planner
+
+namespace {
+
+__global__ void decode_kernel(const uint64_t* codes, int64_t n, int instance, int n_modes, comet_mode_seq* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long code = codes[i];
+    comet_mode_seq q;
+    memset(&q, 0, sizeof(q));
+    q.instance = instance;
+    const unsigned long long base = (unsigned long long)(n_modes + 1);
+    const int L = (int)(code % base);
+    code /= base;
+    q.len = (uint8_t)L;
+    for (int j = 0; j < L && j < COMET_MAX_SEGMENTS; ++j) {
+        q.modes[j] = (uint8_t)(code % base - 1);
+        code /= base;
+    }
+    out[i] = q;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" comet_status comet_default_plan_opts(comet_plan_opts* po) {
+    if (!po) return ffail(COMET_ERR_INVALID_ARG, "opts is NULL");
+    memset(po, 0, sizeof(*po));
+    po->k = 64;
+    po->batch = 4096;
+    po->rounds = 3;
+    po->budget = 0;
+    po->k_ref = 256;
+    po->ref_iters = 0;
+    po->use_graph = 1;
+    return COMET_OK;
+}
+
+extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
+                                   const comet_plan_opts* po_in, comet_plan_result* out, float* out_traj) {
+    if (!p || !seeds || !out || n_seeds < 1) return ffail(COMET_ERR_INVALID_ARG, "problem, seeds and out are required");
+    comet_plan_opts po;
+    if (po_in)
+        po = *po_in;
+    else
+        comet_default_plan_opts(&po);
+    if (po.k < 1 || po.batch < 1 || po.rounds < 0 || po.k_ref < 1 || po.k_ref > comet::kChunk)
+        return ffail(COMET_ERR_INVALID_ARG, "bad planner options");
+    // a graph cannot be captured on the legacy default stream: the planner
+    // runs on a private stream ordered after the problem's stream and the
+    // problem's stream waits for it at the end
+    cudaStream_t user_stream = p->stream;
+    cudaStream_t s = nullptr;
+    FTRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "planner stream");
+    {
+        cudaEvent_t e0;
+        FTRY(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "event");
+        cudaEventRecord(e0, user_stream);
+        cudaStreamWaitEvent(s, e0, 0);
+        cudaEventDestroy(e0);
+    }
+    struct StreamSwap {
+        comet_problem* p;
+        cudaStream_t user, own;
+        ~StreamSwap() {
+            cudaEvent_t e1;
+            if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e1, own);
+                cudaStreamWaitEvent(user, e1, 0);
+                cudaEventDestroy(e1);
+            }
+            cudaStreamSynchronize(own);
+            p->stream = user;
+            cudaStreamDestroy(own);
+        }
+    } swap{p, user_stream, s};
+    p->stream = s;
+    memset(out, 0, sizeof(*out));
+    const int64_t n0 = po.budget > 0 ? std::min<int64_t>(n_seeds, po.budget) : n_seeds;
+    const int64_t capacity =
+        po.budget > 0 ? std::max<int64_t>(po.budget, n0) : n0 + (int64_t)po.rounds * po.batch;
+    const int32_t batch = (int32_t)std::min<int64_t>(po.batch, capacity);
+    comet_frontier* f = nullptr;
+    comet_status st = comet_frontier_create(p, instance, capacity, batch, std::max(po.k, po.k_ref), &f);
+    if (st != COMET_OK) return st;
+    struct Guard {
+        comet_frontier* f;
+        ~Guard() { comet_frontier_destroy(f); }
+    } guard{f};
+    const int64_t n_eval_max = std::max<int64_t>({n0, (int64_t)batch, (int64_t)po.k_ref});
+    st = comet::reserve_eval(p, n_eval_max);
+    if (st != COMET_OK) return st;
+    DevBuf buf;
+    const size_t b_seq = sizeof(comet_mode_seq) * n_eval_max;
+    const size_t b_f = sizeof(float) * n_eval_max;
+    FTRY(cudaMalloc(&buf.p, b_seq + 2 * b_f + sizeof(int32_t) * n_eval_max + sizeof(uint64_t) * po.k_ref + 1024),
+         "planner buffers");
+    char* bp = (char*)buf.p;
+    comet_mode_seq* d_seqs = (comet_mode_seq*)bp;
+    float* d_cost = (float*)(bp + b_seq + 256);
+    int32_t* d_status = (int32_t*)(bp + b_seq + b_f + 512);
+    uint64_t* d_codes = (uint64_t*)(bp + b_seq + b_f + sizeof(int32_t) * n_eval_max + 768);
+    cudaEvent_t ev[4];
+    for (auto& e : ev) FTRY(cudaEventCreate(&e), "events");
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    FTRY(cudaEventRecord(ev[0], s), "event");
+    // seed batch F_0: evaluate with t_exp and add to V
+    FTRY(cudaMemcpyAsync(d_seqs, seeds, sizeof(comet_mode_seq) * n0, cudaMemcpyDefault, s), "copy seeds");
+    st = comet::launch_eval_device(p, d_seqs, n0, nullptr, nullptr, 0, d_cost, nullptr, d_status);
+    if (st != COMET_OK) return st;
+    comet::FrontierDev F = f->d;
+    FTRY(comet::launch_frontier_add(F, d_seqs, n0, nullptr, d_cost, p->d_viol, (float)p->opts.eps_feas,
+                                    (float)p->opts.merit_mu, s),
+         "add seeds");
+    // one round: expand, evaluate F_{s+1} (count read on the device), add
+    auto round = [&]() -> comet_status {
+        cudaError_t e = comet::launch_expand(F, po.k, batch, po.budget, s);
+        if (e != cudaSuccess) return fcuda(e, "expand");
+        comet_status r = comet::launch_eval_device(p, F.next, batch, F.n_next, nullptr, 0, d_cost, nullptr, d_status);
+        if (r != COMET_OK) return r;
+        comet::FrontierDev Fa = F;
+        Fa.batch_cap = batch;
+        e = comet::launch_frontier_add(Fa, F.next, batch, F.n_next, d_cost, p->d_viol, (float)p->opts.eps_feas,
+                                       (float)p->opts.merit_mu, s);
+        if (e != cudaSuccess) return fcuda(e, "add");
+        return COMET_OK;
+    };
+    if (po.use_graph && po.rounds > 0) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        FTRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const comet_status rs = round();
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rs != COMET_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rs;
+        }
+        if (e != cudaSuccess) return fcuda(e, "end capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fcuda(e, "instantiate");
+        for (int r = 0; r < po.rounds && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return fcuda(e, "graph launch");
+    } else {
+        for (int r = 0; r < po.rounds; ++r) {
+            st = round();
+            if (st != COMET_OK) return st;
+        }
+    }
+    FTRY(cudaEventRecord(ev[1], s), "event");
+    // refinement (Algorithm 1, line 13): re-solve the K_ref best orders of V
+    // with budget t_ref and return the best feasible refined one
+    FTRY(cudaEventRecord(ev[2], s), "event");
+    std::vector<uint64_t> codes(po.k_ref);
+    st = comet_frontier_best(f, po.k_ref, codes.data(), nullptr);
+    if (st != COMET_OK) return st;
+    int64_t n_ref = 0;
+    while (n_ref < po.k_ref && codes[n_ref] != 0) ++n_ref;
+    int64_t n_v = 0;
+    int32_t err = 0;
+    st = comet_frontier_size(f, &n_v, &err);
+    if (st != COMET_OK) return st;
+    out->evaluations = n_v;
+    out->rounds_run = po.rounds;
+    out->best.len = 0;
+    out->best_status = COMET_TO_MAX_ITER;
+    if (n_ref > 0) {
+        FTRY(cudaMemcpyAsync(d_codes, codes.data(), sizeof(uint64_t) * n_ref, cudaMemcpyHostToDevice, s), "codes");
+        decode_kernel<<<(unsigned)((n_ref + 127) / 128), 128, 0, s>>>(d_codes, n_ref, instance,
+                                                                       p->inst[instance].n_modes, d_seqs);
+        FTRY(cudaGetLastError(), "decode");
+        const int32_t t_ref = p->opts.ref_iters > 0 ? p->opts.ref_iters : 1500;
+        st = comet::launch_eval_device(p, d_seqs, n_ref, nullptr, nullptr, po.ref_iters > 0 ? po.ref_iters : t_ref,
+                                       d_cost, nullptr, d_status);
+        if (st != COMET_OK) return st;
+        FTRY(cudaEventRecord(ev[3], s), "event");
+        std::vector<float> cost(n_ref), viol(n_ref);
+        std::vector<int32_t> status(n_ref);
+        std::vector<comet_mode_seq> sq(n_ref);
+        FTRY(cudaMemcpyAsync(cost.data(), d_cost, sizeof(float) * n_ref, cudaMemcpyDeviceToHost, s), "copy");
+        FTRY(cudaMemcpyAsync(viol.data(), p->d_viol, sizeof(float) * n_ref, cudaMemcpyDeviceToHost, s), "copy");
+        FTRY(cudaMemcpyAsync(status.data(), d_status, sizeof(int32_t) * n_ref, cudaMemcpyDeviceToHost, s), "copy");
+        FTRY(cudaMemcpyAsync(sq.data(), d_seqs, sizeof(comet_mode_seq) * n_ref, cudaMemcpyDeviceToHost, s), "copy");
+        FTRY(cudaStreamSynchronize(s), "synchronise");
+        int64_t best = -1;
+        for (int64_t i = 0; i < n_ref; ++i) {
+            const bool feas = status[i] == COMET_TO_CONVERGED && viol[i] <= (float)p->opts.eps_feas;
+            if (feas && (best < 0 || cost[i] < cost[best])) best = i;
+        }
+        if (best >= 0) {
+            out->best = sq[best];
+            out->best_cost = cost[best];
+            out->best_viol = viol[best];
+            out->best_status = status[best];
+            if (out_traj) {
+                // solve the winner once more to return its trajectory
+                float* d_traj = nullptr;
+                FTRY(cudaMalloc(&d_traj, sizeof(float) * p->stride), "trajectory");
+                st = comet::launch_eval_device(p, d_seqs + best, 1, nullptr, nullptr,
+                                               po.ref_iters > 0 ? po.ref_iters : t_ref, d_cost, d_traj, d_status);
+                cudaError_t e = cudaMemcpyAsync(out_traj, d_traj, sizeof(float) * p->stride, cudaMemcpyDefault, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                cudaFree(d_traj);
+                if (st != COMET_OK) return st;
+                if (e != cudaSuccess) return fcuda(e, "copy trajectory");
+            }
+        }
+    } else {
+        FTRY(cudaEventRecord(ev[3], s), "event");
+    }
+    FTRY(cudaEventSynchronize(ev[3]), "synchronise");
+    cudaEventElapsedTime(&out->explore_ms, ev[0], ev[1]);
+    cudaEventElapsedTime(&out->refine_ms, ev[2], ev[3]);
+    if (err) return ffail(COMET_ERR_BUDGET, "the evaluated set overflowed its capacity");
+    return COMET_OK;
+}
