@@ -277,6 +277,8 @@ def run_gpu(args):
                              "FMA rate at 2070 MHz (152 SMs x 128 lanes)"},
         "iterations_per_solve": iter_total / (args.steps * n * world),
     }
+    if rank == 0 and args.plan_instances > 0:
+        line["plan"] = plan_times(P, insts[: args.plan_instances])
     if rank == 0 and not args.no_cpu_baseline:
         conv_rate, rate, ns, cores, dt = oracle_rate(insts)
         line["cpu_baseline"] = {"value": conv_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -290,6 +292,36 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def plan_times(P, insts):
+    """Plan time of CoMET's expansion (Algorithm 1: seed batch of all orders
+    of <= 2 segments, beam 64, B = 4096, s_max = 3, K_ref = 256 refined with
+    t_ref = 1500) against full enumeration of the same order space (every
+    order of <= 4 segments, 22,620, then the same refinement), both through
+    the device planner; device time per instance."""
+    seeds = [(m,) for m in range(12)] + [tuple(s) for s in W.all_sequences(12, 2)]
+    every = seeds + [tuple(s) for s in W.all_sequences(12, 3)] + [tuple(s) for s in W.all_sequences(12, 4)]
+    out = {"instances": len(insts), "expansion_ms": [], "enumeration_ms": [], "expansion_evals": [],
+           "enumeration_evals": [], "recovered": 0}
+    for inst in insts:
+        prob = P.Problem([inst])
+        ps = P.pack_mode_seqs(seeds)
+        pe = P.pack_mode_seqs(every)
+        ex = P.comet_plan(prob.handle, 0, ps, len(ps), dict(k=64, batch=4096, rounds=3, k_ref=256))
+        en = P.comet_plan(prob.handle, 0, pe, len(pe), dict(k=64, batch=4096, rounds=0, k_ref=256))
+        out["expansion_ms"].append(ex["explore_ms"] + ex["refine_ms"])
+        out["enumeration_ms"].append(en["explore_ms"] + en["refine_ms"])
+        out["expansion_evals"].append(ex["evaluations"])
+        out["enumeration_evals"].append(en["evaluations"])
+        if ex["best_cost"] <= en["best_cost"] * (1 + 1e-3) + 1e-9:
+            out["recovered"] += 1
+        prob.close()
+    for key in ("expansion_ms", "enumeration_ms", "expansion_evals", "enumeration_evals"):
+        out[key] = float(np.median(out[key]))
+    out["speedup"] = out["enumeration_ms"] / out["expansion_ms"]
+    out["note"] = "median over instances; recovered = expansion's refined best within 1e-3 of enumeration's"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,6 +330,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--orders", type=int, default=0, help="profiling only: solve this prefix of each enumeration")
+    ap.add_argument("--plan-instances", type=int, default=4, help="instances for the plan-time comparison (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

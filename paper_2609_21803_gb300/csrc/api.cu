@@ -235,6 +235,14 @@ comet_status reserve_eval(comet_problem* p, int64_t n) {
         CUDA_TRY(cudaMalloc(&p->d_stat, sizeof(float) * cap), "stats");
         p->stats_cap = cap;
     }
+    if (p->hetero && p->perm_cap < n) {
+        cudaFree(p->d_perm);
+        p->d_perm = nullptr;
+        p->perm_cap = 0;
+        CUDA_TRY(cudaMalloc(&p->d_perm, sizeof(unsigned int) * std::max<int64_t>(n, 1)), "order buffer");
+        p->perm_cap = n;
+        if (!p->d_lpt) CUDA_TRY(cudaMalloc(&p->d_lpt, lpt_scratch_bytes()), "order scratch");
+    }
     const int64_t warps = resident_warps(p, n);
     if (p->ws_warps < warps) {
         cudaFree(p->d_ws);
@@ -254,6 +262,11 @@ comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, 
     if (p->ws_warps < warps || p->stats_cap < n_max) return fail(COMET_ERR_INTERNAL, "evaluator not reserved");
     CUDA_TRY(cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned int), s), "queue reset");
     CUDA_TRY(cudaMemsetAsync(p->d_bad, 0, sizeof(int), s), "flag reset");
+    // mixed interval counts: hand the TOs out longest first
+    const bool lpt = p->hetero && p->perm_cap >= n_max && n_max > 1;
+    if (lpt)
+        CUDA_TRY(launch_lpt_order(d_seqs, n_max, d_n, p->d_inst, (int)p->inst.size(), p->d_lpt, p->d_perm, s),
+                 "longest-first order");
     EvalArgs a;
     memset(&a, 0, sizeof(a));
     a.inst = p->d_inst;
@@ -261,6 +274,7 @@ comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, 
     a.seqs = d_seqs;
     a.n = n_max;
     a.d_n = d_n;
+    a.perm = lpt ? p->d_perm : nullptr;
     a.warm = d_warm;
     a.stride = p->stride;
     a.Nmax = p->Nmax;
@@ -334,6 +348,8 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
     if (!p) return fail(COMET_ERR_OOM, "host allocation failed");
     comet::merge_opts(opts, &p->opts);
     p->inst.assign(inst, inst + n_instances);
+    for (int i = 0; i < n_instances; ++i)
+        if (inst[i].max_segments > 1 || inst[i].knots_per_segment != inst[0].knots_per_segment) p->hetero = true;
     p->stream = (cudaStream_t)cuda_stream;
     p->Nmax = Nmax;
     p->stride = 7 * (int64_t)Nmax + 4;
@@ -376,6 +392,8 @@ comet_status comet_problem_destroy(comet_problem* p) {
     cudaFree(p->d_iters);
     cudaFree(p->d_stat);
     cudaFree(p->d_stage);
+    cudaFree(p->d_perm);
+    cudaFree(p->d_lpt);
     delete p;
     return COMET_OK;
 }

@@ -46,6 +46,7 @@ struct EvalArgs {
     const comet_mode_seq* seqs;
     int64_t n;               // number of TOs (upper bound when d_n is set)
     const int64_t* d_n;      // optional device-resident TO count
+    const unsigned int* perm;  // optional order in which warps take the TOs
     const float* warm;
     int64_t stride;  // floats per trajectory record (7*Nmax+4)
     int Nmax;
@@ -69,6 +70,12 @@ SolverParams make_params(const comet_solver_opts& o, int max_iters);
 comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out);
 void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out);
 void set_error(const char* msg);
+
+// Longest-first order of a batch (schedule.cu): perm[0..n) lists the TOs by
+// decreasing interval count; scratch holds lpt_scratch_bytes().
+size_t lpt_scratch_bytes();
+cudaError_t launch_lpt_order(const comet_mode_seq* seqs, int64_t n, const int64_t* d_n, const DevInstance* inst,
+                             int n_inst, unsigned int* scratch, unsigned int* perm, cudaStream_t s);
 
 // Shared memory (bytes) one warp needs for TOs of up to Nmax intervals.
 size_t smem_per_warp_bytes(int Nmax);

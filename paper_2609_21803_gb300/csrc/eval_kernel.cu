@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
         if (lane == 0) t = atomicAdd(A.queue, 1u);
         t = __shfl_sync(kFull, t, 0);
         if ((int64_t)t >= n_tos) break;
-        const int64_t ti = (int64_t)t;
+        const int64_t ti = A.perm ? (int64_t)A.perm[t] : (int64_t)t;
         // ---- load the order and validate it
         const comet_mode_seq sq = A.seqs[ti];
         bool bad = sq.instance < 0 || sq.instance >= A.n_inst;

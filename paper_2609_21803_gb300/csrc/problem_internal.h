@@ -32,6 +32,11 @@ struct comet_problem {
     float* d_stat = nullptr;
     int64_t stats_cap = 0;
     int64_t last_n = 0;
+    // longest-first ordering of heterogeneous batches
+    unsigned int* d_perm = nullptr;
+    unsigned int* d_lpt = nullptr;
+    int64_t perm_cap = 0;
+    bool hetero = false;  // instances differ in K or allow several lengths
     // staging for host buffers
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
