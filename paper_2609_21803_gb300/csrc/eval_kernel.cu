@@ -66,6 +66,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// Ampere-style asynchronous global -> shared copies (16 bytes per lane) with
+// commit groups; the waits are hardware waits on the issuing lane's own
+// groups, no spin loop
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // lower-triangle flat index of (i, j), i >= j
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -215,9 +229,14 @@ __device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float 
 
 // ------------------------------------------------------------ shared memory
 
+constexpr int kRing = 8;       // stages in flight in the copy rings
+constexpr int kSweepSlot = 48;  // record floats 32..79 (pd flag and reduced matrix)
+constexpr int kGainSlot = 20;   // record floats 36..55 (x_{k+1} gains)
+
 struct Smem {
+    float* ring_b;  // [kRing][48] sweep records in flight (16-byte aligned)
+    float* ring_c;  // [kRing][20] gains in flight (16-byte aligned)
     unsigned char* mb;  // [Nmax] per-interval mode byte: face | kind << 2 | smask << 4
-    float* Ky;   // [Nmax][4][5] x_{k+1} gains of the sweep
     float* xh;   // [4][Nmax+1] state, high part
     float* xl;   // [4][Nmax+1] state, low part
     float* us;   // [3][Nmax]
@@ -231,15 +250,17 @@ struct Smem {
 };
 
 __host__ __device__ inline size_t smem_floats(int Nmax) {
-    return (size_t)(Nmax + 3) / 4 + 20 * (size_t)Nmax + (size_t)8 * (Nmax + 1) + 3 * (size_t)Nmax + 3 +
-           11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4) + 81 + 16 + 4 + 16;
+    const size_t f = (size_t)kRing * (kSweepSlot + kGainSlot) + (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
+                     3 * (size_t)Nmax + 3 + 11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4) + 81 + 16 + 4 + 16;
+    return (f + 3) / 4 * 4;  // every warp's block starts 16-byte aligned
 }
 
 __device__ __forceinline__ Smem carve(float* base, int Nmax) {
     Smem s;
     float* p = base;
+    s.ring_b = p; p += kRing * kSweepSlot;
+    s.ring_c = p; p += kRing * kGainSlot;
     s.mb = reinterpret_cast<unsigned char*>(p); p += (Nmax + 3) / 4;
-    s.Ky = p; p += 20 * Nmax;
     s.xh = p; p += 4 * (Nmax + 1);
     s.xl = p; p += 4 * (Nmax + 1);
     s.us = p; p += 3 * Nmax;
@@ -428,14 +449,14 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
             for (int i = 3; i < 12; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) rec[6 + (i - 3) * 3 + j] = A[tri(i, j)];
+            rec[33] = pd ? 1.f : -1.f;
+            rec[34] = 0.f;
+            rec[35] = 0.f;
 #pragma unroll
             for (int i = 3; i < 12; ++i)
 #pragma unroll
                 for (int j = 3; j <= i; ++j)
-                    if (!(i == 11 && j == 11)) rec[33 + tri(i - 3, j - 3)] = A[tri(i, j)];
-            rec[77] = pd ? 1.f : -1.f;
-            rec[78] = 0.f;
-            rec[79] = 0.f;
+                    if (!(i == 11 && j == 11)) rec[36 + tri(i - 3, j - 3)] = A[tri(i, j)];
             float4* dst = reinterpret_cast<float4*>(C.rec + (size_t)k * kRec);
 #pragma unroll
             for (int q = 0; q < kRec / 4; ++q)
@@ -501,7 +522,6 @@ __device__ __forceinline__ void untri9(int t, int& i, int& j) {
 // columns (pivots, y-y and (x, rhs)-y entries) in its record; the gains are
 // formed afterwards in a stage-parallel pass (phase_b_gains).  Records are
 // fetched three stages ahead.  Returns false if a pivot is not positive.
-constexpr int kPre = 3;
 __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
     const DevInstance& P = *C.P;
     const int N = C.N, Np1 = C.N + 1, lane = C.lane;
@@ -517,38 +537,32 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
     if (lane < 4)
         S.v[lane] = (lane < 3) ? 2.f * P.w_terminal * ((S.xh[lane * Np1 + N] - P.goal[lane]) + S.xl[lane * Np1 + N])
                                : 0.f;
-    float q0[kPre], q1[kPre], qpd[kPre];
+    // copy ring: stage k's record floats 32..79 (pd flag at 33, reduced
+    // matrix at 36..79) arrive kRing stages ahead; one commit group per stage
+    // (lanes 0..11 copy 16 bytes each)
 #pragma unroll
-    for (int d = 0; d < kPre; ++d) {
+    for (int d = 0; d < kRing; ++d) {
         const int kk = N - 1 - d;
-        q0[d] = q1[d] = 0.f;
-        qpd[d] = 1.f;
-        if (kk >= 0) {
-            const float* r = C.rec + (size_t)kk * kRec;
-            q0[d] = r[33 + lane];
-            q1[d] = has1 ? r[33 + lane + 32] : 0.f;
-            qpd[d] = r[77];
-        }
+        if (kk >= 0 && lane < kSweepSlot / 4)
+            cp_async16(S.ring_b + d * kSweepSlot + 4 * lane, C.rec + (size_t)kk * kRec + 32 + 4 * lane);
+        cp_async_commit();
     }
     __syncwarp();
     bool ok = true;
     for (int k = N - 1; k >= 0; --k) {
-        const float c0 = q0[0], c1 = q1[0];
-        const bool pd_u = qpd[0] > 0.f;
-#pragma unroll
-        for (int d = 0; d + 1 < kPre; ++d) {
-            q0[d] = q0[d + 1];
-            q1[d] = q1[d + 1];
-            qpd[d] = qpd[d + 1];
-        }
+        const int slot = (N - 1 - k) % kRing;
+        cp_async_wait<kRing - 1>();
+        __syncwarp();
+        const float* sl = S.ring_b + slot * kSweepSlot;
+        const float c0 = sl[4 + lane], c1 = has1 ? sl[4 + lane + 32] : 0.f;
+        const bool pd_u = sl[1] > 0.f;
+        __syncwarp();
         {
-            const int kk = k - kPre;
-            if (kk >= 0) {
-                const float* r = C.rec + (size_t)kk * kRec;
-                q0[kPre - 1] = r[33 + lane];
-                q1[kPre - 1] = has1 ? r[33 + lane + 32] : 0.f;
-                qpd[kPre - 1] = r[77];
-            }
+            // refill this slot with the record kRing stages further on
+            const int kk = k - kRing;
+            if (kk >= 0 && lane < kSweepSlot / 4)
+                cp_async16(S.ring_b + slot * kSweepSlot + 4 * lane, C.rec + (size_t)kk * kRec + 32 + 4 * lane);
+            cp_async_commit();
         }
         // load the reduced matrix and add V_{k+1}, v_{k+1} to the x_{k+1} block
         // (entries t < 10 are the y-y block; t = 36..39 are (rhs, y_j))
@@ -562,7 +576,7 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
         for (int j = 0; j < 4; ++j) {
             const float p = S.M[j * 9 + j];
             pd = pd && (p > 0.f);
-            const float ip = 1.f / p;
+            const float ip = __fdividef(1.f, p);
             if (j0 > j) S.M[i0 * 9 + j0] -= S.M[i0 * 9 + j] * S.M[j0 * 9 + j] * ip;
             if (has1 && j1 > j) S.M[i1 * 9 + j1] -= S.M[i1 * 9 + j] * S.M[j1 * 9 + j] * ip;
             __syncwarp();
@@ -571,14 +585,14 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
             ok = false;
             break;
         }
-        // raw y-factor columns for the gains: record entries 33.. (consumed)
-        //   33 + tri(i, j) for the y-y block (i, j < 4, 10 entries)
-        //   43 + 4 c + j  for row (x0..x3, rhs) = 4 + c, column j (20 entries)
+        // raw y-factor columns for the gains, over the consumed record entries:
+        //   36 + tri(i, j) for the y-y block (i, j < 4, 10 entries)
+        //   46 + 4 c + j  for row (x0..x3, rhs) = 4 + c, column j (20 entries)
         float* rec = C.rec + (size_t)k * kRec;
-        if (lane < 10) rec[33 + lane] = S.M[i0 * 9 + j0];
+        if (lane < 10) rec[36 + lane] = S.M[i0 * 9 + j0];
         else if (lane < 30) {
             const int c = (lane - 10) >> 2, j = (lane - 10) & 3;
-            rec[43 + 4 * c + j] = S.M[(4 + c) * 9 + j];
+            rec[46 + 4 * c + j] = S.M[(4 + c) * 9 + j];
         }
         // V_k, v_k from the trailing block
         if (lane < 10) {
@@ -590,6 +604,10 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
         }
         __syncwarp();
     }
+    // drain the copies still in flight (an early exit leaves some) before the
+    // ring is reused
+    cp_async_wait_all();
+    __syncwarp();
     if (!ok) return false;
     // x_0 block: V_0 + rho I + beta on the three pose rows
     float d0[4] = {0.f, 0.f, 0.f, 0.f};
@@ -651,15 +669,16 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
 }
 
 // Stage-parallel gains: K_y,k = -L_y^{-T} [l_{x,y} | l_{rhs,y}] (4 x 5) from
-// the raw y-factor columns the sweep left in each record.
+// the raw y-factor columns the sweep left in each record; K_y replaces them
+// (record floats 36..55, row-major).
 __device__ void phase_b_gains(Ctx& C) {
     const int N = C.N, lane = C.lane;
     Smem& S = C.sm;
     for (int k = lane; k < N; k += 32) {
-        const float* rec = C.rec + (size_t)k * kRec;
+        float* rec = C.rec + (size_t)k * kRec;
         float m[30];
 #pragma unroll
-        for (int q = 0; q < 30; ++q) m[q] = rec[33 + q];
+        for (int q = 0; q < 30; ++q) m[q] = rec[36 + q];
         float ly[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -682,7 +701,7 @@ __device__ void phase_b_gains(Ctx& C) {
                 K[i] = s / ly[i][i];
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) S.Ky[k * 20 + i * 5 + c] = K[i];
+            for (int i = 0; i < 4; ++i) rec[36 + i * 5 + c] = K[i];  // row i of K_y at 36 + 5 i
         }
     }
     __syncwarp();
@@ -698,16 +717,31 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
     Smem& S = C.sm;
     float dx[4] = {dx0[0], dx0[1], dx0[2], dx0[3]};
     if (lane < 4) S.dz[lane] = dx0[lane];
+    // copy ring of the gains (record floats 36..55; lanes 0..4 copy 16 bytes)
+#pragma unroll
+    for (int d = 0; d < kRing; ++d) {
+        if (d < N && lane < kGainSlot / 4)
+            cp_async16(S.ring_c + d * kGainSlot + 4 * lane, C.rec + (size_t)d * kRec + 36 + 4 * lane);
+        cp_async_commit();
+    }
     for (int k = 0; k < N; ++k) {
+        const int slot = k % kRing;
+        cp_async_wait<kRing - 1>();
+        __syncwarp();
         float w = 0.f;
         if (lane < 4) {
-            const float* g = S.Ky + k * 20 + 5 * lane;
+            const float* g = S.ring_c + slot * kGainSlot + 5 * lane;
             w = g[0] * dx[0] + g[1] * dx[1] + g[2] * dx[2] + g[3] * dx[3] + g[4];
             S.dz[7 * (k + 1) + lane] = w;
         }
+        __syncwarp();
+        if (k + kRing < N && lane < kGainSlot / 4)
+            cp_async16(S.ring_c + slot * kGainSlot + 4 * lane, C.rec + (size_t)(k + kRing) * kRec + 36 + 4 * lane);
+        cp_async_commit();
 #pragma unroll
         for (int i = 0; i < 4; ++i) dx[i] = __shfl_sync(kFull, w, i);
     }
+    cp_async_wait_all();
     __syncwarp();
     for (int k = lane; k < N; k += 32) {
         const float* rec = C.rec + (size_t)k * kRec;
