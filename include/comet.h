@@ -95,9 +95,11 @@ typedef struct {
     double merit_mu;         /* mu of Eq. search_merit (100) */
     double beta0, beta_max, beta_ref; /* penalty 1/mu_AL: start, cap, reference (100, 1e4, 1e3) */
     double rho0, rho_min;    /* proximal damping: start and lower bound (1e-4, 1e-4) */
-    int32_t precision_flags; /* bit 0: FP64 iterative refinement of the Riccati step when
-                                beta > 1e4 (default on) */
+    int32_t precision_flags; /* bit 0: one step of FP64 iterative refinement of the Riccati
+                                solve while the penalty exceeds refine_beta (default on) */
     int32_t reserved;
+    double refine_beta;      /* penalty above which the refinement runs (1e4; with the
+                                default cap beta_max = 1e4 it is not reached) */
 } comet_solver_opts;
 
 /* One mode order: instance index, length and modes (24 bytes). */

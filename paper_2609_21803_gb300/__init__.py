@@ -47,6 +47,7 @@ class SolverOpts(ctypes.Structure):
         ("beta0", ctypes.c_double), ("beta_max", ctypes.c_double), ("beta_ref", ctypes.c_double),
         ("rho0", ctypes.c_double), ("rho_min", ctypes.c_double),
         ("precision_flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("refine_beta", ctypes.c_double),
     ]
 
 

@@ -154,6 +154,7 @@ SolverParams make_params(const comet_solver_opts& o, int max_iters) {
     sp.eps_feas = o.eps_feas;
     sp.merit_mu = o.merit_mu;
     sp.refine = o.precision_flags & 1;
+    sp.refine_beta = (float)o.refine_beta;
     return sp;
 }
 
@@ -186,6 +187,7 @@ void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out) {
     if (o.beta_ref > 0) out->beta_ref = o.beta_ref;
     if (o.rho0 > 0) out->rho0 = o.rho0;
     if (o.rho_min > 0) out->rho_min = o.rho_min;
+    if (o.refine_beta > 0) out->refine_beta = o.refine_beta;
     out->precision_flags = o.precision_flags;
 }
 }  // namespace comet
@@ -314,6 +316,7 @@ comet_status comet_default_opts(comet_solver_opts* o) {
     o->rho0 = 1e-4;
     o->rho_min = 1e-4;
     o->precision_flags = 1;
+    o->refine_beta = 1e4;
     return COMET_OK;
 }
 

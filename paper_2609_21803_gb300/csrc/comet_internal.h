@@ -37,7 +37,8 @@ struct SolverParams {
     float armijo_c1, ls_slack;
     float eps_primal, eps_dual, eps_comp, omega_ratio, eta_ratio;
     double eps_feas, merit_mu;
-    int refine;
+    int refine;          // FP64 iterative refinement of the step ...
+    float refine_beta;   // ... while the penalty exceeds this value
 };
 
 struct EvalArgs {

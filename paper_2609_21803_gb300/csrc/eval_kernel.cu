@@ -296,7 +296,7 @@ struct Measures {
 };
 
 __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool assemble, bool update,
-                            float beta_old) {
+                            float beta_old, bool rhs_from_gr = false) {
     const DevInstance& P = *C.P;
     const int N = C.N, Np1 = C.N + 1, lane = C.lane;
     Smem& S = C.sm;
@@ -356,15 +356,28 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
 #pragma unroll
             for (int j = 0; j < 3; ++j) gu[j] += y[4 + q] * R.lu[q][j];
         gx[3] += y[9] - y[10];
-        // interleaved gradient: x_k slot gets the x_k part here, the x_{k+1}
-        // part is parked in dz and added in the pass below
+        if (rhs_from_gr) {
+            // the right-hand side is a given vector per variable (the FP64
+            // residual of a refinement step): u_k and x_{k+1} entries go to
+            // this stage, x_0's to stage 0
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            S.gr[7 * k + i] = gx[i];
-            S.dz[7 * (k + 1) + i] = gy[i];
+            for (int j = 0; j < 3; ++j) gu[j] = S.gr[7 * k + 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                gy[i] = S.gr[7 * (k + 1) + i];
+                gx[i] = (k == 0) ? S.gr[i] : 0.f;
+            }
+        } else {
+            // interleaved gradient: x_k slot gets the x_k part here, the x_{k+1}
+            // part is parked in dz and added in the pass below
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                S.gr[7 * k + i] = gx[i];
+                S.dz[7 * (k + 1) + i] = gy[i];
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) S.gr[7 * k + 4 + j] = gu[j];
         }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) S.gr[7 * k + 4 + j] = gu[j];
 
         if (assemble) {
             // augmented local matrix over (u0..2, y0..3, x0..3, rhs), lower triangle
@@ -478,7 +491,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     __syncwarp();
     // combine the x parts of the gradient and take the stationarity measure
     float stat = 0.f;
-    for (int k = lane; k <= N; k += 32) {
+    for (int k = lane; k <= N && !rhs_from_gr; k += 32) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float g = (k < N) ? S.gr[7 * k + i] : 0.f;
@@ -522,7 +535,7 @@ __device__ __forceinline__ void untri9(int t, int& i, int& j) {
 // columns (pivots, y-y and (x, rhs)-y entries) in its record; the gains are
 // formed afterwards in a stage-parallel pass (phase_b_gains).  Records are
 // fetched three stages ahead.  Returns false if a pivot is not positive.
-__device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
+__device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_from_gr = false) {
     const DevInstance& P = *C.P;
     const int N = C.N, Np1 = C.N + 1, lane = C.lane;
     Smem& S = C.sm;
@@ -535,8 +548,9 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
     // V_N: terminal cost w_T |pose_N - goal|^2
     if (lane < 16) S.V[lane] = ((lane % 5 == 0) && lane < 15) ? 2.f * P.w_terminal : 0.f;
     if (lane < 4)
-        S.v[lane] = (lane < 3) ? 2.f * P.w_terminal * ((S.xh[lane * Np1 + N] - P.goal[lane]) + S.xl[lane * Np1 + N])
-                               : 0.f;
+        S.v[lane] = (lane < 3 && !rhs_from_gr)
+                        ? 2.f * P.w_terminal * ((S.xh[lane * Np1 + N] - P.goal[lane]) + S.xl[lane * Np1 + N])
+                        : 0.f;
     // copy ring: stage k's record floats 32..79 (pd flag at 33, reduced
     // matrix at 36..79) arrive kRing stages ahead; one commit group per stage
     // (lanes 0..11 copy 16 bytes each)
@@ -625,7 +639,7 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4]) {
         for (int i = 0; i < 3; ++i) {
             const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
             H[i][i] += beta;
-            g[i] += S.lam[i] + beta * c;
+            if (!rhs_from_gr) g[i] += S.lam[i] + beta * c;
         }
         float L[4][4];
 #pragma unroll
@@ -858,6 +872,100 @@ __device__ void phase_e(Ctx& C, float alpha) {
     __syncwarp();
 }
 
+// FP64 rows of interval kk at the stored iterate (compensated states read as
+// double): values c, physical factors ph, presence on, and the local
+// Jacobian J[r][0..10] over (x_k[4], u_k[3], x_{k+1}[4]); also the pieces of
+// the dynamics curvature.
+struct Rows64 {
+    double c[11], ph[11];
+    bool on[11];
+    double J[11][11];
+    double f0, f1, ct, st;
+    double x0[4], x1[4], u[3];
+};
+
+__device__ void rows_fp64(const Ctx& C, int kk, Rows64& R) {
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = C.N + 1;
+    const Smem& S = C.sm;
+    const ModeInfo mi = mode_of(S.mb[kk]);
+    for (int i = 0; i < 4; ++i) {
+        R.x0[i] = (double)S.xh[i * Np1 + kk] + (double)S.xl[i * Np1 + kk];
+        R.x1[i] = (double)S.xh[i * Np1 + kk + 1] + (double)S.xl[i * Np1 + kk + 1];
+    }
+    for (int j = 0; j < 3; ++j) R.u[j] = (double)S.us[j * N + kk];
+    const double nx = (mi.face == 0) ? 1.0 : ((mi.face == 2) ? -1.0 : 0.0);
+    const double ny = (mi.face == 1) ? 1.0 : ((mi.face == 3) ? -1.0 : 0.0);
+    const double tx = -ny, ty = nx;
+    const double a = P.a_d[mi.face], ell = P.ell_d[mi.face];
+    const double kp = P.kappa_d, ic2 = P.inv_c2_d, dt = P.dt_d;
+    double st, ct;
+    sincos(R.x0[2], &st, &ct);
+    const double fn = R.u[0], ft = R.u[1], sd = R.u[2];
+    const double vx = kp * (fn * nx + ft * tx), vy = kp * (fn * ny + ft * ty);
+    const double f[4] = {ct * vx - st * vy, st * vx + ct * vy, kp * (-a * ft - R.x0[3] * fn) * ic2, sd};
+    R.f0 = f[0];
+    R.f1 = f[1];
+    R.ct = ct;
+    R.st = st;
+    const double Fx02 = -st * vx - ct * vy, Fx12 = ct * vx - st * vy, Fx23 = -kp * fn * ic2;
+    const double Fu[4][3] = {{kp * (ct * nx - st * ny), kp * (ct * tx - st * ty), 0.0},
+                             {kp * (st * nx + ct * ny), kp * (st * tx + ct * ty), 0.0},
+                             {-kp * R.x0[3] * ic2, -kp * a * ic2, 0.0},
+                             {0.0, 0.0, 1.0}};
+    const double mu = P.mu_d, sc = P.sc_cone_d;
+    const bool stick = mi.kind == 0;
+    const double sg = (mi.kind == 1) ? -1.0 : 1.0;
+    for (int r = 0; r < 11; ++r) {
+        R.on[r] = true;
+        R.ph[r] = 1.0;
+        for (int j = 0; j < 11; ++j) R.J[r][j] = 0.0;
+    }
+    for (int r = 0; r < 4; ++r) {
+        const double is = 1.0 / P.sigma_d[r];
+        R.c[r] = (R.x1[r] - R.x0[r] - dt * f[r]) * is;
+        R.ph[r] = P.sigma_d[r];
+        R.J[r][r] = -is;
+        R.J[r][7 + r] = is;
+        for (int j = 0; j < 3; ++j) R.J[r][4 + j] = -dt * Fu[r][j] * is;
+    }
+    R.J[0][2] += -dt * Fx02 / P.sigma_d[0];
+    R.J[1][2] += -dt * Fx12 / P.sigma_d[1];
+    R.J[2][3] += -dt * Fx23 / P.sigma_d[2];
+    if (mi.smask) R.on[3] = false;
+    if (stick) {
+        R.c[4] = sd;
+        R.J[4][6] = 1.0;
+    } else {
+        R.c[4] = sc * (ft + sg * mu * fn);
+        R.J[4][4] = sc * sg * mu;
+        R.J[4][5] = sc;
+        R.ph[4] = 1.0 / sc;
+    }
+    R.c[5] = sc * (ft - mu * fn);
+    R.J[5][4] = -sc * mu;
+    R.J[5][5] = sc;
+    R.c[6] = sc * (-ft - mu * fn);
+    R.J[6][4] = -sc * mu;
+    R.J[6][5] = -sc;
+    R.ph[5] = R.ph[6] = 1.0 / sc;
+    R.on[5] = R.on[6] = stick;
+    R.c[7] = sg * sd;
+    R.J[7][6] = sg;
+    R.on[7] = !stick;
+    R.c[8] = -fn;
+    R.J[8][4] = -1.0;
+    R.c[9] = R.x0[3] - ell;
+    R.J[9][3] = 1.0;
+    R.c[10] = -R.x0[3] - ell;
+    R.J[10][3] = -1.0;
+    for (int r = 0; r < 11; ++r)
+        if (!R.on[r]) {
+            R.c[r] = 0.0;
+            for (int j = 0; j < 11; ++j) R.J[r][j] = 0.0;
+        }
+}
+
 // FP64 certificate (Eq. inexact_mode_value in physical units, KKT residual)
 struct Cert {
     double cost, viol, stat;
@@ -877,98 +985,29 @@ __device__ Cert certify(const Ctx& C, float beta) {
         for (int side = 0; side < 2; ++side) {
             const int kk = (side == 0) ? k - 1 : k;  // interval index
             if (kk < 0 || kk >= N) continue;
-            const ModeInfo mi = mode_info(C.modes, C.len, N, kk);
-            double x0[4], x1[4], u[3];
-            for (int i = 0; i < 4; ++i) {
-                x0[i] = (double)S.xh[i * Np1 + kk] + (double)S.xl[i * Np1 + kk];
-                x1[i] = (double)S.xh[i * Np1 + kk + 1] + (double)S.xl[i * Np1 + kk + 1];
-            }
-            for (int j = 0; j < 3; ++j) u[j] = (double)S.us[j * N + kk];
-            const double nx = (mi.face == 0) ? 1.0 : ((mi.face == 2) ? -1.0 : 0.0);
-            const double ny = (mi.face == 1) ? 1.0 : ((mi.face == 3) ? -1.0 : 0.0);
-            const double tx = -ny, ty = nx;
-            const double a = P.a_d[mi.face], ell = P.ell_d[mi.face];
-            const double kp = P.kappa_d, ic2 = P.inv_c2_d, dt = P.dt_d;
-            double st, ct;
-            sincos(x0[2], &st, &ct);
-            const double fn = u[0], ft = u[1], sd = u[2];
-            const double vx = kp * (fn * nx + ft * tx), vy = kp * (fn * ny + ft * ty);
-            const double f[4] = {ct * vx - st * vy, st * vx + ct * vy, kp * (-a * ft - x0[3] * fn) * ic2, sd};
-            const double Fx02 = -st * vx - ct * vy, Fx12 = ct * vx - st * vy, Fx23 = -kp * fn * ic2;
-            const double Fu[4][3] = {{kp * (ct * nx - st * ny), kp * (ct * tx - st * ty), 0.0},
-                                     {kp * (st * nx + ct * ny), kp * (st * tx + ct * ty), 0.0},
-                                     {-kp * x0[3] * ic2, -kp * a * ic2, 0.0},
-                                     {0.0, 0.0, 1.0}};
-            const double mu = P.mu_d, sc = P.sc_cone_d;
-            const bool stick = mi.kind == 0;
-            const double sg = (mi.kind == 1) ? -1.0 : 1.0;
-            double c[11], ph[11];
-            bool on[11];
-            double J[11][11];
-            for (int r = 0; r < 11; ++r) {
-                on[r] = true;
-                ph[r] = 1.0;
-                for (int j = 0; j < 11; ++j) J[r][j] = 0.0;
-            }
-            for (int r = 0; r < 4; ++r) {
-                const double is = 1.0 / P.sigma_d[r];
-                c[r] = (x1[r] - x0[r] - dt * f[r]) * is;
-                ph[r] = P.sigma_d[r];
-                J[r][r] = -is;
-                J[r][7 + r] = is;
-                for (int j = 0; j < 3; ++j) J[r][4 + j] = -dt * Fu[r][j] * is;
-            }
-            J[0][2] += -dt * Fx02 / P.sigma_d[0];
-            J[1][2] += -dt * Fx12 / P.sigma_d[1];
-            J[2][3] += -dt * Fx23 / P.sigma_d[2];
-            if (mi.smask) on[3] = false;
-            if (stick) {
-                c[4] = sd;
-                J[4][6] = 1.0;
-            } else {
-                c[4] = sc * (ft + sg * mu * fn);
-                J[4][4] = sc * sg * mu;
-                J[4][5] = sc;
-                ph[4] = 1.0 / sc;
-            }
-            c[5] = sc * (ft - mu * fn);
-            J[5][4] = -sc * mu;
-            J[5][5] = sc;
-            c[6] = sc * (-ft - mu * fn);
-            J[6][4] = -sc * mu;
-            J[6][5] = -sc;
-            ph[5] = ph[6] = 1.0 / sc;
-            on[5] = on[6] = stick;
-            c[7] = sg * sd;
-            J[7][6] = sg;
-            on[7] = !stick;
-            c[8] = -fn;
-            J[8][4] = -1.0;
-            c[9] = x0[3] - ell;
-            J[9][3] = 1.0;
-            c[10] = -x0[3] - ell;
-            J[10][3] = -1.0;
+            Rows64 R;
+            rows_fp64(C, kk, R);
             const float* lam = S.lam + 3 + 11 * kk;
             for (int r = 0; r < 11; ++r) {
-                if (!on[r]) continue;
+                if (!R.on[r]) continue;
                 const bool ineq = r >= 5;
-                const double t = (double)lam[r] + (double)beta * c[r];
+                const double t = (double)lam[r] + (double)beta * R.c[r];
                 const double y = ineq ? fmax(t, 0.0) : t;
                 if (side == 1) {  // count each interval once
-                    const double vr = ineq ? fmax(c[r], 0.0) : fabs(c[r]);
-                    viol = fmax(viol, vr * ph[r]);
-                    if (!isfinite(c[r])) finite = false;
+                    const double vr = ineq ? fmax(R.c[r], 0.0) : fabs(R.c[r]);
+                    viol = fmax(viol, vr * R.ph[r]);
+                    if (!isfinite(R.c[r])) finite = false;
                 }
                 // gradient: side 0 contributes the x_{k+1} columns, side 1 the x_k and u_k ones
                 if (side == 0)
-                    for (int i = 0; i < 4; ++i) g[i] += y * J[r][7 + i];
+                    for (int i = 0; i < 4; ++i) g[i] += y * R.J[r][7 + i];
                 else
-                    for (int i = 0; i < 7; ++i) g[i] += y * J[r][i];
+                    for (int i = 0; i < 7; ++i) g[i] += y * R.J[r][i];
             }
             if (side == 1) {
                 for (int j = 0; j < 3; ++j) {
-                    g[4 + j] += 2.0 * P.w_control_d * u[j];
-                    cost += P.w_control_d * u[j] * u[j];
+                    g[4 + j] += 2.0 * P.w_control_d * R.u[j];
+                    cost += P.w_control_d * R.u[j] * R.u[j];
                 }
             }
         }
@@ -996,6 +1035,110 @@ __device__ Cert certify(const Ctx& C, float beta) {
     ct.stat = warp_max_d(stat);
     ct.finite = __all_sync(kFull, finite) && isfinite(ct.cost);
     return ct;
+}
+
+// FP64 residual of the step for one iterative-refinement pass:
+//   res = g + (H + rho I) dz
+// with g the AL gradient and H the local model that was factored (the
+// Gauss-Newton part, plus the dynamics curvature when `curvature`), per
+// variable into S.gr (x_k at 7k .. 7k+3, u_k at 7k+4 .. 7k+6).
+__device__ void residual_fp64(Ctx& C, float beta_f, float rho_f, bool curvature) {
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = C.N + 1, lane = C.lane;
+    Smem& S = C.sm;
+    const double beta = beta_f, rho = rho_f;
+    for (int k = lane; k <= N; k += 32) {
+        double res[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int side = 0; side < 2; ++side) {
+            const int kk = (side == 0) ? k - 1 : k;
+            if (kk < 0 || kk >= N) continue;
+            Rows64 R;
+            rows_fp64(C, kk, R);
+            double dl[11];
+            for (int i = 0; i < 4; ++i) {
+                dl[i] = S.dz[7 * kk + i];
+                dl[7 + i] = S.dz[7 * (kk + 1) + i];
+            }
+            for (int j = 0; j < 3; ++j) dl[4 + j] = S.dz[7 * kk + 4 + j];
+            const float* lam = S.lam + 3 + 11 * kk;
+            for (int r = 0; r < 11; ++r) {
+                if (!R.on[r]) continue;
+                const bool ineq = r >= 5;
+                const double t = (double)lam[r] + beta * R.c[r];
+                if (ineq && !(t > 0.0)) continue;
+                double adz = 0.0;
+                for (int j = 0; j < 11; ++j) adz += R.J[r][j] * dl[j];
+                const double w = t + beta * adz;  // y_r + beta a_r . dz
+                if (side == 0)
+                    for (int i = 0; i < 4; ++i) res[i] += w * R.J[r][7 + i];
+                else
+                    for (int i = 0; i < 7; ++i) res[i] += w * R.J[r][i];
+            }
+            if (side == 0) {
+                for (int i = 0; i < 4; ++i) res[i] += rho * dl[7 + i];  // damping of x_{k+1}
+            } else {
+                for (int j = 0; j < 3; ++j) res[4 + j] += 2.0 * P.w_control_d * (R.u[j] + dl[4 + j]) + rho * dl[4 + j];
+                if (curvature) {
+                    // -dt sum_r yd_r d^2 f_r over (x_k, u_k), yd the unscaled multipliers
+                    double yd[3];
+                    for (int r = 0; r < 3; ++r) {
+                        const double t = (double)lam[r] + beta * R.c[r];
+                        yd[r] = R.on[r] ? t / P.sigma_d[r] : 0.0;
+                    }
+                    const ModeInfo mi = mode_of(S.mb[kk]);
+                    const double nx = (mi.face == 0) ? 1.0 : ((mi.face == 2) ? -1.0 : 0.0);
+                    const double ny = (mi.face == 1) ? 1.0 : ((mi.face == 3) ? -1.0 : 0.0);
+                    const double tx = -ny, ty = nx, kp = P.kappa_d, dt = P.dt_d;
+                    const double h_thth = -yd[0] * R.f0 - yd[1] * R.f1;
+                    const double h_thfn = yd[0] * kp * (-R.st * nx - R.ct * ny) + yd[1] * kp * (R.ct * nx - R.st * ny);
+                    const double h_thft = yd[0] * kp * (-R.st * tx - R.ct * ty) + yd[1] * kp * (R.ct * tx - R.st * ty);
+                    const double h_sfn = -yd[2] * kp * P.inv_c2_d;
+                    res[2] -= dt * (h_thth * dl[2] + h_thfn * dl[4] + h_thft * dl[5]);
+                    res[4] -= dt * (h_thfn * dl[2] + h_sfn * dl[3]);
+                    res[5] -= dt * h_thft * dl[2];
+                    res[3] -= dt * h_sfn * dl[4];
+                }
+            }
+        }
+        if (k == N)
+            for (int i = 0; i < 3; ++i) {
+                const double e = (double)S.xh[i * Np1 + N] + (double)S.xl[i * Np1 + N] - P.goal_d[i];
+                res[i] += 2.0 * P.w_terminal_d * (e + (double)S.dz[7 * N + i]);
+            }
+        if (k == 0) {
+            for (int i = 0; i < 3; ++i) {
+                const double c = (double)S.xh[i * Np1] + (double)S.xl[i * Np1] - P.start_d[i];
+                res[i] += (double)S.lam[i] + beta * (c + (double)S.dz[i]);
+            }
+            for (int i = 0; i < 4; ++i) res[i] += rho * (double)S.dz[i];
+        }
+        const int nv = (k < N) ? 7 : 4;
+        for (int i = 0; i < nv; ++i) S.gr[7 * k + i] = (float)res[i];
+    }
+    __syncwarp();
+}
+
+// One step of iterative refinement of the Riccati solve (at high penalty):
+// the FP64 residual res = g + (H + rho I) dz of the FP32 step is solved
+// with the same model (same factorisation path) and the correction added,
+// dz <- dz + delta with (H + rho I) delta = -res.  Once the records hold
+// the residual, sm.gr is free and keeps the first step meanwhile.
+__device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
+    Smem& S = C.sm;
+    const int nz = 7 * C.N + 4;
+    residual_fp64(C, beta, rho, curvature);
+    phase_a(C, beta, rho, curvature, true, false, beta, /*rhs_from_gr=*/true);
+    for (int t = C.lane; t < nz; t += 32) S.gr[t] = S.dz[t];
+    __syncwarp();
+    float d0[4];
+    if (phase_b(C, beta, rho, d0, /*rhs_from_gr=*/true)) {
+        phase_b_gains(C);
+        phase_c(C, d0);
+        for (int t = C.lane; t < nz; t += 32) S.dz[t] += S.gr[t];
+    } else {
+        for (int t = C.lane; t < nz; t += 32) S.dz[t] = S.gr[t];
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------ kernel
@@ -1104,9 +1247,10 @@ __global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
             // step: Newton with the dynamics curvature, then Gauss-Newton,
             // then rising damping
             float dx0[4];
-            bool fac = false;
+            bool fac = false, model_curv = false;
             if (curv) {
                 fac = phase_b(C, beta, rho, dx0);
+                model_curv = fac;
                 if (!fac) curv_hold = sp.curv_skip;
             } else {
                 --curv_hold;
@@ -1124,6 +1268,7 @@ __global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
             if (!fac) continue;
             phase_b_gains(C);
             const float D = phase_c(C, dx0);
+            if (sp.refine && beta > sp.refine_beta) refine_step(C, beta, rho, model_curv);
             const float alpha = phase_d(C, beta, D, sp);
             if (alpha > 0.f) {
                 phase_e(C, alpha);

@@ -52,3 +52,4 @@ def test_struct_layouts():
     import ctypes
     assert ctypes.sizeof(P.ModeSeq) == 24
     assert ctypes.sizeof(P.InstanceDesc) == 4 * 4 + 8 * 16
+    assert ctypes.sizeof(P.SolverOpts) == 2 * 4 + 10 * 8 + 2 * 4 + 8

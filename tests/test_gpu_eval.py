@@ -180,6 +180,37 @@ def test_iteration_level_parity(P, iters):
         assert np.mean(dJ <= 1e-2 * np.abs(ref["cost"]) + 1e-6) >= 0.95
 
 
+def test_fp64_refinement_at_high_penalty(P):
+    # one FP64 iterative-refinement step of the Riccati solve while the
+    # penalty exceeds refine_beta.  The cap is raised to 1e5 so that the
+    # penalty passes the threshold of 1e4; the run with the threshold at the
+    # cap never refines and must equal the run with refinement switched off
+    # bit for bit, the refined run must differ (the pass changes the step)
+    # and keep the oracle's parity bar at the same options
+    insts = [W.push_l2_instance(s) for s in range(6)]
+    seqs = W.all_sequences(12, 2)
+    n = len(seqs) * len(insts)
+    allseq = np.tile(seqs, (len(insts), 1))
+    idx = np.repeat(np.arange(len(insts)), len(seqs)).astype(np.int32)
+    ref_on = gpu_eval(P, insts, allseq, idx, want_traj=True, opts={"beta_max": 1e5, "refine_beta": 1e4})
+    at_cap = gpu_eval(P, insts, allseq, idx, want_traj=True, opts={"beta_max": 1e5, "refine_beta": 1e5})
+    off = gpu_eval(P, insts, allseq, idx, want_traj=True, opts={"beta_max": 1e5, "precision_flags": 0})
+    for k in ("cost", "status", "iters", "traj"):
+        np.testing.assert_array_equal(at_cap[k], off[k])
+    changed = (ref_on["iters"] != off["iters"]) | (ref_on["cost"] != off["cost"])
+    assert changed.any()
+    ref, _ = oracle.solve_batch(insts, idx, allseq, np.full(n, 2, np.int32), opts=oracle.default_opts(beta_max=1e5),
+                                nthreads=os.cpu_count())
+    cg, co, both, rel, same = compare(ref_on, ref)
+    print(f"refined: changed {changed.mean():.3f} conv gpu {cg.mean():.4f} oracle {co.mean():.4f} "
+          f"same {same.sum() / max(1, both.sum()):.4f} rel<1e-4 {np.mean(rel[both] < 1e-4):.4f}")
+    assert cg.mean() >= 0.9 and abs(cg.mean() - co.mean()) <= 0.05
+    assert same.sum() >= 0.85 * both.sum()
+    for t in np.flatnonzero(cg)[::13]:
+        v, _ = certify_fp64(insts[idx[t]], allseq[t], 16, ref_on["traj"][t], 16)
+        assert v <= 1e-5, (t, v)
+
+
 def test_four_segment_sampled_parity(P):
     # the 4-segment workload at full size on the GPU (one instance, 20,736
     # orders, the bench's launch configuration); the oracle checks a seeded
