@@ -1,0 +1,139 @@
+"""Pins of the learned proposal's FP64 oracle (oracle/mlp.py) to facts that
+do not come from the oracle itself: textbook values of the normal CDF, the
+bfloat16 rounding rule, central differences of the loss, closed forms of
+the first AdamW step, and a width-1 network evaluated through a library
+normal CDF."""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import norm
+
+import workloads as W
+from oracle import mlp
+
+
+def test_bf16_round_to_nearest_even():
+    one = 1.0
+    cases = {
+        one: one,
+        one + 2 ** -8: one,                        # tie -> even (1.0)
+        one + 3 * 2 ** -8: one + 2 ** -6,          # tie -> even (1 + 2 ulp)
+        one + 2 ** -8 + 2 ** -20: one + 2 ** -7,   # above the tie -> up
+        -(one + 2 ** -9): -one,                    # below the tie -> down
+        3.140625: 3.140625,                        # exactly representable
+        65504.0: 65536.0,                          # 0x477FE000: above half-way -> up
+    }
+    for x, want in cases.items():
+        assert mlp.bf16(np.float32(x)) == want, x
+    assert mlp.bf16_bits(np.float32(1.0)) == 0x3F80
+    assert mlp.bf16_bits(np.float32(-2.0)) == 0xC000
+    assert np.isnan(mlp.bf16(np.float32(np.nan)))
+    b = mlp.bf16_bits(np.linspace(-3, 3, 101).astype(np.float32))
+    np.testing.assert_array_equal(mlp.from_bf16_bits(b), mlp.bf16(np.linspace(-3, 3, 101)))
+
+
+def test_gelu_textbook_values():
+    # Phi(1) = 0.8413447460685429, Phi(2) = 0.9772498680518208 (normal CDF)
+    assert mlp.gelu(0.0) == 0.0
+    assert mlp.gelu(1.0) == pytest.approx(0.8413447460685429, abs=1e-15)
+    assert mlp.gelu(-1.0) == pytest.approx(-(1 - 0.8413447460685429), abs=1e-15)
+    assert mlp.gelu(2.0) == pytest.approx(2 * 0.9772498680518208, abs=1e-14)
+    assert mlp.gelu(12.0) == pytest.approx(12.0, abs=1e-12)
+    assert abs(mlp.gelu(-12.0)) < 1e-12
+    # derivative: Phi(0) = 1/2, and central differences elsewhere
+    assert mlp.gelu_grad(0.0) == 0.5
+    x = np.linspace(-5, 5, 41)
+    h = 1e-6
+    np.testing.assert_allclose(mlp.gelu_grad(x), (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), atol=1e-8)
+
+
+def test_width_one_network_through_library_cdf():
+    # 1 -> 1 -> 1 -> 1 -> 1 with weights w and biases b: by hand with
+    # scipy's normal CDF, gelu(z) = z Phi(z)
+    ws = [0.5, -1.25, 2.0, 0.75]
+    bs = [0.125, 0.25, -0.5, 1.0]
+    params = [(np.array([[w]]), np.array([b])) for w, b in zip(ws, bs)]
+    x = 0.875
+    h = x
+    for l in range(3):
+        z = ws[l] * h + bs[l]
+        h = z * norm.cdf(z)
+    want = ws[3] * h + bs[3]
+    y, _ = mlp.forward(params, np.array([[x]]))
+    assert y[0, 0] == pytest.approx(want, rel=1e-14)
+
+
+def _small_problem(seed, B=5, din=6, width=7, dout=4):
+    params = W.mlp_params(din, width, dout, seed, bias_scale=0.3)
+    rng = np.random.default_rng(seed + 100)
+    X = rng.normal(size=(B, din))
+    T = rng.normal(size=(B, dout))
+    Om = rng.uniform(0, 1, size=(B, dout)) * (rng.uniform(size=(B, dout)) > 0.3)
+    return params, X, T, Om
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_backward_matches_central_differences(seed):
+    params, X, T, Om = _small_problem(seed)
+
+    def L(ps):
+        Y, _ = mlp.forward(ps, X, bf16_weights=False)
+        return mlp.loss(Y, T, Om)
+
+    Y, cache = mlp.forward(params, X, bf16_weights=False)
+    grads = mlp.backward(params, cache, Y, T, Om, bf16_weights=False)
+    h = 1e-6
+    for l, (Wl, bl) in enumerate(params):
+        for arr, g in ((Wl, grads[l][0]), (bl, grads[l][1])):
+            num = np.zeros_like(arr)
+            for idx in np.ndindex(arr.shape):
+                old = arr[idx]
+                arr[idx] = old + h
+                lp = L(params)
+                arr[idx] = old - h
+                lm = L(params)
+                arr[idx] = old
+                num[idx] = (lp - lm) / (2 * h)
+            np.testing.assert_allclose(g, num, rtol=1e-6, atol=1e-9)
+
+
+def test_loss_definition_special_cases():
+    Y = np.array([[1.0, 2.0], [3.0, 4.0]])
+    T = np.array([[0.0, 2.0], [1.0, 1.0]])
+    assert mlp.loss(Y, T, np.ones_like(Y)) == pytest.approx((1 + 0 + 4 + 9) / 2)
+    assert mlp.loss(Y, T, np.zeros_like(Y)) == 0.0
+    assert mlp.loss(Y, T, np.array([[1.0, 0], [0, 0.5]])) == pytest.approx((1 + 0.5 * 9) / 2)
+
+
+def test_adamw_first_step_closed_forms():
+    p = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.3, -4.0, 1e-3, 0.0])
+    z = np.zeros(4)
+    lr = 1e-2
+    # bias-corrected first step: m_hat = g, v_hat = g^2 -> p - lr g / (|g| + eps)
+    p1, m1, v1 = mlp.adamw(p, g, z, z, 1, lr, eps=1e-8, wd=0.0)
+    np.testing.assert_allclose(p1[:3], p[:3] - lr * np.sign(g[:3]), rtol=0, atol=1e-7)
+    assert p1[3] == p[3]
+    np.testing.assert_allclose(m1, 0.1 * g)
+    np.testing.assert_allclose(v1, 0.001 * g * g)
+    # decoupled weight decay with a zero gradient: p (1 - lr wd)
+    p2, _, _ = mlp.adamw(p, np.zeros(4), z, z, 1, lr, wd=0.1)
+    np.testing.assert_allclose(p2, p * (1 - lr * 0.1))
+    # constant gradient: m_hat = g and v_hat = g^2 at every step
+    pt, m, v = p[:3].copy(), z[:3].copy(), z[:3].copy()
+    for t in range(1, 6):
+        pt, m, v = mlp.adamw(pt, g[:3], m, v, t, lr, eps=0.0)
+    np.testing.assert_allclose(pt, p[:3] - 5 * lr * np.sign(g[:3]), rtol=1e-12)
+
+
+def test_features_layout():
+    inst = {"start": [0.1, -0.2, 0.3], "goal": [0.4, 0.5, -0.6], "side_x": 0.09, "side_y": 0.12}
+    din, width, dout = mlp.dims(4, 80)
+    assert (din, width, dout) == (64, 256, 256)
+    x = mlp.features(inst, (3, 11), 4, din)
+    np.testing.assert_allclose(x[:8], [0.1, -0.2, 0.3, 0.4, 0.5, -0.6, 0.9, 1.2])
+    onehot = x[8:60].reshape(4, 13)
+    assert onehot.sum() == 4 and onehot[0, 3] == 1 and onehot[1, 11] == 1
+    assert onehot[2, 12] == 1 and onehot[3, 12] == 1 and np.all(x[60:] == 0)
+    assert mlp.dims(6, 180) == (128, 256, 544)

@@ -120,3 +120,16 @@ def pad_sequences(seqs, lmax: int = MAX_SEGMENTS) -> tuple[np.ndarray, np.ndarra
         modes[i, : len(s)] = s
         lens[i] = len(s)
     return modes, lens
+
+
+def mlp_params(in_dim: int, width: int, out_dim: int, seed: int, n_layers: int = 4, bias_scale: float = 0.0):
+    """Seeded weights of an MLP in_dim -> width x (n_layers-1) -> out_dim:
+    W_l ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) row-major [out][in], biases
+    ~ U(-bias_scale, bias_scale).  Returns a list of (W, b) float64 arrays."""
+    rng = np.random.default_rng(seed)
+    d = [in_dim] + [width] * (n_layers - 1) + [out_dim]
+    out = []
+    for l in range(n_layers):
+        a = 1.0 / np.sqrt(d[l])
+        out.append((rng.uniform(-a, a, (d[l + 1], d[l])), rng.uniform(-bias_scale, bias_scale, d[l + 1])))
+    return out
