@@ -163,3 +163,24 @@ def adamw(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
     vh = v / (1.0 - beta2 ** t)
     p = p - lr * (mh / (np.sqrt(vh) + eps) + wd * p)
     return p, m, v
+
+
+def targets(cost, viol, status, traj_controls, N, n_max, out_dim, lambda_w=1.0, merit_mu=100.0, eps_feas=1e-5):
+    """Training target T and weight Omega of one evaluated order.
+
+    T_0 = log max(M_hat, 1e-12), M_hat = J_hat + merit_mu max(v_hat - eps_feas,
+    0) (Eq. search_merit), weight 1 unless the TO ended NONFINITE (status 4);
+    T_{1 + c n_max + k} = control c of interval k (traj_controls[c][k]) for
+    k < N, weight lambda_w / (3 N) when the TO CONVERGED (status 0), else 0."""
+    T = np.zeros(out_dim)
+    Om = np.zeros(out_dim)
+    m = cost + merit_mu * max(viol - eps_feas, 0.0)
+    if status != 4 and np.isfinite(m):
+        T[0] = np.log(max(m, 1e-12))
+        Om[0] = 1.0
+    if status == 0:
+        for c in range(3):
+            for k in range(N):
+                T[1 + c * n_max + k] = traj_controls[c][k]
+                Om[1 + c * n_max + k] = lambda_w / (3.0 * N)
+    return T, Om

@@ -68,6 +68,27 @@ class PlanResult(ctypes.Structure):
                 ("explore_ms", ctypes.c_float), ("refine_ms", ctypes.c_float)]
 
 
+class ProposalDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("rows_cap", ctypes.c_int32), ("dataset_cap", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("lambda_w", ctypes.c_double), ("warm_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class AdamWOpts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("weight_decay", ctypes.c_double)]
+
+
+class GemmEpilogue(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k_splits", ctypes.c_int32), ("bias", ctypes.c_void_p),
+                ("out_f32", ctypes.c_void_p), ("ld_f32", ctypes.c_int64),
+                ("out_bf16", ctypes.c_void_p), ("ld_bf16", ctypes.c_int64),
+                ("out_bf16_t", ctypes.c_void_p), ("ld_bf16_t", ctypes.c_int64),
+                ("z_in", ctypes.c_void_p), ("ld_z", ctypes.c_int64)]
+
+
+GEMM_STORE, GEMM_BIAS_GELU, GEMM_GELU_GRAD, GEMM_ATOMIC_ADD = 0, 1, 2, 3
+
 MODE_SEQ_DTYPE = np.dtype([("instance", "<i4"), ("len", "u1"), ("modes", "u1", (MAX_SEGMENTS,)),
                            ("pad", "u1", (3,))])
 assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == 24
@@ -80,6 +101,12 @@ EXPORTS = (
     "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
     "comet_frontier_next", "comet_frontier_size", "comet_frontier_best", "comet_frontier_copy_next",
     "comet_default_plan_opts", "comet_plan",
+    # include/comet_proposal.h
+    "comet_default_proposal_desc", "comet_default_adamw_opts", "comet_proposal_create", "comet_proposal_destroy",
+    "comet_proposal_dims", "comet_proposal_set_params", "comet_proposal_get_params", "comet_proposal_features",
+    "comet_proposal_forward", "comet_proposal_train_batch", "comet_proposal_add_samples",
+    "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
+    "comet_gemm_bf16",
 )
 
 
@@ -123,8 +150,30 @@ def lib(build_if_missing: bool = False):
             L.comet_mode_code.argtypes = [ctypes.POINTER(ModeSeq), i32]
             L.comet_mode_code.restype = ctypes.c_uint64
             L.comet_last_error.restype = ctypes.c_char_p
+            L.comet_default_proposal_desc.argtypes = [ctypes.POINTER(ProposalDesc)]
+            L.comet_default_proposal_desc.restype = None
+            L.comet_default_adamw_opts.argtypes = [ctypes.POINTER(AdamWOpts)]
+            L.comet_default_adamw_opts.restype = None
+            L.comet_proposal_create.argtypes = [vp, ctypes.POINTER(ProposalDesc), ctypes.POINTER(vp)]
+            L.comet_proposal_destroy.argtypes = [vp]
+            L.comet_proposal_dims.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                              ctypes.POINTER(i64)]
+            L.comet_proposal_set_params.argtypes = [vp, vp]
+            L.comet_proposal_get_params.argtypes = [vp, vp, vp]
+            L.comet_proposal_features.argtypes = [vp, vp, i64, vp]
+            L.comet_proposal_forward.argtypes = [vp, vp, i64, vp]
+            L.comet_proposal_train_batch.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(AdamWOpts),
+                                                     ctypes.POINTER(ctypes.c_float)]
+            L.comet_proposal_add_samples.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+            L.comet_proposal_dataset_size.argtypes = [vp, ctypes.POINTER(i64)]
+            L.comet_proposal_dataset_rows.argtypes = [vp, i64, i64, vp, vp, vp]
+            L.comet_proposal_train.argtypes = [vp, i64, i32, ctypes.POINTER(AdamWOpts), ctypes.c_uint64, vp]
+            L.comet_proposal_predict.argtypes = [vp, vp, i64, vp, vp]
+            L.comet_proposal_prune.argtypes = [vp, vp, i32, vp]
+            L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
             for name in EXPORTS:
-                if name not in ("comet_traj_stride", "comet_mode_code", "comet_last_error"):
+                if name not in ("comet_traj_stride", "comet_mode_code", "comet_last_error",
+                                "comet_default_proposal_desc", "comet_default_adamw_opts"):
                     getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -400,3 +449,113 @@ class Problem:
         comet_eval_stats(self.handle, viol, merit, iters, stat)
         out.update(viol=viol, merit=merit, iters=iters, stat=stat)
         return out
+
+
+# ------------------------------------------------------ learned proposal
+
+def comet_default_proposal_desc() -> ProposalDesc:
+    d = ProposalDesc()
+    lib().comet_default_proposal_desc(ctypes.byref(d))
+    return d
+
+
+def comet_default_adamw_opts() -> AdamWOpts:
+    o = AdamWOpts()
+    lib().comet_default_adamw_opts(ctypes.byref(o))
+    return o
+
+
+def _fill(struct, defaults, over):
+    for k, v in (over or {}).items():
+        if not hasattr(defaults, k):
+            raise KeyError(k)
+        setattr(defaults, k, v)
+    return defaults
+
+
+def comet_proposal_create(problem, desc=None) -> int:
+    d = desc if isinstance(desc, ProposalDesc) else _fill(ProposalDesc, comet_default_proposal_desc(), desc)
+    h = ctypes.c_void_p()
+    _check(lib().comet_proposal_create(problem, ctypes.byref(d), ctypes.byref(h)))
+    return h.value
+
+
+def comet_proposal_destroy(q):
+    _check(lib().comet_proposal_destroy(q))
+
+
+def comet_proposal_dims(q):
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    n = ctypes.c_int64()
+    _check(lib().comet_proposal_dims(q, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)))
+    return a.value, b.value, c.value, n.value
+
+
+def comet_proposal_set_params(q, flat):
+    _check(lib().comet_proposal_set_params(q, _ptr(flat)))
+
+
+def comet_proposal_get_params(q, flat, grad=None):
+    _check(lib().comet_proposal_get_params(q, _ptr(flat), _ptr(grad)))
+
+
+def comet_proposal_features(q, seqs, n, out_x):
+    _check(lib().comet_proposal_features(q, _ptr(seqs), n, _ptr(out_x)))
+
+
+def comet_proposal_forward(q, x, n, out_y):
+    _check(lib().comet_proposal_forward(q, _ptr(x), n, _ptr(out_y)))
+
+
+def comet_proposal_train_batch(q, x, target, weight, n, opts=None) -> float:
+    o = opts if isinstance(opts, AdamWOpts) else _fill(AdamWOpts, comet_default_adamw_opts(), opts)
+    loss = ctypes.c_float()
+    _check(lib().comet_proposal_train_batch(q, _ptr(x), _ptr(target), _ptr(weight), n, ctypes.byref(o),
+                                            ctypes.byref(loss)))
+    return loss.value
+
+
+def comet_proposal_add_samples(q, seqs, n, cost, viol, status, traj):
+    _check(lib().comet_proposal_add_samples(q, _ptr(seqs), n, _ptr(cost), _ptr(viol), _ptr(status), _ptr(traj)))
+
+
+def comet_proposal_dataset_size(q) -> int:
+    n = ctypes.c_int64()
+    _check(lib().comet_proposal_dataset_size(q, ctypes.byref(n)))
+    return n.value
+
+
+def comet_proposal_dataset_rows(q, first, n, out_x=None, out_t=None, out_w=None):
+    _check(lib().comet_proposal_dataset_rows(q, first, n, _ptr(out_x), _ptr(out_t), _ptr(out_w)))
+
+
+def proposal_dataset_rows(q, n, first=0):
+    """(targets, weights, feature bits) of n training rows as numpy arrays."""
+    din, _, dout, _ = comet_proposal_dims(q)
+    x = np.zeros((n, din), np.uint16)
+    t = np.zeros((n, dout), np.float32)
+    w = np.zeros((n, dout), np.float32)
+    comet_proposal_dataset_rows(q, first, n, x, t, w)
+    return t, w, x
+
+
+def comet_proposal_train(q, steps, batch, opts=None, seed=0) -> np.ndarray:
+    o = opts if isinstance(opts, AdamWOpts) else _fill(AdamWOpts, comet_default_adamw_opts(), opts)
+    losses = np.zeros(max(steps, 1), dtype=np.float32)
+    _check(lib().comet_proposal_train(q, steps, batch, ctypes.byref(o), seed, losses.ctypes.data))
+    return losses[:steps]
+
+
+def comet_proposal_predict(q, seqs, n, out_merit=None, out_warm=None):
+    _check(lib().comet_proposal_predict(q, _ptr(seqs), n, _ptr(out_merit), _ptr(out_warm)))
+
+
+def comet_proposal_prune(q, frontier, keep, out_warm=None):
+    _check(lib().comet_proposal_prune(q, frontier, keep, _ptr(out_warm)))
+
+
+def comet_gemm_bf16(a, lda, b, ldb, m, n, k, kind=GEMM_STORE, k_splits=1, bias=None, out_f32=None, ld_f32=0,
+                    out_bf16=None, ld_bf16=0, out_bf16_t=None, ld_bf16_t=0, z_in=None, ld_z=0, stream=None):
+    ep = GemmEpilogue(kind, k_splits, _ptr(bias), _ptr(out_f32), ld_f32, _ptr(out_bf16), ld_bf16,
+                      _ptr(out_bf16_t), ld_bf16_t, _ptr(z_in), ld_z)
+    _check(lib().comet_gemm_bf16(_ptr(a), lda, _ptr(b), ldb, m, n, k, ctypes.byref(ep), stream))

@@ -154,12 +154,12 @@ __global__ void topk_chunk_kernel(const TopKey* in_keys, const unsigned long lon
                 key = in_keys[i];
             } else {
                 key.mk = float_key(merit[i]);
-                key.pad = 0;
+                key.idx = (uint32_t)i;
                 key.code = codes[i];
             }
         } else {
             key.mk = 0xffffffffu;
-            key.pad = 0;
+            key.idx = 0xffffffffu;
             key.code = ~0ull;
         }
         sk[t] = key;
@@ -185,9 +185,6 @@ __global__ void topk_chunk_kernel(const TopKey* in_keys, const unsigned long lon
 
 // --------------------------------------------------------- neighbourhood
 
-__device__ __forceinline__ int slots_for(int L, int M, int lmax) {
-    return L * (M - 1) + ((L + 1 <= lmax) ? (L + 1) * M : 0) + ((L - 1 >= 1) ? L : 0);
-}
 
 // Neighbour j of seq (length L) in enumeration order: substitutions
 // (position, mode ascending, skipping the current mode), insertions

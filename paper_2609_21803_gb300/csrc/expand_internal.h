@@ -15,7 +15,7 @@ constexpr int kChunk = 4096;  // keys sorted per CTA in the top-k passes
 
 struct TopKey {
     uint32_t mk;    // order-preserving key of M_hat
-    uint32_t pad;
+    uint32_t idx;   // position of the entry in the ranked array (first pass)
     uint64_t code;  // mode code (tie break)
 };
 
@@ -48,3 +48,13 @@ const TopKey* launch_topk(const FrontierDev& F, int k, cudaStream_t s, cudaError
 cudaError_t launch_expand(const FrontierDev& F, int k, int batch, int64_t budget, cudaStream_t s);
 
 }  // namespace comet
+
+struct comet_problem;
+
+struct comet_frontier {
+    comet_problem* p = nullptr;
+    comet::FrontierDev d;
+    int32_t batch = 0;
+    int32_t k_max = 0;
+    void* blob = nullptr;  // one allocation for all device arrays
+};

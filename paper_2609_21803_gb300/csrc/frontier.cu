@@ -15,13 +15,6 @@
 #include "expand_internal.h"
 #include "problem_internal.h"
 
-struct comet_frontier {
-    comet_problem* p = nullptr;
-    comet::FrontierDev d;
-    int32_t batch = 0;
-    int32_t k_max = 0;
-    void* blob = nullptr;  // one allocation for all device arrays
-};
 
 namespace {
 

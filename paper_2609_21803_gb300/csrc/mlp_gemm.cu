@@ -1,0 +1,394 @@
+// BF16 GEMM on the 5th-generation tensor cores for the learned proposal.
+//
+//   D[M][N] = A[M][K] . B[N][K]^T   (bf16 operands, FP32 accumulation)
+//
+// One CTA computes a 128 x BN tile (BN <= 256) over its share of K:
+//   * warp 0, one lane: TMA producer.  Tiles of 64 K-elements (128 bytes
+//     per row, the 128-byte swizzle span) of A and B are copied into a
+//     4-stage shared-memory ring; each stage's full barrier counts the bytes.
+//   * warp 1, one lane: MMA issuer.  Four tcgen05.mma (kind::f16, K = 16)
+//     per stage accumulate into TMEM (128 lanes x BN FP32 columns); a
+//     tcgen05.commit frees the stage and, after the last, signals the
+//     accumulator barrier.
+//   * warp 2 allocates and frees the TMEM columns.
+//   * all four warps: epilogue.  Warp w reads TMEM lanes 32w..32w+31 (rows
+//     of the tile) 32 columns at a time with tcgen05.ld and applies the
+//     fused epilogue (bias, GELU, GELU' gating, BF16 conversion, the
+//     transposed copy the weight-gradient GEMM consumes, or split-K atomics).
+//
+// Every mbarrier wait is bounded (about one second of clock cycles); when
+// one runs out the CTA records the failure in the error flag, skips the rest
+// of its work, waits (bounded) for the copies it issued and frees its TMEM.
+#include "mlp_internal.h"
+
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace comet {
+namespace mlp {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;           // bf16 elements per 128-byte swizzle row
+constexpr int kStages = 4;
+constexpr int kThreads = 128;
+constexpr int kTmemCols = 256;
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored as rows
+// of 128 bytes with the 128-byte swizzle (the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_128B): 8-row groups 1024 bytes apart (stride byte
+// offset), leading byte offset unused, descriptor version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint16_t to_bf16(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float x) {
+    const float cdf = 0.5f * (1.f + erff(x * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * __expf(-0.5f * x * x);
+    return cdf + x * pdf;
+}
+
+struct __align__(8) Barriers {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t accum;
+    uint32_t tmem_base;
+    uint32_t failed;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
+                     int N, int K, int k_chunk, int bn, Epilogue ep) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    const uint32_t a_bytes = BM * BK * 2;
+    const uint32_t b_bytes = (uint32_t)bn * BK * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    Barriers* bars = reinterpret_cast<Barriers*>(smem + kStages * stage_bytes);
+    const uint32_t s_base = smem_u32(smem);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * bn;
+    const int k_begin = blockIdx.z * k_chunk;
+    const int k_len = min(k_chunk, K - k_begin);
+    const int nkb = (k_len + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&bars->full[s]), 1);
+            mbar_init(smem_u32(&bars->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&bars->accum), 1);
+        bars->failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&bars->tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer
+        int issued = 0;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % kStages;
+            const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+            if (i >= kStages && !mbar_wait(smem_u32(&bars->empty[s]), ph ^ 1u)) {
+                atomicExch(&bars->failed, 1u);
+                break;
+            }
+            if (*(volatile uint32_t*)&bars->failed) break;
+            const uint32_t full = smem_u32(&bars->full[s]);
+            mbar_expect_tx(full, stage_bytes);
+            const int kx = k_begin + i * BK;
+            tma_load_2d(s_base + s * stage_bytes, &map_a, kx, m0, full);
+            tma_load_2d(s_base + s * stage_bytes + a_bytes, &map_b, kx, n0, full);
+            ++issued;
+        }
+        if (*(volatile uint32_t*)&bars->failed) {
+            // wait (bounded) for the copies still in flight before the CTA
+            // can release its shared memory
+            for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
+                mbar_wait(smem_u32(&bars->full[i % kStages]), (uint32_t)(i / kStages) & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = instr_desc(BM, bn);
+        bool ok = true;
+        for (int i = 0; i < nkb && ok; ++i) {
+            const int s = i % kStages;
+            const uint32_t ph = (uint32_t)(i / kStages) & 1u;
+            if (!mbar_wait(smem_u32(&bars->full[s]), ph)) {
+                atomicExch(&bars->failed, 1u);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = s_base + s * stage_bytes, b = a + a_bytes;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, smem_desc(a + kk * 32), smem_desc(b + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(smem_u32(&bars->empty[s]));
+        }
+        mma_commit(smem_u32(&bars->accum));
+    }
+    __syncwarp();
+
+    // ---- epilogue: all warps
+    const bool have = mbar_wait(smem_u32(&bars->accum), 0);
+    if (!have) atomicExch(&bars->failed, 1u);
+    tc_fence_after();
+    __syncwarp();
+    const bool run = __all_sync(0xffffffffu, have && !*(volatile uint32_t*)&bars->failed);
+    const int row = m0 + warp * 32 + lane;
+    const bool row_ok = row < M;
+    if (run) {
+        for (int c0 = 0; c0 < bn; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            const int nb = n0 + c0;
+            if (nb >= N) continue;
+            const int nv = min(32, N - nb);
+            if (ep.kind == kEpiStore) {
+                if (row_ok) {
+                    float* o = ep.out_f32 + (int64_t)row * ep.ld_out + nb;
+                    for (int j = 0; j < nv; ++j) o[j] = v[j] + (ep.bias ? ep.bias[nb + j] : 0.f);
+                }
+            } else if (ep.kind == kEpiAtomicAdd) {
+                if (row_ok) {
+                    float* o = ep.out_f32 + (int64_t)row * ep.ld_out + nb;
+                    for (int j = 0; j < nv; ++j) atomicAdd(o + j, v[j]);
+                }
+            } else {
+                uint16_t hv[32];
+                if (ep.kind == kEpiBiasGelu) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float z = v[j] + ((ep.bias && j < nv) ? ep.bias[nb + j] : 0.f);
+                        v[j] = z;
+                        hv[j] = to_bf16(gelu_f(z));
+                    }
+                    if (row_ok && ep.out_f32) {
+                        float* o = ep.out_f32 + (int64_t)row * ep.ld_out + nb;
+                        for (int j = 0; j < nv; ++j) o[j] = v[j];
+                    }
+                } else {  // kEpiGeluGrad
+                    const float* z = ep.z_in + (int64_t)(row_ok ? row : 0) * ep.ld_z + nb;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) hv[j] = to_bf16((row_ok && j < nv) ? v[j] * gelu_grad_f(z[j]) : 0.f);
+                }
+                if (row_ok && ep.h) {
+                    uint16_t* o = ep.h + (int64_t)row * ep.ld_h + nb;
+                    for (int j = 0; j < nv; ++j) o[j] = hv[j];
+                }
+                if (ep.h_t) {
+                    // transposed copy: for each column, the warp's 32 rows are
+                    // consecutive in memory
+                    for (int j = 0; j < nv; ++j)
+                        if (row_ok) ep.h_t[(int64_t)(nb + j) * ep.ld_ht + row] = hv[j];
+                }
+            }
+        }
+    }
+    if (*(volatile uint32_t*)&bars->failed && threadIdx.x == 0 && ep.err) atomicExch(ep.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+void resolve_encode() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+}
+
+// 2-D tensor map of the leading rows x cols block of a row-major bf16
+// matrix, box = 64 columns x box_rows; reads past the block return zeros
+bool make_map(CUtensorMap* map, const Mat& m, int64_t rows, int64_t cols, int box_rows) {
+    resolve_encode();
+    if (!g_encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)m.ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(m.ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// dynamic shared memory of a launch with column tile bn: at least ~116 KB
+// so that one CTA runs per SM and its 256 TMEM columns never wait for
+// another CTA's
+size_t smem_request(int bn) {
+    const size_t smem = 1024 + (size_t)kStages * (BM * BK * 2 + (size_t)bn * BK * 2) + sizeof(Barriers) + 64;
+    return smem < 118 * 1024 ? 118 * 1024 : smem;
+}
+
+int g_raised[64] = {};
+std::mutex g_raise_mu;
+
+}  // namespace
+
+cudaError_t gemm_prepare() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int need = (int)smem_request(256);
+    std::lock_guard<std::mutex> lk(g_raise_mu);
+    if (dev < 64 && g_raised[dev] >= need) return cudaSuccess;
+    e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e == cudaSuccess && dev < 64) g_raised[dev] = need;
+    return e;
+}
+
+bool tensor_maps_available() {
+    resolve_encode();
+    return g_encode != nullptr;
+}
+
+cudaError_t gemm_bf16(const Mat& A, const Mat& B, int64_t M, int N, int K, int k_splits, const Epilogue& ep,
+                      cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K <= 0 || k_splits < 1 || M > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(A.ptr) & 15u) || (reinterpret_cast<uintptr_t>(B.ptr) & 15u) || (A.ld & 7) ||
+        (B.ld & 7) || A.cols < K || B.cols < K || A.rows < M || B.rows < N)
+        return cudaErrorInvalidValue;
+    if (k_splits > 1 && ep.kind != kEpiAtomicAdd) return cudaErrorInvalidValue;
+    // column tile: N rounded up to 16, at most 256
+    const int n16 = (N + 15) / 16 * 16;
+    const int bn = n16 <= 256 ? n16 : 256;
+    int k_chunk = (K + k_splits - 1) / k_splits;
+    k_chunk = (k_chunk + BK - 1) / BK * BK;
+    const int splits = (K + k_chunk - 1) / k_chunk;
+    CUtensorMap ma, mb;
+    // the maps cover exactly M x K and N x K: padding rows and columns of the
+    // buffers are never read (the copies fill them with zeros)
+    if (!make_map(&ma, A, M, K, BM) || !make_map(&mb, B, N, K, bn)) return cudaErrorInvalidValue;
+    const size_t smem_req = smem_request(bn);
+    cudaError_t e = gemm_prepare();
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + bn - 1) / bn), (unsigned)splits);
+    gemm_bf16_kernel<<<grid, kThreads, smem_req, s>>>(ma, mb, (int)M, N, K, k_chunk, bn, ep);
+    return cudaGetLastError();
+}
+
+}  // namespace mlp
+}  // namespace comet
