@@ -13,10 +13,11 @@
  * TOs.  The evaluator (comet_eval_modes) stays the judge of every returned
  * plan.
  *
- * Input features of an order of length L (in_dim = 8 + 13 L_max rounded up
- * to a multiple of 64, zero padded): start pose (x, y, theta), goal pose,
- * 10 side_x, 10 side_y, then for each slot i < L_max a 13-way one-hot
- * (entries 0..11 = mode m_i, entry 12 = blank when i >= L).
+ * Input features of an order of length L (in_dim = 12 + 13 L_max rounded
+ * up to a multiple of 64, zero padded): start pose (x, y, theta), goal pose,
+ * 10 side_x, 10 side_y, the goal in the start frame (3 R(-theta_s)(g - s)
+ * for x and y, theta_g - theta_s), one zero, then for each slot i < L_max a
+ * 13-way one-hot (entries 0..11 = mode m_i, entry 12 = blank when i >= L).
  * out_dim = 1 + 3 N_max rounded up to a multiple of 16.
  *
  * Parameters (flat FP32 vector, the optimiser's master copy):
@@ -50,7 +51,8 @@ typedef struct {
     uint64_t seed;         /* weight initialisation: U(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases */
     double lambda_w;       /* weight of the control loss (1.0): Omega = lambda_w / (3 N) per control */
     int32_t warm_mode;     /* warm-start states: 0 = Euler rollout of the predicted controls from
-                              the start pose (s reset to 0 at a face change), 1 = cold-start poses */
+                              the start pose (s reset to 0 at a face change), 1 = the cold start's
+                              poses (1; fewer solver iterations in measurements) */
     int32_t reserved;
 } comet_proposal_desc;
 
@@ -134,6 +136,17 @@ comet_status comet_proposal_predict(comet_proposal* q, const comet_mode_seq* seq
  * `keep` are kept in that order and out_warm (device, [keep][stride],
  * nullable) receives their warm starts.  Stays on the device. */
 comet_status comet_proposal_prune(comet_proposal* q, comet_frontier* f, int32_t keep, float* out_warm);
+
+/* Algorithm 1 with the proposal (see comet_plan in comet.h for the options
+ * and the result): the seed batch is warm-started by the proposal; each round
+ * generates the whole one-edit neighbourhood of the k best orders of V, keeps
+ * the opts->batch (<= 4096) best by predicted merit, warm-starts and
+ * evaluates them, and adds them to V; the K_ref best of V are re-solved
+ * from the cold start as in comet_plan, so the evaluator alone scores the
+ * returned plan.  Synchronises the stream. */
+comet_status comet_plan_learned(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
+                                const comet_plan_opts* opts, comet_proposal* q, comet_plan_result* out,
+                                float* out_traj);
 
 /* ---- raw BF16 tensor-core GEMM (device pointers) --------------------------
  * D[M][N] = A[M][K] B[N][K]^T with A, B row-major BF16 (leading dimensions

@@ -25,9 +25,10 @@ Phi(x) + x phi(x).  With ``round_hidden`` the hidden activations (and, in
 the backward pass, the layer gradients) are rounded to BF16 between layers,
 as the GPU stores them; the arithmetic stays float64.
 
-Feature layout of an order m of length L on an instance (in_dim = 8 +
+Feature layout of an order m of length L on an instance (in_dim = 12 +
 13 L_max, padded with zeros to a multiple of 64): start pose (x, y, theta),
-goal pose, 10 side_x, 10 side_y, then one 13-way one-hot per segment slot
+goal pose, 10 side_x, 10 side_y, the goal in the start frame (3 x', 3 y',
+theta_g - theta_s), one zero, then one 13-way one-hot per segment slot
 i < L_max (entries 0..11 = the mode m_i, entry 12 = blank for i >= L).
 
 Output layout (out_dim = 1 + 3 N_max, padded to a multiple of 16): entry 0
@@ -78,18 +79,26 @@ def pad_to(n: int, m: int) -> int:
 
 def dims(l_max: int, n_max: int, width: int = 256, n_modes: int = 12):
     """(in_dim, width, out_dim) of the proposal for an instance family."""
-    return pad_to(8 + (n_modes + 1) * l_max, 64), width, pad_to(1 + 3 * n_max, 16)
+    return pad_to(12 + (n_modes + 1) * l_max, 64), width, pad_to(1 + 3 * n_max, 16)
 
 
 def features(inst: dict, modes, l_max: int, in_dim: int, n_modes: int = 12) -> np.ndarray:
+    s, g = np.asarray(inst["start"], float), np.asarray(inst["goal"], float)
     x = np.zeros(in_dim)
-    x[0:3] = inst["start"]
-    x[3:6] = inst["goal"]
+    x[0:3] = s
+    x[3:6] = g
     x[6] = 10.0 * inst["side_x"]
     x[7] = 10.0 * inst["side_y"]
+    # the goal in the start frame (the quasi-static model is invariant under
+    # planar rigid motions of the world frame): 3 R(-theta_s)(g - s), dtheta
+    d = g[:2] - s[:2]
+    c, sn = np.cos(s[2]), np.sin(s[2])
+    x[8] = 3.0 * (c * d[0] + sn * d[1])
+    x[9] = 3.0 * (-sn * d[0] + c * d[1])
+    x[10] = g[2] - s[2]
     for i in range(l_max):
         e = modes[i] if i < len(modes) else n_modes
-        x[8 + (n_modes + 1) * i + e] = 1.0
+        x[12 + (n_modes + 1) * i + e] = 1.0
     return x
 
 

@@ -106,7 +106,7 @@ EXPORTS = (
     "comet_proposal_dims", "comet_proposal_set_params", "comet_proposal_get_params", "comet_proposal_features",
     "comet_proposal_forward", "comet_proposal_train_batch", "comet_proposal_add_samples",
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
-    "comet_gemm_bf16",
+    "comet_gemm_bf16", "comet_plan_learned",
 )
 
 
@@ -170,6 +170,8 @@ def lib(build_if_missing: bool = False):
             L.comet_proposal_train.argtypes = [vp, i64, i32, ctypes.POINTER(AdamWOpts), ctypes.c_uint64, vp]
             L.comet_proposal_predict.argtypes = [vp, vp, i64, vp, vp]
             L.comet_proposal_prune.argtypes = [vp, vp, i32, vp]
+            L.comet_plan_learned.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), vp,
+                                             ctypes.POINTER(PlanResult), vp]
             L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
             for name in EXPORTS:
                 if name not in ("comet_traj_stride", "comet_mode_code", "comet_last_error",
@@ -343,17 +345,22 @@ def comet_default_plan_opts() -> PlanOpts:
     return o
 
 
-def comet_plan(problem, instance: int, seeds, n_seeds: int, opts=None, out_traj=None) -> dict:
-    """Algorithm 1 on the device (see include/comet.h); opts: PlanOpts, dict
-    or None.  Returns the result as a dict."""
+def comet_plan(problem, instance: int, seeds, n_seeds: int, opts=None, out_traj=None, proposal=None) -> dict:
+    """Algorithm 1 on the device (see include/comet.h; with `proposal`,
+    comet_plan_learned of include/comet_proposal.h); opts: PlanOpts, dict or
+    None.  Returns the result as a dict."""
     if opts is None or isinstance(opts, dict):
         o = comet_default_plan_opts()
         for k, v in (opts or {}).items():
             setattr(o, k, v)
         opts = o
     r = PlanResult()
-    _check(lib().comet_plan(problem, int(instance), _ptr(seeds), int(n_seeds), ctypes.byref(opts), ctypes.byref(r),
-                            _ptr(out_traj)))
+    if proposal is None:
+        _check(lib().comet_plan(problem, int(instance), _ptr(seeds), int(n_seeds), ctypes.byref(opts),
+                                ctypes.byref(r), _ptr(out_traj)))
+    else:
+        _check(lib().comet_plan_learned(problem, int(instance), _ptr(seeds), int(n_seeds), ctypes.byref(opts),
+                                        proposal, ctypes.byref(r), _ptr(out_traj)))
     best = tuple(int(r.best.modes[i]) for i in range(r.best.len))
     return {"best": best, "best_cost": r.best_cost, "best_viol": r.best_viol, "best_status": r.best_status,
             "rounds_run": r.rounds_run, "evaluations": r.evaluations, "explore_ms": r.explore_ms,

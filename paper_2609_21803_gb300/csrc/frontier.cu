@@ -12,7 +12,9 @@
 
 #include "comet.h"
 #include "comet_internal.h"
+#include "comet_proposal.h"
 #include "expand_internal.h"
+#include "mlp_internal.h"
 #include "problem_internal.h"
 
 
@@ -310,8 +312,14 @@ extern "C" comet_status comet_default_plan_opts(comet_plan_opts* po) {
     return COMET_OK;
 }
 
-extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
-                                   const comet_plan_opts* po_in, comet_plan_result* out, float* out_traj) {
+namespace comet {
+
+// Algorithm 1 on the device; with a proposal q every expansion round
+// generates the whole neighbourhood of the beam, keeps the `batch` best
+// candidates by predicted merit and warm-starts them, and the seed batch is
+// warm-started too.
+comet_status plan_impl(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
+                       const comet_plan_opts* po_in, comet_proposal* q, comet_plan_result* out, float* out_traj) {
     if (!p || !seeds || !out || n_seeds < 1) return ffail(COMET_ERR_INVALID_ARG, "problem, seeds and out are required");
     comet_plan_opts po;
     if (po_in)
@@ -354,8 +362,14 @@ extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const com
     const int64_t capacity =
         po.budget > 0 ? std::max<int64_t>(po.budget, n0) : n0 + (int64_t)po.rounds * po.batch;
     const int32_t batch = (int32_t)std::min<int64_t>(po.batch, capacity);
+    if (q && batch > comet::kChunk) return ffail(COMET_ERR_INVALID_ARG, "a learned plan keeps at most 4096 per round");
+    // with a proposal the frontier's next batch holds the whole neighbourhood
+    // of the beam, which the proposal then prunes to `batch`
+    const comet_instance_desc& di = p->inst[instance];
+    const int slots = di.max_segments * (di.n_modes - 1) + (di.max_segments + 1) * di.n_modes + di.max_segments;
+    const int32_t cand = q ? (int32_t)std::min<int64_t>((int64_t)po.k * slots, capacity) : batch;
     comet_frontier* f = nullptr;
-    comet_status st = comet_frontier_create(p, instance, capacity, batch, std::max(po.k, po.k_ref), &f);
+    comet_status st = comet_frontier_create(p, instance, capacity, std::max(cand, batch), std::max(po.k, po.k_ref), &f);
     if (st != COMET_OK) return st;
     struct Guard {
         comet_frontier* f;
@@ -364,6 +378,17 @@ extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const com
     const int64_t n_eval_max = std::max<int64_t>({n0, (int64_t)batch, (int64_t)po.k_ref});
     st = comet::reserve_eval(p, n_eval_max);
     if (st != COMET_OK) return st;
+    DevBuf warm_buf, rows_buf;
+    float* d_warm = nullptr;
+    int* d_rows = nullptr;
+    if (q) {
+        st = comet::proposal_reserve_prune(q, std::max<int64_t>(f->batch, n0), batch);
+        if (st != COMET_OK) return st;
+        FTRY(cudaMalloc(&warm_buf.p, sizeof(float) * p->stride * std::max<int64_t>(n0, batch)), "warm starts");
+        FTRY(cudaMalloc(&rows_buf.p, sizeof(int) * batch), "rows");
+        d_warm = (float*)warm_buf.p;
+        d_rows = (int*)rows_buf.p;
+    }
     DevBuf buf;
     const size_t b_seq = sizeof(comet_mode_seq) * n_eval_max;
     const size_t b_f = sizeof(float) * n_eval_max;
@@ -385,7 +410,11 @@ extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const com
     FTRY(cudaEventRecord(ev[0], s), "event");
     // seed batch F_0: evaluate with t_exp and add to V
     FTRY(cudaMemcpyAsync(d_seqs, seeds, sizeof(comet_mode_seq) * n0, cudaMemcpyDefault, s), "copy seeds");
-    st = comet::launch_eval_device(p, d_seqs, n0, nullptr, nullptr, 0, d_cost, nullptr, d_status);
+    if (q) {
+        st = comet::proposal_predict_device(q, d_seqs, n0, nullptr, d_warm, s);
+        if (st != COMET_OK) return st;
+    }
+    st = comet::launch_eval_device(p, d_seqs, n0, nullptr, d_warm, 0, d_cost, nullptr, d_status);
     if (st != COMET_OK) return st;
     comet::FrontierDev F = f->d;
     FTRY(comet::launch_frontier_add(F, d_seqs, n0, nullptr, d_cost, p->d_viol, (float)p->opts.eps_feas,
@@ -393,9 +422,13 @@ extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const com
          "add seeds");
     // one round: expand, evaluate F_{s+1} (count read on the device), add
     auto round = [&]() -> comet_status {
-        cudaError_t e = comet::launch_expand(F, po.k, batch, po.budget, s);
+        cudaError_t e = comet::launch_expand(F, po.k, q ? f->batch : batch, po.budget, s);
         if (e != cudaSuccess) return fcuda(e, "expand");
-        comet_status r = comet::launch_eval_device(p, F.next, batch, F.n_next, nullptr, 0, d_cost, nullptr, d_status);
+        if (q) {
+            const comet_status r = comet::proposal_prune_device(q, f, batch, d_warm, d_rows, s);
+            if (r != COMET_OK) return r;
+        }
+        comet_status r = comet::launch_eval_device(p, F.next, batch, F.n_next, d_warm, 0, d_cost, nullptr, d_status);
         if (r != COMET_OK) return r;
         comet::FrontierDev Fa = F;
         Fa.batch_cap = batch;
@@ -493,4 +526,18 @@ extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const com
     cudaEventElapsedTime(&out->refine_ms, ev[2], ev[3]);
     if (err) return ffail(COMET_ERR_BUDGET, "the evaluated set overflowed its capacity");
     return COMET_OK;
+}
+
+}  // namespace comet
+
+extern "C" comet_status comet_plan(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
+                                   const comet_plan_opts* opts, comet_plan_result* out, float* out_traj) {
+    return comet::plan_impl(p, instance, seeds, n_seeds, opts, nullptr, out, out_traj);
+}
+
+extern "C" comet_status comet_plan_learned(comet_problem* p, int32_t instance, const comet_mode_seq* seeds,
+                                           int64_t n_seeds, const comet_plan_opts* opts, comet_proposal* q,
+                                           comet_plan_result* out, float* out_traj) {
+    if (!q) return ffail(COMET_ERR_INVALID_ARG, "proposal is required");
+    return comet::plan_impl(p, instance, seeds, n_seeds, opts, q, out, out_traj);
 }

@@ -29,6 +29,7 @@
 namespace {
 
 constexpr int kLayers = 4;
+constexpr int kInstFeat = 12;  // per-instance features ahead of the one-hot slots
 
 }  // namespace
 
@@ -45,7 +46,7 @@ struct comet_proposal {
     float* m2 = nullptr;
     uint16_t* wq[kLayers] = {};   // bf16 W_l [dout][din]
     uint16_t* wqt[kLayers] = {};  // bf16 W_l^T [din][dout]
-    float* feat_inst = nullptr;   // [n_inst][8]
+    float* feat_inst = nullptr;   // [n_inst][kInstFeat]
     int64_t* d_step = nullptr;    // AdamW step count t
     float* d_loss = nullptr;
     int* d_err = nullptr;
@@ -235,10 +236,10 @@ __global__ void features_kernel(const comet_mode_seq* seqs, int64_t n_rows, cons
         if (i < nn) {
             const comet_mode_seq s = seqs[i];
             if (s.instance >= 0 && s.instance < n_inst && s.len >= 1 && s.len <= l_max) {
-                if (c < 8) {
-                    x = fi[s.instance * 8 + c];
-                } else if (c < 8 + (n_modes + 1) * l_max) {
-                    const int slot = (c - 8) / (n_modes + 1), e = (c - 8) % (n_modes + 1);
+                if (c < kInstFeat) {
+                    x = fi[s.instance * kInstFeat + c];
+                } else if (c < kInstFeat + (n_modes + 1) * l_max) {
+                    const int slot = (c - kInstFeat) / (n_modes + 1), e = (c - kInstFeat) % (n_modes + 1);
                     const int want = slot < s.len ? (int)s.modes[slot] : n_modes;
                     x = (e == want) ? 1.f : 0.f;
                 }
@@ -692,7 +693,7 @@ void comet_default_proposal_desc(comet_proposal_desc* d) {
     d->dataset_cap = 0;
     d->seed = 1;
     d->lambda_w = 1.0;
-    d->warm_mode = 0;
+    d->warm_mode = 1;
 }
 
 void comet_default_adamw_opts(comet_adamw_opts* o) {
@@ -733,7 +734,7 @@ comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* 
     q->n_modes = n_modes;
     q->n_max = p->Nmax;
     q->n_inst = (int)p->inst.size();
-    q->in_dim = (int)pad_to(8 + (int64_t)(n_modes + 1) * l_max, 64);
+    q->in_dim = (int)pad_to(kInstFeat + (int64_t)(n_modes + 1) * l_max, 64);
     q->width = d.width;
     q->out_dim = (int)pad_to(1 + 3 * (int64_t)p->Nmax, 16);
     const int dims[kLayers + 1] = {q->in_dim, q->width, q->width, q->width, q->out_dim};
@@ -755,7 +756,7 @@ comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* 
     cudaStream_t s = p->stream;
     if ((e = qalloc(q, &q->master, off)) != cudaSuccess || (e = qalloc(q, &q->grad, off)) != cudaSuccess ||
         (e = qalloc(q, &q->m1, off)) != cudaSuccess || (e = qalloc(q, &q->m2, off)) != cudaSuccess ||
-        (e = qalloc(q, &q->feat_inst, (size_t)q->n_inst * 8)) != cudaSuccess ||
+        (e = qalloc(q, &q->feat_inst, (size_t)q->n_inst * kInstFeat)) != cudaSuccess ||
         (e = qalloc(q, &q->d_step, 1)) != cudaSuccess || (e = qalloc(q, &q->d_loss, 1)) != cudaSuccess ||
         (e = qalloc(q, &q->d_err, 1)) != cudaSuccess)
         return cleanup(qcuda(e, "proposal allocation"));
@@ -771,15 +772,22 @@ comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* 
             (e = qalloc(q, &q->ds_Om, (size_t)d.dataset_cap * q->out_dim)) != cudaSuccess)
             return cleanup(qcuda(e, "proposal training set"));
     }
-    std::vector<float> fi((size_t)q->n_inst * 8);
+    std::vector<float> fi((size_t)q->n_inst * kInstFeat, 0.f);
     for (int i = 0; i < q->n_inst; ++i) {
         const comet_instance_desc& D = p->inst[i];
+        float* f = fi.data() + (size_t)i * kInstFeat;
         for (int c = 0; c < 3; ++c) {
-            fi[i * 8 + c] = (float)D.start[c];
-            fi[i * 8 + 3 + c] = (float)D.goal[c];
+            f[c] = (float)D.start[c];
+            f[3 + c] = (float)D.goal[c];
         }
-        fi[i * 8 + 6] = (float)(10.0 * D.side_x);
-        fi[i * 8 + 7] = (float)(10.0 * D.side_y);
+        f[6] = (float)(10.0 * D.side_x);
+        f[7] = (float)(10.0 * D.side_y);
+        // the goal in the start frame: 3 R(-theta_s)(g - s), dtheta
+        const double dx = D.goal[0] - D.start[0], dy = D.goal[1] - D.start[1];
+        const double c = cos(D.start[2]), sn = sin(D.start[2]);
+        f[8] = (float)(3.0 * (c * dx + sn * dy));
+        f[9] = (float)(3.0 * (-sn * dx + c * dy));
+        f[10] = (float)(D.goal[2] - D.start[2]);
     }
     if ((e = cudaMemcpyAsync(q->feat_inst, fi.data(), sizeof(float) * fi.size(), cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)

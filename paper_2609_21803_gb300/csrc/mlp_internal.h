@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "comet.h"
+#include "comet_proposal.h"
+
 namespace comet {
 namespace mlp {
 
@@ -54,4 +57,12 @@ bool tensor_maps_available();
 cudaError_t gemm_prepare();
 
 }  // namespace mlp
+
+// The proposal's device-side steps used by the learned planner (mlp.cu).
+comet_status proposal_reserve_prune(comet_proposal* q, int64_t cap, int keep);
+comet_status proposal_prune_device(comet_proposal* q, comet_frontier* f, int keep, float* warm, int* row_scratch,
+                                   cudaStream_t s);
+comet_status proposal_predict_device(comet_proposal* q, const comet_mode_seq* seqs, int64_t n, float* merit,
+                                     float* warm, cudaStream_t s);
+
 }  // namespace comet

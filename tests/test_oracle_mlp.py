@@ -133,7 +133,20 @@ def test_features_layout():
     assert (din, width, dout) == (64, 256, 256)
     x = mlp.features(inst, (3, 11), 4, din)
     np.testing.assert_allclose(x[:8], [0.1, -0.2, 0.3, 0.4, 0.5, -0.6, 0.9, 1.2])
-    onehot = x[8:60].reshape(4, 13)
+    onehot = x[12:64].reshape(4, 13)
     assert onehot.sum() == 4 and onehot[0, 3] == 1 and onehot[1, 11] == 1
-    assert onehot[2, 12] == 1 and onehot[3, 12] == 1 and np.all(x[60:] == 0)
+    assert onehot[2, 12] == 1 and onehot[3, 12] == 1 and x[11] == 0
     assert mlp.dims(6, 180) == (128, 256, 544)
+    # goal in the start frame: start rotated by +90 degrees, goal one unit
+    # ahead along the world y axis -> (x', y') = (3, 0), dtheta = 0.25
+    x = mlp.features({"start": [1.0, 2.0, np.pi / 2], "goal": [1.0, 3.0, np.pi / 2 + 0.25], "side_x": 0.1,
+                      "side_y": 0.1}, (0,), 4, din)
+    np.testing.assert_allclose(x[8:11], [3.0, 0.0, 0.25], atol=1e-12)
+    # invariance: a planar rigid motion of the world frame leaves 8..10 fixed
+    a, t = 0.7, np.array([0.3, -0.1])
+    R = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+    s0, g0 = np.array([0.1, -0.2, 0.3]), np.array([0.4, 0.5, -0.6])
+    moved = {"start": np.r_[R @ s0[:2] + t, s0[2] + a], "goal": np.r_[R @ g0[:2] + t, g0[2] + a],
+             "side_x": 0.09, "side_y": 0.12}
+    np.testing.assert_allclose(mlp.features(moved, (3, 11), 4, din)[8:11], mlp.features(inst, (3, 11), 4, din)[8:11],
+                               atol=1e-12)
