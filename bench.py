@@ -279,6 +279,8 @@ def run_gpu(args):
     }
     if rank == 0 and args.plan_instances > 0:
         line["plan"] = plan_times(P, insts[: args.plan_instances])
+    if rank == 0 and args.learned_instances > 0:
+        line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and not args.no_cpu_baseline:
         conv_rate, rate, ns, cores, dt = oracle_rate(insts)
         line["cpu_baseline"] = {"value": conv_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -322,6 +324,108 @@ def plan_times(P, insts):
     return out
 
 
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
+# multiply-adds per row of the proposal MLP (64 -> 256 -> 256 -> 256 -> 256)
+MLP_MACS = 64 * 256 + 2 * 256 * 256 + 256 * 256
+
+
+def learned_times(P, insts, n_eval):
+    """The learned proposal on the same workload family: a training set of
+    about 1M evaluator results (512 random 4-segment instances, seeds
+    1000..1511, 2,048 random orders each, solved by the GPU evaluator), 3,000
+    AdamW steps of 4,096 samples on the tensor cores, then the planner with
+    and without the proposal on held-out instances (seeds 48.., plain: B =
+    4096; learned: the 512 best neighbours by predicted merit, warm-started;
+    both beam 64, s_max = 3, K_ref = 256)."""
+    import torch
+
+    every = [(m,) for m in range(12)] + [tuple(s) for s in W.all_sequences(12, 2)] + \
+        [tuple(s) for s in W.all_sequences(12, 3)] + [tuple(s) for s in W.all_sequences(12, 4)]
+    n_inst, per = 512, 2048
+    tr = [W.push_l4_instance(1000 + s) for s in range(n_inst)]
+    prob = P.Problem(tr)
+    q = P.comet_proposal_create(prob.handle, {"dataset_cap": n_inst * per})
+    rng = np.random.default_rng(0)
+    pick = rng.integers(0, len(every), size=n_inst * per)
+    packed = P.pack_mode_seqs([every[j] for j in pick], np.repeat(np.arange(n_inst, dtype=np.int32), per))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for a in range(0, len(packed), 65536):
+        d = torch.from_numpy(packed[a:a + 65536].view(np.uint8).reshape(-1, 24)).cuda()
+        r = prob.eval(d, want_traj=True)
+        P.comet_proposal_add_samples(q, d, len(d), r["cost"], r["viol"], r["status"], r["traj"])
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    steps = 3000
+    t0 = time.time()
+    losses = np.concatenate([P.comet_proposal_train(q, steps // 2, 4096, {"lr": 1e-3}, seed=1),
+                             P.comet_proposal_train(q, steps // 4, 4096, {"lr": 3e-4}, seed=2),
+                             P.comet_proposal_train(q, steps // 4, 4096, {"lr": 1e-4}, seed=3)])
+    t_train = time.time() - t0
+    _, _, _, npar = P.comet_proposal_dims(q)
+    flat = np.zeros(npar, np.float32)
+    P.comet_proposal_get_params(q, flat)
+    # forward over one 4-segment enumeration (20,736 rows), device buffers
+    rows = 20736
+    x = torch.zeros((rows, 64), dtype=torch.int16, device="cuda")
+    P.comet_proposal_features(q, torch.from_numpy(packed[:rows].view(np.uint8).reshape(-1, 24)).cuda(), rows, x)
+    y = torch.empty((rows, 256), dtype=torch.float32, device="cuda")
+    P.comet_proposal_forward(q, x, rows, y)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        P.comet_proposal_forward(q, x, rows, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 1e3 / reps
+    P.comet_proposal_destroy(q)
+    prob.close()
+    peak, kind = measured_peak("bf16_tflops", 1900.0)
+    fwd_tflops = 2.0 * MLP_MACS * rows / fwd_s / 1e12
+    train_flop = 2.0 * (3 * MLP_MACS - 64 * 256) * 4096
+    train_tflops = train_flop * steps / t_train / 1e12
+    # the ablation on held-out instances
+    seeds = [(m,) for m in range(12)] + [tuple(s) for s in W.all_sequences(12, 2)]
+    ps = P.pack_mode_seqs(seeds)
+    same, pl_ms, le_ms, pl_ev, le_ev = 0, [], [], [], []
+    for i in range(48, 48 + n_eval):
+        pr = P.Problem([insts[i % len(insts)]])
+        a = P.comet_plan(pr.handle, 0, ps, len(ps), dict(k=64, batch=4096, rounds=3, k_ref=256))
+        qq = P.comet_proposal_create(pr.handle)
+        P.comet_proposal_set_params(qq, flat)
+        b = P.comet_plan(pr.handle, 0, ps, len(ps), dict(k=64, batch=512, rounds=3, k_ref=256), proposal=qq)
+        P.comet_proposal_destroy(qq)
+        pr.close()
+        same += b["best_cost"] <= a["best_cost"] * (1 + 1e-3) + 1e-9
+        pl_ms.append(a["explore_ms"] + a["refine_ms"])
+        le_ms.append(b["explore_ms"] + b["refine_ms"])
+        pl_ev.append(a["evaluations"])
+        le_ev.append(b["evaluations"])
+    return {
+        "dataset_samples": n_inst * per, "dataset_s": t_data, "train_steps": steps, "train_batch": 4096,
+        "train_s": t_train, "train_samples_per_s": steps * 4096 / t_train,
+        "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-100:].mean()),
+        "forward_rows": rows, "forward_ms": fwd_s * 1e3,
+        "roofline": {"kernel": "tcgen05 BF16 GEMM (4 layers, fused epilogues)", "bound": "tensor",
+                     "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tflops / peak,
+                     "peak_kind": f"{kind} bf16 (burst)", "train_step_tflops": train_tflops},
+        "instances": n_eval, "same_best": same,
+        "plain_ms": float(np.median(pl_ms)), "learned_ms": float(np.median(le_ms)),
+        "plain_evals": float(np.median(pl_ev)), "learned_evals": float(np.median(le_ev)),
+        "plan_speedup": float(np.median(pl_ms) / np.median(le_ms)),
+        "note": "plan times are device time (medians); same_best = learned plan within 1e-3 of plain expansion's",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--orders", type=int, default=0, help="profiling only: solve this prefix of each enumeration")
     ap.add_argument("--plan-instances", type=int, default=4, help="instances for the plan-time comparison (0 = skip)")
+    ap.add_argument("--learned-instances", type=int, default=8,
+                    help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
