@@ -2,7 +2,7 @@
 //
 //   D[M][N] = A[M][K] . B[N][K]^T   (bf16 operands, FP32 accumulation)
 //
-// One CTA computes a 128 x BN tile (BN <= 256) over its share of K:
+// One CTA computes a 128 x BN tile (BN <= 64) over its share of K:
 //   * warp 0, one lane: TMA producer.  Tiles of 64 K-elements (128 bytes
 //     per row, the 128-byte swizzle span) of A and B are copied into a
 //     4-stage shared-memory ring; each stage's full barrier counts the bytes.
@@ -12,9 +12,11 @@
 //     accumulator barrier.
 //   * warp 2 allocates and frees the TMEM columns.
 //   * all four warps: epilogue.  Warp w reads TMEM lanes 32w..32w+31 (rows
-//     of the tile) 32 columns at a time with tcgen05.ld and applies the
-//     fused epilogue (bias, GELU, GELU' gating, BF16 conversion, the
-//     transposed copy the weight-gradient GEMM consumes, or split-K atomics).
+//     of the tile) 32 columns at a time with tcgen05.ld, turns each 32 x 32
+//     block around in shared memory and applies the fused epilogue (bias,
+//     GELU, GELU' gating, BF16 conversion, the transposed copy the
+//     weight-gradient GEMM consumes, or split-K atomics) with coalesced
+//     stores.
 //
 // Every mbarrier wait is bounded (about one second of clock cycles); when
 // one runs out the CTA records the failure in the error flag, skips the rest
@@ -34,7 +36,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;           // bf16 elements per 128-byte swizzle row
 constexpr int kStages = 4;
 constexpr int kThreads = 128;
-constexpr int kTmemCols = 256;
+constexpr int kMaxBN = 64;  // column tile: more CTAs for the small GEMMs of the MLP
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -157,7 +159,7 @@ struct __align__(8) Barriers {
 
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
-                     int N, int K, int k_chunk, int bn, Epilogue ep) {
+                     int N, int K, int k_chunk, int bn, int tmem_cols, Epilogue ep) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&bars->tmem_base)),
-                     "r"(kTmemCols)
+                     "r"(tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -247,54 +249,61 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     __syncwarp();
     const bool run = __all_sync(0xffffffffu, have && !*(volatile uint32_t*)&bars->failed);
-    const int row = m0 + warp * 32 + lane;
-    const bool row_ok = row < M;
+    // Each 32 x 32 block of the accumulator goes through shared memory (the
+    // pipeline stages are free once the accumulator is complete), so that
+    // row-major outputs are written with lanes along a row and the
+    // transposed copy with lanes along a column: every store is coalesced.
+    // Warp w stages in its own two 32 x 33 tiles (raw accumulator, result).
     if (run) {
+        float* st1 = reinterpret_cast<float*>(smem) + warp * (2 * 32 * 33);
+        float* st2 = st1 + 32 * 33;
+        const int row0 = m0 + warp * 32;
         for (int c0 = 0; c0 < bn; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             const int nb = n0 + c0;
             if (nb >= N) continue;
-            const int nv = min(32, N - nb);
-            if (ep.kind == kEpiStore) {
-                if (row_ok) {
-                    float* o = ep.out_f32 + (int64_t)row * ep.ld_out + nb;
-                    for (int j = 0; j < nv; ++j) o[j] = v[j] + (ep.bias ? ep.bias[nb + j] : 0.f);
-                }
-            } else if (ep.kind == kEpiAtomicAdd) {
-                if (row_ok) {
-                    float* o = ep.out_f32 + (int64_t)row * ep.ld_out + nb;
-                    for (int j = 0; j < nv; ++j) atomicAdd(o + j, v[j]);
-                }
-            } else {
-                uint16_t hv[32];
-                if (ep.kind == kEpiBiasGelu) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float z = v[j] + ((ep.bias && j < nv) ? ep.bias[nb + j] : 0.f);
-                        v[j] = z;
-                        hv[j] = to_bf16(gelu_f(z));
-                    }
-                    if (row_ok && ep.out_f32) {
-                        float* o = ep.out_f32 + (int64_t)row * ep.ld_out + nb;
-                        for (int j = 0; j < nv; ++j) o[j] = v[j];
-                    }
+            for (int j = 0; j < 32; ++j) st1[lane * 33 + j] = v[j];
+            __syncwarp();
+            // lanes along a row: column nb + lane
+            const int col = nb + lane;
+            const bool col_ok = col < N;
+            const float bias = (ep.bias && col_ok) ? ep.bias[col] : 0.f;
+            for (int r = 0; r < 32; ++r) {
+                const int row = row0 + r;
+                const bool ok = col_ok && row < M;
+                const float a = st1[r * 33 + lane];
+                float res = 0.f;
+                if (ep.kind == kEpiStore) {
+                    if (ok) ep.out_f32[(int64_t)row * ep.ld_out + col] = a + bias;
+                } else if (ep.kind == kEpiAtomicAdd) {
+                    if (ok) atomicAdd(ep.out_f32 + (int64_t)row * ep.ld_out + col, a);
+                } else if (ep.kind == kEpiBiasGelu) {
+                    const float z = a + bias;
+                    if (ok && ep.out_f32) ep.out_f32[(int64_t)row * ep.ld_out + col] = z;
+                    res = gelu_f(z);
                 } else {  // kEpiGeluGrad
-                    const float* z = ep.z_in + (int64_t)(row_ok ? row : 0) * ep.ld_z + nb;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) hv[j] = to_bf16((row_ok && j < nv) ? v[j] * gelu_grad_f(z[j]) : 0.f);
+                    const float z = ok ? ep.z_in[(int64_t)row * ep.ld_z + col] : 0.f;
+                    res = a * gelu_grad_f(z);
                 }
-                if (row_ok && ep.h) {
-                    uint16_t* o = ep.h + (int64_t)row * ep.ld_h + nb;
-                    for (int j = 0; j < nv; ++j) o[j] = hv[j];
-                }
-                if (ep.h_t) {
-                    // transposed copy: for each column, the warp's 32 rows are
-                    // consecutive in memory
-                    for (int j = 0; j < nv; ++j)
-                        if (row_ok) ep.h_t[(int64_t)(nb + j) * ep.ld_ht + row] = hv[j];
+                if (ep.kind == kEpiBiasGelu || ep.kind == kEpiGeluGrad) {
+                    const uint16_t hb = to_bf16(res);
+                    if (ok && ep.h) ep.h[(int64_t)row * ep.ld_h + col] = hb;
+                    st2[r * 33 + lane] = __uint_as_float((uint32_t)hb);
                 }
             }
+            __syncwarp();
+            if (ep.h_t && (ep.kind == kEpiBiasGelu || ep.kind == kEpiGeluGrad)) {
+                // lanes along a column of the transposed copy: row row0 + lane
+                const int row = row0 + lane;
+                if (row < M) {
+                    const int nv = min(32, N - nb);
+                    for (int j = 0; j < nv; ++j)
+                        ep.h_t[(int64_t)(nb + j) * ep.ld_ht + row] = (uint16_t)__float_as_uint(st2[lane * 33 + j]);
+                }
+            }
+            __syncwarp();
         }
     }
     if (*(volatile uint32_t*)&bars->failed && threadIdx.x == 0 && ep.err) atomicExch(ep.err, 1);
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 2) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
     }
 }
 
@@ -334,12 +343,10 @@ bool make_map(CUtensorMap* map, const Mat& m, int64_t rows, int64_t cols, int bo
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// dynamic shared memory of a launch with column tile bn: at least ~116 KB
-// so that one CTA runs per SM and its 256 TMEM columns never wait for
-// another CTA's
+// dynamic shared memory of a launch with column tile bn (at most two CTAs
+// fit on an SM, holding 2 x 64 of its 512 TMEM columns)
 size_t smem_request(int bn) {
-    const size_t smem = 1024 + (size_t)kStages * (BM * BK * 2 + (size_t)bn * BK * 2) + sizeof(Barriers) + 64;
-    return smem < 118 * 1024 ? 118 * 1024 : smem;
+    return 1024 + (size_t)kStages * (BM * BK * 2 + (size_t)bn * BK * 2) + sizeof(Barriers) + 64;
 }
 
 int g_raised[64] = {};
@@ -351,7 +358,7 @@ cudaError_t gemm_prepare() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const int need = (int)smem_request(256);
+    const int need = (int)smem_request(kMaxBN);
     std::lock_guard<std::mutex> lk(g_raise_mu);
     if (dev < 64 && g_raised[dev] >= need) return cudaSuccess;
     e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
@@ -372,9 +379,12 @@ cudaError_t gemm_bf16(const Mat& A, const Mat& B, int64_t M, int N, int K, int k
         (B.ld & 7) || A.cols < K || B.cols < K || A.rows < M || B.rows < N)
         return cudaErrorInvalidValue;
     if (k_splits > 1 && ep.kind != kEpiAtomicAdd) return cudaErrorInvalidValue;
-    // column tile: N rounded up to 16, at most 256
+    // column tile: N rounded up to 16, at most kMaxBN; TMEM columns: a power
+    // of two >= 32 covering the tile
     const int n16 = (N + 15) / 16 * 16;
-    const int bn = n16 <= 256 ? n16 : 256;
+    const int bn = n16 <= kMaxBN ? n16 : kMaxBN;
+    int tmem_cols = 32;
+    while (tmem_cols < bn) tmem_cols <<= 1;
     int k_chunk = (K + k_splits - 1) / k_splits;
     k_chunk = (k_chunk + BK - 1) / BK * BK;
     const int splits = (K + k_chunk - 1) / k_chunk;
@@ -386,7 +396,7 @@ cudaError_t gemm_bf16(const Mat& A, const Mat& B, int64_t M, int N, int K, int k
     cudaError_t e = gemm_prepare();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + bn - 1) / bn), (unsigned)splits);
-    gemm_bf16_kernel<<<grid, kThreads, smem_req, s>>>(ma, mb, (int)M, N, K, k_chunk, bn, ep);
+    gemm_bf16_kernel<<<grid, kThreads, smem_req, s>>>(ma, mb, (int)M, N, K, k_chunk, bn, tmem_cols, ep);
     return cudaGetLastError();
 }
 
