@@ -279,6 +279,8 @@ def run_gpu(args):
     }
     if rank == 0 and args.plan_instances > 0:
         line["plan"] = plan_times(P, insts[: args.plan_instances])
+    if rank == 0 and args.hetero:
+        line["hetero"] = hetero_times(P)
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and not args.no_cpu_baseline:
@@ -322,6 +324,64 @@ def plan_times(P, insts):
     out["speedup"] = out["enumeration_ms"] / out["expansion_ms"]
     out["note"] = "median over instances; recovered = expansion's refined best within 1e-3 of enumeration's"
     return out
+
+
+def hetero_times(P, n_inst=256, per=512, n_split=32):
+    """The mixed workload (rectangular sliders of side 0.05-0.15 m and aspect
+    1-3, mu ~ U[0.2, 0.6], length caps 1..6, 10..30 knots per segment, seeds
+    0..255), 512 random orders per instance (length uniform in 1..cap):
+    every order of every instance in ONE persistent launch (longest TO
+    first, launch shape from the autotuner), against one launch per instance
+    for the first `n_split` instances.  Device time, converged solves/s."""
+    import torch
+
+    insts = [W.push_mixed_instance(s) for s in range(n_inst)]
+    rng = np.random.default_rng(7)
+    seqs, idx = [], []
+    for i, inst in enumerate(insts):
+        for _ in range(per):
+            L = int(rng.integers(1, inst["max_segments"] + 1))
+            seqs.append(tuple(int(m) for m in rng.integers(0, 12, L)))
+            idx.append(i)
+    packed = P.pack_mode_seqs(seqs, np.array(idx, np.int32))
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), 24)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(prob, dd):
+        prob.eval(dd)  # warm (workspace, attributes)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = prob.eval(dd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        conv = int(((r["status"] == 0) & (r["viol"] < 1e-5)).sum())
+        return e0.elapsed_time(e1) / 1e3, conv
+
+    prob = P.Problem(insts)
+    pick, times = P.comet_autotune(prob.handle, d[:8192], 8192, 40)
+    t_one, c_one = timed(prob, d)
+    # the same first n_split instances: one launch vs one per instance
+    m = n_split * per
+    t_sub, c_sub = timed(prob, d[:m])
+    prob.close()
+    t_per, c_per = 0.0, 0
+    for i in range(n_split):
+        pr = P.Problem([insts[i]])
+        sub = P.pack_mode_seqs(seqs[i * per:(i + 1) * per])
+        t, c = timed(pr, torch.from_numpy(sub.view(np.uint8).reshape(per, 24)).cuda())
+        t_per += t
+        c_per += c
+        pr.close()
+    return {
+        "instances": n_inst, "orders": len(seqs), "n_max": int(max(x["knots_per_segment"] * x["max_segments"]
+                                                                    for x in insts)),
+        "autotuned": pick, "autotune_candidate_ms": times,
+        "one_launch_solves_per_s": c_one / t_one, "one_launch_ms": t_one * 1e3,
+        "split_instances": n_split, "split_one_launch_solves_per_s": c_sub / t_sub,
+        "split_per_instance_solves_per_s": c_per / t_per, "split_per_instance_ms": t_per * 1e3,
+        "split_one_launch_ms": t_sub * 1e3,
+        "note": "converged solves/s (device time); one launch over all instances vs one launch per instance",
+    }
 
 
 def measured_peak(key, fallback):
@@ -435,6 +495,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--orders", type=int, default=0, help="profiling only: solve this prefix of each enumeration")
     ap.add_argument("--plan-instances", type=int, default=4, help="instances for the plan-time comparison (0 = skip)")
+    ap.add_argument("--hetero", type=int, default=1, help="mixed-workload leg (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=8,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()

@@ -282,6 +282,34 @@ comet_status comet_default_plan_opts(comet_plan_opts* po);
 comet_status comet_plan(comet_problem* p, int32_t instance, const comet_mode_seq* seeds, int64_t n_seeds,
                         const comet_plan_opts* opts, comet_plan_result* out, float* out_traj);
 
+/* ---- launch shape of the persistent evaluator and its autotuner ------- */
+
+typedef struct {
+    int32_t warps_per_block;    /* TOs per CTA (one warp per TO): 1..4 (default 4) */
+    int32_t blocks_per_sm;      /* resident CTAs per SM the grid is sized for */
+    int32_t max_blocks_per_sm;  /* occupancy limit of warps_per_block (get only) */
+    int32_t reserved;
+} comet_launch_config;
+
+/* The problem's current launch shape. */
+comet_status comet_get_launch_config(comet_problem* p, comet_launch_config* out);
+
+/* Set the launch shape (warps_per_block in 1..4, blocks_per_sm in 1..the
+ * occupancy limit; INVALID_ARG otherwise).  Results never depend on it: every
+ * shape solves each TO in one warp with the same arithmetic.  Synchronises. */
+comet_status comet_set_launch_config(comet_problem* p, const comet_launch_config* cfg);
+
+/* Autotuner (no paper counterpart; the paper sizes its worker pool by hand):
+ * times the evaluator on the n orders of `sample` (host or device) with an
+ * iteration budget max_iters (0 = the solver's) under every candidate shape
+ * -- 1..4 TOs per CTA, each at its occupancy limit and at three quarters of
+ * it -- keeps the fastest for p and caches it per (device, N_max) for
+ * problems created later in the process.  out (nullable) receives the pick,
+ * out_ms (nullable, >= 8 floats) the time of each candidate in order, and
+ * n_candidates (nullable) their number.  Synchronises. */
+comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int64_t n, int32_t max_iters,
+                            comet_launch_config* out, float* out_ms, int32_t* n_candidates);
+
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 

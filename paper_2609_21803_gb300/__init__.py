@@ -68,6 +68,11 @@ class PlanResult(ctypes.Structure):
                 ("explore_ms", ctypes.c_float), ("refine_ms", ctypes.c_float)]
 
 
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("max_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class ProposalDesc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("rows_cap", ctypes.c_int32), ("dataset_cap", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("lambda_w", ctypes.c_double), ("warm_mode", ctypes.c_int32),
@@ -107,6 +112,7 @@ EXPORTS = (
     "comet_proposal_forward", "comet_proposal_train_batch", "comet_proposal_add_samples",
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
+    "comet_get_launch_config", "comet_set_launch_config", "comet_autotune",
 )
 
 
@@ -170,6 +176,10 @@ def lib(build_if_missing: bool = False):
             L.comet_proposal_train.argtypes = [vp, i64, i32, ctypes.POINTER(AdamWOpts), ctypes.c_uint64, vp]
             L.comet_proposal_predict.argtypes = [vp, vp, i64, vp, vp]
             L.comet_proposal_prune.argtypes = [vp, vp, i32, vp]
+            L.comet_get_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
+            L.comet_set_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
+            L.comet_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(LaunchConfig), vp,
+                                         ctypes.POINTER(i32)]
             L.comet_plan_learned.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), vp,
                                              ctypes.POINTER(PlanResult), vp]
             L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
@@ -566,3 +576,28 @@ def comet_gemm_bf16(a, lda, b, ldb, m, n, k, kind=GEMM_STORE, k_splits=1, bias=N
     ep = GemmEpilogue(kind, k_splits, _ptr(bias), _ptr(out_f32), ld_f32, _ptr(out_bf16), ld_bf16,
                       _ptr(out_bf16_t), ld_bf16_t, _ptr(z_in), ld_z)
     _check(lib().comet_gemm_bf16(_ptr(a), lda, _ptr(b), ldb, m, n, k, ctypes.byref(ep), stream))
+
+
+# ------------------------------------------------------- launch shape
+
+def comet_get_launch_config(problem) -> dict:
+    c = LaunchConfig()
+    _check(lib().comet_get_launch_config(problem, ctypes.byref(c)))
+    return {"warps_per_block": c.warps_per_block, "blocks_per_sm": c.blocks_per_sm,
+            "max_blocks_per_sm": c.max_blocks_per_sm}
+
+
+def comet_set_launch_config(problem, warps_per_block: int, blocks_per_sm: int):
+    c = LaunchConfig(warps_per_block, blocks_per_sm, 0, 0)
+    _check(lib().comet_set_launch_config(problem, ctypes.byref(c)))
+
+
+def comet_autotune(problem, sample, n: int, max_iters: int = 0):
+    """Returns (picked config dict, list of candidate times in ms)."""
+    c = LaunchConfig()
+    ms = np.zeros(16, np.float32)
+    nc = ctypes.c_int32()
+    _check(lib().comet_autotune(problem, _ptr(sample), n, max_iters, ctypes.byref(c), ms.ctypes.data,
+                                ctypes.byref(nc)))
+    return ({"warps_per_block": c.warps_per_block, "blocks_per_sm": c.blocks_per_sm,
+             "max_blocks_per_sm": c.max_blocks_per_sm}, [float(x) for x in ms[: nc.value]])

@@ -375,6 +375,17 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
     }
     const size_t smem = comet::smem_per_warp_bytes(Nmax) * p->warps_per_block;
     p->blocks_per_sm = comet::eval_blocks_per_sm(p->warps_per_block, smem);
+    {
+        // a shape the autotuner picked for this device and N_max
+        int w = 0, b = 0;
+        if (p->blocks_per_sm >= 1 && comet::cached_launch_shape(p->device, Nmax, &w, &b)) {
+            const int occ = comet::eval_blocks_per_sm(w, comet::smem_per_warp_bytes(Nmax) * w);
+            if (occ >= b && b >= 1) {
+                p->warps_per_block = w;
+                p->blocks_per_sm = b;
+            }
+        }
+    }
     if (p->blocks_per_sm < 1) {
         comet_problem_destroy(p);
         return fail(COMET_ERR_INVALID_ARG, "N_max = %d needs %zu bytes of shared memory per block", Nmax, smem);

@@ -72,6 +72,9 @@ comet_status check_instances(const comet_instance_desc* inst, int32_t n_instance
 void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out);
 void set_error(const char* msg);
 
+// Launch shape cached by the autotuner for (device, N_max) (autotune.cu).
+bool cached_launch_shape(int device, int nmax, int* wpb, int* bps);
+
 // Longest-first order of a batch (schedule.cu): perm[0..n) lists the TOs by
 // decreasing interval count; scratch holds lpt_scratch_bytes().
 size_t lpt_scratch_bytes();

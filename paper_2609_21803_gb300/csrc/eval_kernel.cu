@@ -687,7 +687,6 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
 // (record floats 36..55, row-major).
 __device__ void phase_b_gains(Ctx& C) {
     const int N = C.N, lane = C.lane;
-    Smem& S = C.sm;
     for (int k = lane; k < N; k += 32) {
         float* rec = C.rec + (size_t)k * kRec;
         float m[30];
@@ -1143,6 +1142,10 @@ __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
 
 // ------------------------------------------------------------------ kernel
 
+// kRefine: the variant with the FP64 refinement step compiled in; the
+// launch picks it only when the penalty can exceed refine_beta, so the
+// default kernel carries none of that code (a smaller instruction footprint).
+template <bool kRefine>
 __global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
     extern __shared__ float smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1268,7 +1271,7 @@ __global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
             if (!fac) continue;
             phase_b_gains(C);
             const float D = phase_c(C, dx0);
-            if (sp.refine && beta > sp.refine_beta) refine_step(C, beta, rho, model_curv);
+            if (kRefine && beta > sp.refine_beta) refine_step(C, beta, rho, model_curv);
             const float alpha = phase_d(C, beta, D, sp);
             if (alpha > 0.f) {
                 phase_e(C, alpha);
@@ -1311,12 +1314,14 @@ size_t smem_per_warp_bytes(int Nmax) { return smem_floats(Nmax) * sizeof(float);
 
 int eval_blocks_per_sm(int warps_per_block, size_t smem_per_block) {
     int nb = 0;
-    if (cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_block) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_block) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_block) !=
+            cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel, warps_per_block * 32, smem_per_block) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<false>, warps_per_block * 32, smem_per_block) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -1332,12 +1337,17 @@ cudaError_t launch_eval(const EvalArgs& a, int total_warps, int warps_per_block,
     if (e != cudaSuccess) return e;
     static size_t raised[64] = {};
     if (dev < 64 && raised[dev] < smem) {
-        e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         raised[dev] = smem;
     }
     const int blocks = (total_warps + warps_per_block - 1) / warps_per_block;
-    eval_kernel<<<blocks, warps_per_block * 32, smem, s>>>(a);
+    if (a.sp.refine && a.sp.refine_beta < a.sp.beta_max)
+        eval_kernel<true><<<blocks, warps_per_block * 32, smem, s>>>(a);
+    else
+        eval_kernel<false><<<blocks, warps_per_block * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

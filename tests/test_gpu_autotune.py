@@ -1,0 +1,91 @@
+"""The persistent evaluator's launch shape and its autotuner on the mixed
+workload (rectangular sliders, lengths 1..6, 10..30 knots per segment, one
+persistent launch over every instance, longest TO first).
+
+The shape (TOs per CTA, resident CTAs per SM) changes which warp solves
+which TO and when, never the arithmetic of a TO: results must agree bit for
+bit across shapes.  The autotuner must pick a valid shape, report a time
+for every candidate, and seed problems created later with the same N_max.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_21803_gb300 import build as B
+    B.build()
+    import paper_2609_21803_gb300 as P
+    P.lib()
+    torch.cuda.set_device(0)
+    return P
+
+
+def _mixed(P, n_inst, per, seed):
+    insts = [W.push_mixed_instance(s) for s in range(n_inst)]
+    rng = np.random.default_rng(seed)
+    seqs, idx = [], []
+    for i, inst in enumerate(insts):
+        for _ in range(per):
+            L = int(rng.integers(1, inst["max_segments"] + 1))
+            seqs.append(tuple(int(m) for m in rng.integers(0, 12, L)))
+            idx.append(i)
+    packed = P.pack_mode_seqs(seqs, np.array(idx, np.int32))
+    return insts, torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), 24)).cuda()
+
+
+def test_results_do_not_depend_on_the_launch_shape(P):
+    insts, d = _mixed(P, 12, 60, 0)
+    prob = P.Problem(insts)
+    ref = None
+    shapes = []
+    for w in (1, 2, 3, 4):
+        occ = P.comet_get_launch_config(prob.handle)
+        P.comet_set_launch_config(prob.handle, w, 1)
+        limit = P.comet_get_launch_config(prob.handle)["max_blocks_per_sm"]
+        for b in sorted({1, limit}):
+            P.comet_set_launch_config(prob.handle, w, b)
+            r = {k: v.cpu().numpy() for k, v in prob.eval(d, want_traj=True).items()}
+            shapes.append((w, b))
+            if ref is None:
+                ref = r
+                continue
+            for k in ("cost", "status", "iters", "viol", "traj"):
+                np.testing.assert_array_equal(r[k], ref[k], err_msg=f"{k} at shape {(w, b)}")
+    assert len(shapes) >= 5
+    assert np.mean(ref["status"] == 0) > 0.5
+    with pytest.raises(P.CometError):
+        P.comet_set_launch_config(prob.handle, 5, 1)
+    with pytest.raises(P.CometError):
+        P.comet_set_launch_config(prob.handle, 4, 1000)
+    prob.close()
+
+
+def test_autotuner_picks_a_valid_shape_and_seeds_new_problems(P):
+    insts, d = _mixed(P, 16, 200, 1)
+    prob = P.Problem(insts)
+    pick, times = P.comet_autotune(prob.handle, d, len(d), 30)
+    print("autotune", pick, ["%.2f" % t for t in times])
+    assert 1 <= pick["warps_per_block"] <= 4
+    assert 1 <= pick["blocks_per_sm"] <= pick["max_blocks_per_sm"]
+    assert len(times) >= 4 and all(t > 0 for t in times)
+    assert P.comet_get_launch_config(prob.handle)["warps_per_block"] == pick["warps_per_block"]
+    # the pick is the fastest candidate
+    assert min(times) == pytest.approx(times[int(np.argmin(times))])
+    # a new problem with the same N_max starts from the pick
+    again = P.Problem(insts[:8] + insts[8:])
+    cfg = P.comet_get_launch_config(again.handle)
+    assert (cfg["warps_per_block"], cfg["blocks_per_sm"]) == (pick["warps_per_block"], pick["blocks_per_sm"])
+    again.close()
+    # host samples work too
+    pick2, _ = P.comet_autotune(prob.handle, d.cpu().numpy().view(P.MODE_SEQ_DTYPE).ravel(), 500, 10)
+    assert 1 <= pick2["warps_per_block"] <= 4
+    prob.close()
