@@ -46,6 +46,10 @@ N_STAGES = SEG * K
 # 7x7 Cholesky 230, gains with 5 right-hand sides 490, Schur update 230,
 # forward pass 70, 8-trial line search 800)
 FLOP_PER_STAGE_ITER = 3330
+# DRAM bytes (read + write) of one evaluator launch over the 20,736 orders:
+# the ncu capture of a 4,096-order launch (1.2 MB read, 138.1 MB written,
+# profiles/eval_kernel_push_l4.md) scaled by the TOs processed
+EVAL_TRAFFIC_BYTES = (1.22e6 + 138.14e6) * 20736 / 4096
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -272,7 +276,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(n * (4 + 4 + 4))},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": EVAL_TRAFFIC_BYTES,
                      "note": "achieved = 3330 flop x 80 stages x solver iterations / device time; peak = FP32 "
                              "FMA rate at 2070 MHz (152 SMs x 128 lanes)"},
         "iterations_per_solve": iter_total / (args.steps * n * world),
