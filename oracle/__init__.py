@@ -25,6 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "comet_oracle.c")
+_SRC_BIM = os.path.join(_HERE, "bimanual.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libcomet_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -35,13 +36,12 @@ CONVERGED, MAX_ITER, INFEASIBLE, FACTOR_FAIL, NONFINITE = range(5)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, IEEE double, no fast-math)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "comet_oracle.h"))
-    ):
+    srcs = [_SRC, _SRC_BIM, os.path.join(_HERE, "comet_oracle.h"), os.path.join(_HERE, "bimanual.h")]
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(f) for f in srcs):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-Wall",
-             "-o", tmp, _SRC, "-lm", "-lpthread"]
+             "-o", tmp, _SRC, _SRC_BIM, "-lm", "-lpthread"]
         )
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -82,6 +82,17 @@ class Result(ctypes.Structure):
     ]
 
 
+class BimInstance(ctypes.Structure):
+    _fields_ = [
+        ("ax", ctypes.c_double), ("az", ctypes.c_double), ("mass", ctypes.c_double),
+        ("mu_g", ctypes.c_double), ("mu_h", ctypes.c_double), ("dt", ctypes.c_double),
+        ("grav", ctypes.c_double), ("knots_per_segment", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("start", ctypes.c_double * 3), ("goal", ctypes.c_double * 3),
+        ("w_terminal", ctypes.c_double), ("w_v", ctypes.c_double), ("w_f", ctypes.c_double),
+        ("w_s", ctypes.c_double), ("w_c", ctypes.c_double),
+    ]
+
+
 RESULT_DTYPE = np.dtype([
     ("cost", "f8"), ("viol", "f8"), ("merit", "f8"), ("stat", "f8"), ("comp", "f8"),
     ("beta", "f8"), ("rho", "f8"), ("status", "i4"), ("iters", "i4"),
@@ -92,6 +103,7 @@ assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result)
 _P = ctypes.POINTER
 _dp = _P(ctypes.c_double)
 _u8p = _P(ctypes.c_uint8)
+_u16p = _P(ctypes.c_uint16)
 _i32p = _P(ctypes.c_int32)
 
 
@@ -121,6 +133,24 @@ def lib():
                                           ctypes.c_int64, _P(Opts), ctypes.c_int32, _dp, ctypes.c_int64,
                                           ctypes.c_void_p]
             L.orc_solve_batch.restype = ctypes.c_int32
+            B = _P(BimInstance)
+            L.bim_interval_rows.argtypes = [B, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp, _dp,
+                                            _u8p, _u8p, _dp, _dp]
+            L.bim_rows.argtypes = [B, ctypes.c_int32, _u16p, ctypes.c_int32, _dp, _dp, _u8p, _dp, _dp]
+            L.bim_dense_jacobian.argtypes = [B, ctypes.c_int32, _u16p, ctypes.c_int32, _dp, _dp]
+            L.bim_cold_start.argtypes = [B, ctypes.c_int32, _dp]
+            L.bim_cost.argtypes = [B, ctypes.c_int32, _dp]
+            L.bim_cost.restype = ctypes.c_double
+            L.bim_gn_step.argtypes = [B, ctypes.c_int32, _u16p, ctypes.c_int32, _dp, _dp, ctypes.c_double,
+                                      ctypes.c_double, _dp, _dp]
+            L.bim_gn_step.restype = ctypes.c_int32
+            L.bim_al_merit.argtypes = [B, ctypes.c_int32, _u16p, ctypes.c_int32, _dp, _dp, ctypes.c_double]
+            L.bim_al_merit.restype = ctypes.c_double
+            L.bim_solve.argtypes = [B, ctypes.c_int32, _u16p, ctypes.c_int32, _dp, _P(Opts), _dp, _dp, _P(Result)]
+            L.bim_solve.restype = ctypes.c_int32
+            L.bim_solve_batch.argtypes = [B, _i32p, _i32p, _u16p, ctypes.c_int32, _i32p, ctypes.c_int64, _P(Opts),
+                                          ctypes.c_int32, _dp, ctypes.c_int64, ctypes.c_void_p]
+            L.bim_solve_batch.restype = ctypes.c_int32
             _lib = L
     return _lib
 
@@ -266,4 +296,137 @@ def solve_batch(insts: list, inst_idx, seqs, lens, Ns=None, opts: Opts | None = 
     lib().orc_solve_batch(arr, _ptr(inst_idx, _i32p), _ptr(lens, _i32p), _ptr(seqs, _u8p), lmax,
                           _ptr(Ns, _i32p), n, ctypes.byref(o), nth, _ptr(tr, _dp), stride,
                           res.ctypes.data_as(ctypes.c_void_p))
+    return res, tr
+
+
+# ------------------------------------------------------------- bimanual
+
+BIM_NX, BIM_NU, BIM_NROW, BIM_NMODES = 5, 12, 32, 507
+GRAVITY = 9.81
+
+
+def bim_make_instance(d: dict) -> BimInstance:
+    """The oracle's bimanual instance from a workload descriptor (the same
+    dict the library takes: side_x, side_y = box width and height, mu = hand
+    friction, ground_mu, mass, w_control = the weight of twist, sliding rates
+    and p_c; forces are weighted by w_control / (m g)^2)."""
+    s = BimInstance()
+    s.ax, s.az = 0.5 * d["side_x"], 0.5 * d["side_y"]
+    s.mass, s.mu_g, s.mu_h = d["mass"], d["ground_mu"], d["mu"]
+    s.dt, s.grav = d["dt"], GRAVITY
+    s.knots_per_segment = int(d["knots_per_segment"])
+    for i in range(3):
+        s.start[i] = d["start"][i]
+        s.goal[i] = d["goal"][i]
+    mg = d["mass"] * GRAVITY
+    s.w_terminal = d["w_terminal"]
+    s.w_v = s.w_s = s.w_c = d["w_control"]
+    s.w_f = d["w_control"] / (mg * mg)
+    return s
+
+
+def bim_traj_len(N: int) -> int:
+    return (BIM_NX + BIM_NU) * N + BIM_NX
+
+
+def bim_interval_rows(inst: dict, mode: int, mask_sL: bool, mask_sR: bool, xk, uk, xk1):
+    """(c[32], mask, ineq, scale, J[32][22]) of one interval."""
+    c = np.zeros(BIM_NROW)
+    mask = np.zeros(BIM_NROW, np.uint8)
+    ineq = np.zeros(BIM_NROW, np.uint8)
+    scale = np.zeros(BIM_NROW)
+    J = np.zeros((BIM_NROW, 2 * BIM_NX + BIM_NU))
+    xk, uk, xk1 = (np.ascontiguousarray(a, dtype=np.float64) for a in (xk, uk, xk1))
+    lib().bim_interval_rows(ctypes.byref(bim_make_instance(inst)), int(mode), int(mask_sL), int(mask_sR),
+                            _ptr(xk, _dp), _ptr(uk, _dp), _ptr(xk1, _dp), _ptr(c, _dp), _ptr(mask, _u8p),
+                            _ptr(ineq, _u8p), _ptr(scale, _dp), _ptr(J, _dp))
+    return c, mask.astype(bool), ineq.astype(bool), scale, J
+
+
+def bim_cold_start(inst: dict, N: int) -> np.ndarray:
+    tr = np.zeros(5 * (N + 1) + 12 * N)
+    lib().bim_cold_start(ctypes.byref(bim_make_instance(inst)), N, _ptr(tr, _dp))
+    return tr
+
+
+def bim_rows(inst: dict, modes, N: int, traj):
+    modes = np.ascontiguousarray(modes, dtype=np.uint16)
+    traj = np.ascontiguousarray(traj, dtype=np.float64)
+    c = np.zeros((N, BIM_NROW))
+    mask = np.zeros((N, BIM_NROW), np.uint8)
+    scale = np.zeros((N, BIM_NROW))
+    ci = np.zeros(3)
+    lib().bim_rows(ctypes.byref(bim_make_instance(inst)), len(modes), _ptr(modes, _u16p), N, _ptr(traj, _dp),
+                   _ptr(c, _dp), _ptr(mask, _u8p), _ptr(scale, _dp), _ptr(ci, _dp))
+    return c, mask.astype(bool), scale, ci
+
+
+def bim_dense_jacobian(inst: dict, modes, N: int, traj) -> np.ndarray:
+    modes = np.ascontiguousarray(modes, dtype=np.uint16)
+    traj = np.ascontiguousarray(traj, dtype=np.float64)
+    nz, nr = bim_traj_len(N), 3 + BIM_NROW * N
+    jac = np.zeros((nr, nz))
+    lib().bim_dense_jacobian(ctypes.byref(bim_make_instance(inst)), len(modes), _ptr(modes, _u16p), N,
+                             _ptr(traj, _dp), _ptr(jac, _dp))
+    return jac
+
+
+def bim_cost(inst: dict, N: int, traj) -> float:
+    traj = np.ascontiguousarray(traj, dtype=np.float64)
+    return lib().bim_cost(ctypes.byref(bim_make_instance(inst)), N, _ptr(traj, _dp))
+
+
+def bim_gn_step(inst: dict, modes, N: int, traj, lam, beta: float, rho: float):
+    modes = np.ascontiguousarray(modes, dtype=np.uint16)
+    traj = np.ascontiguousarray(traj, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    dz = np.zeros(bim_traj_len(N))
+    grad = np.zeros(bim_traj_len(N))
+    ok = lib().bim_gn_step(ctypes.byref(bim_make_instance(inst)), len(modes), _ptr(modes, _u16p), N,
+                           _ptr(traj, _dp), _ptr(lam, _dp), beta, rho, _ptr(dz, _dp), _ptr(grad, _dp))
+    return ok, dz, grad
+
+
+def bim_al_merit(inst: dict, modes, N: int, traj, lam, beta: float) -> float:
+    modes = np.ascontiguousarray(modes, dtype=np.uint16)
+    traj = np.ascontiguousarray(traj, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    return lib().bim_al_merit(ctypes.byref(bim_make_instance(inst)), len(modes), _ptr(modes, _u16p), N,
+                              _ptr(traj, _dp), _ptr(lam, _dp), beta)
+
+
+def bim_solve(inst: dict, modes, N: int | None = None, warm=None, opts: Opts | None = None):
+    """(result dict, trajectory, multipliers) of one bimanual mode order."""
+    modes = np.ascontiguousarray(modes, dtype=np.uint16)
+    N = N if N is not None else inst["knots_per_segment"] * len(modes)
+    tr = np.zeros(bim_traj_len(N))
+    lam = np.zeros(3 + BIM_NROW * N)
+    r = Result()
+    o = opts if opts is not None else default_opts()
+    w = None if warm is None else np.ascontiguousarray(warm, dtype=np.float64)
+    lib().bim_solve(ctypes.byref(bim_make_instance(inst)), len(modes), _ptr(modes, _u16p), N, _ptr(w, _dp),
+                    ctypes.byref(o), _ptr(tr, _dp), _ptr(lam, _dp), ctypes.byref(r))
+    res = {f: getattr(r, f) for f, _ in Result._fields_ if f != "pad1"}
+    return res, tr, lam
+
+
+def bim_solve_batch(insts: list, inst_idx, seqs, lens, opts: Opts | None = None, nthreads: int | None = None,
+                    want_traj: bool = False):
+    """Solve many bimanual orders on host threads; returns (results, trajs)."""
+    n = len(inst_idx)
+    lmax = max(1, max((len(s) for s in seqs), default=1))
+    modes = np.zeros((n, lmax), np.uint16)
+    for i, s in enumerate(seqs):
+        modes[i, : len(s)] = s
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    inst_idx = np.ascontiguousarray(inst_idx, dtype=np.int32)
+    Ns = np.array([insts[j]["knots_per_segment"] * int(L) for j, L in zip(inst_idx, lens)], np.int32)
+    arr = (BimInstance * len(insts))(*[bim_make_instance(d) for d in insts])
+    res = np.zeros(n, dtype=RESULT_DTYPE)
+    stride = bim_traj_len(int(Ns.max())) if n else 0
+    tr = np.zeros((n, stride)) if want_traj else None
+    o = opts if opts is not None else default_opts()
+    lib().bim_solve_batch(arr, _ptr(inst_idx, _i32p), _ptr(lens, _i32p), _ptr(modes, _u16p), lmax,
+                          _ptr(Ns, _i32p), n, ctypes.byref(o), nthreads or (os.cpu_count() or 1),
+                          _ptr(tr, _dp), stride, res.ctypes.data)
     return res, tr

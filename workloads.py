@@ -133,3 +133,37 @@ def mlp_params(in_dim: int, width: int, out_dim: int, seed: int, n_layers: int =
         a = 1.0 / np.sqrt(d[l])
         out.append((rng.uniform(-a, a, (d[l + 1], d[l])), rng.uniform(-bias_scale, bias_scale, d[l + 1])))
     return out
+
+
+def bimanual_instance(seed: int) -> dict:
+    """Bimanual box flip in the vertical plane.  Draw order: width, height
+    (full sides U[0.1, 0.3] m), mass U[0.5, 2] kg, rotation sign sigma (+-1),
+    offset U[0, 0.3].  Ground friction 0.5, hand friction 0.5, dt 0.05 s, 15
+    knots per segment, up to 6 segments, 507 modes per segment.  Start: the
+    box resting on its bottom face at the origin (x, z, theta) = (0, h/2, 0);
+    goal: theta_g = pi/2 + sigma offset, the box turned about its lower-left
+    corner (x_g, z_g follow from that rotation)."""
+    rng = np.random.default_rng(20_000 + seed)
+    w = rng.uniform(0.1, 0.3)
+    h = rng.uniform(0.1, 0.3)
+    mass = rng.uniform(0.5, 2.0)
+    sigma = 1.0 if rng.uniform() < 0.5 else -1.0
+    off = rng.uniform(0.0, 0.3)
+    ax, az = 0.5 * w, 0.5 * h
+    th = math.pi / 2 + sigma * off
+    # corner (-ax, -az) of the start pose sits at (-ax, 0); rotating the box
+    # about it by th puts the centre at corner + R(th) (ax, az)
+    xg = -ax + ax * math.cos(th) - az * math.sin(th)
+    zg = ax * math.sin(th) + az * math.cos(th)
+    return {
+        "task": 1, "side_x": w, "side_y": h, "c_ls": 0.0, "mu": 0.5, "dt": 0.05, "kappa": 1.0,
+        "knots_per_segment": 15, "max_segments": 6, "n_modes": 507,
+        "start": [0.0, az, 0.0], "goal": [xg, zg, th], "w_terminal": 10.0, "w_control": 0.1,
+        "mass": mass, "ground_mu": 0.5,
+    }
+
+
+def bimanual_mode(ground: int, hand_l: int, hand_r: int) -> int:
+    """Mode index of (ground 0 stick / 1 slide / 2 pivot, hand codes 0 none or
+    1 + 3 face + kind)."""
+    return ground * 169 + hand_l * 13 + hand_r
