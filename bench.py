@@ -192,7 +192,7 @@ def run_gpu(args):
         for i in my:
             probs.append(P.Problem([insts[i]], stream=stream))
     packed = P.pack_mode_seqs(seqs)
-    d_seqs = torch.from_numpy(packed.view(np.uint8).reshape(n, 24)).cuda()
+    d_seqs = torch.from_numpy(packed.view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
     cost = torch.empty(n, dtype=torch.float32, device="cuda")
     status = torch.empty(n, dtype=torch.int32, device="cuda")
     viol = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -272,7 +272,7 @@ def run_gpu(args):
                    "instances": N_INSTANCES, "orders_per_step": n, "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * 24),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * P.MODE_SEQ_BYTES),
                 "d2h_bytes_per_step": int(n * (4 + 4 + 4))},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -348,7 +348,7 @@ def hetero_times(P, n_inst=256, per=512, n_split=32):
             seqs.append(tuple(int(m) for m in rng.integers(0, 12, L)))
             idx.append(i)
     packed = P.pack_mode_seqs(seqs, np.array(idx, np.int32))
-    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), 24)).cuda()
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), P.MODE_SEQ_BYTES)).cuda()
     stream = torch.cuda.current_stream()
 
     def timed(prob, dd):
@@ -372,7 +372,7 @@ def hetero_times(P, n_inst=256, per=512, n_split=32):
     for i in range(n_split):
         pr = P.Problem([insts[i]])
         sub = P.pack_mode_seqs(seqs[i * per:(i + 1) * per])
-        t, c = timed(pr, torch.from_numpy(sub.view(np.uint8).reshape(per, 24)).cuda())
+        t, c = timed(pr, torch.from_numpy(sub.view(np.uint8).reshape(per, P.MODE_SEQ_BYTES)).cuda())
         t_per += t
         c_per += c
         pr.close()
@@ -422,7 +422,7 @@ def learned_times(P, insts, n_eval):
     torch.cuda.synchronize()
     t0 = time.time()
     for a in range(0, len(packed), 65536):
-        d = torch.from_numpy(packed[a:a + 65536].view(np.uint8).reshape(-1, 24)).cuda()
+        d = torch.from_numpy(packed[a:a + 65536].view(np.uint8).reshape(-1, P.MODE_SEQ_BYTES)).cuda()
         r = prob.eval(d, want_traj=True)
         P.comet_proposal_add_samples(q, d, len(d), r["cost"], r["viol"], r["status"], r["traj"])
     torch.cuda.synchronize()
@@ -439,7 +439,7 @@ def learned_times(P, insts, n_eval):
     # forward over one 4-segment enumeration (20,736 rows), device buffers
     rows = 20736
     x = torch.zeros((rows, 64), dtype=torch.int16, device="cuda")
-    P.comet_proposal_features(q, torch.from_numpy(packed[:rows].view(np.uint8).reshape(-1, 24)).cuda(), rows, x)
+    P.comet_proposal_features(q, torch.from_numpy(packed[:rows].view(np.uint8).reshape(-1, P.MODE_SEQ_BYTES)).cuda(), rows, x)
     y = torch.empty((rows, 256), dtype=torch.float32, device="cuda")
     P.comet_proposal_forward(q, x, rows, y)
     stream = torch.cuda.current_stream()

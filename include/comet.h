@@ -71,7 +71,16 @@ enum { COMET_TASK_PUSHER_SLIDER = 0, COMET_TASK_BIMANUAL = 1 };
  * (x, y, theta, s), control (f_n, f_t, sdot), K = knots_per_segment
  * intervals of dt [s] per mode segment, orders of at most max_segments
  * segments over n_modes = 12 modes (face 0..3 x stick, slide+, slide-),
- * cost w_terminal |pose_N - goal|^2 + w_control sum_k |u_k|^2. */
+ * cost w_terminal |pose_N - goal|^2 + w_control sum_k |u_k|^2.
+ * Bimanual (task 1): a box of width side_x and height side_y [m] and mass
+ * `mass` [kg] in the vertical plane, hand friction mu, ground friction
+ * ground_mu, state (x, z, theta, s_L, s_R), control (xd, zd, thd, fn_L, ft_L,
+ * sd_L, fn_R, ft_R, sd_R, lam_n, lam_t, p_c), n_modes = 507 (ground stick /
+ * slide / pivot x 13 x 13 hand modes: none or face 0..3 x stick, slide+,
+ * slide-), cost w_terminal |pose_N - goal|^2 + w_control (|twist|^2 +
+ * |sliding rates|^2 + p_c^2 + |forces|^2 / (m g)^2); trajectories
+ * x[5][N_max+1] then u[12][N_max] (stride 17 N_max + 5).  A problem holds
+ * instances of one task. */
 typedef struct {
     int32_t task;
     int32_t knots_per_segment;
@@ -90,7 +99,7 @@ typedef struct {
     int32_t ref_iters;       /* refinement budget t_ref (default 1500) */
     double eps_feas;         /* feasibility tolerance on v_hat (1e-5) */
     double eps_primal;       /* scaled primal tolerance of the stop test (1e-6) */
-    double eps_dual;         /* stationarity tolerance at beta <= beta_ref (1e-4) */
+    double eps_dual;         /* stationarity tolerance at beta <= beta_ref (1e-4; 1e-3 for bimanual problems) */
     double eps_comp;         /* complementarity tolerance (1e-6) */
     double merit_mu;         /* mu of Eq. search_merit (100) */
     double beta0, beta_max, beta_ref; /* penalty 1/mu_AL: start, cap, reference (100, 1e4, 1e3) */
@@ -102,12 +111,13 @@ typedef struct {
                                 default cap beta_max = 1e4 it is not reached) */
 } comet_solver_opts;
 
-/* One mode order: instance index, length and modes (24 bytes). */
+/* One mode order: instance index, length and modes (40 bytes; 16-bit modes
+ * so that alphabets beyond 256 modes, such as the bimanual 507, fit). */
 typedef struct {
     int32_t instance;
     uint8_t len;
-    uint8_t modes[COMET_MAX_SEGMENTS];
     uint8_t pad[3];
+    uint16_t modes[COMET_MAX_SEGMENTS];
 } comet_mode_seq;
 
 typedef struct comet_problem comet_problem;

@@ -58,7 +58,7 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         c[r] = 0.0;
         mask[r] = 1;
         ineq[r] = (r >= 11 && r <= 15) || (r >= 19 && r <= 23) || (r >= 27);
-        scale[r] = 1.0;
+        scale[r] = 1.0; /* v_hat in the rows' internal units (forces per m g) */
         for (int j = 0; j < NL; ++j) J[r * NL + j] = 0.0;
     }
 #define JJ(r, v) J[(r) * NL + (v)]
@@ -111,8 +111,6 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         JJ(6, j) /= mg;
         JJ(7, j) /= mg * lbar;
     }
-    scale[5] = scale[6] = 1.0 / mg;
-    scale[7] = 1.0 / (mg * lbar);
     /* ground */
     const double mu = in->mu_g, cg = sqrt(1.0 + mu * mu);
     const double xd = uk[0], zd = uk[1], thd = uk[2], ln = uk[ULN - 5], lt = uk[ULT - 5], pc = uk[UPC - 5];
@@ -133,7 +131,6 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         c[10] = (lt * lt - mu * mu * ln * ln) / (mg * mg);
         JJ(10, ULT) = 2.0 * lt / (mg * mg);
         JJ(10, ULN) = -2.0 * mu * mu * ln / (mg * mg);
-        scale[10] = 1.0 / (mg * mg);
     } else { /* pivot about the lower-left corner: its velocity is zero, the CoP is the corner */
         c[8] = xd - thd * rcz;
         JJ(8, UXD) = 1.0;
@@ -154,17 +151,14 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         c[12] = (-lt - mu * ln) / (mg * cg);
         JJ(12, ULT) = -1.0 / (mg * cg);
         JJ(12, ULN) = -mu / (mg * cg);
-        scale[11] = scale[12] = 1.0 / (mg * cg);
     } else { /* slide: friction opposes the motion, lam_t xd <= 0 */
         c[11] = lt * xd / mg;
         JJ(11, ULT) = xd / mg;
         JJ(11, UXD) = lt / mg;
-        scale[11] = 1.0 / mg;
         mask[12] = 0;
     }
     c[13] = -ln / mg;
     JJ(13, ULN) = -1.0 / mg;
-    scale[13] = 1.0 / mg;
     if (g != 2) { /* CoP within the support half-width w(theta) */
         c[14] = pc - w;
         JJ(14, UPC) = 1.0;
@@ -189,7 +183,6 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
             JJ(b + 1, uft) = 1.0 / mg;
             c[b + 2] = sd;
             JJ(b + 2, usd) = 1.0;
-            scale[b] = scale[b + 1] = 1.0 / mg;
             for (int r = b + 3; r < b + 8; ++r) mask[r] = 0;
             continue;
         }
@@ -206,20 +199,17 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
             c[b + 4] = (-ft - muh * fn) / (mg * ch);
             JJ(b + 4, uft) = -1.0 / (mg * ch);
             JJ(b + 4, ufn) = -muh / (mg * ch);
-            scale[b + 3] = scale[b + 4] = 1.0 / (mg * ch);
         } else {
             const double sg = (kind == 1) ? -1.0 : 1.0; /* slide+: ft - mu fn = 0, sd >= 0 */
             c[b] = (ft + sg * muh * fn) / (mg * ch);
             JJ(b, uft) = 1.0 / (mg * ch);
             JJ(b, ufn) = sg * muh / (mg * ch);
-            scale[b] = 1.0 / (mg * ch);
             c[b + 3] = sg * sd;
             JJ(b + 3, usd) = sg;
             mask[b + 4] = 0;
         }
         c[b + 5] = -fn / mg;
         JJ(b + 5, ufn) = -1.0 / mg;
-        scale[b + 5] = 1.0 / mg;
         c[b + 6] = s - ell;
         JJ(b + 6, vs) = 1.0;
         c[b + 7] = -s - ell;

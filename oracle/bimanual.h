@@ -32,7 +32,10 @@
  *   8..10 ground equalities, 11..15 ground inequalities
  *   16..18 hand L equalities, 19..23 hand L inequalities
  *   24..26 hand R equalities, 27..31 hand R inequalities
- * plus 3 initial-pose rows.  Cost: w_T |pose_N - goal|^2 + sum_k u_k^T R u_k
+ * plus 3 initial-pose rows.  The violation v_hat (Eq. inexact_mode_value) is
+ * taken in the rows' internal units: lengths in m, velocities in m/s, forces
+ * relative to the weight m g, the torque relative to m g l (every scale
+ * factor is 1).  Cost: w_T |pose_N - goal|^2 + sum_k u_k^T R u_k
  * with R = diag(w_v (twist), w_f (forces), w_s (sliding rates), w_c (p_c)).
  */
 #ifndef COMET_BIMANUAL_ORACLE_H

@@ -59,7 +59,7 @@ class PlanOpts(ctypes.Structure):
 
 class ModeSeq(ctypes.Structure):
     _fields_ = [("instance", ctypes.c_int32), ("len", ctypes.c_uint8),
-                ("modes", ctypes.c_uint8 * MAX_SEGMENTS), ("pad", ctypes.c_uint8 * 3)]
+                ("pad", ctypes.c_uint8 * 3), ("modes", ctypes.c_uint16 * MAX_SEGMENTS)]
 
 
 class PlanResult(ctypes.Structure):
@@ -94,9 +94,9 @@ class GemmEpilogue(ctypes.Structure):
 
 GEMM_STORE, GEMM_BIAS_GELU, GEMM_GELU_GRAD, GEMM_ATOMIC_ADD = 0, 1, 2, 3
 
-MODE_SEQ_DTYPE = np.dtype([("instance", "<i4"), ("len", "u1"), ("modes", "u1", (MAX_SEGMENTS,)),
-                           ("pad", "u1", (3,))])
-assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == 24
+MODE_SEQ_DTYPE = np.dtype([("instance", "<i4"), ("len", "u1"), ("pad", "u1", (3,)), ("modes", "<u2", (MAX_SEGMENTS,))])
+MODE_SEQ_BYTES = 40
+assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == MODE_SEQ_BYTES
 
 # exported symbols of include/comet.h
 EXPORTS = (
@@ -406,7 +406,7 @@ def comet_last_error() -> str:
 # ------------------------------------------------------------- marshalling
 
 def pack_mode_seqs(seqs, inst_idx=None, lens=None) -> np.ndarray:
-    """Pack orders into the 24-byte comet_mode_seq records.  seqs: uint8
+    """Pack orders into the 40-byte comet_mode_seq records.  seqs: integer
     [n, L] (all of length L, or padded with `lens`) or a list of tuples."""
     if isinstance(seqs, np.ndarray) and seqs.ndim == 2:
         n, L = seqs.shape
@@ -447,7 +447,7 @@ class Problem:
             pass
 
     def eval(self, seqs_dev, warm=None, want_traj=False, max_iters=0):
-        """seqs_dev: uint8 CUDA tensor [n, 24] of packed orders.  Returns a dict
+        """seqs_dev: uint8 CUDA tensor [n, 40] of packed orders.  Returns a dict
         of CUDA tensors: cost, status, viol, merit, iters, stat (and traj)."""
         torch = self.torch
         n = seqs_dev.shape[0]

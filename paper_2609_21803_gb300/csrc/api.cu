@@ -125,6 +125,10 @@ void make_dev_instance(const comet_instance_desc& d, DevInstance* out) {
     q.Lmax = d.max_segments;
     q.n_modes = d.n_modes;
     q.task = d.task;
+    q.mass_d = d.mass;
+    q.ground_mu_d = d.ground_mu;
+    q.mass = (float)d.mass;
+    q.ground_mu = (float)d.ground_mu;
 }
 
 // Solver parameters of a call from the options and an iteration budget
@@ -199,9 +203,21 @@ comet_status check_instances(const comet_instance_desc* inst, int32_t n_instance
     int Nmax = 0;
     for (int i = 0; i < n_instances; ++i) {
         const comet_instance_desc& d = inst[i];
-        if (d.task != COMET_TASK_PUSHER_SLIDER)
-            return fail(COMET_ERR_INVALID_ARG, "instance %d: task %d is not built", i, d.task);
-        if (d.n_modes != 12) return fail(COMET_ERR_INVALID_ARG, "instance %d: pushing needs n_modes = 12", i);
+        if (d.task != COMET_TASK_PUSHER_SLIDER && d.task != COMET_TASK_BIMANUAL)
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: unknown task %d", i, d.task);
+        if (d.task != inst[0].task) return fail(COMET_ERR_INVALID_ARG, "instance %d: a problem holds one task", i);
+        if (d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes != 12)
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: pushing needs n_modes = 12", i);
+        if (d.task == COMET_TASK_BIMANUAL) {
+            if (d.n_modes != 507) return fail(COMET_ERR_INVALID_ARG, "instance %d: bimanual needs n_modes = 507", i);
+            if (!(d.mass > 0 && d.ground_mu >= 0 && d.side_x > 0 && d.side_y > 0 && d.dt > 0 && d.mu >= 0))
+                return fail(COMET_ERR_INVALID_ARG, "instance %d: bad bimanual geometry, mass or friction", i);
+            if (d.max_segments < 1 || d.max_segments > COMET_MAX_SEGMENTS || d.knots_per_segment < 1 ||
+                (int64_t)d.knots_per_segment * d.max_segments > 512)
+                return fail(COMET_ERR_INVALID_ARG, "instance %d: bad knots_per_segment / max_segments", i);
+            Nmax = std::max(Nmax, d.knots_per_segment * d.max_segments);
+            continue;
+        }
         if (d.knots_per_segment < 1 || d.max_segments < 1 || d.max_segments > COMET_MAX_SEGMENTS ||
             (int64_t)d.knots_per_segment * d.max_segments > comet::kMaxN)
             return fail(COMET_ERR_INVALID_ARG, "instance %d: bad knots_per_segment / max_segments", i);
@@ -217,11 +233,19 @@ comet_status check_instances(const comet_instance_desc* inst, int32_t n_instance
 namespace comet {
 
 static int64_t resident_warps(const comet_problem* p, int64_t n) {
+    // bimanual: one CTA per TO, the workspace unit is a CTA
+    if (p->task == COMET_TASK_BIMANUAL)
+        return std::min<int64_t>((int64_t)p->num_sms * p->blocks_per_sm, std::max<int64_t>(n, 1));
     // resident warps: every SM filled, never more warps than TOs; the grid is
     // whole CTAs and any warp may pick any TO, so the workspace covers them all
     const int64_t resident = (int64_t)p->num_sms * p->blocks_per_sm * p->warps_per_block;
     return ((std::min<int64_t>(resident, std::max<int64_t>(n, 1)) + p->warps_per_block - 1) / p->warps_per_block) *
            p->warps_per_block;
+}
+
+// floats of workspace per unit (a warp for pushing, a CTA for bimanual)
+static int64_t ws_unit_floats(const comet_problem* p) {
+    return (int64_t)(p->task == COMET_TASK_BIMANUAL ? kBimRec : kRec) * p->Nmax;
 }
 
 comet_status reserve_eval(comet_problem* p, int64_t n) {
@@ -250,7 +274,7 @@ comet_status reserve_eval(comet_problem* p, int64_t n) {
         cudaFree(p->d_ws);
         p->d_ws = nullptr;
         p->ws_warps = 0;
-        CUDA_TRY(cudaMalloc(&p->d_ws, sizeof(float) * (size_t)kRec * p->Nmax * warps), "workspace");
+        CUDA_TRY(cudaMalloc(&p->d_ws, sizeof(float) * (size_t)ws_unit_floats(p) * warps), "workspace");
         p->ws_warps = warps;
     }
     return COMET_OK;
@@ -288,11 +312,14 @@ comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, 
     a.out_iters = p->d_iters;
     a.out_stat = p->d_stat;
     a.ws = p->d_ws;
-    a.ws_per_warp = (int64_t)kRec * p->Nmax;
+    a.ws_per_warp = ws_unit_floats(p);
     a.queue = p->d_queue;
     a.bad_input = p->d_bad;
     a.sp = make_params(p->opts, max_iters);
-    CUDA_TRY(launch_eval(a, (int)warps, p->warps_per_block, s), "evaluator launch");
+    if (p->task == COMET_TASK_BIMANUAL)
+        CUDA_TRY(launch_bimanual(a, (int)warps, s), "bimanual evaluator launch");
+    else
+        CUDA_TRY(launch_eval(a, (int)warps, p->warps_per_block, s), "evaluator launch");
     return COMET_OK;
 }
 
@@ -355,7 +382,12 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
         if (inst[i].max_segments > 1 || inst[i].knots_per_segment != inst[0].knots_per_segment) p->hetero = true;
     p->stream = (cudaStream_t)cuda_stream;
     p->Nmax = Nmax;
-    p->stride = 7 * (int64_t)Nmax + 4;
+    p->task = inst[0].task;
+    // bimanual: the force-balance rows carry FP32 rounding of about 6e-8 of
+    // m g, which the penalty (up to 1e4) lifts to a stationarity floor near
+    // 1e-3 x |J|; the default tolerance there is 1e-3 (overridable)
+    if (p->task == COMET_TASK_BIMANUAL && (!opts || !(opts->eps_dual > 0))) p->opts.eps_dual = 1e-3;
+    p->stride = p->task == COMET_TASK_BIMANUAL ? 17 * (int64_t)Nmax + 5 : 7 * (int64_t)Nmax + 4;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) {
@@ -374,6 +406,16 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
         return cuda_fail(e, "problem allocation");
     }
     const size_t smem = comet::smem_per_warp_bytes(Nmax) * p->warps_per_block;
+    if (p->task == COMET_TASK_BIMANUAL) {
+        p->warps_per_block = comet::kBimThreads / 32;
+        p->blocks_per_sm = comet::bim_blocks_per_sm(Nmax);
+        if (p->blocks_per_sm < 1) {
+            comet_problem_destroy(p);
+            return fail(COMET_ERR_INVALID_ARG, "N_max = %d does not fit the bimanual evaluator", Nmax);
+        }
+        *out = p;
+        return COMET_OK;
+    }
     p->blocks_per_sm = comet::eval_blocks_per_sm(p->warps_per_block, smem);
     {
         // a shape the autotuner picked for this device and N_max

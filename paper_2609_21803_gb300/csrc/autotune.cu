@@ -64,13 +64,15 @@ comet_status comet_get_launch_config(comet_problem* p, comet_launch_config* out)
     if (!p || !out) return tfail(COMET_ERR_INVALID_ARG, "problem and out are required");
     out->warps_per_block = p->warps_per_block;
     out->blocks_per_sm = p->blocks_per_sm;
-    out->max_blocks_per_sm = occupancy(p, p->warps_per_block);
+    out->max_blocks_per_sm = p->task == COMET_TASK_PUSHER_SLIDER ? occupancy(p, p->warps_per_block) : p->blocks_per_sm;
     out->reserved = 0;
     return COMET_OK;
 }
 
 comet_status comet_set_launch_config(comet_problem* p, const comet_launch_config* c) {
     if (!p || !c) return tfail(COMET_ERR_INVALID_ARG, "problem and config are required");
+    if (p->task != COMET_TASK_PUSHER_SLIDER)
+        return tfail(COMET_ERR_INVALID_ARG, "the bimanual evaluator runs one CTA per TO; its shape is fixed");
     if (c->warps_per_block < 1 || c->warps_per_block > 4)
         return tfail(COMET_ERR_INVALID_ARG, "warps_per_block must be in 1..4");
     const int occ = occupancy(p, c->warps_per_block);
@@ -86,6 +88,8 @@ comet_status comet_set_launch_config(comet_problem* p, const comet_launch_config
 comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int64_t n, int32_t max_iters,
                             comet_launch_config* out, float* out_ms, int32_t* n_candidates) {
     if (!p || !sample || n < 1) return tfail(COMET_ERR_INVALID_ARG, "problem and a sample are required");
+    if (p->task != COMET_TASK_PUSHER_SLIDER)
+        return tfail(COMET_ERR_INVALID_ARG, "the bimanual evaluator runs one CTA per TO; its shape is fixed");
     cudaStream_t s = p->stream;
     // candidate shapes: 1..4 TOs per CTA, each at its occupancy limit and at
     // three quarters of it (fewer resident warps, less contention)

@@ -23,11 +23,13 @@ struct DevInstance {
     float start[3], goal[3];
     float w_terminal, w_control;
     int32_t K, Lmax, n_modes, task;
+    float mass, ground_mu;               // bimanual: box mass, ground friction
     double dt_d, kappa_d, inv_c2_d, mu_d, sc_cone_d;
     double sigma_d[4];
     double a_d[4], ell_d[4];
     double start_d[3], goal_d[3];
     double w_terminal_d, w_control_d;
+    double mass_d, ground_mu_d;
 };
 
 struct SolverParams {
@@ -71,6 +73,14 @@ SolverParams make_params(const comet_solver_opts& o, int max_iters);
 comet_status check_instances(const comet_instance_desc* inst, int32_t n_instances, int* Nmax_out);
 void merge_opts(const comet_solver_opts* opts, comet_solver_opts* out);
 void set_error(const char* msg);
+
+// Bimanual variant (bimanual_kernel.cu): one CTA of kBimThreads threads per
+// TO; per-CTA workspace kBimRec floats per stage.
+constexpr int kBimRec = 324;
+constexpr int kBimThreads = 128;
+size_t bim_smem_bytes(int Nmax);
+int bim_blocks_per_sm(int Nmax);
+cudaError_t launch_bimanual(const EvalArgs& a, int n_ctas, cudaStream_t s);
 
 // Launch shape cached by the autotuner for (device, N_max) (autotune.cu).
 bool cached_launch_shape(int device, int nmax, int* wpb, int* bps);

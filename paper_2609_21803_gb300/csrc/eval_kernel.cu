@@ -102,7 +102,7 @@ __device__ __forceinline__ ModeInfo mode_of(unsigned char b) {
     return mi;
 }
 
-__device__ __forceinline__ ModeInfo mode_info(const uint8_t* modes, int len, int N, int k) {
+__device__ __forceinline__ ModeInfo mode_info(const uint16_t* modes, int len, int N, int k) {
     ModeInfo mi;
     const int seg = (int)(((long long)k * len) / N);
     const int m = modes[seg];
@@ -278,7 +278,7 @@ __device__ __forceinline__ Smem carve(float* base, int Nmax) {
 
 struct Ctx {
     const DevInstance* P;
-    uint8_t modes[COMET_MAX_SEGMENTS];
+    uint16_t modes[COMET_MAX_SEGMENTS];
     int len, N, Nmax;
     Smem sm;
     float* rec;  // this warp's stage records

@@ -50,12 +50,12 @@ __device__ unsigned long long encode_seq(const comet_mode_seq& s, int n_modes) {
     return code;
 }
 
-__device__ int decode_code(unsigned long long code, int n_modes, uint8_t* modes) {
+__device__ int decode_code(unsigned long long code, int n_modes, uint16_t* modes) {
     const unsigned long long base = (unsigned long long)(n_modes + 1);
     const int L = (int)(code % base);
     code /= base;
     for (int i = 0; i < L; ++i) {
-        modes[i] = (uint8_t)(code % base - 1);
+        modes[i] = (uint16_t)(code % base - 1);
         code /= base;
     }
     return L;
@@ -190,14 +190,14 @@ __global__ void topk_chunk_kernel(const TopKey* in_keys, const unsigned long lon
 // (position, mode ascending, skipping the current mode), insertions
 // (position 0..L, mode ascending), deletions (position ascending).
 // Returns the new length, or 0 if slot j does not exist.
-__device__ int neighbour(const uint8_t* s, int L, int j, int M, int lmax, uint8_t* out) {
+__device__ int neighbour(const uint16_t* s, int L, int j, int M, int lmax, uint16_t* out) {
     const int nsub = L * (M - 1);
     if (j < nsub) {
         const int pos = j / (M - 1);
         int m = j % (M - 1);
         if (m >= s[pos]) ++m;
         for (int i = 0; i < L; ++i) out[i] = s[i];
-        out[pos] = (uint8_t)m;
+        out[pos] = (uint16_t)m;
         return L;
     }
     j -= nsub;
@@ -206,7 +206,7 @@ __device__ int neighbour(const uint8_t* s, int L, int j, int M, int lmax, uint8_
         if (j < nins) {
             const int pos = j / M, m = j % M;
             for (int i = 0, o = 0; i <= L; ++i) {
-                if (i == pos) out[o++] = (uint8_t)m;
+                if (i == pos) out[o++] = (uint16_t)m;
                 if (i < L) out[o++] = s[i];
             }
             return L + 1;
@@ -229,7 +229,7 @@ __global__ void neighbour_kernel(FrontierDev F, const TopKey* top, int k, int sl
         const int r = (int)(o / slots), j = (int)(o % slots);
         unsigned long long code = kEmpty;
         if (r < kk) {
-            uint8_t s[COMET_MAX_SEGMENTS], nb[COMET_MAX_SEGMENTS];
+            uint16_t s[COMET_MAX_SEGMENTS], nb[COMET_MAX_SEGMENTS];
             const int L = decode_code(top[r].code, F.n_modes, s);
             const int Ln = neighbour(s, L, j, F.n_modes, F.lmax, nb);
             if (Ln > 0) {
@@ -293,7 +293,7 @@ __global__ void compact_kernel(FrontierDev F, int64_t total, int batch, int64_t 
         if (f && excl < cap) {
             comet_mode_seq q;
             const unsigned long long code = F.cand_code[o];
-            uint8_t m[COMET_MAX_SEGMENTS];
+            uint16_t m[COMET_MAX_SEGMENTS];
             const int L = decode_code(code, F.n_modes, m);
             q.instance = F.instance;
             q.len = (uint8_t)L;

@@ -286,7 +286,7 @@ __global__ void decode_kernel(const uint64_t* codes, int64_t n, int instance, in
     code /= base;
     q.len = (uint8_t)L;
     for (int j = 0; j < L && j < COMET_MAX_SEGMENTS; ++j) {
-        q.modes[j] = (uint8_t)(code % base - 1);
+        q.modes[j] = (uint16_t)(code % base - 1);
         code /= base;
     }
     out[i] = q;

@@ -708,6 +708,8 @@ void comet_default_adamw_opts(comet_adamw_opts* o) {
 comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* d_in, comet_proposal** out) {
     if (!p || !out) return qfail(COMET_ERR_INVALID_ARG, "problem and out are required");
     *out = nullptr;
+    if (p->task != COMET_TASK_PUSHER_SLIDER)
+        return qfail(COMET_ERR_INVALID_ARG, "the learned proposal is built for the pushing task");
     comet_proposal_desc d;
     if (d_in)
         d = *d_in;

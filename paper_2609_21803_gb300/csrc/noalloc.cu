@@ -69,6 +69,9 @@ extern "C" comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst
     if (n_instances > kNoallocMaxInstances)
         return noalloc_fail(COMET_ERR_INVALID_ARG,
                             "comet_eval_modes_noalloc: more than 64 instances do not fit the fixed scratch");
+    for (int32_t i = 0; i < n_instances; ++i)
+        if (inst[i].task != COMET_TASK_PUSHER_SLIDER)
+            return noalloc_fail(COMET_ERR_INVALID_ARG, "comet_eval_modes_noalloc: pushing instances only");
     if (n < 0) return noalloc_fail(COMET_ERR_INVALID_ARG, "n < 0");
     if (n > 0xffffffffLL) return noalloc_fail(COMET_ERR_INVALID_ARG, "n too large");
     int Nmax = 0;

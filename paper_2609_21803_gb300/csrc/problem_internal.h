@@ -17,6 +17,7 @@ struct comet_problem {
     comet::DevInstance* d_inst = nullptr;
     comet_solver_opts opts;
     int Nmax = 0;
+    int task = COMET_TASK_PUSHER_SLIDER;
     int64_t stride = 0;
     int num_sms = 0;
     int warps_per_block = 4;

@@ -50,6 +50,6 @@ def test_mode_code_matches_oracle_definition(lib):
 
 def test_struct_layouts():
     import ctypes
-    assert ctypes.sizeof(P.ModeSeq) == 24
+    assert ctypes.sizeof(P.ModeSeq) == 40
     assert ctypes.sizeof(P.InstanceDesc) == 4 * 4 + 8 * 16
     assert ctypes.sizeof(P.SolverOpts) == 2 * 4 + 10 * 8 + 2 * 4 + 8

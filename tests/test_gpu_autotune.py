@@ -39,7 +39,7 @@ def _mixed(P, n_inst, per, seed):
             seqs.append(tuple(int(m) for m in rng.integers(0, 12, L)))
             idx.append(i)
     packed = P.pack_mode_seqs(seqs, np.array(idx, np.int32))
-    return insts, torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), 24)).cuda()
+    return insts, torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), P.MODE_SEQ_BYTES)).cuda()
 
 
 def test_results_do_not_depend_on_the_launch_shape(P):

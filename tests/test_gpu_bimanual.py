@@ -1,0 +1,208 @@
+"""GPU parity of the bimanual evaluator (one CTA per TO) against the FP64
+bimanual oracle, through the C ABI.
+
+Same bar as the pushing evaluator: the TO is local and non-convex and runs
+in FP32 on the GPU, so the two sides can reach different local solutions;
+checked are the first iterate (FP32 rounding), the closed forms, the
+convergence rate, cost agreement where both reach the same solution, and the
+FP64 certification of every converged GPU trajectory by the oracle's rows.
+Stationarity tolerance of the bimanual problems: 1e-3 on both sides (the
+library's default for this task; see include/comet.h).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import search as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+G = oracle.GRAVITY
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_21803_gb300 import build as B
+    B.build()
+    import paper_2609_21803_gb300 as P
+    P.lib()
+    torch.cuda.set_device(0)
+    return P
+
+
+def _ev(P, insts, seqs, idx=None, warm=None, want_traj=True, max_iters=0):
+    prob = P.Problem(insts)
+    packed = P.pack_mode_seqs(seqs, idx)
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), P.MODE_SEQ_BYTES)).cuda()
+    w = None if warm is None else torch.from_numpy(np.ascontiguousarray(warm, np.float32)).cuda()
+    r = prob.eval(d, warm=w, want_traj=want_traj, max_iters=max_iters)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in r.items()}
+    out["stride"] = prob.stride
+    prob.close()
+    return out
+
+
+def _opts(**kw):
+    return oracle.default_opts(eps_dual=1e-3, **kw)
+
+
+def _to_oracle(traj, N, Nmax):
+    """GPU layout x[5][Nmax+1], u[12][Nmax] -> oracle x[5][N+1], u[12][N]."""
+    x = traj[: 5 * (Nmax + 1)].reshape(5, Nmax + 1)[:, : N + 1]
+    u = traj[5 * (Nmax + 1): 5 * (Nmax + 1) + 12 * Nmax].reshape(12, Nmax)[:, :N]
+    return np.concatenate([x.ravel(), u.ravel()]).astype(np.float64)
+
+
+def _certify(inst, modes, N, tr):
+    c, mask, scale, ci = oracle.bim_rows(inst, modes, N, tr)
+    ineq = np.zeros(32, bool)
+    ineq[11:16] = ineq[19:24] = ineq[27:] = True
+    v = np.where(ineq[None, :], np.maximum(c, 0), np.abs(c)) / scale * mask
+    return max(float(v.max()), float(np.abs(ci).max()))
+
+
+def test_box_at_rest_closed_form(P):
+    inst = W.bimanual_instance(2)
+    inst["goal"] = list(inst["start"])
+    g = _ev(P, [inst], [(W.bimanual_mode(0, 0, 0),)])
+    assert g["status"][0] == 0
+    assert g["cost"][0] == pytest.approx(15 * inst["w_control"], rel=1e-4)
+    u = g["traj"][0][5 * 91: 5 * 91 + 12 * 90].reshape(12, 90)[:, :15]
+    np.testing.assert_allclose(u[9], inst["mass"] * G, rtol=1e-5)
+
+
+def test_sliding_push_closed_form(P):
+    inst = W.bimanual_instance(3)
+    ax = 0.5 * inst["side_x"]
+    inst["side_y"] = min(inst["side_y"], 2.5 * ax)
+    az = 0.5 * inst["side_y"]
+    inst["start"] = [0.0, az, 0.0]
+    inst["goal"] = [0.05, az, 0.0]
+    g = _ev(P, [inst], [(W.bimanual_mode(1, 1, 0),)])
+    assert g["status"][0] == 0
+    mg = inst["mass"] * G
+    u = g["traj"][0][5 * 91: 5 * 91 + 12 * 90].reshape(12, 90)[:, :15]
+    np.testing.assert_allclose(u[3] / mg, 0.4, atol=2e-4)
+    np.testing.assert_allclose(u[4] / mg, 0.2, atol=2e-4)
+    np.testing.assert_allclose(u[9] / mg, 0.8, atol=2e-4)
+    np.testing.assert_allclose(u[10] / mg, -0.4, atol=2e-4)
+
+
+def test_first_iterate_matches_oracle(P):
+    insts = [W.bimanual_instance(0)]
+    rng = np.random.default_rng(1)
+    seqs = [(int(m),) for m in rng.choice(507, 24, replace=False)]
+    g = _ev(P, insts, seqs, max_iters=1)
+    ref, tr = oracle.bim_solve_batch(insts, np.zeros(24, np.int32), seqs, np.ones(24, np.int32),
+                                     opts=_opts(max_iters=1), want_traj=True)
+    for i in range(24):
+        got = _to_oracle(g["traj"][i], 15, 90)
+        scale = max(1.0, np.abs(tr[i]).max())
+        assert np.max(np.abs(got - tr[i])) <= 1e-4 * scale, i
+
+
+def test_enumeration_parity_one_segment_and_mixed(P):
+    insts = [W.bimanual_instance(s) for s in range(2)]
+    rng = np.random.default_rng(0)
+    seqs = [(m,) for m in range(507)] * 2 + [tuple(int(m) for m in rng.integers(0, 507, rng.integers(2, 4)))
+                                             for _ in range(120)]
+    idx = np.concatenate([np.repeat([0, 1], 507), rng.integers(0, 2, 120)]).astype(np.int32)
+    lens = np.array([len(s) for s in seqs], np.int32)
+    g = _ev(P, insts, seqs, idx)
+    ref, _ = oracle.bim_solve_batch(insts, idx, seqs, lens, opts=_opts())
+    cg, co = g["status"] == 0, ref["status"] == 0
+    both = cg & co
+    rel = np.abs(g["cost"].astype(np.float64) - ref["cost"]) / np.abs(ref["cost"])
+    same = both & (rel < 1e-2)
+    print(f"bimanual: conv gpu {cg.mean():.3f} oracle {co.mean():.3f}; same {same.sum() / both.sum():.3f}; "
+          f"rel<1e-4 {np.mean(rel[both] < 1e-4):.3f}")
+    assert abs(cg.mean() - co.mean()) <= 0.08
+    assert same.sum() >= 0.97 * both.sum()
+    assert np.mean(rel[same] <= 1e-4 + 2e-4) >= 0.97
+    # feasibility flags agree
+    assert np.mean((g["viol"] <= 1e-5) == (ref["viol"] <= 1e-5)) >= 0.9
+    # every converged GPU trajectory is certified by the oracle's FP64 rows
+    for t in np.flatnonzero(cg)[::17]:
+        N = 15 * len(seqs[t])
+        v = _certify(insts[idx[t]], seqs[t], N, _to_oracle(g["traj"][t], N, 90))
+        assert v <= 1e-5, (t, v)
+    # the enumeration argmin over the one-segment orders of each instance
+    for i in range(2):
+        sl = slice(507 * i, 507 * (i + 1))
+        ag = S.enumeration_argmin(g["cost"][sl], g["viol"][sl])
+        ao = S.enumeration_argmin(ref["cost"][sl], ref["viol"][sl])
+        if ag != ao:
+            # a near tie: the oracle's own costs of the two picks agree
+            assert ref["cost"][sl][ag] <= ref["cost"][sl][ao] * (1 + 1e-3) or not co[sl][ag]
+
+
+def test_warm_start_and_malformed_orders(P):
+    inst = W.bimanual_instance(4)
+    modes = (358,)
+    r, tr, _ = oracle.bim_solve(inst, modes, 15, opts=_opts())
+    assert r["status"] == 0
+    warm = np.zeros(17 * 90 + 5, np.float32)
+    x = tr[: 5 * 16].reshape(5, 16)
+    u = tr[5 * 16:].reshape(12, 15)
+    warm[: 5 * 91].reshape(5, 91)[:, :16] = x
+    warm[5 * 91:].reshape(12, 90)[:, :15] = u
+    g = _ev(P, [inst], [modes], warm=warm[None, :])
+    assert g["status"][0] == 0 and g["iters"][0] <= 40
+    assert g["cost"][0] == pytest.approx(r["cost"], rel=1e-4)
+    # a mode index past the alphabet gives the NONFINITE status, not a fault
+    prob = P.Problem([inst])
+    bad = P.pack_mode_seqs([(507,), (12,)])
+    dbad = torch.from_numpy(bad.view(np.uint8).reshape(2, P.MODE_SEQ_BYTES)).cuda()
+    rr = prob.eval(dbad)
+    st = rr["status"].cpu().numpy()
+    assert st[0] == 4 and st[1] in (0, 1, 2)
+    prob.close()
+    # a problem holds one task; the proposal and the launch-shape calls reject it
+    with pytest.raises(P.CometError):
+        P.Problem([inst, W.push_l4_instance(0)])
+    prob = P.Problem([inst])
+    with pytest.raises(P.CometError):
+        P.comet_proposal_create(prob.handle)
+    with pytest.raises(P.CometError):
+        P.comet_set_launch_config(prob.handle, 2, 1)
+    prob.close()
+
+
+def test_expansion_over_507_modes_matches_oracle(P):
+    inst = W.bimanual_instance(0)
+    prob = P.Problem([inst])
+    M, lmax = 507, 6
+    rng = np.random.default_rng(7)
+    seqs = list({tuple(int(m) for m in rng.integers(0, M, rng.integers(1, 3))) for _ in range(200)})
+    merit = (rng.integers(0, 20, len(seqs)) * 0.125 + 0.5).astype(np.float32)
+    f = P.comet_frontier_create(prob.handle, 0, 200000, 20000, 16)
+    P.comet_frontier_add(f, P.pack_mode_seqs(seqs), len(seqs), merit, np.zeros(len(seqs), np.float32))
+    P.comet_expand(prob.handle, f, 4)
+    got = P.frontier_next_orders(f, 20000)
+    V = {S.encode(s, M): (float(m), s) for s, m in zip(seqs, merit)}
+    want = S.expand(V, k=4, batch=20000, n_modes=M, l_max=lmax)
+    assert got == want
+    P.comet_frontier_destroy(f)
+    prob.close()
+
+
+def test_bimanual_plan(P):
+    # Algorithm 1 on one instance: seed = the 507 one-segment orders, beam
+    # 16, batch 1,024, two rounds; the refined best is a certified plan
+    inst = W.bimanual_instance(6)
+    prob = P.Problem([inst])
+    seeds = P.pack_mode_seqs([(m,) for m in range(507)])
+    traj = np.zeros(prob.stride, np.float32)
+    r = P.comet_plan(prob.handle, 0, seeds, 507, dict(k=16, batch=1024, rounds=2, k_ref=64), out_traj=traj)
+    print("bimanual plan", r)
+    assert r["best_status"] == 0 and r["best_viol"] <= 1e-5
+    N = 15 * len(r["best"])
+    v = _certify(inst, r["best"], N, _to_oracle(traj, N, 90))
+    assert v <= 1e-5
+    prob.close()

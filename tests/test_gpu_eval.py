@@ -45,7 +45,7 @@ def P():
 def gpu_eval(P, insts, seqs, inst_idx=None, lens=None, warm=None, want_traj=False, max_iters=0, opts=None):
     prob = P.Problem(insts, opts=opts)
     packed = P.pack_mode_seqs(seqs, inst_idx, lens)
-    d = torch.from_numpy(packed.view(np.uint8).reshape(len(packed), 24)).cuda()
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(packed), P.MODE_SEQ_BYTES)).cuda()
     w = None if warm is None else torch.from_numpy(np.ascontiguousarray(warm, dtype=np.float32)).cuda()
     r = prob.eval(d, warm=w, want_traj=want_traj, max_iters=max_iters)
     torch.cuda.synchronize()
@@ -274,7 +274,7 @@ def test_edge_cases(P):
     inst = W.push_l2_instance(0)
     prob = P.Problem([inst])
     # n = 0 is a no-op
-    empty = torch.zeros((0, 24), dtype=torch.uint8, device="cuda")
+    empty = torch.zeros((0, P.MODE_SEQ_BYTES), dtype=torch.uint8, device="cuda")
     out = prob.eval(empty)
     assert out["cost"].numel() == 0
     # one TO and a partial warp count
@@ -292,7 +292,7 @@ def test_edge_cases(P):
     with pytest.raises(P.CometError):
         P.comet_eval_modes(prob.handle, bad, 1, None, cost, None, status)
     # malformed orders in device memory: per-TO status, no call failure
-    dbad = torch.from_numpy(P.pack_mode_seqs(np.array([[0, 12]], np.uint8)).view(np.uint8).reshape(1, 24)).cuda()
+    dbad = torch.from_numpy(P.pack_mode_seqs(np.array([[0, 12]], np.uint8)).view(np.uint8).reshape(1, P.MODE_SEQ_BYTES)).cuda()
     out = prob.eval(dbad)
     torch.cuda.synchronize()
     assert int(out["status"][0]) == P.TO_NONFINITE
@@ -314,7 +314,7 @@ def test_host_and_device_buffers_agree_and_runs_are_deterministic(P):
     h_status = np.zeros(n, np.int32)
     h_traj = np.zeros((n, prob.stride), np.float32)
     P.comet_eval_modes(prob.handle, packed, n, None, h_cost, h_traj, h_status)
-    d = torch.from_numpy(packed.view(np.uint8).reshape(n, 24)).cuda()
+    d = torch.from_numpy(packed.view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
     a = prob.eval(d, want_traj=True)
     b = prob.eval(d, want_traj=True)
     torch.cuda.synchronize()

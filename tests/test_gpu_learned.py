@@ -39,7 +39,7 @@ def P():
 
 
 def _dev(P, packed):
-    return torch.from_numpy(packed.view(np.uint8).reshape(len(packed), 24)).cuda()
+    return torch.from_numpy(packed.view(np.uint8).reshape(len(packed), P.MODE_SEQ_BYTES)).cuda()
 
 
 @pytest.fixture(scope="module")

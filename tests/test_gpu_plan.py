@@ -27,7 +27,7 @@ def P():
 
 def _eval(P, prob, seqs, iters=0):
     packed = P.pack_mode_seqs(seqs)
-    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), 24)).cuda()
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), P.MODE_SEQ_BYTES)).cuda()
     r = prob.eval(d, max_iters=iters)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in r.items()}

@@ -64,7 +64,7 @@ def test_noalloc_matches_allocating_entry_point_twice(P):
     for call, (seed, n) in enumerate([(1, 700), (2, 257)]):
         seqs, idx = _orders(seed, n, insts)
         packed = P.pack_mode_seqs(seqs, idx)
-        d = torch.from_numpy(packed.view(np.uint8).reshape(n, 24)).cuda()
+        d = torch.from_numpy(packed.view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
         cost = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
         status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
         traj = torch.zeros((n, stride), dtype=torch.float32, device="cuda")
@@ -85,7 +85,7 @@ def test_noalloc_rejects_what_it_cannot_hold(P):
     inst = W.push_l2_instance(0)
     n = 4
     packed = P.pack_mode_seqs(np.zeros((n, 2), np.uint8))
-    d = torch.from_numpy(packed.view(np.uint8).reshape(n, 24)).cuda()
+    d = torch.from_numpy(packed.view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
     cost = torch.empty(n, dtype=torch.float32, device="cuda")
     status = torch.empty(n, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
