@@ -285,6 +285,8 @@ def run_gpu(args):
         line["plan"] = plan_times(P, insts[: args.plan_instances])
     if rank == 0 and args.hetero:
         line["hetero"] = hetero_times(P)
+    if rank == 0 and args.bimanual:
+        line["bimanual"] = bimanual_times(P)
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and not args.no_cpu_baseline:
@@ -386,6 +388,52 @@ def hetero_times(P, n_inst=256, per=512, n_split=32):
         "split_one_launch_ms": t_sub * 1e3,
         "note": "converged solves/s (device time); one launch over all instances vs one launch per instance",
     }
+
+
+def bimanual_times(P, n_inst=8, per=512, n_plan=2):
+    """The bimanual variant (box flipped by two point hands on a ground
+    contact, 507 modes per segment, 15 knots per segment, one CTA per TO):
+    random orders of 1..6 segments (512 per instance, 8 instances) in one
+    persistent launch, and Algorithm 1 on `n_plan` instances (seed = the 507
+    one-segment orders, beam 16, B = 1,024, s_max = 3, K_ref = 64)."""
+    import torch
+
+    insts = [W.bimanual_instance(s) for s in range(n_inst)]
+    rng = np.random.default_rng(11)
+    seqs, idx = [], []
+    for i in range(n_inst):
+        for _ in range(per):
+            L = int(rng.integers(1, 7))
+            seqs.append(tuple(int(m) for m in rng.integers(0, 507, L)))
+            idx.append(i)
+    packed = P.pack_mode_seqs(seqs, np.array(idx, np.int32))
+    d = torch.from_numpy(packed.view(np.uint8).reshape(len(seqs), P.MODE_SEQ_BYTES)).cuda()
+    prob = P.Problem(insts)
+    prob.eval(d[:256])
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = prob.eval(d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    conv = int(((r["status"] == 0) & (r["viol"] < 1e-5)).sum())
+    iters = float(r["iters"].float().mean())
+    cfg = P.comet_get_launch_config(prob.handle)
+    prob.close()
+    plans = []
+    seeds = P.pack_mode_seqs([(m,) for m in range(507)])
+    for i in range(n_plan):
+        pr = P.Problem([insts[i]])
+        res = P.comet_plan(pr.handle, 0, seeds, 507, dict(k=16, batch=1024, rounds=3, k_ref=64))
+        plans.append({"plan_ms": res["explore_ms"] + res["refine_ms"], "evaluations": res["evaluations"],
+                      "best_len": len(res["best"]), "best_cost": res["best_cost"],
+                      "feasible": bool(res["best_status"] == 0 and res["best_viol"] <= 1e-5)})
+        pr.close()
+    return {"orders": len(seqs), "converged_solves_per_s": conv / t, "solves_per_s": len(seqs) / t,
+            "converged_fraction": conv / len(seqs), "iterations_per_solve": iters, "ms": t * 1e3,
+            "ctas_per_sm": cfg["blocks_per_sm"], "plans": plans,
+            "note": "one CTA (128 threads) per TO; device time"}
 
 
 def measured_peak(key, fallback):
@@ -500,6 +548,7 @@ def main():
     ap.add_argument("--orders", type=int, default=0, help="profiling only: solve this prefix of each enumeration")
     ap.add_argument("--plan-instances", type=int, default=4, help="instances for the plan-time comparison (0 = skip)")
     ap.add_argument("--hetero", type=int, default=1, help="mixed-workload leg (1) or skip it (0)")
+    ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=8,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()
