@@ -229,7 +229,7 @@ __device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float 
 
 // ------------------------------------------------------------ shared memory
 
-constexpr int kRing = 8;       // stages in flight in the copy rings
+constexpr int kRing = 6;       // stages in flight in the copy rings
 constexpr int kSweepSlot = 48;  // record floats 32..79 (pd flag and reduced matrix)
 constexpr int kGainSlot = 20;   // record floats 36..55 (x_{k+1} gains)
 
@@ -1146,7 +1146,7 @@ __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
 // launch picks it only when the penalty can exceed refine_beta, so the
 // default kernel carries none of that code (a smaller instruction footprint).
 template <bool kRefine>
-__global__ void __launch_bounds__(128) eval_kernel(EvalArgs A) {
+__global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
     extern __shared__ float smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
