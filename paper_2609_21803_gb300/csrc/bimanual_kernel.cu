@@ -67,10 +67,15 @@ template <typename T>
 struct BInst {
     T ax, az, mg, lbar, mu_g, mu_h, cg, ch, dt;
     T start[3], goal[3];
-    T wT;
-    T R[NU];
+    T wT, wc, wf;  // control weights: wc (twist, sliding rates, p_c), wf (forces)
     int K;
 };
+
+// weight of control j (forces: f_n, f_t of both hands, lam_n, lam_t)
+template <typename T>
+__device__ __forceinline__ T rweight(const BInst<T>& P, int j) {
+    return (j == 3 || j == 4 || j == 6 || j == 7 || j == 9 || j == 10) ? P.wf : P.wc;
+}
 
 template <typename T>
 __device__ void load_inst(const DevInstance& d, BInst<T>& P) {
@@ -91,9 +96,8 @@ __device__ void load_inst(const DevInstance& d, BInst<T>& P) {
     }
     P.wT = dbl ? (T)d.w_terminal_d : (T)d.w_terminal;
     const T wc = dbl ? (T)d.w_control_d : (T)d.w_control;
-    const T wf = wc / (P.mg * P.mg);
-    const T w[NU] = {wc, wc, wc, wf, wf, wc, wf, wf, wc, wf, wf, wc};
-    for (int j = 0; j < NU; ++j) P.R[j] = w[j];
+    P.wc = wc;
+    P.wf = wc / (P.mg * P.mg);
     P.K = d.K;
 }
 
@@ -128,6 +132,7 @@ __device__ void stage_ctx(const BInst<T>& P, int mode, const T* x, const T* u, B
     S.Fwx = u[ULT - 5];
     S.Fwz = u[ULN - 5];
     S.tau = u[UPC - 5] * u[ULN - 5] + x[VZ] * u[ULT - 5];
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
         const int h = S.h[side];
         const int f = h == 0 ? 0 : (h - 1) / 3;
@@ -171,7 +176,9 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
     const T mg = P.mg;
     if (r < 5) {
         const int vel = (r < 3) ? UXD + r : (r == 3 ? USDL : USDR);
-        c = dx[r] - P.dt * u[vel - 5];
+        const T dxr = (r == 0) ? dx[0] : (r == 1) ? dx[1] : (r == 2) ? dx[2] : (r == 3) ? dx[3] : dx[4];
+        const T ur = (r == 0) ? u[0] : (r == 1) ? u[1] : (r == 2) ? u[2] : (r == 3) ? u[USDL - 5] : u[USDR - 5];
+        c = dxr - P.dt * ur;
         if (WJ) {
             J[r] = -1;
             J[VX1 + r] = 1;
@@ -193,6 +200,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 J[VZ] = u[ULT - 5] * sc;
                 J[ULT] = x[VZ] * sc;
             }
+#pragma unroll
             for (int side = 0; side < 2; ++side) {
                 if (S.h[side] == 0) continue;
                 const int ufn = side ? UFNR : UFNL, uft = side ? UFTR : UFTL, vs = side ? VSR : VSL;
@@ -210,7 +218,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                     J[uft] = (sth * tx + cth * tz) * sc;
                 } else {
                     J[uft] = -S.a[side] * sc;
-                    J[ufn] = -x[vs] * sc;
+                    J[ufn] = -(side ? x[VSR] : x[VSL]) * sc;
                     J[vs] = -fn * sc;
                 }
             }
@@ -300,11 +308,14 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
             }
         }
     } else {
-        const int side = (r >= 24) ? 1 : 0, q = r - (side ? 24 : 16);
-        const int h = S.h[side];
+        const bool side = r >= 24;
+        const int q = r - (side ? 24 : 16);
+        const int h = side ? S.h[1] : S.h[0];
         const int ufn = side ? UFNR : UFNL, uft = side ? UFTR : UFTL, usd = side ? USDR : USDL;
         const int vs = side ? VSR : VSL;
-        const T fn = u[ufn - 5], ft = u[uft - 5], sd = u[usd - 5], s = x[vs];
+        const T fn = side ? u[UFNR - 5] : u[UFNL - 5], ft = side ? u[UFTR - 5] : u[UFTL - 5];
+        const T sd = side ? u[USDR - 5] : u[USDL - 5], s = side ? x[VSR] : x[VSL];
+        const T ell = side ? S.ell[1] : S.ell[0];
         if (h == 0) {
             if (q == 0) {
                 c = fn / mg;
@@ -362,7 +373,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 if (WJ) J[ufn] = -1 / mg;
             } else {
                 const T sg = (q == 6) ? (T)1 : (T)-1;
-                c = sg * s - S.ell[side];
+                c = sg * s - ell;
                 if (WJ) J[vs] = sg;
             }
         }
@@ -423,6 +434,7 @@ __device__ BSmem bcarve(float* p, int Nmax) {
 }
 
 struct BCtx {
+    const unsigned short* tab;  // (i << 8 | j) of the flat lower-triangle index t < 276
     const DevInstance* D;
     BInst<float> P;
     BSmem S;
@@ -470,9 +482,12 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
         const int mi = S.mi[k];
         BStage<float> St;
         stage_ctx(P, mi & 1023, x, u, St);
-        float c, J[NL], sc;
+        // the row's Jacobian goes straight into its shared-memory row (a
+        // register array indexed at run time would live in local memory)
+        float* Jr = Jw + lane * NL;
+        float c, sc;
         bool on, iq;
-        brow<float, true>(lane, P, St, (mi >> 10) & 1, (mi >> 11) & 1, x, u, dx, c, J, on, iq, sc);
+        brow<float, true>(lane, P, St, (mi >> 10) & 1, (mi >> 11) & 1, x, u, dx, c, Jr, on, iq, sc);
         float* lam = S.lam + 3 + NR * k;
         float l = lam[lane];
         if (update && on) {
@@ -488,15 +503,15 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
             if (iq) comp = fmaxf(comp, fabsf(y * c));
             if (!isfinite(c)) finite = false;
         }
-#pragma unroll
-        for (int j = 0; j < NL; ++j) Jw[lane * NL + j] = act ? J[j] : 0.f;
+        if (!act)
+            for (int j = 0; j < NL; ++j) Jr[j] = 0.f;
         yw[lane] = y;
         __syncwarp();
         // AL gradient over the local variables (lane = variable)
         if (lane < NL) {
             float g = 0.f;
             for (int r = 0; r < NR; ++r) g += yw[r] * Jw[r * NL + lane];
-            if (lane >= 5 && lane < 17) g += 2.f * P.R[lane - 5] * u[lane - 5];
+            if (lane >= 5 && lane < 17) g += 2.f * rweight(P, lane - 5) * S.us[(lane - 5) * N + k];
             if (lane < 17)
                 S.gr[NWV * k + lane] = g;
             else
@@ -507,14 +522,13 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
             // lower triangle of beta sum_r J J^T + cost + rho over (u, y, x); the
             // rhs row was written above
             for (int tt = lane; tt < tri(22, 0); tt += 32) {
-                int i, j;
-                untri(tt, i, j);
+                const int i = C.tab[tt] >> 8, j = C.tab[tt] & 255;
                 const int vi = evar(i), vj = evar(j);
                 float h = 0.f;
                 for (int r = 0; r < NR; ++r) h += Jw[r * NL + vi] * Jw[r * NL + vj];
                 h *= beta;
                 if (i == j) {
-                    if (i < 12) h += 2.f * P.R[i] + rho;
+                    if (i < 12) h += 2.f * rweight(P, i) + rho;
                     else if (i < 17) h += rho;
                 }
                 At[tt] = h;
@@ -532,10 +546,10 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
                 if (lane == 0) At[tri(j, j)] = l;
                 for (int i = j + 1 + lane; i < NE; i += 32) At[tri(i, j)] *= il;
                 __syncwarp();
-                for (int tt = lane; tt < NTRI; tt += 32) {
-                    int i, cc;
-                    untri(tt, i, cc);
-                    if (cc > j && i >= cc) At[tt] -= At[tri(i, j)] * At[tri(cc, j)];
+                // entries of columns > j (flat index >= tri(j + 1, j + 1))
+                for (int tt = tri(j + 1, j + 1) + lane; tt < NTRI; tt += 32) {
+                    const int i = C.tab[tt] >> 8, cc = C.tab[tt] & 255;
+                    if (cc > j) At[tt] -= At[tri(i, j)] * At[tri(cc, j)];
                 }
                 __syncwarp();
             }
@@ -546,8 +560,7 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
                 rec[R_CPL + q] = At[tri(12 + p, j)];
             }
             for (int q = lane; q < NTRI_RED; q += 32) {
-                int i, j;
-                untri(q, i, j);
+                const int i = C.tab[q] >> 8, j = C.tab[q] & 255;
                 rec[R_RED + q] = At[tri(12 + i, 12 + j)];
             }
             if (lane == 0) rec[R_PD] = pd ? 1.f : -1.f;
@@ -689,35 +702,46 @@ __device__ bool bphase_b(BCtx& C, float beta, float rho) {
         bool pd0 = ok;
         if (ok && lane == 0) {
             float H[5][5], g[5], L[5][5];
+            #pragma unroll
             for (int i = 0; i < 5; ++i) {
+                #pragma unroll
                 for (int j = 0; j < 5; ++j) H[i][j] = S.V[i * 5 + j];
                 H[i][i] += rho;
                 g[i] = S.v[i];
             }
+            #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 H[i][i] += beta;
                 g[i] += S.lam[i] + beta * ((S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1]);
             }
+            #pragma unroll
             for (int j = 0; j < 5; ++j) {
                 float d = H[j][j];
+                #pragma unroll
                 for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
                 pd0 = pd0 && d > 0.f;
                 const float l = sqrtf(fmaxf(d, 1e-30f));
                 L[j][j] = l;
+                #pragma unroll
                 for (int i = j + 1; i < 5; ++i) {
                     float s = H[i][j];
+                    #pragma unroll
                     for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
                     L[i][j] = s / l;
                 }
             }
             float yv[5];
+            #pragma unroll
             for (int i = 0; i < 5; ++i) {
                 float s = g[i];
+                #pragma unroll
                 for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
                 yv[i] = s / L[i][i];
             }
+            #pragma unroll
             for (int i = 4; i >= 0; --i) {
                 float s = yv[i];
+                #pragma unroll
                 for (int q = i + 1; q < 5; ++q) s -= L[q][i] * d0[q];
                 d0[i] = s / L[i][i];
             }
@@ -737,22 +761,30 @@ __device__ void bphase_gains(BCtx& C) {
     for (int k = C.tid; k < C.N; k += kBimThreads) {
         float* rec = C.rec + (size_t)k * kBimRec;
         float m[45];
+        #pragma unroll
         for (int q = 0; q < 45; ++q) m[q] = rec[R_YF + q];
         float ly[5][5];
+        #pragma unroll
         for (int j = 0; j < 5; ++j) {
             const float l = sqrtf(m[tri(j, j)]);
             const float il = 1.f / l;
             ly[j][j] = l;
+            #pragma unroll
             for (int i = j + 1; i < 5; ++i) ly[i][j] = m[tri(i, j)] * il;
+            #pragma unroll
             for (int c = 0; c < 6; ++c) m[15 + 5 * c + j] *= il;
         }
+        #pragma unroll
         for (int c = 0; c < 6; ++c) {
             float K[5];
+            #pragma unroll
             for (int i = 4; i >= 0; --i) {
                 float s = -m[15 + 5 * c + i];
+                #pragma unroll
                 for (int q = i + 1; q < 5; ++q) s -= ly[q][i] * K[q];
                 K[i] = s / ly[i][i];
             }
+            #pragma unroll
             for (int i = 0; i < 5; ++i) rec[R_YF + i * 6 + c] = K[i];
         }
     }
@@ -768,15 +800,18 @@ __device__ float bphase_c(BCtx& C) {
         float dxi = (C.lane < 5) ? S.red[16 + C.lane] : 0.f;
         if (C.lane < 5) S.dz[C.lane] = dxi;
         float dxv[5];
+        #pragma unroll
         for (int i = 0; i < 5; ++i) dxv[i] = __shfl_sync(kFullB, dxi, i);
         for (int k = 0; k < N; ++k) {
             float w = 0.f;
             if (C.lane < 5) {
                 const float* g = C.rec + (size_t)k * kBimRec + R_YF + 6 * C.lane;
                 w = g[5];
+                #pragma unroll
                 for (int j = 0; j < 5; ++j) w += g[j] * dxv[j];
                 S.dz[NWV * (k + 1) + C.lane] = w;
             }
+            #pragma unroll
             for (int i = 0; i < 5; ++i) dxv[i] = __shfl_sync(kFullB, w, i);
         }
     }
@@ -784,22 +819,28 @@ __device__ float bphase_c(BCtx& C) {
     for (int k = C.tid; k < N; k += kBimThreads) {
         const float* rec = C.rec + (size_t)k * kBimRec;
         float xa[5], xb[5];
+        #pragma unroll
         for (int i = 0; i < 5; ++i) {
             xa[i] = S.dz[NWV * k + i];
             xb[i] = S.dz[NWV * (k + 1) + i];
         }
         float R[NU];
+        #pragma unroll
         for (int j = 0; j < NU; ++j) {
             float s = rec[R_CPL + 10 * 12 + j];
+            #pragma unroll
             for (int i = 0; i < 5; ++i) s += rec[R_CPL + i * 12 + j] * xb[i] + rec[R_CPL + (5 + i) * 12 + j] * xa[i];
             R[j] = s;
         }
         float du[NU];
+        #pragma unroll
         for (int j = NU - 1; j >= 0; --j) {
             float s = -R[j];
+            #pragma unroll
             for (int i = j + 1; i < NU; ++i) s -= rec[R_LUU + tri(i, j)] * du[i];
             du[j] = s / rec[R_LUU + tri(j, j)];
         }
+        #pragma unroll
         for (int j = 0; j < NU; ++j) S.dz[NWV * k + NX + j] = du[j];
     }
     __syncthreads();
@@ -836,7 +877,7 @@ __device__ float bphase_d(BCtx& C, float beta, float D, const SolverParams& sp) 
             BStage<float> St;
             stage_ctx(P, mi & 1023, x, u, St);
             const float* lam = S.lam + 3 + NR * k;
-            for (int j = 0; j < NU; ++j) phi += P.R[j] * u[j] * u[j];
+            for (int j = 0; j < NU; ++j) phi += rweight(P, j) * u[j] * u[j];
             for (int r = 0; r < NR; ++r) {
                 float c, sc;
                 bool on, iq;
@@ -931,8 +972,8 @@ __device__ BCert bcertify(BCtx& C, float beta_f) {
         double g[NL];
         for (int j = 0; j < NL; ++j) g[j] = 0.0;
         for (int j = 0; j < NU; ++j) {
-            g[NX + j] += 2.0 * P.R[j] * u[j];
-            cost += P.R[j] * u[j] * u[j];
+            g[NX + j] += 2.0 * rweight(P, j) * u[j];
+            cost += rweight(P, j) * u[j] * u[j];
         }
         const float* lam = S.lam + 3 + NR * k;
         for (int r = 0; r < NR; ++r) {
@@ -1009,6 +1050,14 @@ __global__ void __launch_bounds__(kBimThreads) bimanual_kernel(EvalArgs A) {
     const SolverParams& sp = A.sp;
     const int64_t n_tos = A.d_n ? min(*A.d_n, A.n) : A.n;
     __shared__ unsigned int s_t;
+    __shared__ unsigned short s_tab[NTRI];
+    for (int t = C.tid; t < NTRI; t += kBimThreads) {
+        int i, j;
+        untri(t, i, j);
+        s_tab[t] = (unsigned short)(i << 8 | j);
+    }
+    C.tab = s_tab;
+    __syncthreads();
     for (;;) {
         if (C.tid == 0) s_t = atomicAdd(A.queue, 1u);
         __syncthreads();
