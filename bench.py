@@ -112,6 +112,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def shard(n_items: int, rank: int, world: int) -> list:
+    """Replicas: rank r takes items r, r + world, ... (no exchange on the data
+    path; every item is taken by exactly one rank)."""
+    return list(range(rank, n_items, world))
+
+
+def reduce_over_ranks(t_dev: float, counts, device):
+    """Max over ranks of the timed region and the sum of the work counts
+    (one all_reduce each; no-op with one process)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_dev, [int(c) for c in counts]
+    t = torch.tensor([t_dev], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t[0]), [int(round(float(x))) for x in c]
+
+
 def instances():
     return [W.push_l4_instance(s) for s in range(N_INSTANCES)]
 
@@ -187,7 +208,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     # one problem per instance; orders resident on the device (replicas: rank
     # r takes instances r, r + world, ...)
-    my = list(range(rank, N_INSTANCES, world))
+    my = shard(N_INSTANCES, rank, world)
     probs = []
     with torch.cuda.stream(stream):
         for i in my:
@@ -236,13 +257,7 @@ def run_gpu(args):
         conv_total += int(outs[s][0])
         iter_total += int(outs[s][2])
     # max over ranks of the timed region, sum of the work
-    if world > 1:
-        t = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t)
-        c = torch.tensor([conv_total, iter_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        conv_total, iter_total = int(c[0]), int(c[1])
+    t_dev, (conv_total, iter_total) = reduce_over_ranks(t_dev, [conv_total, iter_total], "cuda")
     clk = clocks.stop()
     value = conv_total / t_dev
 
