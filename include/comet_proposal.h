@@ -23,8 +23,11 @@
  * Parameters (flat FP32 vector, the optimiser's master copy):
  *   [W_1 (width x in_dim), b_1, W_2 (width x width), b_2, W_3, b_3,
  *    W_4 (out_dim x width), b_4], W row-major [out][in].
- * Forward: Z_l = H_{l-1} W_l^T + b_l, H_l = GELU(Z_l) (exact erf form) for
+ * Forward: Z_l = H_{l-1} W_l^T + b_l, H_l = GELU(Z_l) (tanh form:
+ * 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))) for
  * l = 1..3 with H_0 = X; Y = H_3 W_4^T + b_4.  X, W and H_l are BF16.
+ * Inference runs the four layers in one persistent kernel (the activations
+ * stay in shared memory and TMEM); training runs them as separate GEMMs.
  * Loss of a batch of B rows: L = (1/B) sum_{b,j} Omega_bj (Y_bj - T_bj)^2.
  * Optimiser: AdamW with bias-corrected moments and decoupled weight decay.
  *
@@ -89,6 +92,13 @@ comet_status comet_proposal_features(comet_proposal* q, const comet_mode_seq* se
 /* Forward pass: x [n][in_dim] BF16 (host or device) -> out_y [n][out_dim]
  * FP32 (host or device). */
 comet_status comet_proposal_forward(comet_proposal* q, const uint16_t* x, int64_t n, float* out_y);
+
+/* Device time of the forward pass (the kernels only): x [n][in_dim] BF16
+ * (host or device) is copied once, then `reps` forward passes run back to
+ * back on the problem's stream between two CUDA events; *out_ms receives the
+ * mean per pass.  Synchronous. */
+comet_status comet_proposal_time_forward(comet_proposal* q, const uint16_t* x, int64_t n, int32_t reps,
+                                         float* out_ms);
 
 /* One training step on a given batch: forward, loss, backward, AdamW.
  * x [n][in_dim] BF16, target and weight [n][out_dim] FP32 (host or device);

@@ -20,8 +20,9 @@ compared with the GPU's BF16 tensor-core path:
   * ``adamw``          one AdamW step (decoupled weight decay, bias-corrected
                        moments).
 
-GELU is the exact form 0.5 x (1 + erf(x / sqrt 2)); its derivative is
-Phi(x) + x phi(x).  With ``round_hidden`` the hidden activations (and, in
+GELU is the tanh form of Hendrycks and Gimpel, 0.5 x (1 + tanh(a (x + b x^3)))
+with a = sqrt(2 / pi), b = 0.044715; its derivative follows by the chain
+rule.  With ``round_hidden`` the hidden activations (and, in
 the backward pass, the layer gradients) are rounded to BF16 between layers,
 as the GPU stores them; the arithmetic stays float64.
 
@@ -63,14 +64,24 @@ def from_bf16_bits(b) -> np.ndarray:
     return (np.asarray(b, dtype=np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
+GELU_A = np.sqrt(2.0 / np.pi)
+GELU_B = 0.044715
+
+
 def gelu(x):
-    return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
+    x = np.asarray(x, dtype=np.float64)
+    return 0.5 * x * (1.0 + np.tanh(GELU_A * (x + GELU_B * x ** 3)))
 
 
 def gelu_grad(x):
-    cdf = 0.5 * (1.0 + erf(x / np.sqrt(2.0)))
-    pdf = np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)
-    return cdf + x * pdf
+    x = np.asarray(x, dtype=np.float64)
+    t = np.tanh(GELU_A * (x + GELU_B * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * GELU_A * (1.0 + 3.0 * GELU_B * x * x)
+
+
+def gelu_erf(x):
+    """The exact form 0.5 x (1 + erf(x / sqrt 2)) (for comparison only)."""
+    return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
 
 
 def pad_to(n: int, m: int) -> int:

@@ -112,7 +112,7 @@ EXPORTS = (
     "comet_proposal_forward", "comet_proposal_train_batch", "comet_proposal_add_samples",
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
-    "comet_get_launch_config", "comet_set_launch_config", "comet_autotune",
+    "comet_get_launch_config", "comet_set_launch_config", "comet_autotune", "comet_proposal_time_forward",
 )
 
 
@@ -180,6 +180,7 @@ def lib(build_if_missing: bool = False):
             L.comet_set_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
             L.comet_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(LaunchConfig), vp,
                                          ctypes.POINTER(i32)]
+            L.comet_proposal_time_forward.argtypes = [vp, vp, i64, i32, ctypes.POINTER(ctypes.c_float)]
             L.comet_plan_learned.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), vp,
                                              ctypes.POINTER(PlanResult), vp]
             L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
@@ -522,6 +523,12 @@ def comet_proposal_features(q, seqs, n, out_x):
 
 def comet_proposal_forward(q, x, n, out_y):
     _check(lib().comet_proposal_forward(q, _ptr(x), n, _ptr(out_y)))
+
+
+def comet_proposal_time_forward(q, x, n, reps=20) -> float:
+    ms = ctypes.c_float()
+    _check(lib().comet_proposal_time_forward(q, _ptr(x), n, reps, ctypes.byref(ms)))
+    return ms.value
 
 
 def comet_proposal_train_batch(q, x, target, weight, n, opts=None) -> float:

@@ -513,6 +513,14 @@ cudaError_t ensure_rows(comet_proposal* q, int64_t rows) {
 cudaError_t forward(comet_proposal* q, int64_t M, bool train, cudaStream_t s) {
     using namespace comet::mlp;
     const int W = q->width;
+    // inference: the four layers in one persistent kernel (the layered GEMMs
+    // remain for training, which keeps Z and the transposed activations)
+    if (!train && (q->in_dim == 64 || q->in_dim == 128) && W == 256 && q->out_dim <= 256) {
+        const uint16_t* w[4] = {q->wq[0], q->wq[1], q->wq[2], q->wq[3]};
+        const float* b[4] = {q->master + q->b_off[0], q->master + q->b_off[1], q->master + q->b_off[2],
+                             q->master + q->b_off[3]};
+        return mlp_forward_fused(q->X, M, q->in_dim, w, q->out_dim, b, q->Y, q->out_dim, q->d_err, q->p->num_sms, s);
+    }
     for (int l = 0; l < kLayers; ++l) {
         Epilogue ep;
         memset(&ep, 0, sizeof(ep));
@@ -721,7 +729,8 @@ comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* 
     if (!comet::mlp::tensor_maps_available())
         return qfail(COMET_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     {
-        const cudaError_t ge = comet::mlp::gemm_prepare();
+        cudaError_t ge = comet::mlp::gemm_prepare();
+        if (ge == cudaSuccess) ge = comet::mlp::fused_prepare();
         if (ge != cudaSuccess) return qcuda(ge, "GEMM kernel attributes");
     }
     int l_max = 0, n_modes = 0;
@@ -882,6 +891,30 @@ comet_status comet_proposal_forward(comet_proposal* q, const uint16_t* x, int64_
     QTRY(cudaMemsetAsync(q->d_err, 0, sizeof(int), s), "reset");
     QTRY(forward(q, n, false, s), "forward");
     QTRY(cudaMemcpyAsync(out_y, q->Y, sizeof(float) * n * q->out_dim, cudaMemcpyDefault, s), "copy y");
+    return check_err(q, s);
+}
+
+comet_status comet_proposal_time_forward(comet_proposal* q, const uint16_t* x, int64_t n, int32_t reps,
+                                         float* out_ms) {
+    if (!q || !x || n < 1 || reps < 1 || !out_ms) return qfail(COMET_ERR_INVALID_ARG, "arguments are required");
+    cudaStream_t s = q->p->stream;
+    QTRY(ensure_rows(q, n), "proposal activations");
+    QTRY(to_device(q->X, x, sizeof(uint16_t) * n * q->in_dim, s), "copy x");
+    QTRY(cudaMemsetAsync(q->d_err, 0, sizeof(int), s), "reset");
+    QTRY(forward(q, n, false, s), "forward");  // warm
+    cudaEvent_t e0, e1;
+    QTRY(cudaEventCreate(&e0), "event");
+    QTRY(cudaEventCreate(&e1), "event");
+    cudaError_t e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = forward(q, n, false, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return qcuda(e, "timed forward");
+    *out_ms = ms / (float)reps;
     return check_err(q, s);
 }
 

@@ -51,6 +51,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -141,12 +145,27 @@ __device__ __forceinline__ uint16_t to_bf16(float x) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// GELU in the tanh form of Hendrycks and Gimpel,
+//   0.5 x (1 + tanh(a (x + b x^3))), a = sqrt(2 / pi), b = 0.044715,
+// with the hardware tanh approximation (relative error about 2^-11, below
+// the BF16 rounding of the stored activations)
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kGeluA = 0.79788456080286536f;  // sqrt(2 / pi)
+constexpr float kGeluB = 0.044715f;
+
+__device__ __forceinline__ float gelu_f(float x) {
+    const float t = tanh_hw(kGeluA * (x + kGeluB * x * x * x));
+    return 0.5f * x * (1.f + t);
+}
 
 __device__ __forceinline__ float gelu_grad_f(float x) {
-    const float cdf = 0.5f * (1.f + erff(x * 0.70710678118654752f));
-    const float pdf = 0.39894228040143268f * __expf(-0.5f * x * x);
-    return cdf + x * pdf;
+    const float t = tanh_hw(kGeluA * (x + kGeluB * x * x * x));
+    return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * kGeluA * (1.f + 3.f * kGeluB * x * x);
 }
 
 struct __align__(8) Barriers {
@@ -315,6 +334,232 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ------------------------------------------------------------------------
+// Fused forward pass of the 4-layer MLP (in_dim <= 128, width 256, out_dim
+// <= 256): one persistent CTA per SM walks 128-row tiles; the four layers
+// are chained through one 256-column TMEM accumulator and a 64 KB
+// activation tile in shared memory, so a tile never leaves the SM between
+// layers.  Warps 0..15: epilogue (warp w reads TMEM lanes 32 (w mod 4).. and
+// columns 64 (w / 4)..), writing bias + GELU as BF16 into the activation
+// tile in the 128-byte-swizzled K-major layout the next tcgen05.mma reads
+// (16-byte chunk c of row r at chunk c ^ (r mod 8)); warp 16, one lane: TMA
+// producer (the X tile, and the weights as 64-column K slices of 256 rows
+// through a 3-stage ring); warp 17, one lane: MMA issuer.
+
+constexpr int kFEpiWarps = 16;
+constexpr int kFThreads = (kFEpiWarps + 2) * 32;
+constexpr int kFEpilogue = kFEpiWarps * 32;  // threads of the epilogue warps
+constexpr int kFRing = 3;
+constexpr uint32_t kWStage = 256 * BK * 2;   // 32 KB: one K slice of a weight
+constexpr uint32_t kXBlock = BM * BK * 2;    // 16 KB: one K slice of a tile
+
+struct __align__(8) FusedBars {
+    uint64_t x_full, x_free, acc_full, h_ready;
+    uint64_t w_full[kFRing], w_empty[kFRing];
+    uint32_t tmem_base, failed;
+};
+
+struct FusedParams {
+    const float* bias[4];
+    float* y;
+    int64_t ld_y;
+    int M, in_dim, out_dim;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    mlp_fused_forward_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w0,
+                             const __grid_constant__ CUtensorMap map_w1, const __grid_constant__ CUtensorMap map_w2,
+                             const __grid_constant__ CUtensorMap map_w3, FusedParams fp) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    const int n_xkb = fp.in_dim / BK;                       // 1 or 2 K slices of X
+    uint8_t* xs = smem;                                     // n_xkb x 16 KB
+    uint8_t* hs = xs + 2 * kXBlock;                         // 4 x 16 KB activations
+    uint8_t* ws = hs + 4 * kXBlock;                         // kFRing x 32 KB weights
+    FusedBars* bars = reinterpret_cast<FusedBars*>(ws + kFRing * kWStage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (fp.M + BM - 1) / BM;
+    const int kb_layer[4] = {n_xkb, 4, 4, 4};
+    const CUtensorMap* wmap[4] = {&map_w0, &map_w1, &map_w2, &map_w3};
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bars->x_full), 1);
+        mbar_init(smem_u32(&bars->x_free), 1);
+        mbar_init(smem_u32(&bars->acc_full), 1);
+        mbar_init(smem_u32(&bars->h_ready), kFEpilogue);
+        for (int s = 0; s < kFRing; ++s) {
+            mbar_init(smem_u32(&bars->w_full[s]), 1);
+            mbar_init(smem_u32(&bars->w_empty[s]), 1);
+        }
+        bars->failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&bars->tmem_base)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile uint32_t* failed = &bars->failed;
+
+    if (warp == kFEpiWarps) {
+        if (lane == 0) {
+            // ---- producer
+            uint32_t g = 0;  // weight slices issued
+            int it = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*failed; tile += gridDim.x, ++it) {
+                if (it > 0 && !mbar_wait(smem_u32(&bars->x_free), (uint32_t)(it - 1) & 1u)) {
+                    atomicExch(&bars->failed, 1u);
+                    break;
+                }
+                const uint32_t xb = smem_u32(&bars->x_full);
+                mbar_expect_tx(xb, (uint32_t)n_xkb * kXBlock);
+                for (int kb = 0; kb < n_xkb; ++kb)
+                    tma_load_2d(smem_u32(xs) + kb * kXBlock, &map_x, kb * BK, tile * BM, xb);
+                for (int l = 0; l < 4 && !*failed; ++l)
+                    for (int kb = 0; kb < kb_layer[l]; ++kb, ++g) {
+                        const int s = (int)(g % kFRing);
+                        const uint32_t use = g / kFRing;
+                        if (g >= (uint32_t)kFRing && !mbar_wait(smem_u32(&bars->w_empty[s]), (use & 1u) ^ 1u)) {
+                            atomicExch(&bars->failed, 1u);
+                            break;
+                        }
+                        const uint32_t fb = smem_u32(&bars->w_full[s]);
+                        mbar_expect_tx(fb, kWStage);
+                        tma_load_2d(smem_u32(ws) + s * kWStage, wmap[l], kb * BK, 0, fb);
+                    }
+            }
+        }
+    } else if (warp == kFEpiWarps + 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t idesc = instr_desc(BM, 256);
+            uint32_t g = 0, L = 0;
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+                if (!mbar_wait(smem_u32(&bars->x_full), (uint32_t)it & 1u)) {
+                    ok = false;
+                    break;
+                }
+                for (int l = 0; l < 4 && ok; ++l, ++L) {
+                    // the accumulator is free and the activations of the
+                    // previous layer are in place
+                    if (L > 0 && !mbar_wait(smem_u32(&bars->h_ready), (L - 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    for (int kb = 0; kb < kb_layer[l] && ok; ++kb, ++g) {
+                        const int s = (int)(g % kFRing);
+                        if (!mbar_wait(smem_u32(&bars->w_full[s]), (g / kFRing) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a = (l == 0 ? smem_u32(xs) : smem_u32(hs)) + kb * kXBlock;
+                        const uint32_t b = smem_u32(ws) + s * kWStage;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_bf16(tmem, smem_desc(a + kk * 32), smem_desc(b + kk * 32), idesc,
+                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(smem_u32(&bars->w_empty[s]));
+                    }
+                    mma_commit(smem_u32(&bars->acc_full));
+                    if (l == 0) mma_commit(smem_u32(&bars->x_free));
+                }
+            }
+            if (!ok) {
+                // unblock the epilogue warps: they see the flag and stop (in
+                // the normal case every accumulator phase is committed exactly
+                // once, so that each epilogue wait sees its own phase)
+                atomicExch(&bars->failed, 1u);
+                mma_commit(smem_u32(&bars->acc_full));
+            }
+        }
+    } else {
+        // ---- epilogue warps: row r = 32 (warp mod 4) + lane of the tile,
+        // a band of 256 / (kFEpiWarps / 4) columns
+        constexpr int kBand = 256 / (kFEpiWarps / 4);
+        const int quarter = warp & 3, part = warp >> 2;
+        const int r = quarter * 32 + lane;
+        uint32_t L = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            bool stop = false;
+            for (int l = 0; l < 4; ++l, ++L) {
+                const bool have = mbar_wait(smem_u32(&bars->acc_full), L & 1u);
+                if (!have) atomicExch(&bars->failed, 1u);
+                if (__any_sync(0xffffffffu, !have || *failed)) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const int row = tile * BM + r;
+                const int ncol = (l == 3) ? fp.out_dim : 256;
+                for (int c0 = kBand * part; c0 < kBand * part + kBand; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+                    if (c0 >= ncol) continue;
+                    const float* bias = fp.bias[l];
+                    if (l < 3) {
+                        // 32 BF16 = 64 bytes = four 16-byte chunks of row r of
+                        // K slice c0 / 64, placed by the 128-byte swizzle
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float a0 = gelu_f(v[2 * j] + bias[c0 + 2 * j]);
+                            const float a1 = gelu_f(v[2 * j + 1] + bias[c0 + 2 * j + 1]);
+                            pk[j] = (uint32_t)to_bf16(a0) | ((uint32_t)to_bf16(a1) << 16);
+                        }
+                        uint8_t* blk = hs + (c0 / 64) * kXBlock + r * 128;
+                        const int ch0 = ((c0 % 64) * 2) / 16;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int pc = (ch0 + q) ^ (r & 7);
+                            *reinterpret_cast<uint4*>(blk + pc * 16) =
+                                make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                        }
+                    } else if (row < fp.M) {
+                        float* out = fp.y + (int64_t)row * fp.ld_y + c0;
+                        const int nv = min(32, ncol - c0);
+                        if (nv == 32) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                *reinterpret_cast<float4*>(out + 4 * q) =
+                                    make_float4(v[4 * q] + bias[c0 + 4 * q], v[4 * q + 1] + bias[c0 + 4 * q + 1],
+                                                v[4 * q + 2] + bias[c0 + 4 * q + 2], v[4 * q + 3] + bias[c0 + 4 * q + 3]);
+                        } else {
+                            for (int j = 0; j < nv; ++j) out[j] = v[j] + bias[c0 + j];
+                        }
+                    }
+                }
+                // TMEM read and activations written: make the shared-memory
+                // writes visible to the tensor cores, then release the layer
+                tc_fence_before();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&bars->h_ready));
+            }
+            if (stop) break;
+        }
+    }
+    if (*failed && threadIdx.x == 0 && fp.err) atomicExch(fp.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+size_t fused_smem_bytes() { return 1024 + 6 * (size_t)kXBlock + kFRing * (size_t)kWStage + sizeof(FusedBars) + 64; }
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 
@@ -398,6 +643,54 @@ cudaError_t gemm_bf16(const Mat& A, const Mat& B, int64_t M, int N, int K, int k
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + bn - 1) / bn), (unsigned)splits);
     gemm_bf16_kernel<<<grid, kThreads, smem_req, s>>>(ma, mb, (int)M, N, K, k_chunk, bn, tmem_cols, ep);
     return cudaGetLastError();
+}
+
+cudaError_t mlp_forward_fused(const uint16_t* x, int64_t M, int in_dim, const uint16_t* const w[4], int out_dim,
+                              const float* const bias[4], float* y, int64_t ld_y, int* err, int num_sms,
+                              cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    if ((in_dim != 64 && in_dim != 128) || out_dim < 16 || out_dim > 256 || out_dim % 16 || M > (int64_t)INT32_MAX)
+        return cudaErrorInvalidValue;
+    for (int l = 0; l < 4; ++l)
+        if (reinterpret_cast<uintptr_t>(w[l]) & 15u) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(x) & 15u) return cudaErrorInvalidValue;
+    CUtensorMap mx, mw[4];
+    const Mat X{x, M, in_dim, in_dim};
+    const int din[4] = {in_dim, 256, 256, 256}, dout[4] = {256, 256, 256, out_dim};
+    if (!make_map(&mx, X, M, in_dim, BM)) return cudaErrorInvalidValue;
+    for (int l = 0; l < 4; ++l) {
+        const Mat W{w[l], dout[l], din[l], din[l]};
+        if (!make_map(&mw[l], W, dout[l], din[l], 256)) return cudaErrorInvalidValue;
+    }
+    const size_t smem = fused_smem_bytes();
+    cudaError_t e = fused_prepare();
+    if (e != cudaSuccess) return e;
+    FusedParams fp;
+    for (int l = 0; l < 4; ++l) fp.bias[l] = bias[l];
+    fp.y = y;
+    fp.ld_y = ld_y;
+    fp.M = (int)M;
+    fp.in_dim = in_dim;
+    fp.out_dim = out_dim;
+    fp.err = err;
+    const int tiles = (int)((M + BM - 1) / BM);
+    const int grid = tiles < num_sms ? tiles : num_sms;
+    mlp_fused_forward_kernel<<<grid, kFThreads, smem, s>>>(mx, mw[0], mw[1], mw[2], mw[3], fp);
+    return cudaGetLastError();
+}
+
+cudaError_t fused_prepare() {
+    static int raised[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && raised[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(mlp_fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem_bytes());
+    if (e == cudaSuccess && dev < 64) raised[dev] = 1;
+    return e;
 }
 
 }  // namespace mlp

@@ -51,6 +51,15 @@ cudaError_t gemm_bf16(const Mat& A, const Mat& B, int64_t M, int N, int K, int k
 // The tensor-map encoder from the driver (resolved once); false if absent.
 bool tensor_maps_available();
 
+// Fused forward pass of the 4-layer MLP (width 256): x [M][in_dim] BF16
+// (in_dim 64 or 128), w[l] BF16 row-major [out][in] (K-major), biases FP32,
+// y [M][ld_y] FP32 (out_dim <= 256, a multiple of 16).  One persistent CTA
+// per SM (at most num_sms CTAs).
+cudaError_t mlp_forward_fused(const uint16_t* x, int64_t M, int in_dim, const uint16_t* const w[4], int out_dim,
+                              const float* const bias[4], float* y, int64_t ld_y, int* err, int num_sms,
+                              cudaStream_t s);
+cudaError_t fused_prepare();
+
 // Raise the GEMM kernel's shared-memory limit to its largest configuration
 // on the current device (once; not a stream operation, so later launches
 // stay capturable).

@@ -1,13 +1,12 @@
 """Pins of the learned proposal's FP64 oracle (oracle/mlp.py) to facts that
-do not come from the oracle itself: textbook values of the normal CDF, the
-bfloat16 rounding rule, central differences of the loss, closed forms of
-the first AdamW step, and a width-1 network evaluated through a library
-normal CDF."""
+do not come from the oracle itself: the tanh-form GELU by hand with the
+library tanh and its distance to the exact (erf) GELU, the bfloat16 rounding
+rule, central differences of the loss, closed forms of the first AdamW step,
+and a width-1 network evaluated by hand."""
 import math
 
 import numpy as np
 import pytest
-from scipy.stats import norm
 
 import workloads as W
 from oracle import mlp
@@ -33,32 +32,38 @@ def test_bf16_round_to_nearest_even():
     np.testing.assert_array_equal(mlp.from_bf16_bits(b), mlp.bf16(np.linspace(-3, 3, 101)))
 
 
-def test_gelu_textbook_values():
-    # Phi(1) = 0.8413447460685429, Phi(2) = 0.9772498680518208 (normal CDF)
+def test_gelu_tanh_form():
+    # the tanh form, by hand with the library tanh at a few points
+    a, b = math.sqrt(2 / math.pi), 0.044715
+    for x in (-3.0, -1.0, -0.25, 0.5, 1.0, 2.5):
+        want = 0.5 * x * (1 + math.tanh(a * (x + b * x ** 3)))
+        assert float(mlp.gelu(x)) == pytest.approx(want, rel=1e-15, abs=1e-300)
     assert mlp.gelu(0.0) == 0.0
-    assert mlp.gelu(1.0) == pytest.approx(0.8413447460685429, abs=1e-15)
-    assert mlp.gelu(-1.0) == pytest.approx(-(1 - 0.8413447460685429), abs=1e-15)
-    assert mlp.gelu(2.0) == pytest.approx(2 * 0.9772498680518208, abs=1e-14)
-    assert mlp.gelu(12.0) == pytest.approx(12.0, abs=1e-12)
-    assert abs(mlp.gelu(-12.0)) < 1e-12
-    # derivative: Phi(0) = 1/2, and central differences elsewhere
-    assert mlp.gelu_grad(0.0) == 0.5
-    x = np.linspace(-5, 5, 41)
+    assert float(mlp.gelu(12.0)) == pytest.approx(12.0, abs=1e-12)
+    assert abs(float(mlp.gelu(-12.0))) < 1e-12
+    # a close approximation of the exact GELU 0.5 x (1 + erf(x / sqrt 2)):
+    # Phi(1) = 0.8413447460685429 (normal CDF) and |tanh form - exact| < 1e-3
+    assert float(mlp.gelu(1.0)) == pytest.approx(0.8413447460685429, abs=1e-3)
+    x = np.linspace(-6, 6, 241)
+    assert np.max(np.abs(mlp.gelu(x) - mlp.gelu_erf(x))) < 1e-3
+    # derivative: 1/2 at 0, central differences elsewhere
+    assert float(mlp.gelu_grad(0.0)) == 0.5
     h = 1e-6
     np.testing.assert_allclose(mlp.gelu_grad(x), (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), atol=1e-8)
 
 
-def test_width_one_network_through_library_cdf():
-    # 1 -> 1 -> 1 -> 1 -> 1 with weights w and biases b: by hand with
-    # scipy's normal CDF, gelu(z) = z Phi(z)
+def test_width_one_network_through_library_tanh():
+    # 1 -> 1 -> 1 -> 1 -> 1 with weights w and biases b, by hand with
+    # math.tanh
     ws = [0.5, -1.25, 2.0, 0.75]
     bs = [0.125, 0.25, -0.5, 1.0]
     params = [(np.array([[w]]), np.array([b])) for w, b in zip(ws, bs)]
+    a, c3 = math.sqrt(2 / math.pi), 0.044715
     x = 0.875
     h = x
     for l in range(3):
         z = ws[l] * h + bs[l]
-        h = z * norm.cdf(z)
+        h = 0.5 * z * (1 + math.tanh(a * (z + c3 * z ** 3)))
     want = ws[3] * h + bs[3]
     y, _ = mlp.forward(params, np.array([[x]]))
     assert y[0, 0] == pytest.approx(want, rel=1e-14)
