@@ -378,12 +378,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
     uint8_t* xs = smem;                                     // n_xkb x 16 KB
     uint8_t* hs = xs + 2 * kXBlock;                         // 4 x 16 KB activations
     uint8_t* ws = hs + 4 * kXBlock;                         // kFRing x 32 KB weights
-    FusedBars* bars = reinterpret_cast<FusedBars*>(ws + kFRing * kWStage);
+    float* bs = reinterpret_cast<float*>(ws + kFRing * kWStage);  // 4 x 256 biases
+    FusedBars* bars = reinterpret_cast<FusedBars*>(bs + 4 * 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (fp.M + BM - 1) / BM;
     const int kb_layer[4] = {n_xkb, 4, 4, 4};
     const CUtensorMap* wmap[4] = {&map_w0, &map_w1, &map_w2, &map_w3};
 
+    for (int t = threadIdx.x; t < 4 * 256; t += kFThreads) {
+        const int l = t >> 8, c = t & 255;
+        bs[t] = (l < 3 || c < fp.out_dim) ? fp.bias[l][c] : 0.f;
+    }
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&bars->x_full), 1);
         mbar_init(smem_u32(&bars->x_free), 1);
@@ -501,13 +506,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const int row = tile * BM + r;
                 const int ncol = (l == 3) ? fp.out_dim : 256;
                 for (int c0 = kBand * part; c0 < kBand * part + kBand; c0 += 32) {
                     float v[32];
                     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
                     if (c0 >= ncol) continue;
-                    const float* bias = fp.bias[l];
+                    const float* bias = bs + 256 * l;
                     if (l < 3) {
                         // 32 BF16 = 64 bytes = four 16-byte chunks of row r of
                         // K slice c0 / 64, placed by the 128-byte swizzle
@@ -526,18 +530,20 @@ __global__ void __launch_bounds__(kFThreads, 1)
                             *reinterpret_cast<uint4*>(blk + pc * 16) =
                                 make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                         }
-                    } else if (row < fp.M) {
-                        float* out = fp.y + (int64_t)row * fp.ld_y + c0;
-                        const int nv = min(32, ncol - c0);
-                        if (nv == 32) {
+                    } else {
+                        // turn the 32 x 32 block around in this warp's 4 KB of
+                        // the (now free) activation tile, XOR-swizzled, so that
+                        // each store writes 32 consecutive floats of one row
+                        float* tb = reinterpret_cast<float*>(hs) + warp * 1024;
 #pragma unroll
-                            for (int q = 0; q < 8; ++q)
-                                *reinterpret_cast<float4*>(out + 4 * q) =
-                                    make_float4(v[4 * q] + bias[c0 + 4 * q], v[4 * q + 1] + bias[c0 + 4 * q + 1],
-                                                v[4 * q + 2] + bias[c0 + 4 * q + 2], v[4 * q + 3] + bias[c0 + 4 * q + 3]);
-                        } else {
-                            for (int j = 0; j < nv; ++j) out[j] = v[j] + bias[c0 + j];
+                        for (int j = 0; j < 32; ++j) tb[lane * 32 + (j ^ lane)] = v[j] + bias[c0 + j];
+                        __syncwarp();
+                        const int row0 = tile * BM + quarter * 32, col = c0 + lane;
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int rw = row0 + rr;
+                            if (rw < fp.M && col < ncol) fp.y[(int64_t)rw * fp.ld_y + col] = tb[rr * 32 + (lane ^ rr)];
                         }
+                        __syncwarp();
                     }
                 }
                 // TMEM read and activations written: make the shared-memory
@@ -558,7 +564,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
 }
 
-size_t fused_smem_bytes() { return 1024 + 6 * (size_t)kXBlock + kFRing * (size_t)kWStage + sizeof(FusedBars) + 64; }
+size_t fused_smem_bytes() {
+    return 1024 + 6 * (size_t)kXBlock + kFRing * (size_t)kWStage + 4 * 256 * sizeof(float) + sizeof(FusedBars) + 64;
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
