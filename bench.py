@@ -301,6 +301,8 @@ def run_gpu(args):
         line["plan"] = plan_times(P, insts[: args.plan_instances])
     if rank == 0 and args.hetero:
         line["hetero"] = hetero_times(P)
+    if rank == 0 and args.batch_plan:
+        line["batch_plan"] = batch_plan_times(P)
     if rank == 0 and args.bimanual:
         line["bimanual"] = bimanual_times(P)
     if rank == 0 and args.learned_instances > 0:
@@ -403,6 +405,45 @@ def hetero_times(P, n_inst=256, per=512, n_split=32):
         "split_per_instance_solves_per_s": c_per / t_per, "split_per_instance_ms": t_per * 1e3,
         "split_one_launch_ms": t_sub * 1e3,
         "note": "converged solves/s (device time); one launch over all instances vs one launch per instance",
+    }
+
+
+def batch_plan_times(P, n_inst=256, n_seq=16):
+    """Algorithm 1 on the mixed workload for many instances at once: every
+    instance seeded with its one-segment orders and a fifth of its
+    two-segment ones, beam 16, B = 256 per instance, three rounds, K_ref = 16
+    refined with t_ref = 600.  All instances through the batched planner (one
+    evaluator launch per round for all of them) against the single-instance
+    planner called once per instance on the first `n_seq` instances.  Device
+    time of exploration + refinement, plans per second."""
+    insts = [W.push_mixed_instance(s) for s in range(n_inst)]
+
+    def seeds(inst):
+        two = [(a, b) for a in range(12) for b in range(12)] if inst["max_segments"] >= 2 else []
+        return [(m,) for m in range(12)] + two[::5]
+
+    sd = [seeds(i) for i in insts]
+    opts = dict(k=16, batch=256, rounds=3, k_ref=16, ref_iters=600)
+    prob = P.Problem(insts)
+    P.comet_plan_batch(prob.handle, list(range(n_seq)), sd[:n_seq], opts)  # warm
+    rb = P.comet_plan_batch(prob.handle, list(range(n_inst)), sd, opts)
+    t_all = (rb[0]["explore_ms"] + rb[0]["refine_ms"]) / 1e3
+    rs = P.comet_plan_batch(prob.handle, list(range(n_seq)), sd[:n_seq], opts)
+    t_sub = (rs[0]["explore_ms"] + rs[0]["refine_ms"]) / 1e3
+    t_one, same = 0.0, 0
+    for i in range(n_seq):
+        r = P.comet_plan(prob.handle, i, P.pack_mode_seqs(sd[i], np.full(len(sd[i]), i, np.int32)), len(sd[i]),
+                         opts)
+        t_one += (r["explore_ms"] + r["refine_ms"]) / 1e3
+        same += int(r["best"] == rs[i]["best"] and r["best_cost"] == rs[i]["best_cost"])
+    prob.close()
+    feas = sum(int(r["best_status"] == 0) for r in rb)
+    return {
+        "instances": n_inst, "batched_ms": t_all * 1e3, "batched_plans_per_s": n_inst / t_all,
+        "feasible_plans": feas, "evaluations_median": float(np.median([r["evaluations"] for r in rb])),
+        "subset": n_seq, "subset_batched_ms": t_sub * 1e3, "subset_one_by_one_ms": t_one * 1e3,
+        "subset_speedup": t_one / t_sub, "subset_same_plans": same,
+        "note": "device time (exploration + refinement); one-by-one = the single-instance planner per instance",
     }
 
 
@@ -555,6 +596,7 @@ def main():
     ap.add_argument("--orders", type=int, default=0, help="profiling only: solve this prefix of each enumeration")
     ap.add_argument("--plan-instances", type=int, default=4, help="instances for the plan-time comparison (0 = skip)")
     ap.add_argument("--hetero", type=int, default=1, help="mixed-workload leg (1) or skip it (0)")
+    ap.add_argument("--batch-plan", type=int, default=1, help="batched multi-instance planner leg (1) or skip it (0)")
     ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=8,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")

@@ -320,6 +320,20 @@ comet_status comet_set_launch_config(comet_problem* p, const comet_launch_config
 comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int64_t n, int32_t max_iters,
                             comet_launch_config* out, float* out_ms, int32_t* n_candidates);
 
+/* Algorithm 1 for many instances at once: one frontier per instance; the
+ * seed batches of all instances are evaluated in one persistent launch, and
+ * each round expands every frontier and evaluates all next batches (opts->batch
+ * slots per instance) in ONE persistent launch before each frontier adds its
+ * results; the round is captured once as a CUDA graph (use_graph) and
+ * replayed.  Refinement re-solves the K_ref best of every instance in one
+ * launch.  seeds: host or device orders, instance i's in
+ * [seed_offsets[i], seed_offsets[i+1]) (seed_offsets[0] = 0, each slice
+ * non-empty, orders of instance instances[i]); out[i] as comet_plan, with
+ * explore_ms and refine_ms the times of the whole batch.  Synchronises. */
+comet_status comet_plan_batch(comet_problem* p, int32_t n_instances, const int32_t* instances,
+                              const comet_mode_seq* seeds, const int64_t* seed_offsets, const comet_plan_opts* opts,
+                              comet_plan_result* out);
+
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 

@@ -113,6 +113,7 @@ EXPORTS = (
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
     "comet_get_launch_config", "comet_set_launch_config", "comet_autotune", "comet_proposal_time_forward",
+    "comet_plan_batch",
 )
 
 
@@ -181,6 +182,7 @@ def lib(build_if_missing: bool = False):
             L.comet_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(LaunchConfig), vp,
                                          ctypes.POINTER(i32)]
             L.comet_proposal_time_forward.argtypes = [vp, vp, i64, i32, ctypes.POINTER(ctypes.c_float)]
+            L.comet_plan_batch.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(PlanOpts), vp]
             L.comet_plan_learned.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), vp,
                                              ctypes.POINTER(PlanResult), vp]
             L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
@@ -376,6 +378,33 @@ def comet_plan(problem, instance: int, seeds, n_seeds: int, opts=None, out_traj=
     return {"best": best, "best_cost": r.best_cost, "best_viol": r.best_viol, "best_status": r.best_status,
             "rounds_run": r.rounds_run, "evaluations": r.evaluations, "explore_ms": r.explore_ms,
             "refine_ms": r.refine_ms}
+
+
+def comet_plan_batch(problem, instances, seeds_per_instance, opts=None) -> list:
+    """Algorithm 1 for several instances at once (comet_plan_batch);
+    seeds_per_instance: a list (one per instance) of lists of mode tuples."""
+    if opts is None or isinstance(opts, dict):
+        o = comet_default_plan_opts()
+        for k, v in (opts or {}).items():
+            setattr(o, k, v)
+        opts = o
+    inst = np.ascontiguousarray(instances, dtype=np.int32)
+    offs = np.zeros(len(inst) + 1, np.int64)
+    allseq, idx = [], []
+    for i, seeds in enumerate(seeds_per_instance):
+        allseq += list(seeds)
+        idx += [int(inst[i])] * len(seeds)
+        offs[i + 1] = offs[i] + len(seeds)
+    packed = pack_mode_seqs(allseq, np.array(idx, np.int32))
+    res = (PlanResult * len(inst))()
+    _check(lib().comet_plan_batch(problem, len(inst), inst.ctypes.data, packed.ctypes.data, offs.ctypes.data,
+                                  ctypes.byref(opts), res))
+    out = []
+    for r in res:
+        out.append({"best": tuple(int(r.best.modes[i]) for i in range(r.best.len)), "best_cost": r.best_cost,
+                    "best_viol": r.best_viol, "best_status": r.best_status, "rounds_run": r.rounds_run,
+                    "evaluations": r.evaluations, "explore_ms": r.explore_ms, "refine_ms": r.refine_ms})
+    return out
 
 
 def decode_code(code: int, n_modes: int = 12):

@@ -541,3 +541,257 @@ extern "C" comet_status comet_plan_learned(comet_problem* p, int32_t instance, c
     if (!q) return ffail(COMET_ERR_INVALID_ARG, "proposal is required");
     return comet::plan_impl(p, instance, seeds, n_seeds, opts, q, out, out_traj);
 }
+
+// ------------------------------------------------- batched planner
+
+namespace {
+
+struct SlotSrc {
+    const comet_mode_seq* next;
+    const int64_t* n;
+};
+
+// next batches of all frontiers into fixed slots of `batch` orders; slots
+// past a frontier's count get length 0 (the evaluator skips them)
+__global__ void gather_next_kernel(const SlotSrc* src, int n_inst, int batch, comet_mode_seq* out) {
+    const int64_t total = (int64_t)n_inst * batch;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / batch), j = (int)(t - (int64_t)i * batch);
+        comet_mode_seq q;
+        if (j < *src[i].n) {
+            q = src[i].next[j];
+        } else {
+            memset(&q, 0, sizeof(q));
+        }
+        out[t] = q;
+    }
+}
+
+// ranked entries of one frontier -> orders; ranks past |V| become empty
+// slots (length 0), which the evaluator skips
+__global__ void decode_top_kernel(const comet::TopKey* top, int k, const unsigned long long* nV, int instance,
+                                  int n_modes, comet_mode_seq* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    comet_mode_seq q;
+    memset(&q, 0, sizeof(q));
+    q.instance = instance;
+    if ((unsigned long long)i < *nV) {
+        unsigned long long code = top[i].code;
+        const unsigned long long base = (unsigned long long)(n_modes + 1);
+        const int L = (int)(code % base);
+        code /= base;
+        q.len = (uint8_t)L;
+        for (int j = 0; j < L && j < COMET_MAX_SEGMENTS; ++j) {
+            q.modes[j] = (uint16_t)(code % base - 1);
+            code /= base;
+        }
+    }
+    out[i] = q;
+}
+
+}  // namespace
+
+extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const int32_t* instances,
+                                         const comet_mode_seq* seeds, const int64_t* seed_offsets,
+                                         const comet_plan_opts* po_in, comet_plan_result* out) {
+    if (!p || n_inst < 1 || !instances || !seeds || !seed_offsets || !out)
+        return ffail(COMET_ERR_INVALID_ARG, "problem, instances, seeds, offsets and out are required");
+    comet_plan_opts po;
+    if (po_in)
+        po = *po_in;
+    else
+        comet_default_plan_opts(&po);
+    if (po.k < 1 || po.batch < 1 || po.rounds < 0 || po.k_ref < 1 || po.k_ref > comet::kChunk)
+        return ffail(COMET_ERR_INVALID_ARG, "bad planner options");
+    for (int i = 0; i < n_inst; ++i) {
+        if (instances[i] < 0 || instances[i] >= (int)p->inst.size())
+            return ffail(COMET_ERR_INVALID_ARG, "instance out of range");
+        if (seed_offsets[i + 1] <= seed_offsets[i]) return ffail(COMET_ERR_INVALID_ARG, "every instance needs seeds");
+    }
+    if (seed_offsets[0] != 0) return ffail(COMET_ERR_INVALID_ARG, "seed_offsets[0] must be 0");
+    const int64_t S = seed_offsets[n_inst];
+    // private stream (a graph cannot be captured on the legacy stream)
+    cudaStream_t user_stream = p->stream;
+    cudaStream_t s = nullptr;
+    FTRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "planner stream");
+    {
+        cudaEvent_t e0;
+        FTRY(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "event");
+        cudaEventRecord(e0, user_stream);
+        cudaStreamWaitEvent(s, e0, 0);
+        cudaEventDestroy(e0);
+    }
+    struct StreamSwap {
+        comet_problem* p;
+        cudaStream_t user, own;
+        ~StreamSwap() {
+            cudaEvent_t e1;
+            if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e1, own);
+                cudaStreamWaitEvent(user, e1, 0);
+                cudaEventDestroy(e1);
+            }
+            cudaStreamSynchronize(own);
+            p->stream = user;
+            cudaStreamDestroy(own);
+        }
+    } swap{p, user_stream, s};
+    p->stream = s;
+    // one frontier per instance
+    std::vector<comet_frontier*> fr(n_inst, nullptr);
+    struct FGuard {
+        std::vector<comet_frontier*>* f;
+        ~FGuard() {
+            for (auto* x : *f)
+                if (x) comet_frontier_destroy(x);
+        }
+    } fguard{&fr};
+    const int32_t batch = po.batch;
+    for (int i = 0; i < n_inst; ++i) {
+        const int64_t n0 = seed_offsets[i + 1] - seed_offsets[i];
+        const int64_t cap = po.budget > 0 ? std::max<int64_t>(po.budget, n0) : n0 + (int64_t)po.rounds * batch;
+        const comet_status st = comet_frontier_create(p, instances[i], cap, (int32_t)std::min<int64_t>(batch, cap),
+                                                      std::max(po.k, po.k_ref), &fr[i]);
+        if (st != COMET_OK) return st;
+    }
+    const int64_t n_round = (int64_t)n_inst * batch, n_ref_all = (int64_t)n_inst * po.k_ref;
+    const int64_t n_eval_max = std::max<int64_t>({S, n_round, n_ref_all});
+    comet_status st = comet::reserve_eval(p, n_eval_max);
+    if (st != COMET_OK) return st;
+    DevBuf buf;
+    const size_t b_seq = ((sizeof(comet_mode_seq) * n_eval_max + 255) / 256) * 256;
+    const size_t b_f = ((sizeof(float) * n_eval_max + 255) / 256) * 256;
+    const size_t b_src = ((sizeof(SlotSrc) * n_inst + 255) / 256) * 256;
+    FTRY(cudaMalloc(&buf.p, b_seq + 2 * b_f + b_src), "planner buffers");
+    char* bp = (char*)buf.p;
+    comet_mode_seq* d_seqs = (comet_mode_seq*)bp;
+    float* d_cost = (float*)(bp + b_seq);
+    int32_t* d_status = (int32_t*)(bp + b_seq + b_f);
+    SlotSrc* d_src = (SlotSrc*)(bp + b_seq + 2 * b_f);
+    {
+        std::vector<SlotSrc> h(n_inst);
+        for (int i = 0; i < n_inst; ++i) h[i] = SlotSrc{fr[i]->d.next, fr[i]->d.n_next};
+        FTRY(cudaMemcpyAsync(d_src, h.data(), sizeof(SlotSrc) * n_inst, cudaMemcpyHostToDevice, s), "slots");
+    }
+    cudaEvent_t ev[4];
+    for (auto& e : ev) FTRY(cudaEventCreate(&e), "events");
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    const float eps = (float)p->opts.eps_feas, mmu = (float)p->opts.merit_mu;
+    FTRY(cudaEventRecord(ev[0], s), "event");
+    // seed batches of every instance in one launch
+    FTRY(cudaMemcpyAsync(d_seqs, seeds, sizeof(comet_mode_seq) * S, cudaMemcpyDefault, s), "copy seeds");
+    st = comet::launch_eval_device(p, d_seqs, S, nullptr, nullptr, 0, d_cost, nullptr, d_status);
+    if (st != COMET_OK) return st;
+    for (int i = 0; i < n_inst; ++i) {
+        const int64_t o = seed_offsets[i], n = seed_offsets[i + 1] - o;
+        FTRY(comet::launch_frontier_add(fr[i]->d, d_seqs + o, n, nullptr, d_cost + o, p->d_viol + o, eps, mmu, s),
+             "add seeds");
+    }
+    // one round: every frontier expands, all next batches are evaluated in
+    // one persistent launch, each frontier adds its slots
+    auto round = [&]() -> comet_status {
+        for (int i = 0; i < n_inst; ++i) {
+            const cudaError_t e = comet::launch_expand(fr[i]->d, po.k, fr[i]->batch, po.budget, s);
+            if (e != cudaSuccess) return fcuda(e, "expand");
+        }
+        gather_next_kernel<<<(unsigned)std::min<int64_t>((n_round + 255) / 256, 4096), 256, 0, s>>>(d_src, n_inst,
+                                                                                                   batch, d_seqs);
+        FTRY(cudaGetLastError(), "gather");
+        comet_status r = comet::launch_eval_device(p, d_seqs, n_round, nullptr, nullptr, 0, d_cost, nullptr, d_status);
+        if (r != COMET_OK) return r;
+        for (int i = 0; i < n_inst; ++i) {
+            comet::FrontierDev Fa = fr[i]->d;
+            Fa.batch_cap = batch;
+            const int64_t o = (int64_t)i * batch;
+            const cudaError_t e = comet::launch_frontier_add(Fa, d_seqs + o, batch, fr[i]->d.n_next, d_cost + o,
+                                                             p->d_viol + o, eps, mmu, s);
+            if (e != cudaSuccess) return fcuda(e, "add");
+        }
+        return COMET_OK;
+    };
+    if (po.use_graph && po.rounds > 0) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        FTRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const comet_status rs = round();
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rs != COMET_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rs;
+        }
+        if (e != cudaSuccess) return fcuda(e, "end capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fcuda(e, "instantiate");
+        for (int r = 0; r < po.rounds && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return fcuda(e, "graph launch");
+    } else {
+        for (int r = 0; r < po.rounds; ++r) {
+            st = round();
+            if (st != COMET_OK) return st;
+        }
+    }
+    FTRY(cudaEventRecord(ev[1], s), "event");
+    // refinement: the K_ref best of every instance, ranked and decoded on the
+    // device (ranks past |V_i| become empty slots), re-solved in one launch
+    FTRY(cudaEventRecord(ev[2], s), "event");
+    for (int i = 0; i < n_inst; ++i) {
+        cudaError_t e = cudaSuccess;
+        const comet::TopKey* top = comet::launch_topk(fr[i]->d, po.k_ref, s, &e);
+        if (!top) return fcuda(e, "top-k");
+        decode_top_kernel<<<(unsigned)((po.k_ref + 127) / 128), 128, 0, s>>>(
+            top, po.k_ref, fr[i]->d.nV, instances[i], p->inst[instances[i]].n_modes, d_seqs + (int64_t)i * po.k_ref);
+        FTRY(cudaGetLastError(), "decode");
+    }
+    const int32_t t_ref = po.ref_iters > 0 ? po.ref_iters : (p->opts.ref_iters > 0 ? p->opts.ref_iters : 1500);
+    st = comet::launch_eval_device(p, d_seqs, n_ref_all, nullptr, nullptr, t_ref, d_cost, nullptr, d_status);
+    if (st != COMET_OK) return st;
+    FTRY(cudaEventRecord(ev[3], s), "event");
+    std::vector<float> cost(n_ref_all), viol(n_ref_all);
+    std::vector<int32_t> status(n_ref_all);
+    std::vector<comet_mode_seq> sq(n_ref_all);
+    FTRY(cudaMemcpyAsync(cost.data(), d_cost, sizeof(float) * n_ref_all, cudaMemcpyDeviceToHost, s), "copy");
+    FTRY(cudaMemcpyAsync(viol.data(), p->d_viol, sizeof(float) * n_ref_all, cudaMemcpyDeviceToHost, s), "copy");
+    FTRY(cudaMemcpyAsync(status.data(), d_status, sizeof(int32_t) * n_ref_all, cudaMemcpyDeviceToHost, s), "copy");
+    FTRY(cudaMemcpyAsync(sq.data(), d_seqs, sizeof(comet_mode_seq) * n_ref_all, cudaMemcpyDeviceToHost, s), "copy");
+    FTRY(cudaStreamSynchronize(s), "synchronise");
+    std::vector<int64_t> n_ev(n_inst, 0);
+    for (int i = 0; i < n_inst; ++i) {
+        int32_t err = 0;
+        st = comet_frontier_size(fr[i], &n_ev[i], &err);
+        if (st != COMET_OK) return st;
+        if (err) return ffail(COMET_ERR_BUDGET, "an evaluated set overflowed its capacity");
+    }
+    float explore_ms = 0.f, refine_ms = 0.f;
+    cudaEventElapsedTime(&explore_ms, ev[0], ev[1]);
+    cudaEventElapsedTime(&refine_ms, ev[2], ev[3]);
+    for (int i = 0; i < n_inst; ++i) {
+        comet_plan_result& r = out[i];
+        memset(&r, 0, sizeof(r));
+        r.best_status = COMET_TO_MAX_ITER;
+        r.rounds_run = po.rounds;
+        r.evaluations = n_ev[i];
+        r.explore_ms = explore_ms;
+        r.refine_ms = refine_ms;
+        int64_t best = -1;
+        for (int64_t j = 0; j < po.k_ref; ++j) {
+            const int64_t t = (int64_t)i * po.k_ref + j;
+            const bool feas = status[t] == COMET_TO_CONVERGED && viol[t] <= (float)p->opts.eps_feas;
+            if (feas && (best < 0 || cost[t] < cost[best])) best = t;
+        }
+        if (best >= 0) {
+            r.best = sq[best];
+            r.best_cost = cost[best];
+            r.best_viol = viol[best];
+            r.best_status = status[best];
+        }
+    }
+    return COMET_OK;
+}
