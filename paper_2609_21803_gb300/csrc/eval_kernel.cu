@@ -243,15 +243,11 @@ struct Smem {
     float* lam;  // [3 + 11 Nmax]
     float* dz;   // [7 Nmax + 4] interleaved step
     float* gr;   // [7 Nmax + 4] interleaved AL gradient
-    float* M;    // [81] sweep matrix
-    float* V;    // [16] value-function Hessian
-    float* v;    // [4]  value-function gradient
-    float* misc; // [16]
 };
 
 __host__ __device__ inline size_t smem_floats(int Nmax) {
     const size_t f = (size_t)kRing * (kSweepSlot + kGainSlot) + (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
-                     3 * (size_t)Nmax + 3 + 11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4) + 81 + 16 + 4 + 16;
+                     3 * (size_t)Nmax + 3 + 11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4);
     return (f + 3) / 4 * 4;  // every warp's block starts 16-byte aligned
 }
 
@@ -266,11 +262,7 @@ __device__ __forceinline__ Smem carve(float* base, int Nmax) {
     s.us = p; p += 3 * Nmax;
     s.lam = p; p += 3 + 11 * Nmax;
     s.dz = p; p += 7 * Nmax + 4;
-    s.gr = p; p += 7 * Nmax + 4;
-    s.M = p; p += 81;
-    s.V = p; p += 16;
-    s.v = p; p += 4;
-    s.misc = p;
+    s.gr = p;
     return s;
 }
 
@@ -281,9 +273,17 @@ struct Ctx {
     uint16_t modes[COMET_MAX_SEGMENTS];
     int len, N, Nmax;
     Smem sm;
-    float* rec;  // this warp's stage records
+    float* rec;  // this warp's stage records (chunk-major, see rec_chunk)
     int lane;
 };
+
+// Stage records are stored chunk-major: float4 chunk q (record floats
+// 4q .. 4q+3) of stage k sits at rec + 4 (q N_max + k), so that the
+// stage-parallel passes (lane = stage) move whole 128-byte lines, while the
+// sequential passes still fetch a stage's chunks 16 bytes at a time.
+__device__ __forceinline__ float4* rec_chunk(const Ctx& C, int q, int k) {
+    return reinterpret_cast<float4*>(C.rec + 4 * ((size_t)q * C.Nmax + k));
+}
 
 // Phase A over all stages.  Computes the violation / stationarity /
 // complementarity measures of the current iterate, the AL gradient (into
@@ -439,15 +439,15 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
 #pragma unroll
             for (int i = 0; i < 4; ++i) A[tri(11, 7 + i)] = gx[i];
             // eliminate the u block (3 Cholesky steps); a non-positive pivot
-            // marks the record (the sweep then reports failure)
+            // marks the record (the sweep then reports failure).  The
+            // diagonal keeps 1 / l_jj, which is all the control step needs.
             bool pd = true;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const float d = A[tri(j, j)];
                 pd = pd && (d > 0.f);
-                const float l = sqrtf(fmaxf(d, 1e-30f));
-                const float il = 1.f / l;
-                A[tri(j, j)] = l;
+                const float il = rsqrtf(fmaxf(d, 1e-30f));
+                A[tri(j, j)] = il;
 #pragma unroll
                 for (int i = j + 1; i < 12; ++i) A[tri(i, j)] *= il;
 #pragma unroll
@@ -470,10 +470,9 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
 #pragma unroll
                 for (int j = 3; j <= i; ++j)
                     if (!(i == 11 && j == 11)) rec[36 + tri(i - 3, j - 3)] = A[tri(i, j)];
-            float4* dst = reinterpret_cast<float4*>(C.rec + (size_t)k * kRec);
 #pragma unroll
             for (int q = 0; q < kRec / 4; ++q)
-                dst[q] = make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
+                *rec_chunk(C, q, k) = make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
         }
     }
     __syncwarp();
@@ -523,34 +522,29 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     return m;
 }
 
-// Entry (i, j) of the 9x9 lower triangle at flat index t (row-major).
-__device__ __forceinline__ void untri9(int t, int& i, int& j) {
-    i = 0;
-    while ((i + 1) * (i + 2) / 2 <= t) ++i;
-    j = t - i * (i + 1) / 2;
-}
-
 // Phase B: backward sweep over k = N-1 .. 0.  Only the x_{k+1} block is
-// eliminated on this sequential path.  Each stage leaves the raw y-factor
-// columns (pivots, y-y and (x, rhs)-y entries) in its record; the gains are
-// formed afterwards in a stage-parallel pass (phase_b_gains).  Records are
-// fetched three stages ahead.  Returns false if a pivot is not positive.
+// eliminated on this sequential path.  The sweep is a dependent chain of
+// small operations, so every lane runs the whole stage in registers: the
+// reduced 9 x 9 lower triangle of the record (rows y_0..3, x_0..3, rhs) is
+// read as shared-memory broadcasts, V_{k+1} and v_{k+1} stay in registers,
+// and no lane waits on another within a stage.  Each stage leaves the raw
+// y-factor columns (pivots, y-y and (x, rhs)-y entries) in its record; the
+// gains are formed afterwards in a stage-parallel pass (phase_b_gains).
+// Records arrive kRing stages ahead.  Returns false if a pivot is not
+// positive.
 __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_from_gr = false) {
     const DevInstance& P = *C.P;
     const int N = C.N, Np1 = C.N + 1, lane = C.lane;
     Smem& S = C.sm;
-    // this lane's two entries of the 9x9 lower triangle (flat t0 = lane,
-    // t1 = lane + 32; only the first 44 are stored in the record)
-    int i0, j0, i1, j1;
-    untri9(lane, i0, j0);
-    untri9(lane + 32, i1, j1);
-    const bool has1 = lane + 32 < 44;
-    // V_N: terminal cost w_T |pose_N - goal|^2
-    if (lane < 16) S.V[lane] = ((lane % 5 == 0) && lane < 15) ? 2.f * P.w_terminal : 0.f;
-    if (lane < 4)
-        S.v[lane] = (lane < 3 && !rhs_from_gr)
-                        ? 2.f * P.w_terminal * ((S.xh[lane * Np1 + N] - P.goal[lane]) + S.xl[lane * Np1 + N])
-                        : 0.f;
+    // V_N, v_N: terminal cost w_T |pose_N - goal|^2 (lower triangle tri(i, j))
+    float V[10], v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) V[tri(i, j)] = (i == j && i < 3) ? 2.f * P.w_terminal : 0.f;
+        v[i] = (i < 3 && !rhs_from_gr) ? 2.f * P.w_terminal * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N])
+                                       : 0.f;
+    }
     // copy ring: stage k's record floats 32..79 (pd flag at 33, reduced
     // matrix at 36..79) arrive kRing stages ahead; one commit group per stage
     // (lanes 0..11 copy 16 bytes each)
@@ -558,42 +552,52 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
     for (int d = 0; d < kRing; ++d) {
         const int kk = N - 1 - d;
         if (kk >= 0 && lane < kSweepSlot / 4)
-            cp_async16(S.ring_b + d * kSweepSlot + 4 * lane, C.rec + (size_t)kk * kRec + 32 + 4 * lane);
+            cp_async16(S.ring_b + d * kSweepSlot + 4 * lane, rec_chunk(C, 8 + lane, kk));
         cp_async_commit();
     }
-    __syncwarp();
     bool ok = true;
     for (int k = N - 1; k >= 0; --k) {
         const int slot = (N - 1 - k) % kRing;
         cp_async_wait<kRing - 1>();
         __syncwarp();
-        const float* sl = S.ring_b + slot * kSweepSlot;
-        const float c0 = sl[4 + lane], c1 = has1 ? sl[4 + lane + 32] : 0.f;
-        const bool pd_u = sl[1] > 0.f;
+        const float4* sl = reinterpret_cast<const float4*>(S.ring_b + slot * kSweepSlot);
+        float m[44];
+        const float4 hd = sl[0];
+#pragma unroll
+        for (int q = 0; q < 11; ++q) {
+            const float4 t = sl[1 + q];
+            m[4 * q] = t.x;
+            m[4 * q + 1] = t.y;
+            m[4 * q + 2] = t.z;
+            m[4 * q + 3] = t.w;
+        }
+        bool pd = hd.y > 0.f;
         __syncwarp();
         {
             // refill this slot with the record kRing stages further on
             const int kk = k - kRing;
             if (kk >= 0 && lane < kSweepSlot / 4)
-                cp_async16(S.ring_b + slot * kSweepSlot + 4 * lane, C.rec + (size_t)kk * kRec + 32 + 4 * lane);
+                cp_async16(S.ring_b + slot * kSweepSlot + 4 * lane, rec_chunk(C, 8 + lane, kk));
             cp_async_commit();
         }
-        // load the reduced matrix and add V_{k+1}, v_{k+1} to the x_{k+1} block
-        // (entries t < 10 are the y-y block; t = 36..39 are (rhs, y_j))
-        S.M[i0 * 9 + j0] = (lane < 10) ? c0 + S.V[i0 * 4 + j0] : c0;
-        if (has1) S.M[i1 * 9 + j1] = (i1 == 8 && j1 < 4) ? c1 + S.v[j1] : c1;
-        __syncwarp();
-        // eliminate the 4 x_{k+1} columns (each lane updates only entries in
-        // columns > j and reads only column j: no intra-step hazard)
-        bool pd = pd_u;
+        // add V_{k+1} to the y-y block and v_{k+1} to the (rhs, y) row
+#pragma unroll
+        for (int t = 0; t < 10; ++t) m[t] += V[t];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[tri(8, j)] += v[j];
+        // eliminate the 4 x_{k+1} columns (the (rhs, rhs) entry is not kept)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float p = S.M[j * 9 + j];
+            const float p = m[tri(j, j)];
             pd = pd && (p > 0.f);
             const float ip = __fdividef(1.f, p);
-            if (j0 > j) S.M[i0 * 9 + j0] -= S.M[i0 * 9 + j] * S.M[j0 * 9 + j] * ip;
-            if (has1 && j1 > j) S.M[i1 * 9 + j1] -= S.M[i1 * 9 + j] * S.M[j1 * 9 + j] * ip;
-            __syncwarp();
+#pragma unroll
+            for (int i = j + 1; i < 9; ++i) {
+                const float a = m[tri(i, j)] * ip;
+#pragma unroll
+                for (int l = j + 1; l <= i; ++l)
+                    if (!(i == 8 && l == 8)) m[tri(i, l)] -= a * m[tri(l, j)];
+            }
         }
         if (!__all_sync(kFull, pd)) {
             ok = false;
@@ -602,84 +606,80 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
         // raw y-factor columns for the gains, over the consumed record entries:
         //   36 + tri(i, j) for the y-y block (i, j < 4, 10 entries)
         //   46 + 4 c + j  for row (x0..x3, rhs) = 4 + c, column j (20 entries)
-        float* rec = C.rec + (size_t)k * kRec;
-        if (lane < 10) rec[36 + lane] = S.M[i0 * 9 + j0];
-        else if (lane < 30) {
-            const int c = (lane - 10) >> 2, j = (lane - 10) & 3;
-            rec[46 + 4 * c + j] = S.M[(4 + c) * 9 + j];
+        if (lane == 0) {
+            *rec_chunk(C, 9, k) = make_float4(m[0], m[1], m[2], m[3]);
+            *rec_chunk(C, 10, k) = make_float4(m[4], m[5], m[6], m[7]);
+            *rec_chunk(C, 11, k) = make_float4(m[8], m[9], m[tri(4, 0)], m[tri(4, 1)]);
+            *rec_chunk(C, 12, k) = make_float4(m[tri(4, 2)], m[tri(4, 3)], m[tri(5, 0)], m[tri(5, 1)]);
+            *rec_chunk(C, 13, k) = make_float4(m[tri(5, 2)], m[tri(5, 3)], m[tri(6, 0)], m[tri(6, 1)]);
+            *rec_chunk(C, 14, k) = make_float4(m[tri(6, 2)], m[tri(6, 3)], m[tri(7, 0)], m[tri(7, 1)]);
+            *rec_chunk(C, 15, k) = make_float4(m[tri(7, 2)], m[tri(7, 3)], m[tri(8, 0)], m[tri(8, 1)]);
+            *reinterpret_cast<float2*>(rec_chunk(C, 16, k)) = make_float2(m[tri(8, 2)], m[tri(8, 3)]);
         }
         // V_k, v_k from the trailing block
-        if (lane < 10) {
-            const float val = S.M[(4 + i0) * 9 + (4 + j0)];
-            S.V[i0 * 4 + j0] = val;
-            S.V[j0 * 4 + i0] = val;
-        } else if (lane < 14) {
-            S.v[lane - 10] = S.M[8 * 9 + 4 + (lane - 10)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j <= i; ++j) V[tri(i, j)] = m[tri(4 + i, 4 + j)];
+            v[i] = m[tri(8, 4 + i)];
         }
-        __syncwarp();
     }
     // drain the copies still in flight (an early exit leaves some) before the
     // ring is reused
     cp_async_wait_all();
     __syncwarp();
     if (!ok) return false;
-    // x_0 block: V_0 + rho I + beta on the three pose rows
-    float d0[4] = {0.f, 0.f, 0.f, 0.f};
-    bool pd0 = true;
-    if (lane == 0) {
-        float H[4][4], g[4];
+    // x_0 block: V_0 + rho I + beta on the three pose rows (every lane)
+    float H[4][4], g[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 4; ++i) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) H[i][j] = S.V[i * 4 + j];
-            H[i][i] += rho;
-            g[i] = S.v[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
-            H[i][i] += beta;
-            if (!rhs_from_gr) g[i] += S.lam[i] + beta * c;
-        }
-        float L[4][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float d = H[j][j];
-#pragma unroll
-            for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
-            pd0 = pd0 && d > 0.f;
-            const float l = sqrtf(fmaxf(d, 1e-30f));
-            L[j][j] = l;
-#pragma unroll
-            for (int i = j + 1; i < 4; ++i) {
-                float s = H[i][j];
-#pragma unroll
-                for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
-                L[i][j] = s / l;
-            }
-        }
-        float yv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float s = g[i];
-#pragma unroll
-            for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
-            yv[i] = s / L[i][i];
-        }
-#pragma unroll
-        for (int i = 3; i >= 0; --i) {
-            float s = yv[i];
-#pragma unroll
-            for (int q = i + 1; q < 4; ++q) s -= L[q][i] * d0[q];
-            d0[i] = s / L[i][i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) d0[i] = -d0[i];
+        for (int j = 0; j < 4; ++j) H[i][j] = V[i >= j ? tri(i, j) : tri(j, i)];
+        H[i][i] += rho;
+        g[i] = v[i];
     }
-    pd0 = __shfl_sync(kFull, pd0 ? 1 : 0, 0) != 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) dx0[i] = __shfl_sync(kFull, d0[i], 0);
-    return pd0;
+    for (int i = 0; i < 3; ++i) {
+        const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
+        H[i][i] += beta;
+        if (!rhs_from_gr) g[i] += S.lam[i] + beta * c;
+    }
+    float L[4][4];
+    bool pd0 = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float d = H[j][j];
+#pragma unroll
+        for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
+        pd0 = pd0 && d > 0.f;
+        const float l = sqrtf(fmaxf(d, 1e-30f));
+        L[j][j] = l;
+#pragma unroll
+        for (int i = j + 1; i < 4; ++i) {
+            float s = H[i][j];
+#pragma unroll
+            for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
+            L[i][j] = s / l;
+        }
+    }
+    float yv[4], d0[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float s = g[i];
+#pragma unroll
+        for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
+        yv[i] = s / L[i][i];
+    }
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        float s = yv[i];
+#pragma unroll
+        for (int q = i + 1; q < 4; ++q) s -= L[q][i] * d0[q];
+        d0[i] = s / L[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dx0[i] = -d0[i];
+    return __all_sync(kFull, pd0);
 }
 
 // Stage-parallel gains: K_y,k = -L_y^{-T} [l_{x,y} | l_{rhs,y}] (4 x 5) from
@@ -688,34 +688,42 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
 __device__ void phase_b_gains(Ctx& C) {
     const int N = C.N, lane = C.lane;
     for (int k = lane; k < N; k += 32) {
-        float* rec = C.rec + (size_t)k * kRec;
-        float m[30];
+        // record floats 36..67 as 8 vector loads (the last two are unused)
+        float m[32];
 #pragma unroll
-        for (int q = 0; q < 30; ++q) m[q] = rec[36 + q];
-        float ly[4][4];
+        for (int q = 0; q < 8; ++q) {
+            const float4 t = *rec_chunk(C, 9 + q, k);
+            m[4 * q] = t.x;
+            m[4 * q + 1] = t.y;
+            m[4 * q + 2] = t.z;
+            m[4 * q + 3] = t.w;
+        }
+        float ly[4][4], il[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float l = sqrtf(m[tri(j, j)]);
-            const float il = 1.f / l;
-            ly[j][j] = l;
+            il[j] = rsqrtf(m[tri(j, j)]);
 #pragma unroll
-            for (int i = j + 1; i < 4; ++i) ly[i][j] = m[tri(i, j)] * il;
+            for (int i = j + 1; i < 4; ++i) ly[i][j] = m[tri(i, j)] * il[j];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) m[10 + 4 * c + j] *= il;  // l_{(4+c), j}
+            for (int c = 0; c < 5; ++c) m[10 + 4 * c + j] *= il[j];  // l_{(4+c), j}
         }
+        float K[4][5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            float K[4];
 #pragma unroll
             for (int i = 3; i >= 0; --i) {
                 float s = -m[10 + 4 * c + i];
 #pragma unroll
-                for (int q = i + 1; q < 4; ++q) s -= ly[q][i] * K[q];
-                K[i] = s / ly[i][i];
+                for (int q = i + 1; q < 4; ++q) s -= ly[q][i] * K[q][c];
+                K[i][c] = s * il[i];
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) rec[36 + i * 5 + c] = K[i];  // row i of K_y at 36 + 5 i
         }
+        // row i of K_y at 36 + 5 i
+        *rec_chunk(C, 9, k) = make_float4(K[0][0], K[0][1], K[0][2], K[0][3]);
+        *rec_chunk(C, 10, k) = make_float4(K[0][4], K[1][0], K[1][1], K[1][2]);
+        *rec_chunk(C, 11, k) = make_float4(K[1][3], K[1][4], K[2][0], K[2][1]);
+        *rec_chunk(C, 12, k) = make_float4(K[2][2], K[2][3], K[2][4], K[3][0]);
+        *rec_chunk(C, 13, k) = make_float4(K[3][1], K[3][2], K[3][3], K[3][4]);
     }
     __syncwarp();
 }
@@ -734,7 +742,7 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
 #pragma unroll
     for (int d = 0; d < kRing; ++d) {
         if (d < N && lane < kGainSlot / 4)
-            cp_async16(S.ring_c + d * kGainSlot + 4 * lane, C.rec + (size_t)d * kRec + 36 + 4 * lane);
+            cp_async16(S.ring_c + d * kGainSlot + 4 * lane, rec_chunk(C, 9 + lane, d));
         cp_async_commit();
     }
     for (int k = 0; k < N; ++k) {
@@ -749,7 +757,7 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
         }
         __syncwarp();
         if (k + kRing < N && lane < kGainSlot / 4)
-            cp_async16(S.ring_c + slot * kGainSlot + 4 * lane, C.rec + (size_t)(k + kRing) * kRec + 36 + 4 * lane);
+            cp_async16(S.ring_c + slot * kGainSlot + 4 * lane, rec_chunk(C, 9 + lane, k + kRing));
         cp_async_commit();
 #pragma unroll
         for (int i = 0; i < 4; ++i) dx[i] = __shfl_sync(kFull, w, i);
@@ -757,10 +765,17 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
     cp_async_wait_all();
     __syncwarp();
     for (int k = lane; k < N; k += 32) {
-        const float* rec = C.rec + (size_t)k * kRec;
-        float f[33];
+        // record floats 0..35 as 9 vector loads (u-block factor, 1 / l_jj on
+        // its diagonal, and the coupling columns)
+        float f[36];
 #pragma unroll
-        for (int q = 0; q < 33; ++q) f[q] = rec[q];
+        for (int q = 0; q < 9; ++q) {
+            const float4 t = *rec_chunk(C, q, k);
+            f[4 * q] = t.x;
+            f[4 * q + 1] = t.y;
+            f[4 * q + 2] = t.z;
+            f[4 * q + 3] = t.w;
+        }
         float xa[4], xb[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -775,9 +790,9 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
             for (int i = 0; i < 4; ++i) s += f[6 + i * 3 + j] * xb[i] + f[6 + (4 + i) * 3 + j] * xa[i];
             R[j] = s;
         }
-        const float du2 = -R[2] / f[5];
-        const float du1 = (-R[1] - f[4] * du2) / f[2];
-        const float du0 = (-R[0] - f[1] * du1 - f[3] * du2) / f[0];
+        const float du2 = -R[2] * f[5];
+        const float du1 = (-R[1] - f[4] * du2) * f[2];
+        const float du0 = (-R[0] - f[1] * du1 - f[3] * du2) * f[0];
         S.dz[7 * k + 4] = du0;
         S.dz[7 * k + 5] = du1;
         S.dz[7 * k + 6] = du2;
@@ -829,28 +844,36 @@ __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, f
     return phi;
 }
 
-// Phase D: trial merits for alpha in {0, 1, 1/2, ..., 2^-(n_alpha-1)}.
-// Returns the accepted alpha (0 = rejected).
+// Phase D: trial merits for alpha in {0, 1, 1/2, ..., 2^-(n_alpha-1)};
+// the accepted alpha is the largest one passing the test (0 = rejected).
+// Trials run four at a time (lane = trial + 4 x stage group), largest alpha
+// first: the second batch {1/8 .. 1/64} is evaluated only when none of
+// {1, 1/2, 1/4} passes, which leaves the accepted alpha unchanged.
 __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& sp) {
     const int lane = C.lane;
-    const int a = lane & 7, grp = lane >> 3;
-    const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
-    float phi = 0.f;
+    const int sub = lane & 3, grp = lane >> 2;
     const float inv2b = 0.5f / beta;
-    if (a <= sp.n_alpha)
-        for (int k = grp; k < C.N; k += 4) phi += stage_merit(C, k, alpha, beta, inv2b);
-    phi += __shfl_xor_sync(kFull, phi, 8);
-    phi += __shfl_xor_sync(kFull, phi, 16);
-    const float phi0 = __shfl_sync(kFull, phi, 0);
-    const float phi1 = __shfl_sync(kFull, phi, 1);
-    const float slack = sp.ls_slack * fabsf(phi0);
-    const bool flat = fabsf(D) <= slack;
-    bool pass = (a >= 1) && (a <= sp.n_alpha) && (phi <= phi0 + sp.armijo_c1 * alpha * D);
-    if (a == 1 && flat && phi1 <= phi0 + slack) pass = true;
-    const unsigned bal = __ballot_sync(kFull, pass) & 0xffu;
-    if (!bal) return 0.f;
-    const int first = __ffs(bal) - 1;
-    return ldexpf(1.f, -(first - 1));
+    float phi0 = 0.f, slack = 0.f;
+    for (int batch = 0; batch < 2; ++batch) {
+        const int a = 4 * batch + sub;  // trial index: alpha = 2^-(a-1), a = 0 -> alpha = 0
+        if (batch == 1 && sp.n_alpha < 4) break;
+        const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
+        float phi = 0.f;
+        if (a <= sp.n_alpha)
+            for (int k = grp; k < C.N; k += 8) phi += stage_merit(C, k, alpha, beta, inv2b);
+        phi += __shfl_xor_sync(kFull, phi, 4);
+        phi += __shfl_xor_sync(kFull, phi, 8);
+        phi += __shfl_xor_sync(kFull, phi, 16);
+        if (batch == 0) {
+            phi0 = __shfl_sync(kFull, phi, 0);
+            slack = sp.ls_slack * fabsf(phi0);
+        }
+        bool pass = (a >= 1) && (a <= sp.n_alpha) && (phi <= phi0 + sp.armijo_c1 * alpha * D);
+        if (a == 1 && fabsf(D) <= slack && phi <= phi0 + slack) pass = true;
+        const unsigned bal = __ballot_sync(kFull, pass) & 0xfu;
+        if (bal) return ldexpf(1.f, -(4 * batch + __ffs(bal) - 2));
+    }
+    return 0.f;
 }
 
 // Phase E: compensated update z += alpha dz
