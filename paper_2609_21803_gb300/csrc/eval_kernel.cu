@@ -1248,48 +1248,63 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
         bool nonfinite = false;
         for (it = 0; it < sp.max_iters; ++it) {
             const bool curv = curv_hold == 0;
-            Measures m = phase_a(C, beta, rho, curv, true, false, beta);
-            if (!m.finite) {
-                status = COMET_TO_NONFINITE;
-                nonfinite = true;
-                break;
-            }
-            const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
-            if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
-                status = COMET_TO_CONVERGED;
-                break;
-            }
-            const float omega = fmaxf(eps_d, sp.omega_ratio * m.viol);
-            const bool solved = m.stat <= omega;
-            if (solved || inner >= sp.max_inner) {
-                const float beta_old = beta;
-                if (solved && m.viol > sp.eps_primal && m.viol > sp.eta_ratio * eta)
-                    beta = fminf(sp.beta_max, beta * sp.beta_growth);
-                eta = m.viol;
-                inner = 0;
-                // dual update at beta_old, then the model at the new (lam, beta)
-                phase_a(C, beta, rho, curv, true, true, beta_old);
-            }
-            // step: Newton with the dynamics curvature, then Gauss-Newton,
-            // then rising damping
+            if (!curv) --curv_hold;
+            // One iteration is a sequence of (assemble, sweep) trips through a
+            // single call site of each phase (one inlined copy of the largest
+            // code in the hot loop):
+            //   MEASURE  the measures and the model at the current iterate;
+            //   UPDATE   after a solved subproblem: dual update at beta_old,
+            //            then the model at the new (lam, beta);
+            //   RETRY    Gauss-Newton reassembly after a failed sweep.
+            // The step model is Newton with the dynamics curvature, then
+            // Gauss-Newton with the same damping, then rising damping.
+            enum { kMeasure, kUpdate, kRetry };
+            int trip = kMeasure, retries = 0;
+            bool model_curv = curv, fac = false, done = false;
+            float beta_old = beta;
             float dx0[4];
-            bool fac = false, model_curv = false;
-            if (curv) {
+            for (;;) {
+                const Measures m = phase_a(C, beta, rho, model_curv, true, trip == kUpdate, beta_old);
+                if (trip == kMeasure) {
+                    if (!m.finite) {
+                        status = COMET_TO_NONFINITE;
+                        nonfinite = true;
+                        done = true;
+                        break;
+                    }
+                    const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
+                    if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
+                        status = COMET_TO_CONVERGED;
+                        done = true;
+                        break;
+                    }
+                    const float omega = fmaxf(eps_d, sp.omega_ratio * m.viol);
+                    const bool solved = m.stat <= omega;
+                    if (solved || inner >= sp.max_inner) {
+                        beta_old = beta;
+                        if (solved && m.viol > sp.eps_primal && m.viol > sp.eta_ratio * eta)
+                            beta = fminf(sp.beta_max, beta * sp.beta_growth);
+                        eta = m.viol;
+                        inner = 0;
+                        trip = kUpdate;
+                        continue;
+                    }
+                }
                 fac = phase_b(C, beta, rho, dx0);
-                model_curv = fac;
-                if (!fac) curv_hold = sp.curv_skip;
-            } else {
-                --curv_hold;
+                if (fac) break;
+                if (model_curv) {
+                    // indefinite with the curvature: Gauss-Newton for the next
+                    // curv_skip iterations, starting now at the same damping
+                    curv_hold = sp.curv_skip;
+                    model_curv = false;
+                } else {
+                    if (retries >= sp.max_retries) break;
+                    ++retries;
+                    rho = fminf(sp.rho_max, rho * 10.f);
+                }
+                trip = kRetry;
             }
-            // the first Gauss-Newton retry reuses the model assembled above
-            // when no curvature term was included
-            bool have_gn = !curv;
-            for (int r = 0; !fac && r <= sp.max_retries; ++r) {
-                if (r > 0) rho = fminf(sp.rho_max, rho * 10.f);
-                if (!have_gn) phase_a(C, beta, rho, false, true, false, beta);
-                have_gn = false;
-                fac = phase_b(C, beta, rho, dx0);
-            }
+            if (done) break;
             ++inner;
             if (!fac) continue;
             phase_b_gains(C);
