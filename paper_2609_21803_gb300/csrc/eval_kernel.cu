@@ -220,6 +220,17 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
         if (!R.on[r]) R.c[r] = 0.f;
 }
 
+// Nonzero pattern of dynamics row r over the stage variables (u0..2 at
+// 0..2, y = x_{k+1} at 3..6, x_k at 7..10), ascending; -1 pads.  Rows 0, 1
+// (x, y): f_n, f_t, their own y, their own x and theta; row 2 (theta): f_n,
+// f_t, y_2, theta, s; row 3 (s): the pusher velocity, y_3, s.
+__host__ __device__ constexpr int dyn_nz(int r, int a) {
+    return r == 0 ? (a == 0 ? 0 : a == 1 ? 1 : a == 2 ? 3 : a == 3 ? 7 : 9)
+         : r == 1 ? (a == 0 ? 0 : a == 1 ? 1 : a == 2 ? 4 : a == 3 ? 8 : 9)
+         : r == 2 ? (a == 0 ? 0 : a == 1 ? 1 : a == 2 ? 5 : a == 3 ? 9 : 10)
+                  : (a == 0 ? 2 : a == 1 ? 6 : a == 2 ? 10 : -1);
+}
+
 // PHR augmented-Lagrangian pieces of one row
 __device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float inv2b, float c) {
     if (!ineq) return lam * c + 0.5f * beta * c * c;
@@ -302,6 +313,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     Smem& S = C.sm;
     float viol = 0.f, comp = 0.f;
     bool finite = true;
+#pragma unroll 1
     for (int k = lane; k < N; k += 32) {
         const ModeInfo mi = mode_of(S.mb[k]);
         float xk[4], dx[4], u[3];
@@ -389,7 +401,8 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
             for (int j = 0; j < 3; ++j) A[tri(j, j)] += R2 + rho;
 #pragma unroll
             for (int i = 0; i < 4; ++i) A[tri(3 + i, 3 + i)] += rho;
-            // beta a a^T over active rows; dynamics rows first
+            // beta a a^T over active rows; dynamics rows first, on their fixed
+            // nonzero pattern (dyn_nz) over (u0..2, y0..3, x0..3)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 float vv[11];
@@ -401,9 +414,13 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
                 for (int i = 0; i < 4; ++i) vv[7 + i] = R.ax[r][i];
                 const float bw = act[r] ? beta : 0.f;
 #pragma unroll
-                for (int i = 0; i < 11; ++i)
+                for (int a = 0; a < 5; ++a) {
+                    const int i = dyn_nz(r, a);
+                    if (i < 0) continue;
+                    const float t = bw * vv[i];
 #pragma unroll
-                    for (int j = 0; j <= i; ++j) A[tri(i, j)] += bw * vv[i] * vv[j];
+                    for (int b = 0; b <= a; ++b) A[tri(i, dyn_nz(r, b))] += t * vv[dyn_nz(r, b)];
+                }
             }
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
@@ -556,6 +573,7 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
         cp_async_commit();
     }
     bool ok = true;
+#pragma unroll 1
     for (int k = N - 1; k >= 0; --k) {
         const int slot = (N - 1 - k) % kRing;
         cp_async_wait<kRing - 1>();
@@ -644,7 +662,8 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
         H[i][i] += beta;
         if (!rhs_from_gr) g[i] += S.lam[i] + beta * c;
     }
-    float L[4][4];
+    // Cholesky with reciprocal pivots: il[j] = 1 / l_jj
+    float L[4][4], il[4];
     bool pd0 = true;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -652,14 +671,13 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
 #pragma unroll
         for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
         pd0 = pd0 && d > 0.f;
-        const float l = sqrtf(fmaxf(d, 1e-30f));
-        L[j][j] = l;
+        il[j] = rsqrtf(fmaxf(d, 1e-30f));
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
             float s = H[i][j];
 #pragma unroll
             for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
-            L[i][j] = s / l;
+            L[i][j] = s * il[j];
         }
     }
     float yv[4], d0[4];
@@ -668,14 +686,14 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
         float s = g[i];
 #pragma unroll
         for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
-        yv[i] = s / L[i][i];
+        yv[i] = s * il[i];
     }
 #pragma unroll
     for (int i = 3; i >= 0; --i) {
         float s = yv[i];
 #pragma unroll
         for (int q = i + 1; q < 4; ++q) s -= L[q][i] * d0[q];
-        d0[i] = s / L[i][i];
+        d0[i] = s * il[i];
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) dx0[i] = -d0[i];
@@ -687,6 +705,7 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
 // (record floats 36..55, row-major).
 __device__ void phase_b_gains(Ctx& C) {
     const int N = C.N, lane = C.lane;
+#pragma unroll 1
     for (int k = lane; k < N; k += 32) {
         // record floats 36..67 as 8 vector loads (the last two are unused)
         float m[32];
@@ -745,6 +764,7 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
             cp_async16(S.ring_c + d * kGainSlot + 4 * lane, rec_chunk(C, 9 + lane, d));
         cp_async_commit();
     }
+#pragma unroll 1
     for (int k = 0; k < N; ++k) {
         const int slot = k % kRing;
         cp_async_wait<kRing - 1>();
@@ -764,6 +784,7 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
     }
     cp_async_wait_all();
     __syncwarp();
+#pragma unroll 1
     for (int k = lane; k < N; k += 32) {
         // record floats 0..35 as 9 vector loads (u-block factor, 1 / l_jj on
         // its diagonal, and the coupling columns)
@@ -854,12 +875,14 @@ __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& 
     const int sub = lane & 3, grp = lane >> 2;
     const float inv2b = 0.5f / beta;
     float phi0 = 0.f, slack = 0.f;
+#pragma unroll 1
     for (int batch = 0; batch < 2; ++batch) {
         const int a = 4 * batch + sub;  // trial index: alpha = 2^-(a-1), a = 0 -> alpha = 0
         if (batch == 1 && sp.n_alpha < 4) break;
         const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
         float phi = 0.f;
         if (a <= sp.n_alpha)
+#pragma unroll 1
             for (int k = grp; k < C.N; k += 8) phi += stage_merit(C, k, alpha, beta, inv2b);
         phi += __shfl_xor_sync(kFull, phi, 4);
         phi += __shfl_xor_sync(kFull, phi, 8);
