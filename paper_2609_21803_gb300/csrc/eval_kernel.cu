@@ -80,6 +80,14 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// reciprocal from the SFU (rcp.approx, about 1 ulp); the sweep's pivots are
+// damped and never subnormal
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // lower-triangle flat index of (i, j), i >= j
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -608,7 +616,7 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
         for (int j = 0; j < 4; ++j) {
             const float p = m[tri(j, j)];
             pd = pd && (p > 0.f);
-            const float ip = __fdividef(1.f, p);
+            const float ip = rcp_approx(p);
 #pragma unroll
             for (int i = j + 1; i < 9; ++i) {
                 const float a = m[tri(i, j)] * ip;
@@ -1027,6 +1035,7 @@ __device__ Cert certify(const Ctx& C, float beta) {
     // recomputes the two adjacent intervals (k-1 as x_{k+1}, k as x_k)
     for (int k = lane; k <= N; k += 32) {
         double g[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 1
         for (int side = 0; side < 2; ++side) {
             const int kk = (side == 0) ? k - 1 : k;  // interval index
             if (kk < 0 || kk >= N) continue;
