@@ -581,9 +581,10 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_fr
         cp_async_commit();
     }
     bool ok = true;
+    int slot = kRing - 1;  // ring slot of stage k: (N - 1 - k) mod kRing
 #pragma unroll 1
     for (int k = N - 1; k >= 0; --k) {
-        const int slot = (N - 1 - k) % kRing;
+        slot = (slot == kRing - 1) ? 0 : slot + 1;
         cp_async_wait<kRing - 1>();
         __syncwarp();
         const float4* sl = reinterpret_cast<const float4*>(S.ring_b + slot * kSweepSlot);
@@ -772,9 +773,10 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
             cp_async16(S.ring_c + d * kGainSlot + 4 * lane, rec_chunk(C, 9 + lane, d));
         cp_async_commit();
     }
+    int slot = kRing - 1;  // ring slot of stage k: k mod kRing
 #pragma unroll 1
     for (int k = 0; k < N; ++k) {
-        const int slot = k % kRing;
+        slot = (slot == kRing - 1) ? 0 : slot + 1;
         cp_async_wait<kRing - 1>();
         __syncwarp();
         float w = 0.f;
@@ -911,17 +913,18 @@ __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& 
 __device__ void phase_e(Ctx& C, float alpha) {
     const int N = C.N, Np1 = C.N + 1, lane = C.lane;
     Smem& S = C.sm;
-    for (int t = lane; t < 4 * Np1; t += 32) {
-        const int i = t / Np1, k = t - i * Np1;
-        float s, e;
-        two_sum(S.xh[t], S.xl[t] + alpha * S.dz[7 * k + i], s, e);
-        S.xh[t] = s;
-        S.xl[t] = e;
-    }
-    for (int t = lane; t < 3 * N; t += 32) {
-        const int j = t / N, k = t - j * N;
-        S.us[t] += alpha * S.dz[7 * k + 4 + j];
-    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        for (int k = lane; k < Np1; k += 32) {
+            const int t = i * Np1 + k;
+            float s, e;
+            two_sum(S.xh[t], S.xl[t] + alpha * S.dz[7 * k + i], s, e);
+            S.xh[t] = s;
+            S.xl[t] = e;
+        }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        for (int k = lane; k < N; k += 32) S.us[j * N + k] += alpha * S.dz[7 * k + 4 + j];
     __syncwarp();
 }
 
