@@ -250,11 +250,9 @@ __device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float 
 
 constexpr int kRing = 6;       // stages in flight in the copy rings
 constexpr int kSweepSlot = 48;  // record floats 32..79 (pd flag and reduced matrix)
-constexpr int kGainSlot = 20;   // record floats 36..55 (x_{k+1} gains)
 
 struct Smem {
     float* ring_b;  // [kRing][48] sweep records in flight (16-byte aligned)
-    float* ring_c;  // [kRing][20] gains in flight (16-byte aligned)
     unsigned char* mb;  // [Nmax] per-interval mode byte: face | kind << 2 | smask << 4
     float* xh;   // [4][Nmax+1] state, high part
     float* xl;   // [4][Nmax+1] state, low part
@@ -265,7 +263,7 @@ struct Smem {
 };
 
 __host__ __device__ inline size_t smem_floats(int Nmax) {
-    const size_t f = (size_t)kRing * (kSweepSlot + kGainSlot) + (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
+    const size_t f = (size_t)kRing * kSweepSlot + (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
                      3 * (size_t)Nmax + 3 + 11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4);
     return (f + 3) / 4 * 4;  // every warp's block starts 16-byte aligned
 }
@@ -274,7 +272,6 @@ __device__ __forceinline__ Smem carve(float* base, int Nmax) {
     Smem s;
     float* p = base;
     s.ring_b = p; p += kRing * kSweepSlot;
-    s.ring_c = p; p += kRing * kGainSlot;
     s.mb = reinterpret_cast<unsigned char*>(p); p += (Nmax + 3) / 4;
     s.xh = p; p += 4 * (Nmax + 1);
     s.xl = p; p += 4 * (Nmax + 1);
@@ -756,43 +753,95 @@ __device__ void phase_b_gains(Ctx& C) {
     __syncwarp();
 }
 
-// Phase C: forward pass.  The state chain dx_{k+1} = K_y,k [dx_k; 1] is the
-// only sequential part; the control steps
+// x_{k+1} gains of stage k as an affine map dx_{k+1} = G dx_k + g (record
+// floats 36..55, row i at 36 + 5 i: G[i][0..3], g[i])
+__device__ __forceinline__ void load_gain(const Ctx& C, int k, float G[4][4], float g[4]) {
+    float v[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const float4 t = *rec_chunk(C, 9 + q, k);
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) G[i][j] = v[5 * i + j];
+        g[i] = v[5 * i + 4];
+    }
+}
+
+// Phase C: forward pass.  The state chain dx_{k+1} = G_k dx_k + g_k is an
+// affine recurrence, split over the lanes: lane l owns `per` consecutive
+// stages and first composes their maps into one block map (P_l, q_l); the
+// entry states then pass along the lanes, x_in(l+1) = P_l x_in(l) + q_l
+// (ceil(N / per) - 1 dependent steps instead of N); finally every lane walks
+// its own stages from its entry state.  The control steps
 //   du_k = -L_u^{-T} (l_{y,u}^T dx_{k+1} + l_{x,u}^T dx_k + l_{rhs,u}^T)
 // follow in a stage-parallel pass from the u-block factors of phase A.
 // Returns D = grad . dz.
 __device__ float phase_c(Ctx& C, const float dx0[4]) {
     const int N = C.N, lane = C.lane;
     Smem& S = C.sm;
-    float dx[4] = {dx0[0], dx0[1], dx0[2], dx0[3]};
     if (lane < 4) S.dz[lane] = dx0[lane];
-    // copy ring of the gains (record floats 36..55; lanes 0..4 copy 16 bytes)
+    const int per = (N + 31) >> 5;
+    const int k0 = min(N, lane * per), k1 = min(N, k0 + per);
+    const int nl = (N + per - 1) / per;  // lanes that own stages
+    // the lane's block map (P, q) = composition of its stages' maps
+    float P[4][4], q[4];
 #pragma unroll
-    for (int d = 0; d < kRing; ++d) {
-        if (d < N && lane < kGainSlot / 4)
-            cp_async16(S.ring_c + d * kGainSlot + 4 * lane, rec_chunk(C, 9 + lane, d));
-        cp_async_commit();
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[i][j] = (i == j) ? 1.f : 0.f;
+        q[i] = 0.f;
     }
-    int slot = kRing - 1;  // ring slot of stage k: k mod kRing
 #pragma unroll 1
-    for (int k = 0; k < N; ++k) {
-        slot = (slot == kRing - 1) ? 0 : slot + 1;
-        cp_async_wait<kRing - 1>();
-        __syncwarp();
-        float w = 0.f;
-        if (lane < 4) {
-            const float* g = S.ring_c + slot * kGainSlot + 5 * lane;
-            w = g[0] * dx[0] + g[1] * dx[1] + g[2] * dx[2] + g[3] * dx[3] + g[4];
-            S.dz[7 * (k + 1) + lane] = w;
-        }
-        __syncwarp();
-        if (k + kRing < N && lane < kGainSlot / 4)
-            cp_async16(S.ring_c + slot * kGainSlot + 4 * lane, rec_chunk(C, 9 + lane, k + kRing));
-        cp_async_commit();
+    for (int k = k0; k < k1; ++k) {
+        float G[4][4], g[4];
+        load_gain(C, k, G, g);
+        float P2[4][4], q2[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) dx[i] = __shfl_sync(kFull, w, i);
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                P2[i][j] = G[i][0] * P[0][j] + G[i][1] * P[1][j] + G[i][2] * P[2][j] + G[i][3] * P[3][j];
+            q2[i] = G[i][0] * q[0] + G[i][1] * q[1] + G[i][2] * q[2] + G[i][3] * q[3] + g[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) P[i][j] = P2[i][j];
+            q[i] = q2[i];
+        }
     }
-    cp_async_wait_all();
+    // entry states along the lanes
+    float x[4] = {dx0[0], dx0[1], dx0[2], dx0[3]};
+#pragma unroll 1
+    for (int l = 0; l + 1 < nl; ++l) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float xo = P[i][0] * x[0] + P[i][1] * x[1] + P[i][2] * x[2] + P[i][3] * x[3] + q[i];
+            const float t = __shfl_sync(kFull, xo, l);
+            // lane l + 1 takes it; x of lane l is not needed again
+            if (lane == l + 1) x[i] = t;
+        }
+    }
+    // each lane walks its own stages
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        float G[4][4], g[4];
+        load_gain(C, k, G, g);
+        float w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = G[i][0] * x[0] + G[i][1] * x[1] + G[i][2] * x[2] + G[i][3] * x[3] + g[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            S.dz[7 * (k + 1) + i] = w[i];
+            x[i] = w[i];
+        }
+    }
     __syncwarp();
 #pragma unroll 1
     for (int k = lane; k < N; k += 32) {
