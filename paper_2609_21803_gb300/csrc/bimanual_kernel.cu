@@ -43,13 +43,38 @@ constexpr int R_LUU = 0;     // 78: u-block factor, lower triangle
 constexpr int R_CPL = 78;    // 132: coupling rows (y, x, rhs) x 12 u columns
 constexpr int R_PD = 210;    // u-block pivots positive
 constexpr int R_RED = 212;   // 66: reduced (y, x, rhs) block
-constexpr int R_YF = 278;    // 15 + 30 raw y-factor, then 30 gains
-static_assert(R_YF + 45 <= kBimRec, "record layout");
+constexpr int R_YF = 280;    // 15 + 30 raw y-factor (+3 pad), then 30 gains
+static_assert(R_YF + 48 <= kBimRec, "record layout");
+static_assert(R_YF % 4 == 0 && kBimRec % 4 == 0, "vector access to the raw factor");
+// sweep copy ring: record floats 208..279 (the u-block flag at 210, the
+// reduced block at 212..277), kBRing stages ahead
+constexpr int R_SLOT = 208, kBSlot = 72, kBRing = 6;
+static_assert(R_SLOT + 2 == R_PD && R_SLOT + 4 == R_RED && R_SLOT + kBSlot >= R_RED + NTRI_RED, "ring slot");
 
 // local variables: x_k 0..4, u_k 5..16, x_{k+1} 17..21
 enum { VX = 0, VZ, VTH, VSL, VSR, UXD, UZD, UTHD, UFNL, UFTL, USDL, UFNR, UFTR, USDR, ULN, ULT, UPC, VX1 };
 
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// asynchronous global -> shared copies of 16 bytes with commit groups (the
+// waits are hardware waits on the issuing thread's own groups)
+__device__ __forceinline__ void bcp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void bcp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bcp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bcp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// reciprocal from the SFU (rcp.approx, about 1 ulp); the damped pivots are
+// never subnormal
+__device__ __forceinline__ float brcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // elimination position of local variable v; rhs = 22
 __device__ __forceinline__ int epos(int v) { return v >= 17 ? v - 5 : (v >= 5 ? v - 5 : v + 17); }
@@ -404,18 +429,19 @@ struct BSmem {
     float *xh, *xl, *us, *lam, *dz, *gr;
     int* mi;     // per interval: mode | maskL << 10 | maskR << 11
     float *Jw, *yw, *At;  // per warp: [32][22], [32], [276]
-    float *M, *V, *v;     // sweep
+    float* ring;          // sweep copy ring [kBRing][kBSlot] (16-byte aligned)
     float* red;           // reductions / broadcasts [64]
 };
 
 __host__ __device__ inline size_t bsmem_floats(int Nmax) {
     const size_t f = (size_t)10 * (Nmax + 1) + (size_t)NU * Nmax + 3 + (size_t)NR * Nmax +
-                     2 * ((size_t)NWV * Nmax + NX) + (size_t)Nmax + 4 * (NR * NL + NR + NTRI) + 121 + 25 + 5 + 64;
+                     2 * ((size_t)NWV * Nmax + NX) + (size_t)Nmax + 4 * (NR * NL + NR + NTRI) + kBRing * kBSlot + 64;
     return (f + 3) / 4 * 4;
 }
 
 __device__ BSmem bcarve(float* p, int Nmax) {
     BSmem s;
+    s.ring = p; p += kBRing * kBSlot;  // first: 16-byte aligned
     s.xh = p; p += NX * (Nmax + 1);
     s.xl = p; p += NX * (Nmax + 1);
     s.us = p; p += NU * Nmax;
@@ -426,9 +452,6 @@ __device__ BSmem bcarve(float* p, int Nmax) {
     s.Jw = p; p += 4 * NR * NL;
     s.yw = p; p += 4 * NR;
     s.At = p; p += 4 * NTRI;
-    s.M = p; p += 121;
-    s.V = p; p += 25;
-    s.v = p; p += 5;
     s.red = p;
     return s;
 }
@@ -476,6 +499,7 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
     float* At = S.At + warp * NTRI;
     float viol = 0.f, comp = 0.f;
     bool finite = true;
+#pragma unroll 1
     for (int k = warp; k < N; k += 4) {
         float x[NX], u[NU], dx[NX];
         load_stage(C, k, 0.f, x, u, dx);
@@ -621,134 +645,157 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
     return m;
 }
 
-// Phase B: the sequential sweep (warp 0), then the x_0 block.  Returns the
-// factorisation status to all threads; dx0 into red[16..20].
+// Sweep over k = N-1 .. 0 on warp 0.  Every lane runs the whole stage in
+// registers (the sequential chain is short and dependent): the reduced
+// 11 x 11 lower triangle (rows y 0..4, x 0..4, rhs) arrives from the record
+// through a cp.async ring kBRing stages ahead and is read as shared-memory
+// broadcasts, V_{k+1} and v_{k+1} stay in registers, the 5 y columns are
+// eliminated with SFU reciprocal pivots, and lane 0 writes the raw y-factor
+// columns (15 y-y entries, then the (x, rhs) rows) for the gains.  Then the
+// x_0 block; publishes the factorisation status to all threads and dx0 into
+// red[16..20].
 __device__ bool bphase_b(BCtx& C, float beta, float rho) {
     BSmem& S = C.S;
     const BInst<float>& P = C.P;
     const int N = C.N, Np1 = C.Np1, lane = C.lane;
     if (C.warp == 0) {
-        // entries of the 11 x 11 lower triangle held by this lane
-        int ii[3], jj[3];
-        bool has[3];
-        for (int q = 0; q < 3; ++q) {
-            const int t = lane + 32 * q;
-            has[q] = t < NTRI_RED;
-            if (has[q]) untri(t, ii[q], jj[q]);
-            else ii[q] = jj[q] = 0;
+        float V[15], v[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+#pragma unroll
+            for (int j = 0; j <= i; ++j) V[tri(i, j)] = (i == j && i < 3) ? 2.f * P.wT : 0.f;
+            v[i] = i < 3 ? 2.f * P.wT * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N]) : 0.f;
         }
-        if (lane < 25) S.V[lane] = (lane % 6 == 0 && lane < 15) ? 2.f * P.wT : 0.f;
-        if (lane < 5)
-            S.v[lane] = lane < 3 ? 2.f * P.wT * ((S.xh[lane * Np1 + N] - P.goal[lane]) + S.xl[lane * Np1 + N]) : 0.f;
-        float nxt[3];
-        for (int q = 0; q < 3; ++q)
-            nxt[q] = has[q] ? C.rec[(size_t)(N - 1) * kBimRec + R_RED + lane + 32 * q] : 0.f;
-        float pdn = C.rec[(size_t)(N - 1) * kBimRec + R_PD];
-        __syncwarp();
+#pragma unroll
+        for (int d = 0; d < kBRing; ++d) {
+            const int kk = N - 1 - d;
+            if (kk >= 0 && lane < kBSlot / 4)
+                bcp_async16(S.ring + d * kBSlot + 4 * lane, C.rec + (size_t)kk * kBimRec + R_SLOT + 4 * lane);
+            bcp_async_commit();
+        }
         bool ok = true;
+        int slot = kBRing - 1;  // ring slot of stage k: (N - 1 - k) mod kBRing
+#pragma unroll 1
         for (int k = N - 1; k >= 0; --k) {
-            float cur[3];
-            for (int q = 0; q < 3; ++q) cur[q] = nxt[q];
-            const bool pd_u = pdn > 0.f;
-            if (k > 0) {
-                for (int q = 0; q < 3; ++q)
-                    nxt[q] = has[q] ? C.rec[(size_t)(k - 1) * kBimRec + R_RED + lane + 32 * q] : 0.f;
-                pdn = C.rec[(size_t)(k - 1) * kBimRec + R_PD];
-            }
-            for (int q = 0; q < 3; ++q) {
-                if (!has[q]) continue;
-                float val = cur[q];
-                if (ii[q] < 5) val += S.V[ii[q] * 5 + jj[q]];
-                else if (ii[q] == 10 && jj[q] < 5) val += S.v[jj[q]];
-                S.M[ii[q] * 11 + jj[q]] = val;
-            }
+            slot = (slot == kBRing - 1) ? 0 : slot + 1;
+            bcp_async_wait<kBRing - 1>();
             __syncwarp();
-            bool pd = pd_u;
+            const float4* sl = reinterpret_cast<const float4*>(S.ring + slot * kBSlot);
+            const float4 hd = sl[0];  // record floats 208..211: the u-block flag at 210
+            float m[68];
+#pragma unroll
+            for (int q = 0; q < 17; ++q) {
+                const float4 t = sl[1 + q];
+                m[4 * q] = t.x;
+                m[4 * q + 1] = t.y;
+                m[4 * q + 2] = t.z;
+                m[4 * q + 3] = t.w;
+            }
+            bool pd = hd.z > 0.f;
+            __syncwarp();
+            {
+                const int kk = k - kBRing;
+                if (kk >= 0 && lane < kBSlot / 4)
+                    bcp_async16(S.ring + slot * kBSlot + 4 * lane, C.rec + (size_t)kk * kBimRec + R_SLOT + 4 * lane);
+                bcp_async_commit();
+            }
+#pragma unroll
+            for (int t = 0; t < 15; ++t) m[t] += V[t];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) m[tri(10, j)] += v[j];
+#pragma unroll
             for (int j = 0; j < 5; ++j) {
-                const float p = S.M[j * 11 + j];
+                const float p = m[tri(j, j)];
                 pd = pd && (p > 0.f);
-                const float ip = 1.f / p;
-                float upd[3];
-                for (int q = 0; q < 3; ++q)
-                    upd[q] = (has[q] && jj[q] > j) ? S.M[ii[q] * 11 + j] * S.M[jj[q] * 11 + j] * ip : 0.f;
-                __syncwarp();
-                for (int q = 0; q < 3; ++q)
-                    if (has[q] && jj[q] > j) S.M[ii[q] * 11 + jj[q]] -= upd[q];
-                __syncwarp();
+                const float ip = brcp_approx(p);
+#pragma unroll
+                for (int i = j + 1; i < 11; ++i) {
+                    const float a = m[tri(i, j)] * ip;
+#pragma unroll
+                    for (int l = j + 1; l <= i; ++l)
+                        if (!(i == 10 && l == 10)) m[tri(i, l)] -= a * m[tri(l, j)];
+                }
             }
             if (!__all_sync(kFullB, pd)) {
                 ok = false;
                 break;
             }
-            // raw y factor: y-y (15) and (x, rhs)-y (30) entries
-            float* rec = C.rec + (size_t)k * kBimRec;
-            if (lane < 15) {
-                int i, j;
-                untri(lane, i, j);
-                rec[R_YF + lane] = S.M[i * 11 + j];
+            if (lane == 0) {
+                // 45 raw factor entries (+3 pad) as 12 vector stores
+                float o[48];
+#pragma unroll
+                for (int t = 0; t < 15; ++t) o[t] = m[t];
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) o[15 + 5 * c + j] = m[tri(5 + c, j)];
+                o[45] = o[46] = o[47] = 0.f;
+                float4* r4 = reinterpret_cast<float4*>(C.rec + (size_t)k * kBimRec + R_YF);
+#pragma unroll
+                for (int q = 0; q < 12; ++q) r4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
             }
-            for (int q = lane; q < 30; q += 32) rec[R_YF + 15 + q] = S.M[(5 + q / 5) * 11 + q % 5];
-            // V_k, v_k from the trailing (x, rhs) block
-            if (lane < 25) {
-                const int i = lane / 5, j = lane % 5;
-                const int a = i > j ? i : j, b = i > j ? j : i;
-                S.V[lane] = S.M[(5 + a) * 11 + 5 + b];
-            } else if (lane < 30) {
-                S.v[lane - 25] = S.M[10 * 11 + 5 + (lane - 25)];
-            }
-            __syncwarp();
-        }
-        float d0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        bool pd0 = ok;
-        if (ok && lane == 0) {
-            float H[5][5], g[5], L[5][5];
-            #pragma unroll
+#pragma unroll
             for (int i = 0; i < 5; ++i) {
-                #pragma unroll
-                for (int j = 0; j < 5; ++j) H[i][j] = S.V[i * 5 + j];
-                H[i][i] += rho;
-                g[i] = S.v[i];
+#pragma unroll
+                for (int j = 0; j <= i; ++j) V[tri(i, j)] = m[tri(5 + i, 5 + j)];
+                v[i] = m[tri(10, 5 + i)];
             }
-            #pragma unroll
+        }
+        bcp_async_wait_all();
+        __syncwarp();
+        // x_0 block (every lane), Cholesky with reciprocal pivots
+        bool pd0 = ok;
+        float d0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ok) {
+            float H[5][5], g[5], L[5][5], il[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+#pragma unroll
+                for (int j = 0; j < 5; ++j) H[i][j] = V[i >= j ? tri(i, j) : tri(j, i)];
+                H[i][i] += rho;
+                g[i] = v[i];
+            }
+#pragma unroll
             for (int i = 0; i < 3; ++i) {
                 H[i][i] += beta;
                 g[i] += S.lam[i] + beta * ((S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1]);
             }
-            #pragma unroll
+#pragma unroll
             for (int j = 0; j < 5; ++j) {
                 float d = H[j][j];
-                #pragma unroll
+#pragma unroll
                 for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
                 pd0 = pd0 && d > 0.f;
-                const float l = sqrtf(fmaxf(d, 1e-30f));
-                L[j][j] = l;
-                #pragma unroll
+                il[j] = rsqrtf(fmaxf(d, 1e-30f));
+#pragma unroll
                 for (int i = j + 1; i < 5; ++i) {
                     float s = H[i][j];
-                    #pragma unroll
+#pragma unroll
                     for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
-                    L[i][j] = s / l;
+                    L[i][j] = s * il[j];
                 }
             }
             float yv[5];
-            #pragma unroll
+#pragma unroll
             for (int i = 0; i < 5; ++i) {
                 float s = g[i];
-                #pragma unroll
+#pragma unroll
                 for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
-                yv[i] = s / L[i][i];
+                yv[i] = s * il[i];
             }
-            #pragma unroll
+#pragma unroll
             for (int i = 4; i >= 0; --i) {
                 float s = yv[i];
-                #pragma unroll
+#pragma unroll
                 for (int q = i + 1; q < 5; ++q) s -= L[q][i] * d0[q];
-                d0[i] = s / L[i][i];
+                d0[i] = s * il[i];
             }
-            for (int i = 0; i < 5; ++i) S.red[16 + i] = -d0[i];
+        }
+        if (lane == 0) {
+            if (ok)
+                for (int i = 0; i < 5; ++i) S.red[16 + i] = -d0[i];
             S.red[21] = pd0 ? 1.f : 0.f;
         }
-        if (!ok && lane == 0) S.red[21] = 0.f;
     }
     __syncthreads();
     const bool res = S.red[21] > 0.f;
@@ -758,35 +805,45 @@ __device__ bool bphase_b(BCtx& C, float beta, float rho) {
 
 // gains K_y = -L_y^{-T} [l_{x,y} | l_{rhs,y}] (5 x 6) per stage
 __device__ void bphase_gains(BCtx& C) {
+#pragma unroll 1
     for (int k = C.tid; k < C.N; k += kBimThreads) {
         float* rec = C.rec + (size_t)k * kBimRec;
-        float m[45];
-        #pragma unroll
-        for (int q = 0; q < 45; ++q) m[q] = rec[R_YF + q];
-        float ly[5][5];
-        #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            const float l = sqrtf(m[tri(j, j)]);
-            const float il = 1.f / l;
-            ly[j][j] = l;
-            #pragma unroll
-            for (int i = j + 1; i < 5; ++i) ly[i][j] = m[tri(i, j)] * il;
-            #pragma unroll
-            for (int c = 0; c < 6; ++c) m[15 + 5 * c + j] *= il;
+        // raw factor: 15 y-y entries, then the (x, rhs) rows, as vector loads
+        float m[48];
+        const float4* r4 = reinterpret_cast<const float4*>(rec + R_YF);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const float4 t = r4[q];
+            m[4 * q] = t.x;
+            m[4 * q + 1] = t.y;
+            m[4 * q + 2] = t.z;
+            m[4 * q + 3] = t.w;
         }
-        #pragma unroll
+        float ly[5][5], il[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            il[j] = rsqrtf(m[tri(j, j)]);
+#pragma unroll
+            for (int i = j + 1; i < 5; ++i) ly[i][j] = m[tri(i, j)] * il[j];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) m[15 + 5 * c + j] *= il[j];
+        }
+        // K (row i at R_YF + 6 i), two pad floats, as vector stores
+        float o[32];
+#pragma unroll
         for (int c = 0; c < 6; ++c) {
-            float K[5];
-            #pragma unroll
+#pragma unroll
             for (int i = 4; i >= 0; --i) {
                 float s = -m[15 + 5 * c + i];
-                #pragma unroll
-                for (int q = i + 1; q < 5; ++q) s -= ly[q][i] * K[q];
-                K[i] = s / ly[i][i];
+#pragma unroll
+                for (int q = i + 1; q < 5; ++q) s -= ly[q][i] * o[6 * q + c];
+                o[6 * i + c] = s * il[i];
             }
-            #pragma unroll
-            for (int i = 0; i < 5; ++i) rec[R_YF + i * 6 + c] = K[i];
         }
+        o[30] = o[31] = 0.f;
+        float4* w4 = reinterpret_cast<float4*>(rec + R_YF);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
     }
     __syncthreads();
 }
@@ -802,6 +859,7 @@ __device__ float bphase_c(BCtx& C) {
         float dxv[5];
         #pragma unroll
         for (int i = 0; i < 5; ++i) dxv[i] = __shfl_sync(kFullB, dxi, i);
+#pragma unroll 1
         for (int k = 0; k < N; ++k) {
             float w = 0.f;
             if (C.lane < 5) {
@@ -816,6 +874,7 @@ __device__ float bphase_c(BCtx& C) {
         }
     }
     __syncthreads();
+#pragma unroll 1
     for (int k = C.tid; k < N; k += kBimThreads) {
         const float* rec = C.rec + (size_t)k * kBimRec;
         float xa[5], xb[5];
@@ -870,6 +929,7 @@ __device__ float bphase_d(BCtx& C, float beta, float D, const SolverParams& sp) 
     const float inv2b = 0.5f / beta;
     float phi = 0.f;
     if (a <= sp.n_alpha) {
+#pragma unroll 1
         for (int k = grp; k < N; k += 16) {
             float x[NX], u[NU], dx[NX];
             load_stage(C, k, alpha, x, u, dx);
@@ -1038,7 +1098,7 @@ __device__ BCert bcertify(BCtx& C, float beta_f) {
     return ct;
 }
 
-__global__ void __launch_bounds__(kBimThreads) bimanual_kernel(EvalArgs A) {
+__global__ void __launch_bounds__(kBimThreads, 3) bimanual_kernel(EvalArgs A) {
     extern __shared__ float bsm[];
     BCtx C;
     C.tid = threadIdx.x;
@@ -1132,33 +1192,50 @@ __global__ void __launch_bounds__(kBimThreads) bimanual_kernel(EvalArgs A) {
         int inner = 0, it = 0, status = COMET_TO_MAX_ITER;
         bool nonfinite = false;
         for (it = 0; it < sp.max_iters; ++it) {
-            BMeasures m = bphase_a(C, beta, rho, true, false, beta);
-            if (!m.finite) {
-                status = COMET_TO_NONFINITE;
-                nonfinite = true;
-                break;
-            }
-            const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
-            if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
-                status = COMET_TO_CONVERGED;
-                break;
-            }
-            const float omega = fmaxf(eps_d, sp.omega_ratio * m.viol);
-            const bool solved = m.stat <= omega;
-            if (solved || inner >= sp.max_inner) {
-                const float beta_old = beta;
-                if (solved && m.viol > sp.eps_primal && m.viol > sp.eta_ratio * eta)
-                    beta = fminf(sp.beta_max, beta * sp.beta_growth);
-                eta = m.viol;
-                inner = 0;
-                bphase_a(C, beta, rho, true, true, beta_old);
-            }
-            bool fac = bphase_b(C, beta, rho);
-            for (int r = 1; !fac && r <= sp.max_retries; ++r) {
-                rho = fminf(sp.rho_max, rho * 10.f);
-                bphase_a(C, beta, rho, true, false, beta);
+            // (assemble, sweep) trips through one call site of each phase
+            // (one inlined copy in the hot loop): the measures and model at
+            // the iterate, the dual update at beta_old after a solved
+            // subproblem, and reassembly at rising damping after a failed
+            // sweep.  Every decision is taken on CTA-wide reductions, so all
+            // threads follow the same trips.
+            enum { kMeasure, kUpdate, kRetry };
+            int trip = kMeasure, retries = 0;
+            bool fac = false, done = false;
+            float beta_old = beta;
+            for (;;) {
+                const BMeasures m = bphase_a(C, beta, rho, true, trip == kUpdate, beta_old);
+                if (trip == kMeasure) {
+                    if (!m.finite) {
+                        status = COMET_TO_NONFINITE;
+                        nonfinite = true;
+                        done = true;
+                        break;
+                    }
+                    const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
+                    if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
+                        status = COMET_TO_CONVERGED;
+                        done = true;
+                        break;
+                    }
+                    const float omega = fmaxf(eps_d, sp.omega_ratio * m.viol);
+                    const bool solved = m.stat <= omega;
+                    if (solved || inner >= sp.max_inner) {
+                        beta_old = beta;
+                        if (solved && m.viol > sp.eps_primal && m.viol > sp.eta_ratio * eta)
+                            beta = fminf(sp.beta_max, beta * sp.beta_growth);
+                        eta = m.viol;
+                        inner = 0;
+                        trip = kUpdate;
+                        continue;
+                    }
+                }
                 fac = bphase_b(C, beta, rho);
+                if (fac || retries >= sp.max_retries) break;
+                ++retries;
+                rho = fminf(sp.rho_max, rho * 10.f);
+                trip = kRetry;
             }
+            if (done) break;
             ++inner;
             if (!fac) continue;
             bphase_gains(C);

@@ -76,7 +76,7 @@ void set_error(const char* msg);
 
 // Bimanual variant (bimanual_kernel.cu): one CTA of kBimThreads threads per
 // TO; per-CTA workspace kBimRec floats per stage.
-constexpr int kBimRec = 324;
+constexpr int kBimRec = 328;
 constexpr int kBimThreads = 128;
 size_t bim_smem_bytes(int Nmax);
 int bim_blocks_per_sm(int Nmax);
