@@ -304,7 +304,7 @@ def run_gpu(args):
     if rank == 0 and args.batch_plan:
         line["batch_plan"] = batch_plan_times(P)
     if rank == 0 and args.bimanual:
-        line["bimanual"] = bimanual_times(P)
+        line["bimanual"] = bimanual_times(P, per=args.bim_per)
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and not args.no_cpu_baseline:
@@ -597,6 +597,7 @@ def main():
     ap.add_argument("--plan-instances", type=int, default=4, help="instances for the plan-time comparison (0 = skip)")
     ap.add_argument("--hetero", type=int, default=1, help="mixed-workload leg (1) or skip it (0)")
     ap.add_argument("--batch-plan", type=int, default=1, help="batched multi-instance planner leg (1) or skip it (0)")
+    ap.add_argument("--bim-per", type=int, default=512, help="random orders per instance in the bimanual leg")
     ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=8,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
