@@ -332,3 +332,52 @@ def test_budget_entry_point(P):
     assert np.all(g5["iters"] <= 5)
     g = gpu_eval(P, [inst], seqs, max_iters=1500)
     assert np.mean(g["status"] == 0) >= np.mean(gpu_eval(P, [inst], seqs)["status"] == 0)
+
+
+def test_long_horizon_parity(P):
+    # mixed-workload sliders with N = 126..174: the forward pass gives each
+    # lane 4..6 consecutive stages (ragged last lane at N = 126) and one
+    # launch holds four horizons
+    insts = [W.push_mixed_instance(s) for s in (8, 38, 39, 46)]
+    Ns = [i["knots_per_segment"] * i["max_segments"] for i in insts]
+    Nm = max(Ns)
+    rng = np.random.default_rng(5)
+    seqs, idx = [], []
+    for i, inst in enumerate(insts):
+        for _ in range(24):
+            seqs.append(tuple(int(m) for m in rng.integers(0, 12, inst["max_segments"])))
+            idx.append(i)
+    idx = np.array(idx, np.int32)
+    modes, lens = W.pad_sequences(seqs, 6)
+
+    def xu(traj, N, stride_n):
+        # x[4][stride_n + 1] then u[3][stride_n]: the GPU pads every TO to
+        # N_max, the oracle writes each at its own N
+        x = traj[: 4 * (stride_n + 1)].reshape(4, stride_n + 1)[:, : N + 1]
+        u = traj[4 * (stride_n + 1): 4 * (stride_n + 1) + 3 * stride_n].reshape(3, stride_n)[:, :N]
+        return np.concatenate([x.ravel(), u.ravel()]).astype(np.float64)
+
+    # one iteration from the same cold start agrees to the FP32 error of the
+    # first Newton step.  Over 126..174 stages that step's relative error
+    # reaches a few 1e-4 (the KKT system at beta = 100, rho = 1e-4 is far
+    # worse conditioned than at N = 16, where 1e-4 holds); the sequential
+    # and the lane-split forward passes give identical iterates here, so the
+    # bar is 1e-3 relative (max measured 2.7e-4)
+    g1 = gpu_eval(P, insts, seqs, idx, want_traj=True, max_iters=1)
+    r1, t1 = oracle.solve_batch(insts, idx, modes, lens, opts=oracle.default_opts(max_iters=1), want_traj=True)
+    assert g1["stride"] == t1.shape[1]
+    ok = []
+    for t in range(len(seqs)):
+        N = Ns[idx[t]]
+        a, b = xu(g1["traj"][t], N, Nm), xu(t1[t], N, N)
+        ok.append(np.max(np.abs(a - b)) <= 1e-3 * max(1.0, np.max(np.abs(b))))
+    assert np.mean(ok) >= 0.99, np.mean(ok)
+    # full solves: same convergence, same local solutions, certified
+    g = gpu_eval(P, insts, seqs, idx, want_traj=True)
+    ref, _ = oracle.solve_batch(insts, idx, modes, lens)
+    cg, co, both, rel, same = compare(g, ref)
+    print(f"N 126..174: converged gpu {cg.mean():.3f} oracle {co.mean():.3f}; same {same.sum()}/{both.sum()}")
+    assert abs(cg.mean() - co.mean()) <= 0.1
+    assert same.sum() >= 0.8 * both.sum()
+    for t in np.flatnonzero(cg & (g["viol"] <= 1e-5))[::5]:
+        assert certify_fp64(insts[idx[t]], seqs[t], Ns[idx[t]], g["traj"][t], Nm)[0] <= 1e-5, t
