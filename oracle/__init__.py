@@ -31,6 +31,8 @@ _lock = threading.Lock()
 _lib = None
 
 CONVERGED, MAX_ITER, INFEASIBLE, FACTOR_FAIL, NONFINITE = range(5)
+# pushing mode 12: free motion (faces 0..3 x {stick, slide+, slide-} are 0..11)
+MODE_FREE = 12
 
 
 def build(force: bool = False) -> str:

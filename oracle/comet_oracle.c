@@ -163,12 +163,56 @@ static double dyn_row_scale(const orc_instance* in, int32_t i) {
     return 0.5 * (nrm[1] + nrm[2]);
 }
 
+/* Rows of a free-motion interval (mode ORC_MODE_FREE) at the same fixed
+ * positions: the slider rests, d_k = x_{k+1} - x_k - dt (0, 0, 0, sdot)
+ * (same row scales); the mode equality is f_n = 0 and the cone rows with
+ * zero friction, f_t <= 0 and -f_t <= 0, make f_t = 0; the sliding
+ * direction and the face bounds are off, -f_n <= 0 stays. */
+static void free_rows(const orc_instance* in, int32_t s_row_masked, const double* xk, const double* uk,
+                      const double* xk1, double* c, uint8_t* mask, double* scale, double* J) {
+    for (int i = 0; i < ORC_NROW * 11; ++i) J[i] = 0.0;
+    for (int r = 0; r < ORC_NROW; ++r) {
+        c[r] = 0.0;
+        mask[r] = 1;
+        scale[r] = 1.0;
+    }
+    for (int i = 0; i < 4; ++i) {
+        const double sg = dyn_row_scale(in, i);
+        const double rate = (i == 3) ? uk[2] : 0.0;
+        c[i] = (xk1[i] - xk[i] - in->dt * rate) / sg;
+        J[i * 11 + i] = -1.0 / sg;
+        J[i * 11 + 7 + i] = 1.0 / sg;
+        scale[i] = 1.0 / sg;
+    }
+    J[3 * 11 + 6] = -in->dt / dyn_row_scale(in, 3);
+    if (s_row_masked) mask[3] = 0;
+    c[4] = uk[0];
+    J[4 * 11 + 4] = 1.0;
+    c[5] = uk[1];
+    J[5 * 11 + 5] = 1.0;
+    c[6] = -uk[1];
+    J[6 * 11 + 5] = -1.0;
+    mask[7] = 0;
+    c[8] = -uk[0];
+    J[8 * 11 + 4] = -1.0;
+    mask[9] = mask[10] = 0;
+    for (int r = 0; r < ORC_NROW; ++r)
+        if (!mask[r]) {
+            c[r] = 0.0;
+            for (int j = 0; j < 11; ++j) J[r * 11 + j] = 0.0;
+        }
+}
+
 /* Rows of interval k at local variables v = (x_k[4], u_k[3], x_{k+1}[4]).
  * Outputs scaled values c[11], mask[11], scale[11] (physical = c/scale)
  * and the local Jacobian J[11][11] (row r, local variable j). */
 static void interval_rows(const orc_instance* in, int32_t mode, int32_t s_row_masked,
                           const double* xk, const double* uk, const double* xk1,
                           double* c, uint8_t* mask, double* scale, double* J) {
+    if (mode == ORC_MODE_FREE) {
+        free_rows(in, s_row_masked, xk, uk, xk1, c, mask, scale, J);
+        return;
+    }
     const int32_t face = mode / 3, kind = mode % 3; /* 0 stick, 1 slide+, 2 slide- */
     double n[2], t[2], a, ell;
     face_frame(in, face, n, t, &a, &ell);
@@ -240,11 +284,15 @@ static int32_t mode_of_interval(const uint8_t* modes, int32_t len, int32_t N, in
     return modes[orc_segment_of(k, len, N)];
 }
 
-/* s-row of d_k is masked when the next interval pushes on another face:
+/* s-row of d_k is masked when the pusher is not on the same face on both
+ * sides of knot k+1 (another face next, or free motion on either side):
  * the pusher relocates and the contact offset may jump. */
 static int32_t s_row_masked(const uint8_t* modes, int32_t len, int32_t N, int32_t k) {
+    const int32_t m0 = mode_of_interval(modes, len, N, k);
+    if (m0 == ORC_MODE_FREE) return 1;
     if (k + 1 >= N) return 0;
-    return (mode_of_interval(modes, len, N, k) / 3) != (mode_of_interval(modes, len, N, k + 1) / 3);
+    const int32_t m1 = mode_of_interval(modes, len, N, k + 1);
+    return m1 == ORC_MODE_FREE || (m0 / 3) != (m1 / 3);
 }
 
 static void load_local(const double* tr, int32_t N, int32_t k, double* xk, double* uk, double* xk1) {
@@ -425,9 +473,12 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
             double yd[4], Hf[49];
             for (int r = 0; r < 4; ++r)
                 yd[r] = mk[r] ? row_y(0, lam[3 + 11 * k + r], beta, cc[r]) / dyn_row_scale(in, r) : 0.0;
-            dynamics_curvature(in, mode_of_interval(modes, len, N, k) / 3, xk, uk, yd, Hf);
-            for (int i = 0; i < 7; ++i)
-                for (int j = 0; j < 7; ++j) H[i * 11 + j] -= in->dt * Hf[i * 7 + j];
+            const int32_t mk_k = mode_of_interval(modes, len, N, k);
+            if (mk_k != ORC_MODE_FREE) {  /* free motion: f is linear, no curvature */
+                dynamics_curvature(in, mk_k / 3, xk, uk, yd, Hf);
+                for (int i = 0; i < 7; ++i)
+                    for (int j = 0; j < 7; ++j) H[i * 11 + j] -= in->dt * Hf[i * 7 + j];
+            }
         }
         for (int i = 0; i < 4; ++i) grad[7 * (int64_t)k + i] += g[i];
         for (int j = 0; j < 3; ++j) grad[7 * (int64_t)k + 4 + j] += g[4 + j];
