@@ -161,3 +161,114 @@ def count_admissible_push(n_faces: int, cap: int) -> int:
         counts = nxt
         total += sum(counts.values())
     return total
+
+
+# ------------------------------------------- grammar over the 13-mode alphabet
+#
+# The paper's pushing modes are sticking contact on a face or free motion
+# (Sec. III-A, IV-A).  In the 13-mode pushing alphabet (faces x {stick,
+# slide+, slide-} = 0..11, free motion = 12) they are the modes 3 f and 12.
+# Admissible orders follow the rules of count_admissible_push: start in free
+# motion, no two consecutive segments share a mode, and a direct
+# contact-to-contact switch joins adjacent faces of the cyclic face list.
+
+PUSH_FREE = 12
+
+
+def push_alphabet(n_faces: int = 4) -> tuple[int, ...]:
+    """The task alphabet in ascending mode order: stick on each face, free."""
+    return tuple(3 * f for f in range(n_faces)) + (PUSH_FREE,)
+
+
+def admissible_push(seq: Sequence[int], n_faces: int = 4) -> bool:
+    s = tuple(int(m) for m in seq)
+    if not s or s[0] != PUSH_FREE:
+        return False
+    alpha = set(push_alphabet(n_faces))
+    if any(m not in alpha for m in s):
+        return False
+    for a, b in zip(s, s[1:]):
+        if a == b:
+            return False
+        if a != PUSH_FREE and b != PUSH_FREE and (a // 3 - b // 3) % n_faces not in (1, n_faces - 1):
+            return False
+    return True
+
+
+def admissible_orders(cap: int, n_faces: int = 4) -> list[tuple[int, ...]]:
+    """All admissible orders of 1..cap segments, by length, then
+    lexicographically in alphabet order (the seed batch F_0 of Sec. III-B)."""
+    alpha = push_alphabet(n_faces)
+    out: list[tuple[int, ...]] = []
+    level = [(PUSH_FREE,)]
+    for _ in range(cap):
+        out += level
+        level = [s + (m,) for s in level for m in alpha if admissible_push(s + (m,), n_faces)]
+    return out
+
+
+def alphabet_neighbours(seq: Sequence[int], alpha: Sequence[int], l_max: int) -> list[tuple[int, ...]]:
+    """One-edit neighbours over `alpha` in the enumeration order of
+    `neighbours`: substitutions, insertions, deletions, by position and then
+    by alphabet position."""
+    s = tuple(int(m) for m in seq)
+    L = len(s)
+    out: list[tuple[int, ...]] = []
+    for i in range(L):
+        for m in alpha:
+            if m != s[i]:
+                out.append(s[:i] + (m,) + s[i + 1:])
+    if L + 1 <= l_max:
+        for i in range(L + 1):
+            for m in alpha:
+                out.append(s[:i] + (m,) + s[i:])
+    if L - 1 >= 1:
+        for i in range(L):
+            out.append(s[:i] + s[i + 1:])
+    return out
+
+
+def grammar_neighbours(seq: Sequence[int], l_max: int, r: int = 1, n_faces: int = 4) -> list[tuple[int, ...]]:
+    """N_r(m) (Sec. III-B): orders within r <= 2 edits of m with every
+    intermediate order admissible, in enumeration order: the admissible
+    one-edit neighbours of m, then (r = 2) for each of them in that order its
+    own admissible one-edit neighbours; first occurrences kept, m excluded."""
+    alpha = push_alphabet(n_faces)
+    s = tuple(int(m) for m in seq)
+
+    def n1(t):
+        return [u for u in alphabet_neighbours(t, alpha, l_max) if admissible_push(u, n_faces)]
+
+    out, seen = [], {s}
+    first = n1(s)
+    for t in first:
+        if t not in seen:
+            seen.add(t)
+            out.append(t)
+    if r >= 2:
+        for t in first:
+            for u in n1(t):
+                if u not in seen:
+                    seen.add(u)
+                    out.append(u)
+    return out
+
+
+def expand_grammar(evaluated: dict, k: int, batch: int, l_max: int, r: int = 1, n_faces: int = 4,
+                   n_modes: int = 13) -> list[tuple[int, ...]]:
+    """One round of Algorithm 1 over admissible orders: walk the k best
+    orders of V by (merit, code) and admit unseen orders of each r-edit
+    neighbourhood until `batch` are collected."""
+    ranked = sorted(evaluated.items(), key=lambda kv: (kv[1][0], kv[0]))[:k]
+    seen = set(evaluated)
+    out: list[tuple[int, ...]] = []
+    for _, (_, seq) in ranked:
+        for nb in grammar_neighbours(seq, l_max, r, n_faces):
+            c = encode(nb, n_modes)
+            if c in seen:
+                continue
+            seen.add(c)
+            out.append(nb)
+            if len(out) == batch:
+                return out
+    return out

@@ -108,3 +108,56 @@ def test_enumeration_argmin_prefers_feasible_then_index():
     costs = [1.0, 0.5, 0.5, 0.1]
     viols = [0.0, 0.0, 0.0, 1e-3]
     assert S.enumeration_argmin(costs, viols) == 1
+
+
+# ------------------------------------------------ grammar (admissible orders)
+
+def _lev(a, b):
+    """Edit distance over segments (insert, delete, substitute one mode)."""
+    d = list(range(len(b) + 1))
+    for i in range(1, len(a) + 1):
+        prev, d[0] = d[0], i
+        for j in range(1, len(b) + 1):
+            cur = d[j]
+            d[j] = min(d[j] + 1, d[j - 1] + 1, prev + (a[i - 1] != b[j - 1]))
+            prev = cur
+    return d[len(b)]
+
+
+def test_admissible_orders_match_brute_force_and_the_paper():
+    import itertools
+    alpha = S.push_alphabet(4)
+    brute = [s for L in range(1, 6) for s in itertools.product(alpha, repeat=L) if S.admissible_push(s)]
+    assert S.admissible_orders(5) == brute          # same set and order (length, then lexicographic)
+    # the paper's counts for the four-faced box (golden file)
+    assert len(S.admissible_orders(6)) == S.count_admissible_push(4, 6) == 601
+    assert len(S.admissible_orders(8)) == S.count_admissible_push(4, 8) == 6297
+
+
+@pytest.mark.parametrize("seq", [(12,), (12, 0), (12, 3, 12, 9), (12, 0, 3, 6, 12)])
+def test_grammar_neighbourhoods_by_edit_distance(seq):
+    l_max = 6
+    pool = S.admissible_orders(l_max)
+    n1 = S.grammar_neighbours(seq, l_max, 1)
+    assert set(n1) == {t for t in pool if _lev(seq, t) == 1}
+    assert len(n1) == len(set(n1))
+    n2 = S.grammar_neighbours(seq, l_max, 2)
+    # every intermediate admissible: t is one edit from an admissible order
+    # that is itself one edit from seq
+    want = {t for t in pool if t != seq and any(_lev(t, u) <= 1 for u in n1)}
+    assert set(n2) == want
+    assert n2[: len(n1)] == n1                      # one-edit orders first, in order
+    assert all(_lev(seq, t) <= 2 for t in n2)
+
+
+def test_grammar_expansion_round():
+    rng = np.random.default_rng(3)
+    seeds = S.admissible_orders(3)
+    V = {S.encode(s, 13): (float(rng.uniform()), s) for s in seeds}
+    out = S.expand_grammar(V, k=4, batch=60, l_max=5, r=2)
+    assert 0 < len(out) <= 60 and len(set(out)) == len(out)
+    assert all(S.admissible_push(s) and S.encode(s, 13) not in V for s in out)
+    # the first admitted orders come from the best-ranked parent
+    best = min(V.values(), key=lambda v: (v[0], S.encode(v[1], 13)))[1]
+    nb = [t for t in S.grammar_neighbours(best, 5, 2) if S.encode(t, 13) not in V]
+    assert out[: len(nb)] == nb[: len(out)]
