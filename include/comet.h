@@ -70,8 +70,12 @@ enum { COMET_TASK_PUSHER_SLIDER = 0, COMET_TASK_BIMANUAL = 1 };
  * c_ls [m] and force-to-velocity gain kappa, pusher friction mu, state
  * (x, y, theta, s), control (f_n, f_t, sdot), K = knots_per_segment
  * intervals of dt [s] per mode segment, orders of at most max_segments
- * segments over n_modes = 12 modes (face 0..3 x stick, slide+, slide-),
- * cost w_terminal |pose_N - goal|^2 + w_control sum_k |u_k|^2.
+ * segments over n_modes = 12 modes (face 0..3 x stick, slide+, slide-:
+ * mode 3 face + kind) or n_modes = 13, where mode 12 is free motion
+ * (Sec. III-A: the pusher is off the slider, the contact force is zero, the
+ * slider rests, and the contact offset may jump across it; max_segments
+ * <= 15 so that mode codes fit in 64 bits), cost w_terminal
+ * |pose_N - goal|^2 + w_control sum_k |u_k|^2.
  * Bimanual (task 1): a box of width side_x and height side_y [m] and mass
  * `mass` [kg] in the vertical plane, hand friction mu, ground friction
  * ground_mu, state (x, z, theta, s_L, s_R), control (xd, zd, thd, fn_L, ft_L,
@@ -131,7 +135,8 @@ comet_status comet_default_opts(comet_solver_opts* opts);
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream).  The
  * problem owns its device scratch (descriptors, per-warp workspaces, staging
  * buffers).  Errors: INVALID_ARG for bad descriptors (non-positive sizes,
- * K * max_segments > 4096, max_segments > 16, n_modes != 12 for pushing),
+ * K * max_segments > 4096, max_segments > 16, n_modes not 12 or 13 for
+ * pushing, max_segments > 15 with 13 modes),
  * CUDA / OOM from the runtime. */
 comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_instances,
                                   const comet_solver_opts* opts, void* cuda_stream,

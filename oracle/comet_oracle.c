@@ -165,9 +165,10 @@ static double dyn_row_scale(const orc_instance* in, int32_t i) {
 
 /* Rows of a free-motion interval (mode ORC_MODE_FREE) at the same fixed
  * positions: the slider rests, d_k = x_{k+1} - x_k - dt (0, 0, 0, sdot)
- * (same row scales); the mode equality is f_n = 0 and the cone rows with
- * zero friction, f_t <= 0 and -f_t <= 0, make f_t = 0; the sliding
- * direction and the face bounds are off, -f_n <= 0 stays. */
+ * (same row scales), and the mode equality is f_n = 0 (no contact).  Every
+ * other row is off: f_t then acts on nothing and the effort cost sets it
+ * to zero, which keeps the active rows independent (an f_t = 0 written as
+ * two opposite inequalities, or -f_n <= 0 beside f_n = 0, would not be). */
 static void free_rows(const orc_instance* in, int32_t s_row_masked, const double* xk, const double* uk,
                       const double* xk1, double* c, uint8_t* mask, double* scale, double* J) {
     for (int i = 0; i < ORC_NROW * 11; ++i) J[i] = 0.0;
@@ -188,14 +189,7 @@ static void free_rows(const orc_instance* in, int32_t s_row_masked, const double
     if (s_row_masked) mask[3] = 0;
     c[4] = uk[0];
     J[4 * 11 + 4] = 1.0;
-    c[5] = uk[1];
-    J[5 * 11 + 5] = 1.0;
-    c[6] = -uk[1];
-    J[6 * 11 + 5] = -1.0;
-    mask[7] = 0;
-    c[8] = -uk[0];
-    J[8 * 11 + 4] = -1.0;
-    mask[9] = mask[10] = 0;
+    for (int r = 5; r < ORC_NROW; ++r) mask[r] = 0;
     for (int r = 0; r < ORC_NROW; ++r)
         if (!mask[r]) {
             c[r] = 0.0;

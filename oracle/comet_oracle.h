@@ -41,8 +41,8 @@ extern "C" {
 #define ORC_MAX_SEG 16
 /* Pushing modes 0..11: face (mode / 3) x {stick, slide+, slide-} (mode % 3).
  * Mode 12: free motion (Sec. III-A: a contact changes faces only through a
- * free-motion segment): the pusher is off the slider, the contact force is
- * zero, the slider rests and the contact offset is unconstrained. */
+ * free-motion segment): the pusher is off the slider (f_n = 0), the slider
+ * rests and the contact offset is unconstrained. */
 #define ORC_MODE_FREE 12
 
 typedef struct {

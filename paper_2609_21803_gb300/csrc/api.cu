@@ -206,8 +206,11 @@ comet_status check_instances(const comet_instance_desc* inst, int32_t n_instance
         if (d.task != COMET_TASK_PUSHER_SLIDER && d.task != COMET_TASK_BIMANUAL)
             return fail(COMET_ERR_INVALID_ARG, "instance %d: unknown task %d", i, d.task);
         if (d.task != inst[0].task) return fail(COMET_ERR_INVALID_ARG, "instance %d: a problem holds one task", i);
-        if (d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes != 12)
-            return fail(COMET_ERR_INVALID_ARG, "instance %d: pushing needs n_modes = 12", i);
+        if (d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes != 12 && d.n_modes != 13)
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: pushing needs n_modes = 12 or 13 (with free motion)", i);
+        // mode codes (base n_modes + 1) stay below 2^64: 13^17 and 14^16 fit
+        if (d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes == 13 && d.max_segments > 15)
+            return fail(COMET_ERR_INVALID_ARG, "instance %d: with free motion max_segments <= 15", i);
         if (d.task == COMET_TASK_BIMANUAL) {
             if (d.n_modes != 507) return fail(COMET_ERR_INVALID_ARG, "instance %d: bimanual needs n_modes = 507", i);
             if (!(d.mass > 0 && d.ground_mu >= 0 && d.side_x > 0 && d.side_y > 0 && d.dt > 0 && d.mu >= 0))

@@ -97,9 +97,14 @@ __device__ __forceinline__ void face_nt(int face, float& nx, float& ny) {
     ny = (face == 1) ? 1.f : ((face == 3) ? -1.f : 0.f);
 }
 
+// Pushing modes 0..11 are face (m / 3) x {stick, slide+, slide-} (m % 3);
+// mode 12 is free motion (Sec. III-A): the pusher is off the slider, the
+// contact force is zero and the slider rests.
+constexpr int kModeFree = 12;
+
 struct ModeInfo {
-    int face, kind;  // kind 0 stick, 1 slide+, 2 slide-
-    bool smask;      // s-row of d_k masked (face change after interval k)
+    int face, kind;  // kind 0 stick, 1 slide+, 2 slide-, 3 free motion
+    bool smask;      // s-row of d_k masked (the pusher is not on the same face at both ends)
 };
 
 __device__ __forceinline__ ModeInfo mode_of(unsigned char b) {
@@ -114,12 +119,16 @@ __device__ __forceinline__ ModeInfo mode_info(const uint16_t* modes, int len, in
     ModeInfo mi;
     const int seg = (int)(((long long)k * len) / N);
     const int m = modes[seg];
-    mi.face = m / 3;
-    mi.kind = m - 3 * mi.face;
-    mi.smask = false;
-    if (k + 1 < N) {
+    const bool free = m == kModeFree;
+    mi.face = free ? 0 : m / 3;
+    mi.kind = free ? 3 : m - 3 * mi.face;
+    // the contact offset may jump when the pusher leaves the face: free
+    // motion on either side of knot k+1, or another face next
+    mi.smask = free;
+    if (!free && k + 1 < N) {
         const int seg1 = (int)(((long long)(k + 1) * len) / N);
-        mi.smask = (modes[seg1] / 3) != mi.face;
+        const int m1 = modes[seg1];
+        mi.smask = m1 == kModeFree || (m1 / 3) != mi.face;
     }
     return mi;
 }
@@ -139,8 +148,9 @@ struct Rows {
     float ay[4];  // d c_r / d x_{k+1, r}
     // linear rows' u-Jacobians (rows 4..8)
     float lu[5][3];
-    // dynamics values for the curvature term
-    float f0, f1, ct, st;
+    // dynamics values for the curvature term; kf = force-to-velocity gain
+    // of the interval (0 in free motion)
+    float f0, f1, ct, st, kf;
 };
 
 __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& mi, const float xk[4],
@@ -149,7 +159,9 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
     face_nt(mi.face, nx, ny);
     const float tx = -ny, ty = nx;
     const float a = P.a[mi.face], ell = P.ell[mi.face];
-    const float k = P.kappa, ic2 = P.inv_c2, dt = P.dt;
+    // free motion: zero force-to-velocity gain, so the slider rests and only
+    // the contact offset moves (at the pusher's rate)
+    const float k = (mi.kind == 3) ? 0.f : P.kappa, ic2 = P.inv_c2, dt = P.dt;
     const float th = xk[2], s = xk[3];
     const float fn = u[0], ft = u[1], sd = u[2];
     float st, ct;
@@ -164,6 +176,7 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
     R.f1 = f[1];
     R.ct = ct;
     R.st = st;
+    R.kf = k;
     // Jacobians of f
     const float Fx02 = -st * vx - ct * vy, Fx12 = ct * vx - st * vy, Fx23 = -k * fn * ic2;
     const float Fu[4][3] = {{k * (ct * nx - st * ny), k * (ct * tx - st * ty), 0.f},
@@ -186,6 +199,20 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
     R.ax[1][2] += -dt * Fx12 * P.inv_sigma[1];
     R.ax[2][3] += -dt * Fx23 * P.inv_sigma[2];
     if (mi.smask) R.on[3] = false;
+    if (mi.kind == 3) {
+        // free motion: the mode equality f_n = 0 (row 4) is the only force
+        // row; f_t acts on nothing and the effort cost sets it to zero
+#pragma unroll
+        for (int q = 0; q < 5; ++q) R.lu[q][0] = R.lu[q][1] = R.lu[q][2] = 0.f;
+        R.lu[0][0] = 1.f;
+#pragma unroll
+        for (int r = 4; r < 11; ++r) {
+            R.c[r] = (r == 4) ? fn : 0.f;
+            R.phys[r] = 1.f;
+            R.on[r] = r == 4;
+        }
+        return;
+    }
 
     const float mu = P.mu, sc = P.sc_cone;
     const bool stick = mi.kind == 0;
@@ -441,7 +468,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
                 // with yd_r the multiplier of the unscaled row
                 float nx, ny;
                 face_nt(mi.face, nx, ny);
-                const float tx = -ny, ty = nx, kk = P.kappa;
+                const float tx = -ny, ty = nx, kk = R.kf;  // 0 in free motion
                 const float yd0 = y[0] * P.inv_sigma[0], yd1 = y[1] * P.inv_sigma[1];
                 const float yd2 = y[2] * P.inv_sigma[2];
                 const float h_thth = -yd0 * R.f0 - yd1 * R.f1;
@@ -985,7 +1012,7 @@ struct Rows64 {
     double c[11], ph[11];
     bool on[11];
     double J[11][11];
-    double f0, f1, ct, st;
+    double f0, f1, ct, st, kf;  // kf: force-to-velocity gain (0 in free motion)
     double x0[4], x1[4], u[3];
 };
 
@@ -1003,7 +1030,8 @@ __device__ void rows_fp64(const Ctx& C, int kk, Rows64& R) {
     const double ny = (mi.face == 1) ? 1.0 : ((mi.face == 3) ? -1.0 : 0.0);
     const double tx = -ny, ty = nx;
     const double a = P.a_d[mi.face], ell = P.ell_d[mi.face];
-    const double kp = P.kappa_d, ic2 = P.inv_c2_d, dt = P.dt_d;
+    const double kp = (mi.kind == 3) ? 0.0 : P.kappa_d, ic2 = P.inv_c2_d, dt = P.dt_d;
+    R.kf = kp;
     double st, ct;
     sincos(R.x0[2], &st, &ct);
     const double fn = R.u[0], ft = R.u[1], sd = R.u[2];
@@ -1038,32 +1066,39 @@ __device__ void rows_fp64(const Ctx& C, int kk, Rows64& R) {
     R.J[1][2] += -dt * Fx12 / P.sigma_d[1];
     R.J[2][3] += -dt * Fx23 / P.sigma_d[2];
     if (mi.smask) R.on[3] = false;
-    if (stick) {
-        R.c[4] = sd;
-        R.J[4][6] = 1.0;
+    if (mi.kind == 3) {
+        // free motion: f_n = 0 is the only force row
+        R.c[4] = fn;
+        R.J[4][4] = 1.0;
+        for (int r = 5; r < 11; ++r) R.on[r] = false;
     } else {
-        R.c[4] = sc * (ft + sg * mu * fn);
-        R.J[4][4] = sc * sg * mu;
-        R.J[4][5] = sc;
-        R.ph[4] = 1.0 / sc;
+        if (stick) {
+            R.c[4] = sd;
+            R.J[4][6] = 1.0;
+        } else {
+            R.c[4] = sc * (ft + sg * mu * fn);
+            R.J[4][4] = sc * sg * mu;
+            R.J[4][5] = sc;
+            R.ph[4] = 1.0 / sc;
+        }
+        R.c[5] = sc * (ft - mu * fn);
+        R.J[5][4] = -sc * mu;
+        R.J[5][5] = sc;
+        R.c[6] = sc * (-ft - mu * fn);
+        R.J[6][4] = -sc * mu;
+        R.J[6][5] = -sc;
+        R.ph[5] = R.ph[6] = 1.0 / sc;
+        R.on[5] = R.on[6] = stick;
+        R.c[7] = sg * sd;
+        R.J[7][6] = sg;
+        R.on[7] = !stick;
+        R.c[8] = -fn;
+        R.J[8][4] = -1.0;
+        R.c[9] = R.x0[3] - ell;
+        R.J[9][3] = 1.0;
+        R.c[10] = -R.x0[3] - ell;
+        R.J[10][3] = -1.0;
     }
-    R.c[5] = sc * (ft - mu * fn);
-    R.J[5][4] = -sc * mu;
-    R.J[5][5] = sc;
-    R.c[6] = sc * (-ft - mu * fn);
-    R.J[6][4] = -sc * mu;
-    R.J[6][5] = -sc;
-    R.ph[5] = R.ph[6] = 1.0 / sc;
-    R.on[5] = R.on[6] = stick;
-    R.c[7] = sg * sd;
-    R.J[7][6] = sg;
-    R.on[7] = !stick;
-    R.c[8] = -fn;
-    R.J[8][4] = -1.0;
-    R.c[9] = R.x0[3] - ell;
-    R.J[9][3] = 1.0;
-    R.c[10] = -R.x0[3] - ell;
-    R.J[10][3] = -1.0;
     for (int r = 0; r < 11; ++r)
         if (!R.on[r]) {
             R.c[r] = 0.0;
@@ -1194,7 +1229,7 @@ __device__ void residual_fp64(Ctx& C, float beta_f, float rho_f, bool curvature)
                     const ModeInfo mi = mode_of(S.mb[kk]);
                     const double nx = (mi.face == 0) ? 1.0 : ((mi.face == 2) ? -1.0 : 0.0);
                     const double ny = (mi.face == 1) ? 1.0 : ((mi.face == 3) ? -1.0 : 0.0);
-                    const double tx = -ny, ty = nx, kp = P.kappa_d, dt = P.dt_d;
+                    const double tx = -ny, ty = nx, kp = R.kf, dt = P.dt_d;  // kf = 0 in free motion
                     const double h_thth = -yd[0] * R.f0 - yd[1] * R.f1;
                     const double h_thfn = yd[0] * kp * (-R.st * nx - R.ct * ny) + yd[1] * kp * (R.ct * nx - R.st * ny);
                     const double h_thft = yd[0] * kp * (-R.st * tx - R.ct * ty) + yd[1] * kp * (R.ct * tx - R.st * ty);

@@ -381,3 +381,60 @@ def test_long_horizon_parity(P):
     assert same.sum() >= 0.8 * both.sum()
     for t in np.flatnonzero(cg & (g["viol"] <= 1e-5))[::5]:
         assert certify_fp64(insts[idx[t]], seqs[t], Ns[idx[t]], g["traj"][t], Nm)[0] <= 1e-5, t
+
+
+def test_free_motion_closed_form_and_grammar_parity(P):
+    # free motion (mode 12 of the 13-mode pushing alphabet): free then a
+    # straight sticking push from face 0 equals the straight push over the
+    # contact intervals alone, J* = W R d^2 / (R + W K dt^2)
+    inst = dict(W.push_l2_straight(0.1), n_modes=13)
+    K, Wt, R, dt, d = inst["knots_per_segment"], inst["w_terminal"], inst["w_control"], inst["dt"], 0.1
+    g = gpu_eval(P, [inst], np.array([[12, 0]], np.uint8), want_traj=True)
+    assert g["status"][0] == 0 and g["viol"][0] <= 1e-5
+    Jstar = Wt * R * d * d / (R + Wt * K * dt * dt)
+    assert abs(g["cost"][0] - Jstar) <= 5e-4 * Jstar
+    U = g["traj"][0][4 * 17: 4 * 17 + 3 * 16].reshape(3, 16)
+    assert np.max(np.abs(U[:, :K])) <= 1e-4
+    # every admissible order of 2..4 segments (start in free motion, faces
+    # change through free motion or to an adjacent face) on three instances
+    insts = [dict(W.push_l4_instance(s), n_modes=13) for s in range(3)]
+    orders = [s for s in S.admissible_orders(4) if len(s) >= 2]
+    seqs = [s for s in orders for _ in range(3)]
+    idx = np.array([i for _ in orders for i in range(3)], np.int32)
+    modes, lens = W.pad_sequences(seqs, 4)
+    Ns = [20 * len(s) for s in seqs]
+    # first iterate: FP32 rounding of the same step (1e-3: N up to 80)
+    g1 = gpu_eval(P, insts, seqs, idx, want_traj=True, max_iters=1)
+    r1, t1 = oracle.solve_batch(insts, idx, modes, lens, opts=oracle.default_opts(max_iters=1), want_traj=True)
+    ok = []
+    for t in range(len(seqs)):
+        N = Ns[t]
+        a = np.concatenate([g1["traj"][t][: 4 * 81].reshape(4, 81)[:, : N + 1].ravel(),
+                            g1["traj"][t][4 * 81: 4 * 81 + 240].reshape(3, 80)[:, :N].ravel()])
+        b = t1[t][: 7 * N + 4]
+        ok.append(np.max(np.abs(a - b)) <= 1e-3 * max(1.0, np.max(np.abs(b))))
+    assert np.mean(ok) >= 0.99
+    # full solves.  Orders with free motion converge more slowly in FP32 than
+    # in FP64 (measured at the 300-iteration budget: 77 % against the
+    # oracle's 93 %, the same orders without free segments 98 % against
+    # 97 %): where both converge they reach the same solutions, and with a
+    # 1,500-iteration budget the GPU converges as often as the oracle at 300
+    g = gpu_eval(P, insts, seqs, idx, want_traj=True)
+    ref, _ = oracle.solve_batch(insts, idx, modes, lens)
+    cg, co, both, rel, same = compare(g, ref)
+    g_long = gpu_eval(P, insts, seqs, idx, max_iters=1500)
+    cl = g_long["status"] == 0
+    print(f"grammar orders: converged gpu {cg.mean():.3f} (1,500 iterations {cl.mean():.3f}) "
+          f"oracle {co.mean():.3f}; same {same.sum()}/{both.sum()}")
+    assert cg.mean() >= co.mean() - 0.2
+    assert abs(cl.mean() - co.mean()) <= 0.08
+    assert same.sum() >= 0.9 * both.sum()
+    for t in np.flatnonzero(cg & (g["viol"] <= 1e-5))[::4]:
+        v, tr = certify_fp64(insts[idx[t]], seqs[t], Ns[t], g["traj"][t], 80)
+        assert v <= 1e-5, t
+        # no contact force during free motion: f_n = 0 is a row (feasibility
+        # 1e-5), f_t is set by the effort cost alone (stationarity 1e-4 over
+        # 2 w_control = 0.2, i.e. 5e-4)
+        seg = [oracle.segment_of(k, len(seqs[t]), Ns[t]) for k in range(Ns[t])]
+        Uf = tr[4 * (Ns[t] + 1):].reshape(3, Ns[t])[:2, [seqs[t][q] == 12 for q in seg]]
+        assert np.max(np.abs(Uf[0]), initial=0.0) <= 1e-5 and np.max(np.abs(Uf[1]), initial=0.0) <= 5e-4, t

@@ -1,9 +1,10 @@
 """Pins of the free-motion pushing mode in the oracle (Sec. III-A: a mode is
 which face the pusher contacts, or free motion, and a contact changes faces
 only through a free-motion segment).  Reading: during free motion the
-contact force is zero (f_n = 0, and f_t = 0 through the cone rows at zero
-friction), the slider rests, the contact offset is unconstrained (its
-dynamics row and the face bounds are off) and may jump at either end.
+pusher is off the slider (the mode equality f_n = 0 is the only force row;
+f_t acts on nothing and the effort cost sets it to zero), the slider rests,
+the contact offset is unconstrained (its dynamics row and the face bounds
+are off) and may jump at either end.
 Checked: the rows and masks of a free interval, their Jacobian against
 central differences of the row values, two closed forms (a free order
 cannot move the slider; free motion followed by a straight sticking push
@@ -29,12 +30,11 @@ def test_free_rows_and_masks():
     U = tr[4 * (N + 1):].reshape(3, N)
     c, mask, scale, _ = oracle.rows(INST, [FREE, 0], N, tr)
     for k in range(8):                      # free intervals
-        assert list(mask[k]) == [1, 1, 1, 0, 1, 1, 1, 0, 1, 0, 0]
+        assert list(mask[k]) == [1, 1, 1, 0, 1, 0, 0, 0, 0, 0, 0]
         # the slider rests: physical defect of the pose rows is x_{k+1} - x_k
         np.testing.assert_allclose(c[k, :3] / scale[k, :3], X[:3, k + 1] - X[:3, k], rtol=1e-12)
-        assert c[k, 4] == pytest.approx(U[0, k]) and c[k, 8] == pytest.approx(-U[0, k])
-        assert c[k, 5] == pytest.approx(U[1, k]) and c[k, 6] == pytest.approx(-U[1, k])
-        assert c[k, 3] == 0 and c[k, 7] == 0 and c[k, 9] == 0 and c[k, 10] == 0
+        assert c[k, 4] == pytest.approx(U[0, k])
+        assert c[k, 3] == 0 and np.all(c[k, 5:] == 0)
     # contact intervals keep the sticking rows; the offset is continuous on
     # the face after the free segment
     assert mask[8:, 3].all() and mask[8:, 9].all() and mask[8:, 5].all()
@@ -138,5 +138,5 @@ def test_kkt_with_free_segments(seed):
         seg = np.array([oracle.segment_of(k, 2, N) for k in range(N)])
         free_k = np.array([modes[s] == FREE for s in seg])
         U = tr[4 * (N + 1):].reshape(3, N)
-        assert np.max(np.abs(U[:2, free_k])) <= 1e-9
+        assert np.max(np.abs(U[:2, free_k])) <= 1e-8
     assert seen >= 2
