@@ -224,6 +224,27 @@ comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst, int32_t n
 comet_status comet_frontier_create(comet_problem* p, int32_t instance, int64_t capacity, int32_t batch,
                                    int32_t k_max, comet_frontier** out);
 
+/* Neighbourhood rules of the expansion (Sec. III-A, III-B). */
+enum {
+    COMET_GRAMMAR_NONE = 0, /* every order over the instance's modes, lengths 1..max_segments */
+    COMET_GRAMMAR_PUSH = 1  /* the pushing task grammar over the 13-mode alphabet: modes are
+                             * stick on face f (3 f) or free motion (12); an order starts in free
+                             * motion, no two consecutive segments share a mode, and a direct
+                             * contact-to-contact switch joins adjacent faces (0-1-2-3-0) */
+};
+
+/* comet_frontier_create with a neighbourhood rule: the expansion walks
+ * N_r(m), the orders within `radius` (1 or 2) edits (insert, delete or
+ * substitute one segment) of m whose intermediate orders are all admissible
+ * under `grammar`, in enumeration order: the one-edit orders (substitutions,
+ * insertions, deletions, by position and then alphabet position), then with
+ * radius 2 the one-edit orders of each of them in that order.  The pushing
+ * grammar needs a pushing instance with n_modes = 13.  Errors: INVALID_ARG
+ * (as comet_frontier_create, a bad radius or grammar, or k_max times the
+ * slots of one neighbourhood above 2^26). */
+comet_status comet_frontier_create_ex(comet_problem* p, int32_t instance, int64_t capacity, int32_t batch,
+                                      int32_t k_max, int32_t radius, int32_t grammar, comet_frontier** out);
+
 comet_status comet_frontier_destroy(comet_frontier* f);
 
 /* Add n evaluated orders to V with their J_hat (cost) and v_hat (viol); the
@@ -269,6 +290,8 @@ typedef struct {
     int64_t budget;     /* evaluation budget, 0 = none; the last batch is truncated to fit */
     int32_t ref_iters;  /* refinement budget t_ref, 0 = the problem's ref_iters */
     int32_t use_graph;  /* capture one round (expand, evaluate, add) as a CUDA graph and replay it (1) */
+    int32_t radius;     /* edit radius r of the neighbourhoods N_r (1; 2 allowed, see comet_frontier_create_ex) */
+    int32_t grammar;    /* COMET_GRAMMAR_NONE (0) or COMET_GRAMMAR_PUSH: expand admissible orders only */
 } comet_plan_opts;
 
 typedef struct {

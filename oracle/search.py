@@ -88,15 +88,37 @@ def neighbour_slots(n_modes: int, l_max: int) -> int:
     return L * (n_modes - 1) + (L + 1) * n_modes + L
 
 
-def expand(evaluated: dict, k: int, batch: int, n_modes: int, l_max: int) -> list[tuple[int, ...]]:
+def neighbours_r(seq: Sequence[int], n_modes: int, l_max: int, r: int = 1) -> list[tuple[int, ...]]:
+    """N_r(m) over every order of 1..l_max segments (r <= 2): the one-edit
+    neighbours in the order of `neighbours`, then with r = 2 the one-edit
+    neighbours of each of them in that order; first occurrences kept, m
+    excluded."""
+    s = tuple(int(m) for m in seq)
+    first = neighbours(s, n_modes, l_max)
+    out, seen = [], {s}
+    for t in first:
+        if t not in seen:
+            seen.add(t)
+            out.append(t)
+    if r >= 2:
+        for t in first:
+            for u in neighbours(t, n_modes, l_max):
+                if u not in seen:
+                    seen.add(u)
+                    out.append(u)
+    return out
+
+
+def expand(evaluated: dict, k: int, batch: int, n_modes: int, l_max: int, r: int = 1) -> list[tuple[int, ...]]:
     """One round of Algorithm 1 (lines 5-10) on the evaluated set
     V = {code: (merit, seq)}: walk the k best orders by (merit, code) and
-    admit unseen neighbours until `batch` orders are collected."""
+    admit unseen orders of each r-edit neighbourhood until `batch` orders
+    are collected."""
     ranked = sorted(evaluated.items(), key=lambda kv: (kv[1][0], kv[0]))[:k]
     seen = set(evaluated)
     out: list[tuple[int, ...]] = []
     for _, (_, seq) in ranked:
-        for nb in neighbours(seq, n_modes, l_max):
+        for nb in (neighbours(seq, n_modes, l_max) if r == 1 else neighbours_r(seq, n_modes, l_max, r)):
             c = encode(nb, n_modes)
             if c in seen:
                 continue

@@ -54,7 +54,11 @@ class SolverOpts(ctypes.Structure):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("batch", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("k_ref", ctypes.c_int32), ("budget", ctypes.c_int64), ("ref_iters", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("radius", ctypes.c_int32), ("grammar", ctypes.c_int32)]
+
+
+GRAMMAR_NONE, GRAMMAR_PUSH = 0, 1   # neighbourhood rules (comet_frontier_create_ex)
+MODE_FREE = 12                      # free motion in the 13-mode pushing alphabet
 
 
 class ModeSeq(ctypes.Structure):
@@ -113,7 +117,7 @@ EXPORTS = (
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
     "comet_get_launch_config", "comet_set_launch_config", "comet_autotune", "comet_proposal_time_forward",
-    "comet_plan_batch",
+    "comet_plan_batch", "comet_frontier_create_ex",
 )
 
 
@@ -145,6 +149,7 @@ def lib(build_if_missing: bool = False):
             L.comet_eval_modes_noalloc.argtypes = [ctypes.POINTER(InstanceDesc), i32, ctypes.POINTER(SolverOpts), vp,
                                                    vp, i64, vp, vp, vp, vp]
             L.comet_frontier_create.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(vp)]
+            L.comet_frontier_create_ex.argtypes = [vp, i32, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
             L.comet_frontier_destroy.argtypes = [vp]
             L.comet_frontier_add.argtypes = [vp, vp, i64, vp, vp]
             L.comet_expand.argtypes = [vp, vp, i32]
@@ -299,9 +304,10 @@ def comet_eval_modes_noalloc(instances, opts, cuda_stream, mode_seqs, n, warm_st
                                           _ptr(warm_starts), _ptr(out_cost), _ptr(out_traj), _ptr(out_status)))
 
 
-def comet_frontier_create(problem, instance: int, capacity: int, batch: int, k_max: int) -> int:
+def comet_frontier_create(problem, instance: int, capacity: int, batch: int, k_max: int, radius: int = 1,
+                          grammar: int = GRAMMAR_NONE) -> int:
     h = ctypes.c_void_p()
-    _check(lib().comet_frontier_create(problem, instance, capacity, batch, k_max, ctypes.byref(h)))
+    _check(lib().comet_frontier_create_ex(problem, instance, capacity, batch, k_max, radius, grammar, ctypes.byref(h)))
     return h.value
 
 

@@ -186,34 +186,59 @@ __global__ void topk_chunk_kernel(const TopKey* in_keys, const unsigned long lon
 // --------------------------------------------------------- neighbourhood
 
 
-// Neighbour j of seq (length L) in enumeration order: substitutions
-// (position, mode ascending, skipping the current mode), insertions
-// (position 0..L, mode ascending), deletions (position ascending).
-// Returns the new length, or 0 if slot j does not exist.
-__device__ int neighbour(const uint16_t* s, int L, int j, int M, int lmax, uint16_t* out) {
-    const int nsub = L * (M - 1);
-    if (j < nsub) {
-        const int pos = j / (M - 1);
-        int m = j % (M - 1);
-        if (m >= s[pos]) ++m;
+// Mode of alphabet position a: every mode (grammar 0), or for the pushing
+// grammar stick on face a (mode 3 a, a < 4) and free motion (a = 4).
+__device__ __forceinline__ int alpha_mode(const FrontierDev& F, int a) {
+    return F.grammar == kGrammarPush ? (a < 4 ? 3 * a : kPushFree) : a;
+}
+
+// Pushing grammar (Sec. III-A; the reading fixed by the paper's printed
+// counts): the order starts in free motion, no two consecutive segments
+// share a mode, every mode is stick-on-a-face or free, and a direct
+// contact-to-contact switch joins adjacent faces of the cyclic face list.
+__device__ bool admissible(const FrontierDev& F, const uint16_t* s, int L) {
+    if (F.grammar != kGrammarPush) return true;
+    if (L < 1 || s[0] != kPushFree) return false;
+    for (int i = 0; i < L; ++i)
+        if (s[i] != kPushFree && (s[i] % 3 != 0 || s[i] >= 12)) return false;
+    for (int i = 0; i + 1 < L; ++i) {
+        const int a = s[i], b = s[i + 1];
+        if (a == b) return false;
+        if (a != kPushFree && b != kPushFree) {
+            const int d = (a / 3 - b / 3 + 4) & 3;
+            if (d != 1 && d != 3) return false;
+        }
+    }
+    return true;
+}
+
+// One-edit neighbour of seq (length L) at slot j of the fixed layout:
+// substitutions (position < l_max, alphabet position; the current mode is
+// skipped), insertions (position <= l_max, alphabet position), deletions
+// (position < l_max).  Slots that do not apply to this L are empty.  Within
+// an order the slots run in the enumeration order of the neighbourhood.
+// Returns the new length, or 0 for an empty slot.
+__device__ int neighbour(const FrontierDev& F, const uint16_t* s, int L, int j, uint16_t* out) {
+    const int nA = F.n_alpha, lmax = F.lmax;
+    if (j < lmax * nA) {
+        const int pos = j / nA, m = alpha_mode(F, j % nA);
+        if (pos >= L || m == s[pos]) return 0;
         for (int i = 0; i < L; ++i) out[i] = s[i];
         out[pos] = (uint16_t)m;
         return L;
     }
-    j -= nsub;
-    if (L + 1 <= lmax) {
-        const int nins = (L + 1) * M;
-        if (j < nins) {
-            const int pos = j / M, m = j % M;
-            for (int i = 0, o = 0; i <= L; ++i) {
-                if (i == pos) out[o++] = (uint16_t)m;
-                if (i < L) out[o++] = s[i];
-            }
-            return L + 1;
+    j -= lmax * nA;
+    if (j < (lmax + 1) * nA) {
+        const int pos = j / nA, m = alpha_mode(F, j % nA);
+        if (L + 1 > lmax || pos > L) return 0;
+        for (int i = 0, o = 0; i <= L; ++i) {
+            if (i == pos) out[o++] = (uint16_t)m;
+            if (i < L) out[o++] = s[i];
         }
-        j -= nins;
+        return L + 1;
     }
-    if (L - 1 >= 1 && j < L) {
+    j -= (lmax + 1) * nA;
+    if (j < lmax && L - 1 >= 1 && j < L) {
         for (int i = 0, o = 0; i < L; ++i)
             if (i != j) out[o++] = s[i];
         return L - 1;
@@ -221,17 +246,42 @@ __device__ int neighbour(const uint16_t* s, int L, int j, int M, int lmax, uint1
     return 0;
 }
 
-__global__ void neighbour_kernel(FrontierDev F, const TopKey* top, int k, int slots) {
+// N_r(m) slot j (Sec. III-B): j < slots1 is a one-edit neighbour; with
+// radius 2, j = slots1 + j1 slots1 + j2 is neighbour j2 of neighbour j1 (so
+// the one-edit orders come first, then the two-edit ones grouped by their
+// intermediate).  Every order on the way must be admissible; the parent
+// itself is not a neighbour.  Returns the length, or 0.
+__device__ int neighbour_r(const FrontierDev& F, const uint16_t* s, int L, int j, uint16_t* out) {
+    if (j < F.slots1) {
+        const int Ln = neighbour(F, s, L, j, out);
+        return (Ln > 0 && admissible(F, out, Ln)) ? Ln : 0;
+    }
+    j -= F.slots1;
+    uint16_t mid[COMET_MAX_SEGMENTS];
+    const int Lm = neighbour(F, s, L, j / F.slots1, mid);
+    if (Lm == 0 || !admissible(F, mid, Lm)) return 0;
+    const int Ln = neighbour(F, mid, Lm, j % F.slots1, out);
+    if (Ln == 0 || !admissible(F, out, Ln)) return 0;
+    if (Ln == L) {
+        bool same = true;
+        for (int i = 0; i < L; ++i) same = same && out[i] == s[i];
+        if (same) return 0;
+    }
+    return Ln;
+}
+
+__global__ void neighbour_kernel(FrontierDev F, const TopKey* top, int k, int64_t slots) {
     const int64_t total = (int64_t)k * slots;
     const unsigned long long nV = min(*F.nV, (unsigned long long)F.capacity);
     const int kk = (int)min((unsigned long long)k, nV);
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(o / slots), j = (int)(o % slots);
+        const int r = (int)(o / slots);
+        const int j = (int)(o - (int64_t)r * slots);
         unsigned long long code = kEmpty;
         if (r < kk) {
             uint16_t s[COMET_MAX_SEGMENTS], nb[COMET_MAX_SEGMENTS];
             const int L = decode_code(top[r].code, F.n_modes, s);
-            const int Ln = neighbour(s, L, j, F.n_modes, F.lmax, nb);
+            const int Ln = neighbour_r(F, s, L, j, nb);
             if (Ln > 0) {
                 comet_mode_seq q;
                 q.len = (uint8_t)Ln;
@@ -367,7 +417,7 @@ cudaError_t launch_expand(const FrontierDev& F, int k, int batch, int64_t budget
     const TopKey* top = launch_topk(F, k, s, &e);
     if (!top) return e;
 
-    const int slots = F.slots;
+    const int64_t slots = F.slots;
     const int64_t total = (int64_t)k * slots;
     e = cudaMemsetAsync(F.cand_keys, 0, sizeof(unsigned long long) * (F.cand_mask + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(F.cand_ord, 0xff, sizeof(unsigned int) * (F.cand_mask + 1), s);

@@ -21,6 +21,10 @@ struct TopKey {
 
 struct FrontierDev {
     int instance, n_modes, lmax, slots;
+    // neighbourhood rule: edit radius (1, 2), grammar (0 = every order over
+    // the instance's modes; 1 = the pushing grammar over stick-on-a-face and
+    // free motion), alphabet size and one-edit slots per order
+    int radius, grammar, n_alpha, slots1;
     int64_t capacity;     // |V| maximum
     int64_t batch_cap;    // largest batch added at once
     unsigned long long* codes;  // [capacity]
@@ -39,6 +43,17 @@ struct FrontierDev {
     int64_t* n_next;
     int* error;                     // 1 malformed order, 2 capacity exceeded
 };
+
+// one-edit slots of an order under a rule (fixed layout over l_max:
+// substitutions l_max x n_alpha, insertions (l_max + 1) x n_alpha, deletions
+// l_max) and all slots per parent (radius 2 adds slots1 x slots1)
+inline int64_t edit_slots1(int lmax, int n_alpha) { return (int64_t)lmax * n_alpha * 2 + n_alpha + lmax; }
+inline int64_t edit_slots(int lmax, int n_alpha, int radius) {
+    const int64_t s1 = edit_slots1(lmax, n_alpha);
+    return radius == 2 ? s1 + s1 * s1 : s1;
+}
+constexpr int kGrammarNone = 0, kGrammarPush = 1;
+constexpr int kPushFree = 12;  // free motion in the 13-mode pushing alphabet
 
 size_t topk_smem_bytes();
 cudaError_t prepare_expand();

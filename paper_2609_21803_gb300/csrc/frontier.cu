@@ -58,12 +58,26 @@ extern "C" {
 
 comet_status comet_frontier_create(comet_problem* p, int32_t instance, int64_t capacity, int32_t batch,
                                    int32_t k_max, comet_frontier** out) {
+    return comet_frontier_create_ex(p, instance, capacity, batch, k_max, 1, COMET_GRAMMAR_NONE, out);
+}
+
+comet_status comet_frontier_create_ex(comet_problem* p, int32_t instance, int64_t capacity, int32_t batch,
+                                      int32_t k_max, int32_t radius, int32_t grammar, comet_frontier** out) {
     if (!p || !out) return ffail(COMET_ERR_INVALID_ARG, "problem and out are required");
     *out = nullptr;
     if (instance < 0 || instance >= (int)p->inst.size()) return ffail(COMET_ERR_INVALID_ARG, "instance out of range");
     if (capacity < 1 || batch < 1 || k_max < 1 || k_max > comet::kChunk || batch > capacity)
         return ffail(COMET_ERR_INVALID_ARG, "need 1 <= batch <= capacity and 1 <= k_max <= 4096");
     const comet_instance_desc& d = p->inst[instance];
+    if (radius != 1 && radius != 2) return ffail(COMET_ERR_INVALID_ARG, "the edit radius is 1 or 2");
+    if (grammar != COMET_GRAMMAR_NONE && grammar != COMET_GRAMMAR_PUSH)
+        return ffail(COMET_ERR_INVALID_ARG, "unknown grammar");
+    if (grammar == COMET_GRAMMAR_PUSH && (d.task != COMET_TASK_PUSHER_SLIDER || d.n_modes != 13))
+        return ffail(COMET_ERR_INVALID_ARG, "the pushing grammar needs a pushing instance with n_modes = 13");
+    const int n_alpha = grammar == COMET_GRAMMAR_PUSH ? 5 : d.n_modes;
+    const int64_t slots = comet::edit_slots(d.max_segments, n_alpha, radius);
+    if ((int64_t)k_max * slots > ((int64_t)1 << 26))
+        return ffail(COMET_ERR_INVALID_ARG, "k_max x neighbourhood slots above 2^26 (use radius 1 or a smaller beam)");
     {
         const cudaError_t pe = comet::prepare_expand();
         if (pe != cudaSuccess) return fcuda(pe, "expand kernels");
@@ -77,7 +91,11 @@ comet_status comet_frontier_create(comet_problem* p, int32_t instance, int64_t c
     F.instance = instance;
     F.n_modes = d.n_modes;
     F.lmax = d.max_segments;
-    F.slots = F.lmax * (F.n_modes - 1) + (F.lmax + 1) * F.n_modes + F.lmax;
+    F.radius = radius;
+    F.grammar = grammar;
+    F.n_alpha = n_alpha;
+    F.slots1 = (int)comet::edit_slots1(F.lmax, n_alpha);
+    F.slots = (int)slots;
     F.capacity = capacity;
     F.batch_cap = std::max<int64_t>(batch, 1);
     const uint64_t set_cap = pow2_at_least((uint64_t)capacity * 2);
@@ -309,6 +327,8 @@ extern "C" comet_status comet_default_plan_opts(comet_plan_opts* po) {
     po->k_ref = 256;
     po->ref_iters = 0;
     po->use_graph = 1;
+    po->radius = 1;
+    po->grammar = COMET_GRAMMAR_NONE;
     return COMET_OK;
 }
 
@@ -366,10 +386,12 @@ comet_status plan_impl(comet_problem* p, int32_t instance, const comet_mode_seq*
     // with a proposal the frontier's next batch holds the whole neighbourhood
     // of the beam, which the proposal then prunes to `batch`
     const comet_instance_desc& di = p->inst[instance];
-    const int slots = di.max_segments * (di.n_modes - 1) + (di.max_segments + 1) * di.n_modes + di.max_segments;
+    const int64_t slots =
+        comet::edit_slots(di.max_segments, po.grammar == COMET_GRAMMAR_PUSH ? 5 : di.n_modes, po.radius);
     const int32_t cand = q ? (int32_t)std::min<int64_t>((int64_t)po.k * slots, capacity) : batch;
     comet_frontier* f = nullptr;
-    comet_status st = comet_frontier_create(p, instance, capacity, std::max(cand, batch), std::max(po.k, po.k_ref), &f);
+    comet_status st = comet_frontier_create_ex(p, instance, capacity, std::max(cand, batch), std::max(po.k, po.k_ref),
+                                               po.radius, po.grammar, &f);
     if (st != COMET_OK) return st;
     struct Guard {
         comet_frontier* f;
@@ -651,8 +673,9 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
     for (int i = 0; i < n_inst; ++i) {
         const int64_t n0 = seed_offsets[i + 1] - seed_offsets[i];
         const int64_t cap = po.budget > 0 ? std::max<int64_t>(po.budget, n0) : n0 + (int64_t)po.rounds * batch;
-        const comet_status st = comet_frontier_create(p, instances[i], cap, (int32_t)std::min<int64_t>(batch, cap),
-                                                      std::max(po.k, po.k_ref), &fr[i]);
+        const comet_status st =
+            comet_frontier_create_ex(p, instances[i], cap, (int32_t)std::min<int64_t>(batch, cap),
+                                     std::max(po.k, po.k_ref), po.radius, po.grammar, &fr[i]);
         if (st != COMET_OK) return st;
     }
     const int64_t n_round = (int64_t)n_inst * batch, n_ref_all = (int64_t)n_inst * po.k_ref;

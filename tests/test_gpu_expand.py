@@ -135,3 +135,49 @@ def test_frontier_edge_cases(P):
         _add(P, f, many, np.ones(60, np.float32))
     P.comet_frontier_destroy(f)
     prob.close()
+
+
+@pytest.mark.parametrize("seed,lmax,k,batch,r", [(0, 4, 8, 20000, 2), (1, 3, 16, 500, 2), (2, 5, 4, 20000, 1)])
+def test_two_edit_expansion_matches_oracle(P, seed, lmax, k, batch, r):
+    # N_r over every order (Sec. III-B "at most r edits"): the one-edit orders
+    # of a parent first, then the one-edit orders of each of them in order
+    prob, inst = _problem(P, lmax)
+    M = 12
+    rng = np.random.default_rng(seed)
+    seqs = list({tuple(int(m) for m in rng.integers(0, M, rng.integers(1, lmax + 1))) for _ in range(200)})
+    merit = rng.integers(0, 20, len(seqs)).astype(np.float32) * np.float32(0.125) + np.float32(0.5)
+    f = P.comet_frontier_create(prob.handle, 0, 2000000, batch, 64, radius=r)
+    _add(P, f, seqs, merit)
+    P.comet_expand(prob.handle, f, k)
+    got = P.frontier_next_orders(f, batch)
+    V = {S.encode(s, M): (float(m), s) for s, m in zip(seqs, merit)}
+    assert got == S.expand(V, k=k, batch=batch, n_modes=M, l_max=lmax, r=r)
+    P.comet_frontier_destroy(f)
+    prob.close()
+
+
+@pytest.mark.parametrize("r,batch", [(1, 20000), (2, 20000), (2, 300)])
+def test_grammar_expansion_matches_oracle(P, r, batch):
+    # the pushing grammar over the 13-mode alphabet (stick on a face, free
+    # motion): only admissible orders, every intermediate admissible
+    inst = dict(W.push_l4_instance(0), n_modes=13, max_segments=6, knots_per_segment=4)
+    prob = P.Problem([inst])
+    rng = np.random.default_rng(5 + r)
+    seqs = S.admissible_orders(3)
+    merit = rng.integers(0, 10, len(seqs)).astype(np.float32) * np.float32(0.25) + np.float32(1.0)
+    f = P.comet_frontier_create(prob.handle, 0, 200000, batch, 64, radius=r, grammar=P.GRAMMAR_PUSH)
+    _add(P, f, seqs, merit)
+    P.comet_expand(prob.handle, f, 8)
+    got = P.frontier_next_orders(f, batch)
+    V = {S.encode(s, 13): (float(m), s) for s, m in zip(seqs, merit)}
+    want = S.expand_grammar(V, k=8, batch=batch, l_max=6, r=r)
+    assert got == want and all(S.admissible_push(s) for s in got)
+    P.comet_frontier_destroy(f)
+    # the rule is checked: the grammar needs the 13-mode alphabet
+    prob12, _ = _problem(P, 4)
+    with pytest.raises(P.CometError):
+        P.comet_frontier_create(prob12.handle, 0, 1000, 100, 8, radius=1, grammar=P.GRAMMAR_PUSH)
+    with pytest.raises(P.CometError):
+        P.comet_frontier_create(prob12.handle, 0, 1000, 100, 8, radius=3)
+    prob12.close()
+    prob.close()

@@ -161,3 +161,18 @@ def test_grammar_expansion_round():
     best = min(V.values(), key=lambda v: (v[0], S.encode(v[1], 13)))[1]
     nb = [t for t in S.grammar_neighbours(best, 5, 2) if S.encode(t, 13) not in V]
     assert out[: len(nb)] == nb[: len(out)]
+
+
+@pytest.mark.parametrize("seq", [(3,), (0, 7), (11, 2, 5)])
+def test_two_edit_neighbourhood_by_edit_distance(seq):
+    # N_2 over every order of 1..3 segments = the orders at edit distance 1
+    # or 2 (any intermediate of length 1..l_max is an order), one-edit first
+    l_max, M = 3, 12
+    pool = [s for L in range(1, l_max + 1) for s in itertools.product(range(M), repeat=L)]
+    n1 = S.neighbours_r(seq, M, l_max, 1)
+    n2 = S.neighbours_r(seq, M, l_max, 2)
+    assert set(n1) == {t for t in pool if _lev(seq, t) == 1}
+    assert n2[: len(n1)] == n1
+    # with l_max = 3 an intermediate may not exceed 3 segments
+    want = {t for t in pool if t != seq and any(_lev(t, u) <= 1 for u in n1)}
+    assert set(n2) == want and len(n2) == len(set(n2))
