@@ -104,3 +104,25 @@ def test_unlimited_expansion_recovers_enumeration(P):
         i = int(np.argmin(np.where(ok, ref["cost"], np.inf)))
         assert r["best"] == top[i]
         prob.close()
+
+
+def test_grammar_plan_recovers_admissible_enumeration(P):
+    # the pushing grammar: every admissible order is reached from (free,) by
+    # admissible one-edit steps, so walking all of V with enough rounds
+    # evaluates all 57 admissible orders of at most 4 segments and returns
+    # the enumeration's answer after the same refinement
+    inst = dict(W.push_grammar_instance(3), max_segments=4, knots_per_segment=6)
+    prob = P.Problem([inst])
+    every = W.admissible_push_orders(4)
+    assert len(every) == 57
+    seeds = P.pack_mode_seqs([(12,)])
+    r = P.comet_plan(prob.handle, 0, seeds, 1, dict(k=256, batch=64, rounds=12, k_ref=8, ref_iters=600, grammar=1))
+    assert r["evaluations"] == 57
+    e = P.comet_plan(prob.handle, 0, P.pack_mode_seqs(every), 57, dict(rounds=0, k_ref=8, ref_iters=600))
+    assert r["best"] == e["best"] and r["best_cost"] == e["best_cost"]
+    assert r["best"][0] == 12 and r["best_status"] == 0
+    # radius 2 reaches the same set in fewer rounds
+    r2 = P.comet_plan(prob.handle, 0, seeds, 1, dict(k=256, batch=256, rounds=6, k_ref=8, ref_iters=600,
+                                                     grammar=1, radius=2))
+    assert r2["evaluations"] == 57 and r2["best"] == e["best"]
+    prob.close()

@@ -176,3 +176,12 @@ def test_two_edit_neighbourhood_by_edit_distance(seq):
     # with l_max = 3 an intermediate may not exceed 3 segments
     want = {t for t in pool if t != seq and any(_lev(t, u) <= 1 for u in n1)}
     assert set(n2) == want and len(n2) == len(set(n2))
+
+
+def test_workload_seed_orders_match_the_oracle_grammar():
+    # the bench's seed generator (workloads) is written apart from the
+    # oracle's grammar; both give the same orders in the same order
+    import workloads as W
+    for cap in (1, 4, 6):
+        assert W.admissible_push_orders(cap) == S.admissible_orders(cap)
+    assert len(W.admissible_push_orders(8)) == 6297

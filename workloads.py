@@ -167,3 +167,37 @@ def bimanual_mode(ground: int, hand_l: int, hand_r: int) -> int:
     """Mode index of (ground 0 stick / 1 slide / 2 pivot, hand codes 0 none or
     1 + 3 face + kind)."""
     return ground * 169 + hand_l * 13 + hand_r
+
+
+def push_grammar_instance(seed: int) -> dict:
+    """Square box of the grammar experiments: the push_l4 slider and poses
+    (same draws), the 13-mode pushing alphabet (mode 12 = free motion),
+    orders of at most 8 segments of K = 10 intervals."""
+    d = push_l4_instance(seed)
+    d["n_modes"] = 13
+    d["max_segments"] = 8
+    d["knots_per_segment"] = 10
+    return d
+
+
+def admissible_push_orders(cap: int) -> list[tuple[int, ...]]:
+    """Seed orders for the pushing grammar of the four-faced box: every order
+    of 1..cap segments over {stick on face f = mode 3 f, free motion = 12}
+    that starts in free motion, never repeats a mode in consecutive
+    segments, and switches directly between contacts only on adjacent faces;
+    by length, then lexicographically (601 orders at cap 6, 6,297 at 8)."""
+    alpha = (0, 3, 6, 9, 12)
+    out, level = [], [(12,)]
+    for _ in range(cap):
+        out += level
+        nxt = []
+        for s in level:
+            for m in alpha:
+                a = s[-1]
+                if m == a:
+                    continue
+                if a != 12 and m != 12 and (a // 3 - m // 3) % 4 not in (1, 3):
+                    continue
+                nxt.append(s + (m,))
+        level = nxt
+    return out
