@@ -467,19 +467,22 @@ struct BCtx {
 };
 
 // compensated local variables of stage k at step alpha along dz
+// (at alpha = 0 the step is not read: phase A runs before the first step of
+// a TO exists, and its buffer also parks gradient parts during phase A)
 __device__ __forceinline__ void load_stage(const BCtx& C, int k, float alpha, float* x, float* u, float* dx) {
     const int Np1 = C.Np1, N = C.N;
     const BSmem& S = C.S;
+    const bool step = alpha != 0.f;
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
         const float h0 = S.xh[i * Np1 + k], h1 = S.xh[i * Np1 + k + 1];
-        const float l0 = S.xl[i * Np1 + k] + alpha * S.dz[NWV * k + i];
-        const float l1 = S.xl[i * Np1 + k + 1] + alpha * S.dz[NWV * (k + 1) + i];
+        const float l0 = S.xl[i * Np1 + k] + (step ? alpha * S.dz[NWV * k + i] : 0.f);
+        const float l1 = S.xl[i * Np1 + k + 1] + (step ? alpha * S.dz[NWV * (k + 1) + i] : 0.f);
         x[i] = h0 + l0;
         dx[i] = (h1 - h0) + (l1 - l0);
     }
 #pragma unroll
-    for (int j = 0; j < NU; ++j) u[j] = S.us[j * N + k] + alpha * S.dz[NWV * k + NX + j];
+    for (int j = 0; j < NU; ++j) u[j] = S.us[j * N + k] + (step ? alpha * S.dz[NWV * k + NX + j] : 0.f);
 }
 
 struct BMeasures {
@@ -1172,6 +1175,7 @@ __global__ void __launch_bounds__(kBimThreads, 3) bimanual_kernel(EvalArgs A) {
             S.us[q] = warm ? warm[NX * Nm1 + j * A.Nmax + k] : ((j == ULN - 5) ? P.mg : 0.f);
         }
         for (int q = C.tid; q < 3 + NR * N; q += kBimThreads) S.lam[q] = 0.f;
+        for (int q = C.tid; q < NWV * N + NX; q += kBimThreads) S.dz[q] = S.gr[q] = 0.f;
         for (int k = C.tid; k < N; k += kBimThreads) {
             const int seg = (int)(((long long)k * len) / N);
             const int m = sq.modes[seg];
