@@ -319,6 +319,7 @@ comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, 
     a.queue = p->d_queue;
     a.bad_input = p->d_bad;
     a.sp = make_params(p->opts, max_iters);
+    for (const comet_instance_desc& d : p->inst) a.sp.free_motion |= d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes == 13;
     if (p->task == COMET_TASK_BIMANUAL)
         CUDA_TRY(launch_bimanual(a, (int)warps, s), "bimanual evaluator launch");
     else

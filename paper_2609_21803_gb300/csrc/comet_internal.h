@@ -41,6 +41,7 @@ struct SolverParams {
     double eps_feas, merit_mu;
     int refine;          // FP64 iterative refinement of the step ...
     float refine_beta;   // ... while the penalty exceeds this value
+    int free_motion;     // some instance has the free-motion mode (13 pushing modes)
 };
 
 struct EvalArgs {

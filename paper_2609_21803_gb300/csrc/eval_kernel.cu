@@ -153,6 +153,9 @@ struct Rows {
     float f0, f1, ct, st, kf;
 };
 
+// kFree: free motion (mode 12) compiled in; problems over the 12 contact
+// modes run the variant without it
+template <bool kFree>
 __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& mi, const float xk[4],
                                           const float dx[4], const float u[3], Rows& R) {
     float nx, ny;
@@ -161,7 +164,8 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
     const float a = P.a[mi.face], ell = P.ell[mi.face];
     // free motion: zero force-to-velocity gain, so the slider rests and only
     // the contact offset moves (at the pusher's rate)
-    const float k = (mi.kind == 3) ? 0.f : P.kappa, ic2 = P.inv_c2, dt = P.dt;
+    const bool free = kFree && mi.kind == 3;
+    const float k = free ? 0.f : P.kappa, ic2 = P.inv_c2, dt = P.dt;
     const float th = xk[2], s = xk[3];
     const float fn = u[0], ft = u[1], sd = u[2];
     float st, ct;
@@ -199,26 +203,17 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
     R.ax[1][2] += -dt * Fx12 * P.inv_sigma[1];
     R.ax[2][3] += -dt * Fx23 * P.inv_sigma[2];
     if (mi.smask) R.on[3] = false;
-    if (mi.kind == 3) {
-        // free motion: the mode equality f_n = 0 (row 4) is the only force
-        // row; f_t acts on nothing and the effort cost sets it to zero
-#pragma unroll
-        for (int q = 0; q < 5; ++q) R.lu[q][0] = R.lu[q][1] = R.lu[q][2] = 0.f;
-        R.lu[0][0] = 1.f;
-#pragma unroll
-        for (int r = 4; r < 11; ++r) {
-            R.c[r] = (r == 4) ? fn : 0.f;
-            R.phys[r] = 1.f;
-            R.on[r] = r == 4;
-        }
-        return;
-    }
 
     const float mu = P.mu, sc = P.sc_cone;
     const bool stick = mi.kind == 0;
     const float sg = (mi.kind == 1) ? -1.f : 1.f;
-    // row 4: mode equality
-    if (stick) {
+    // row 4: mode equality.  Free motion: f_n = 0 is the only force row
+    // (rows 5..10 off); f_t acts on nothing and the effort cost sets it to 0
+    if (free) {
+        R.c[4] = fn;
+        R.phys[4] = 1.f;
+        R.lu[0][0] = 1.f; R.lu[0][1] = 0.f; R.lu[0][2] = 0.f;
+    } else if (stick) {
         R.c[4] = sd;
         R.phys[4] = 1.f;
         R.lu[0][0] = 0.f; R.lu[0][1] = 0.f; R.lu[0][2] = 1.f;
@@ -239,17 +234,17 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
     R.c[7] = sg * sd;
     R.lu[3][0] = 0.f; R.lu[3][1] = 0.f; R.lu[3][2] = sg;
     R.phys[7] = 1.f;
-    R.on[7] = !stick;
+    R.on[7] = !stick && !free;
     // row 8: unilateral contact -f_n <= 0
     R.c[8] = -fn;
     R.lu[4][0] = -1.f; R.lu[4][1] = 0.f; R.lu[4][2] = 0.f;
     R.phys[8] = 1.f;
-    R.on[8] = true;
+    R.on[8] = !free;
     // rows 9, 10: contact point on the face, |s_k| <= ell
     R.c[9] = s - ell;
     R.c[10] = -s - ell;
     R.phys[9] = R.phys[10] = 1.f;
-    R.on[9] = R.on[10] = true;
+    R.on[9] = R.on[10] = !free;
 #pragma unroll
     for (int r = 0; r < 11; ++r)
         if (!R.on[r]) R.c[r] = 0.f;
@@ -338,6 +333,7 @@ struct Measures {
     bool finite;
 };
 
+template <bool kFree>
 __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool assemble, bool update,
                             float beta_old, bool rhs_from_gr = false) {
     const DevInstance& P = *C.P;
@@ -359,7 +355,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
 #pragma unroll
         for (int j = 0; j < 3; ++j) u[j] = S.us[j * N + k];
         Rows R;
-        eval_rows(P, mi, xk, dx, u, R);
+        eval_rows<kFree>(P, mi, xk, dx, u, R);
         float* lam = S.lam + 3 + 11 * k;
         float y[11];
         bool act[11];
@@ -468,7 +464,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
                 // with yd_r the multiplier of the unscaled row
                 float nx, ny;
                 face_nt(mi.face, nx, ny);
-                const float tx = -ny, ty = nx, kk = R.kf;  // 0 in free motion
+                const float tx = -ny, ty = nx, kk = kFree ? R.kf : P.kappa;  // R.kf = 0 in free motion
                 const float yd0 = y[0] * P.inv_sigma[0], yd1 = y[1] * P.inv_sigma[1];
                 const float yd2 = y[2] * P.inv_sigma[2];
                 const float h_thth = -yd0 * R.f0 - yd1 * R.f1;
@@ -911,6 +907,7 @@ __device__ float phase_c(Ctx& C, const float dx0[4]) {
 }
 
 // merit contribution of interval k at the trial step alpha
+template <bool kFree>
 __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, float beta, float inv2b) {
     const DevInstance& P = *C.P;
     const int N = C.N, Np1 = C.N + 1;
@@ -928,7 +925,7 @@ __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, f
 #pragma unroll
     for (int j = 0; j < 3; ++j) u[j] = S.us[j * N + k] + alpha * S.dz[7 * k + 4 + j];
     Rows R;
-    eval_rows(P, mi, xk, dx, u, R);
+    eval_rows<kFree>(P, mi, xk, dx, u, R);
     const float* lam = S.lam + 3 + 11 * k;
     float phi = P.w_control * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 #pragma unroll
@@ -956,6 +953,7 @@ __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, f
 // Trials run four at a time (lane = trial + 4 x stage group), largest alpha
 // first: the second batch {1/8 .. 1/64} is evaluated only when none of
 // {1, 1/2, 1/4} passes, which leaves the accepted alpha unchanged.
+template <bool kFree>
 __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& sp) {
     const int lane = C.lane;
     const int sub = lane & 3, grp = lane >> 2;
@@ -969,7 +967,7 @@ __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& 
         float phi = 0.f;
         if (a <= sp.n_alpha)
 #pragma unroll 1
-            for (int k = grp; k < C.N; k += 8) phi += stage_merit(C, k, alpha, beta, inv2b);
+            for (int k = grp; k < C.N; k += 8) phi += stage_merit<kFree>(C, k, alpha, beta, inv2b);
         phi += __shfl_xor_sync(kFull, phi, 4);
         phi += __shfl_xor_sync(kFull, phi, 8);
         phi += __shfl_xor_sync(kFull, phi, 16);
@@ -1264,11 +1262,12 @@ __device__ void residual_fp64(Ctx& C, float beta_f, float rho_f, bool curvature)
 // with the same model (same factorisation path) and the correction added,
 // dz <- dz + delta with (H + rho I) delta = -res.  Once the records hold
 // the residual, sm.gr is free and keeps the first step meanwhile.
+template <bool kFree>
 __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
     Smem& S = C.sm;
     const int nz = 7 * C.N + 4;
     residual_fp64(C, beta, rho, curvature);
-    phase_a(C, beta, rho, curvature, true, false, beta, /*rhs_from_gr=*/true);
+    phase_a<kFree>(C, beta, rho, curvature, true, false, beta, /*rhs_from_gr=*/true);
     for (int t = C.lane; t < nz; t += 32) S.gr[t] = S.dz[t];
     __syncwarp();
     float d0[4];
@@ -1287,7 +1286,7 @@ __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
 // kRefine: the variant with the FP64 refinement step compiled in; the
 // launch picks it only when the penalty can exceed refine_beta, so the
 // default kernel carries none of that code (a smaller instruction footprint).
-template <bool kRefine>
+template <bool kRefine, bool kFree>
 __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
     extern __shared__ float smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1383,7 +1382,7 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
             float beta_old = beta;
             float dx0[4];
             for (;;) {
-                const Measures m = phase_a(C, beta, rho, model_curv, true, trip == kUpdate, beta_old);
+                const Measures m = phase_a<kFree>(C, beta, rho, model_curv, true, trip == kUpdate, beta_old);
                 if (trip == kMeasure) {
                     if (!m.finite) {
                         status = COMET_TO_NONFINITE;
@@ -1428,8 +1427,8 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
             if (!fac) continue;
             phase_b_gains(C);
             const float D = phase_c(C, dx0);
-            if (kRefine && beta > sp.refine_beta) refine_step(C, beta, rho, model_curv);
-            const float alpha = phase_d(C, beta, D, sp);
+            if (kRefine && beta > sp.refine_beta) refine_step<kFree>(C, beta, rho, model_curv);
+            const float alpha = phase_d<kFree>(C, beta, D, sp);
             if (alpha > 0.f) {
                 phase_e(C, alpha);
                 rho = fmaxf(sp.rho_min, rho / 10.f);
@@ -1469,17 +1468,30 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
 
 size_t smem_per_warp_bytes(int Nmax) { return smem_floats(Nmax) * sizeof(float); }
 
+namespace {
+// every instantiation of the evaluator: (refinement, free motion)
+cudaError_t set_smem_all(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(eval_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(eval_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(eval_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(eval_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+}  // namespace
+
 int eval_blocks_per_sm(int warps_per_block, size_t smem_per_block) {
     int nb = 0;
-    if (cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_block) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_block) !=
-            cudaSuccess) {
+    if (set_smem_all(smem_per_block) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<false>, warps_per_block * 32, smem_per_block) !=
-        cudaSuccess)
+    // the variants share the register cap and shared memory, so one
+    // occupancy query serves all
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<false, false>, warps_per_block * 32,
+                                                      smem_per_block) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -1494,17 +1506,24 @@ cudaError_t launch_eval(const EvalArgs& a, int total_warps, int warps_per_block,
     if (e != cudaSuccess) return e;
     static size_t raised[64] = {};
     if (dev < 64 && raised[dev] < smem) {
-        e = cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = set_smem_all(smem);
         if (e != cudaSuccess) return e;
         raised[dev] = smem;
     }
     const int blocks = (total_warps + warps_per_block - 1) / warps_per_block;
-    if (a.sp.refine && a.sp.refine_beta < a.sp.beta_max)
-        eval_kernel<true><<<blocks, warps_per_block * 32, smem, s>>>(a);
-    else
-        eval_kernel<false><<<blocks, warps_per_block * 32, smem, s>>>(a);
+    const bool refine = a.sp.refine && a.sp.refine_beta < a.sp.beta_max;
+    const unsigned threads = warps_per_block * 32;
+    if (a.sp.free_motion) {
+        if (refine)
+            eval_kernel<true, true><<<blocks, threads, smem, s>>>(a);
+        else
+            eval_kernel<false, true><<<blocks, threads, smem, s>>>(a);
+    } else {
+        if (refine)
+            eval_kernel<true, false><<<blocks, threads, smem, s>>>(a);
+        else
+            eval_kernel<false, false><<<blocks, threads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -150,6 +150,7 @@ extern "C" comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst
     a.queue = queue;
     a.bad_input = bad;
     a.sp = comet::make_params(o, 0);
+    for (int i = 0; i < n_instances; ++i) a.sp.free_motion |= inst[i].n_modes == 13;
     e = comet::launch_eval(a, (int)warps, warps_per_block, s);
     if (e != cudaSuccess) return noalloc_fail(COMET_ERR_CUDA, cudaGetErrorString(e));
     return COMET_OK;
