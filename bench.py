@@ -47,10 +47,10 @@ N_STAGES = SEG * K
 # forward pass 70, 8-trial line search 800)
 FLOP_PER_STAGE_ITER = 3330
 # DRAM bytes (read + write) of one evaluator launch over the 20,736 orders:
-# the ncu capture of a 4,096-order launch at 4 CTAs per SM (2.06 MB read,
-# 3.41 GB written: stage records written back from L2,
+# the ncu capture of a 4,096-order launch at 4 CTAs per SM (2.24 MB read,
+# 3.52 GB written: stage records written back from L2,
 # profiles/eval_kernel_push_l4.md) scaled by the TOs processed
-EVAL_TRAFFIC_BYTES = (2.064e6 + 3.40791e9) * 20736 / 4096
+EVAL_TRAFFIC_BYTES = (2.24128e6 + 3.516693e9) * 20736 / 4096
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
