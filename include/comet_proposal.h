@@ -10,8 +10,8 @@
  *                          k of the order's solved trajectory (Eq. mode_nlp).
  * It is trained on the GPU on (order, evaluator result) samples, orders and
  * prunes the neighbours an expansion round generates, and warm-starts their
- * TOs.  The evaluator (comet_eval_modes) stays the judge of every returned
- * plan.
+ * TOs.  The evaluator (comet_eval_modes) still solves and certifies every
+ * returned plan.
  *
  * Input features of an order of length L (in_dim = 12 + 13 L_max rounded
  * up to a multiple of 64, zero padded): start pose (x, y, theta), goal pose,

@@ -21,7 +21,8 @@
  *   Eq. inexact_mode_value             -- J_hat and v_hat
  *   Eq. search_merit                   -- M_hat
  * Where the paper is silent (dynamics equations, hyper-parameters, row
- * scaling constants) the readings listed in the design notes are used.
+ * scaling constants) the readings are stated beside the code that takes
+ * them.
  */
 #include "comet_oracle.h"
 

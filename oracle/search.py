@@ -9,7 +9,7 @@ Follows Sec. III-B of the paper:
   * Algorithm 1: walk the evaluated set V in increasing merit and admit unseen
     neighbours (not in V or the next batch) until the batch holds B orders.
 
-Readings where the paper is silent (listed in the design notes):
+Readings where the paper is silent:
   * enumeration order of a neighbourhood: substitutions (position, then mode
     ascending), then insertions (position 0..L, mode ascending), then
     deletions (position ascending); lengths outside [1, L_max] are skipped;

@@ -95,7 +95,7 @@ def test_straight_push_closed_form(P):
 
 
 def test_two_segment_enumeration_parity(P):
-    # BASELINE workload of 2-segment orders: every 144 orders x 32 seeded goals
+    # the 2-segment workload: every one of the 144 orders x 32 seeded goals
     seeds = range(32)
     insts = [W.push_l2_instance(s) for s in seeds]
     seqs = W.all_sequences(12, 2)

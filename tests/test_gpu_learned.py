@@ -1,6 +1,6 @@
 """The learned proposal in use: trained on the GPU on evaluator results, it
 orders and prunes the expansion of Algorithm 1 and warm-starts the TOs; the
-evaluator stays the judge of every returned plan.
+evaluator still solves and certifies every returned plan.
 
 The ablation (the same planner with and without the proposal, on held-out
 instances) checks what the trained network buys: plans as good as plain

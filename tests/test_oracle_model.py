@@ -1,6 +1,6 @@
 """Pins of the oracle's model layer against closed forms and finite
 differences (no GPU).  Paper: Sec. III-A (problem), Sec. III-C (shared
-masked representation); model readings in the design notes."""
+masked representation)."""
 import math
 
 import numpy as np
