@@ -140,3 +140,44 @@ def test_kkt_with_free_segments(seed):
         U = tr[4 * (N + 1):].reshape(3, N)
         assert np.max(np.abs(U[:2, free_k])) <= 1e-8
     assert seen >= 2
+
+
+def test_scipy_slsqp_finds_no_better_point_with_free_motion():
+    # tiny orders with free motion (two segments of K = 3): SciPy's SLSQP on
+    # the same NLP (Eq. mode_nlp with the free-motion rows), started next to
+    # the oracle's solution, finds no lower cost
+    so = pytest.importorskip("scipy.optimize")
+    inst = W.push_l2_instance(9)
+    inst["knots_per_segment"] = 3
+    N = 6
+    for modes in ([FREE, 0], [FREE, 3], [6, FREE]):
+        tr, lam, res = oracle.solve(inst, modes, opts=oracle.default_opts(**TIGHT))
+        assert res["status"] == oracle.CONVERGED
+
+        def fun(z):
+            return inst["w_terminal"] * np.sum((z[7 * N: 7 * N + 3] - inst["goal"]) ** 2) + inst["w_control"] * sum(
+                np.sum(z[7 * k + 4: 7 * k + 7] ** 2) for k in range(N))
+
+        def rows(z):
+            c, mask, _, ci = oracle.rows(inst, modes, N, to_component(z, N))
+            return np.concatenate([ci, c.ravel()]), mask.ravel().astype(bool)
+
+        def eq(z):
+            cc, mk = rows(z)
+            return cc[np.concatenate([np.ones(3, bool), np.tile(np.arange(11) < 5, N) & mk])]
+
+        def ineq(z):
+            cc, mk = rows(z)
+            return -cc[np.concatenate([np.zeros(3, bool), np.tile(np.arange(11) >= 5, N) & mk])]
+
+        cons = [{"type": "eq", "fun": eq}, {"type": "ineq", "fun": ineq}]
+        rng = np.random.default_rng(sum(modes))
+        zo = to_interleaved(tr, N)
+        solved = 0
+        for _ in range(3):
+            r = so.minimize(fun, zo + rng.normal(size=zo.shape) * 1e-4, method="SLSQP", constraints=cons,
+                            options={"maxiter": 1000, "ftol": 1e-14})
+            if r.success:
+                solved += 1
+                assert r.fun >= res["cost"] - 1e-7 * max(1.0, res["cost"])
+        assert solved >= 1
