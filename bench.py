@@ -290,7 +290,9 @@ def run_gpu(args):
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * P.MODE_SEQ_BYTES),
                 "d2h_bytes_per_step": int(n * (4 + 4 + 4))},
-        "gpu_launches": args.steps,
+        # per step: the longest-first ordering (hist, scan, scatter kernels;
+        # the problem holds orders of up to 4 segments) and the evaluator
+        "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": EVAL_TRAFFIC_BYTES,
                      "note": "achieved = 3330 flop x 80 stages x solver iterations / device time; peak = FP32 "
