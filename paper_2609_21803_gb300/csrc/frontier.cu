@@ -421,14 +421,15 @@ comet_status plan_impl(comet_problem* p, int32_t instance, const comet_mode_seq*
     float* d_cost = (float*)(bp + b_seq + 256);
     int32_t* d_status = (int32_t*)(bp + b_seq + b_f + 512);
     uint64_t* d_codes = (uint64_t*)(bp + b_seq + b_f + sizeof(int32_t) * n_eval_max + 768);
-    cudaEvent_t ev[4];
-    for (auto& e : ev) FTRY(cudaEventCreate(&e), "events");
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     struct EvGuard {
         cudaEvent_t* e;
         ~EvGuard() {
-            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 4; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
         }
     } evg{ev};
+    for (auto& e : ev) FTRY(cudaEventCreate(&e), "events");
     FTRY(cudaEventRecord(ev[0], s), "event");
     // seed batch F_0: evaluate with t_exp and add to V
     FTRY(cudaMemcpyAsync(d_seqs, seeds, sizeof(comet_mode_seq) * n0, cudaMemcpyDefault, s), "copy seeds");
@@ -697,14 +698,15 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
         for (int i = 0; i < n_inst; ++i) h[i] = SlotSrc{fr[i]->d.next, fr[i]->d.n_next};
         FTRY(cudaMemcpyAsync(d_src, h.data(), sizeof(SlotSrc) * n_inst, cudaMemcpyHostToDevice, s), "slots");
     }
-    cudaEvent_t ev[4];
-    for (auto& e : ev) FTRY(cudaEventCreate(&e), "events");
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     struct EvGuard {
         cudaEvent_t* e;
         ~EvGuard() {
-            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 4; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
         }
     } evg{ev};
+    for (auto& e : ev) FTRY(cudaEventCreate(&e), "events");
     const float eps = (float)p->opts.eps_feas, mmu = (float)p->opts.merit_mu;
     FTRY(cudaEventRecord(ev[0], s), "event");
     // seed batches of every instance in one launch
