@@ -456,30 +456,35 @@ def grammar_times(P, n_inst=4):
     are stick on a face or free motion, orders of at most 8 segments
     (6,297 admissible).  Seed only (the 601 admissible orders of at most 6
     segments), expansion from that seed (beam 64, B = 1,024, r = 2, three
-    rounds) and full enumeration of all 6,297, each followed by the same
+    rounds), uniform sampling of as many admissible orders as the expansion
+    evaluated, and full enumeration of all 6,297, each followed by the same
     refinement (K_ref = 256 at t_ref = 1,500).  Device time per instance."""
     seeds = W.admissible_push_orders(6)
     every = W.admissible_push_orders(8)
     ps, pe = P.pack_mode_seqs(seeds), P.pack_mode_seqs(every)
     out = {"instances": n_inst, "seed_orders": len(seeds), "admissible_orders": len(every),
-           "expansion_ms": [], "seed_only_ms": [], "enumeration_ms": [], "expansion_evals": [],
-           "recovered": 0, "seed_only_recovered": 0, "feasible": 0}
+           "expansion_ms": [], "seed_only_ms": [], "uniform_ms": [], "enumeration_ms": [], "expansion_evals": [],
+           "recovered": 0, "seed_only_recovered": 0, "uniform_recovered": 0, "feasible": 0}
     for s in range(n_inst):
         prob = P.Problem([W.push_grammar_instance(s)])
         base = dict(k=64, batch=1024, k_ref=256, ref_iters=1500)
         ex = P.comet_plan(prob.handle, 0, ps, len(seeds), dict(base, rounds=3, radius=2, grammar=1))
         so = P.comet_plan(prob.handle, 0, ps, len(seeds), dict(base, rounds=0))
         en = P.comet_plan(prob.handle, 0, pe, len(every), dict(base, rounds=0))
+        pu = P.comet_sample_orders(prob.handle, 0, 1000 + s, 0, ex["evaluations"], P.GRAMMAR_PUSH)
+        un = P.comet_plan(prob.handle, 0, pu, len(pu), dict(base, rounds=0))
         out["expansion_ms"].append(ex["explore_ms"] + ex["refine_ms"])
         out["seed_only_ms"].append(so["explore_ms"] + so["refine_ms"])
+        out["uniform_ms"].append(un["explore_ms"] + un["refine_ms"])
         out["enumeration_ms"].append(en["explore_ms"] + en["refine_ms"])
         out["expansion_evals"].append(ex["evaluations"])
         tol = en["best_cost"] * (1 + 1e-3) + 1e-9
         out["recovered"] += int(ex["best_status"] == 0 and ex["best_cost"] <= tol)
         out["seed_only_recovered"] += int(so["best_status"] == 0 and so["best_cost"] <= tol)
+        out["uniform_recovered"] += int(un["best_status"] == 0 and un["best_cost"] <= tol)
         out["feasible"] += int(en["best_status"] == 0)
         prob.close()
-    for key in ("expansion_ms", "seed_only_ms", "enumeration_ms", "expansion_evals"):
+    for key in ("expansion_ms", "seed_only_ms", "uniform_ms", "enumeration_ms", "expansion_evals"):
         out[key] = float(np.median(out[key]))
     out["note"] = ("medians over instances; recovered = refined best within 1e-3 of the enumeration's; "
                    "free-motion orders converge more slowly in FP32 than in FP64: 77 % against 93 % "

@@ -362,6 +362,20 @@ comet_status comet_plan_batch(comet_problem* p, int32_t n_instances, const int32
                               const comet_mode_seq* seeds, const int64_t* seed_offsets, const comet_plan_opts* opts,
                               comet_plan_result* out);
 
+/* The uniform-sampling search policy (a comparison policy on the same
+ * evaluator): orders first .. first + n - 1 of a uniform sample of the
+ * instance's order space -- every order of 1..max_segments segments
+ * (COMET_GRAMMAR_NONE) or the admissible pushing orders (COMET_GRAMMAR_PUSH,
+ * n_modes = 13).  Order i is the order at index draw_i mod T of the
+ * (length, lexicographic) enumeration, T the number of orders and draw_i the
+ * i-th output of SplitMix64 (Steele, Lea and Flood 2014) from `seed`
+ * (state seed + (i + 1) * 0x9E3779B97F4A7C15).  Uniform sampling followed by
+ * refinement is comet_plan with the sample as seeds and rounds = 0.  out:
+ * host or device array of n records (host: synchronises).  Errors:
+ * INVALID_ARG. */
+comet_status comet_sample_orders(comet_problem* p, int32_t instance, uint64_t seed, int64_t first, int64_t n,
+                                 int32_t grammar, comet_mode_seq* out);
+
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 

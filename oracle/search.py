@@ -294,3 +294,82 @@ def expand_grammar(evaluated: dict, k: int, batch: int, l_max: int, r: int = 1, 
             if len(out) == batch:
                 return out
     return out
+
+
+# ------------------------------------------------- uniform sampling of orders
+#
+# The uniform-sampling search policy (a comparison policy on the same
+# evaluator): order i of a sample is drawn from a counter-based generator,
+# SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+# generators", 2014): state_i = seed + (i + 1) * 0x9E3779B97F4A7C15 (mod
+# 2^64), draw_i = mix(state_i).  The draw modulo the number T of orders picks
+# the order at that index of the (length, lexicographic) enumeration.
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, i: int) -> int:
+    z = (seed + (i + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def unrank_order(index: int, n_modes: int, l_max: int) -> tuple[int, ...]:
+    """Order number `index` among every order of 1..l_max segments over
+    n_modes modes, by length and then lexicographically."""
+    for L in range(1, l_max + 1):
+        cnt = n_modes ** L
+        if index < cnt:
+            digits = []
+            for _ in range(L):
+                digits.append(index % n_modes)
+                index //= n_modes
+            return tuple(reversed(digits))
+        index -= cnt
+    raise ValueError("index past the order space")
+
+
+def _ok(a: int, b: int, n_faces: int = 4) -> bool:
+    if a == b:
+        return False
+    if a == PUSH_FREE or b == PUSH_FREE:
+        return True
+    return (a // 3 - b // 3) % n_faces in (1, n_faces - 1)
+
+
+def unrank_admissible(index: int, cap: int, n_faces: int = 4) -> tuple[int, ...]:
+    """Admissible order number `index` in the order of admissible_orders(cap)
+    (by length, then lexicographically), built left to right from the
+    number of admissible completions after each candidate mode."""
+    alpha = push_alphabet(n_faces)
+    comp = [{m: 1 for m in alpha}]
+    for r in range(1, cap):
+        comp.append({m: sum(comp[r - 1][b] for b in alpha if _ok(m, b, n_faces)) for m in alpha})
+    for L in range(1, cap + 1):
+        cnt = comp[L - 1][PUSH_FREE]
+        if index < cnt:
+            seq = [PUSH_FREE]
+            for pos in range(1, L):
+                rem = L - 1 - pos
+                for b in alpha:
+                    if not _ok(seq[-1], b, n_faces):
+                        continue
+                    c = comp[rem][b]
+                    if index < c:
+                        seq.append(b)
+                        break
+                    index -= c
+            return tuple(seq)
+        index -= cnt
+    raise ValueError("index past the admissible orders")
+
+
+def sample_orders(seed: int, first: int, n: int, n_modes: int, l_max: int, grammar: int = 0) -> list:
+    """Orders first .. first + n - 1 of the uniform sample (grammar 0: every
+    order; 1: the admissible pushing orders)."""
+    if grammar == 1:
+        total = len(admissible_orders(l_max))
+        return [unrank_admissible(splitmix64(seed, i) % total, l_max) for i in range(first, first + n)]
+    total = sum(n_modes ** L for L in range(1, l_max + 1))
+    return [unrank_order(splitmix64(seed, i) % total, n_modes, l_max) for i in range(first, first + n)]

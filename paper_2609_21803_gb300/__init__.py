@@ -117,7 +117,7 @@ EXPORTS = (
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
     "comet_get_launch_config", "comet_set_launch_config", "comet_autotune", "comet_proposal_time_forward",
-    "comet_plan_batch", "comet_frontier_create_ex",
+    "comet_plan_batch", "comet_frontier_create_ex", "comet_sample_orders",
 )
 
 
@@ -150,6 +150,7 @@ def lib(build_if_missing: bool = False):
                                                    vp, i64, vp, vp, vp, vp]
             L.comet_frontier_create.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(vp)]
             L.comet_frontier_create_ex.argtypes = [vp, i32, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]
+            L.comet_sample_orders.argtypes = [vp, i32, ctypes.c_uint64, i64, i64, i32, vp]
             L.comet_frontier_destroy.argtypes = [vp]
             L.comet_frontier_add.argtypes = [vp, vp, i64, vp, vp]
             L.comet_expand.argtypes = [vp, vp, i32]
@@ -410,6 +411,14 @@ def comet_plan_batch(problem, instances, seeds_per_instance, opts=None) -> list:
         out.append({"best": tuple(int(r.best.modes[i]) for i in range(r.best.len)), "best_cost": r.best_cost,
                     "best_viol": r.best_viol, "best_status": r.best_status, "rounds_run": r.rounds_run,
                     "evaluations": r.evaluations, "explore_ms": r.explore_ms, "refine_ms": r.refine_ms})
+    return out
+
+
+def comet_sample_orders(problem, instance: int, seed: int, first: int, n: int, grammar: int = GRAMMAR_NONE):
+    """Orders first .. first + n - 1 of the uniform sample (comet_sample_orders),
+    as a host array of packed records."""
+    out = np.zeros(n, dtype=MODE_SEQ_DTYPE)
+    _check(lib().comet_sample_orders(problem, instance, seed, first, n, grammar, out.ctypes.data))
     return out
 
 

@@ -820,3 +820,130 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
     }
     return COMET_OK;
 }
+
+// ------------------------------------------------ uniform sampling of orders
+
+namespace {
+
+// what the sampler needs of an instance's order space
+struct SampleSpec {
+    int instance, n_modes, lmax, grammar;
+    unsigned long long total;             // number of orders
+    unsigned long long per_len[COMET_MAX_SEGMENTS];  // orders of each length 1..lmax
+    unsigned long long comp[COMET_MAX_SEGMENTS][5];  // grammar: completions after mode (alphabet index)
+};
+
+__device__ __forceinline__ unsigned long long splitmix_draw(unsigned long long seed, unsigned long long i) {
+    // SplitMix64 (Steele, Lea and Flood 2014): state seed + (i + 1) golden gamma
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int push_alpha(int a) { return a < 4 ? 3 * a : 12; }
+
+__device__ __forceinline__ bool push_ok(int a, int b) {
+    if (a == b) return false;
+    if (a == 12 || b == 12) return true;
+    const int d = (a / 3 - b / 3 + 4) & 3;
+    return d == 1 || d == 3;
+}
+
+// order number idx of the (length, lexicographic) enumeration
+__global__ void sample_kernel(SampleSpec sp, unsigned long long seed, int64_t first, int64_t n, comet_mode_seq* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long idx = splitmix_draw(seed, (unsigned long long)(first + i)) % sp.total;
+    comet_mode_seq q;
+    memset(&q, 0, sizeof(q));
+    q.instance = sp.instance;
+    int L = 1;
+    while (L < sp.lmax && idx >= sp.per_len[L - 1]) idx -= sp.per_len[L - 1], ++L;
+    q.len = (uint8_t)L;
+    if (sp.grammar == 0) {
+        for (int pos = L - 1; pos >= 0; --pos) {
+            q.modes[pos] = (uint16_t)(idx % (unsigned long long)sp.n_modes);
+            idx /= (unsigned long long)sp.n_modes;
+        }
+    } else {
+        int last = 12;  // orders start in free motion
+        q.modes[0] = 12;
+        for (int pos = 1; pos < L; ++pos) {
+            const int rem = L - 1 - pos;
+            for (int a = 0; a < 5; ++a) {
+                const int b = push_alpha(a);
+                if (!push_ok(last, b)) continue;
+                const unsigned long long c = sp.comp[rem][a];
+                if (idx < c) {
+                    q.modes[pos] = (uint16_t)b;
+                    last = b;
+                    break;
+                }
+                idx -= c;
+            }
+        }
+    }
+    out[i] = q;
+}
+
+}  // namespace
+
+extern "C" comet_status comet_sample_orders(comet_problem* p, int32_t instance, uint64_t seed, int64_t first,
+                                            int64_t n, int32_t grammar, comet_mode_seq* out) {
+    if (!p || !out || n < 0 || first < 0) return ffail(COMET_ERR_INVALID_ARG, "problem, out and n >= 0 are required");
+    if (instance < 0 || instance >= (int)p->inst.size()) return ffail(COMET_ERR_INVALID_ARG, "instance out of range");
+    const comet_instance_desc& d = p->inst[instance];
+    if (grammar != COMET_GRAMMAR_NONE && grammar != COMET_GRAMMAR_PUSH)
+        return ffail(COMET_ERR_INVALID_ARG, "unknown grammar");
+    if (grammar == COMET_GRAMMAR_PUSH && (d.task != COMET_TASK_PUSHER_SLIDER || d.n_modes != 13))
+        return ffail(COMET_ERR_INVALID_ARG, "the pushing grammar needs a pushing instance with n_modes = 13");
+    if (n == 0) return COMET_OK;
+    SampleSpec sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.instance = instance;
+    sp.n_modes = d.n_modes;
+    sp.lmax = d.max_segments;
+    sp.grammar = grammar;
+    // order counts per length (they fit in 64 bits: the mode codes do)
+    const int alpha[5] = {0, 3, 6, 9, 12};
+    auto ok = [](int a, int b) {
+        if (a == b) return false;
+        if (a == 12 || b == 12) return true;
+        const int dd = ((a / 3 - b / 3) % 4 + 4) % 4;
+        return dd == 1 || dd == 3;
+    };
+    if (grammar == COMET_GRAMMAR_PUSH) {
+        for (int a = 0; a < 5; ++a) sp.comp[0][a] = 1;
+        for (int r = 1; r < sp.lmax; ++r)
+            for (int a = 0; a < 5; ++a) {
+                unsigned long long c = 0;
+                for (int b = 0; b < 5; ++b)
+                    if (ok(alpha[a], alpha[b])) c += sp.comp[r - 1][b];
+                sp.comp[r][a] = c;
+            }
+        for (int L = 1; L <= sp.lmax; ++L) sp.per_len[L - 1] = sp.comp[L - 1][4];  // starting in free motion
+    } else {
+        unsigned long long c = 1;
+        for (int L = 1; L <= sp.lmax; ++L) {
+            c *= (unsigned long long)sp.n_modes;
+            sp.per_len[L - 1] = c;
+        }
+    }
+    for (int L = 1; L <= sp.lmax; ++L) sp.total += sp.per_len[L - 1];
+    cudaStream_t s = p->stream;
+    const bool dev = dev_ptr(out);
+    DevBuf buf;
+    comet_mode_seq* d_out = out;
+    if (!dev) {
+        FTRY(cudaMalloc(&buf.p, sizeof(comet_mode_seq) * n), "sample buffer");
+        d_out = (comet_mode_seq*)buf.p;
+    }
+    sample_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, seed, first, n, d_out);
+    FTRY(cudaGetLastError(), "sample kernel");
+    if (!dev) {
+        FTRY(cudaMemcpyAsync(out, d_out, sizeof(comet_mode_seq) * n, cudaMemcpyDeviceToHost, s), "copy samples");
+        FTRY(cudaStreamSynchronize(s), "synchronise");
+    }
+    return COMET_OK;
+}

@@ -181,3 +181,17 @@ def test_grammar_expansion_matches_oracle(P, r, batch):
         P.comet_frontier_create(prob12.handle, 0, 1000, 100, 8, radius=3)
     prob12.close()
     prob.close()
+
+
+@pytest.mark.parametrize("grammar", [0, 1])
+def test_uniform_sampler_matches_oracle(P, grammar):
+    # the uniform-sampling policy's orders, bit for bit: SplitMix64 draws and
+    # the unranking of the (length, lexicographic) enumeration
+    inst = W.push_grammar_instance(0) if grammar else W.push_l4_instance(0)
+    prob = P.Problem([inst])
+    for seed in (0, 7, 2 ** 63 + 5):
+        rec = P.comet_sample_orders(prob.handle, 0, seed, 100, 3000, grammar)
+        got = [tuple(int(m) for m in r["modes"][: r["len"]]) for r in rec]
+        assert all(int(r["instance"]) == 0 for r in rec)
+        assert got == S.sample_orders(seed, 100, 3000, inst["n_modes"], inst["max_segments"], grammar)
+    prob.close()

@@ -185,3 +185,29 @@ def test_workload_seed_orders_match_the_oracle_grammar():
     for cap in (1, 4, 6):
         assert W.admissible_push_orders(cap) == S.admissible_orders(cap)
     assert len(W.admissible_push_orders(8)) == 6297
+
+
+# ------------------------------------------------ uniform sampling of orders
+
+def test_splitmix64_published_outputs():
+    # the generator's first outputs from seed 0 (Steele, Lea and Flood 2014)
+    assert [S.splitmix64(0, i) for i in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_unranking_follows_the_enumerations():
+    pool = [s for L in range(1, 4) for s in itertools.product(range(5), repeat=L)]
+    assert [S.unrank_order(i, 5, 3) for i in range(len(pool))] == pool
+    A = S.admissible_orders(6)
+    assert [S.unrank_admissible(i, 6) for i in range(len(A))] == A
+
+
+def test_uniform_sample_frequencies():
+    # 12 orders (3 modes, up to 2 segments), 24,000 draws: every count within
+    # 5 standard deviations of 2,000
+    from collections import Counter
+    c = Counter(S.sample_orders(11, 0, 24000, 3, 2))
+    assert len(c) == 12
+    sd = (24000 * (1 / 12) * (11 / 12)) ** 0.5
+    assert all(abs(v - 2000) <= 5 * sd for v in c.values())
+    g = Counter(S.sample_orders(5, 0, 20000, 13, 4, grammar=1))
+    assert set(g) == set(S.admissible_orders(4)) and all(S.admissible_push(s) for s in g)
