@@ -317,6 +317,8 @@ struct DevBuf {
 
 }  // namespace
 
+static_assert(sizeof(comet_plan_opts) == 40, "comet_plan_opts layout (the binding mirrors it)");
+
 extern "C" comet_status comet_default_plan_opts(comet_plan_opts* po) {
     if (!po) return ffail(COMET_ERR_INVALID_ARG, "opts is NULL");
     memset(po, 0, sizeof(*po));

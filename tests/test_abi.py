@@ -46,10 +46,14 @@ def test_mode_code_matches_oracle_definition(lib):
     for s in [(0,), (11, 3), (4, 4, 7, 1), tuple(range(12)) + (0, 1, 2, 3)]:
         assert P.comet_mode_code(s) == S.encode(s, 12)
     assert P.comet_mode_code((12,)) == 0          # mode out of range
+    # the 13-mode pushing alphabet (free motion = 12)
+    for s in [(12,), (12, 0, 12, 9), (12, 3, 6, 12, 0)]:
+        assert P.comet_mode_code(s, 13) == S.encode(s, 13)
 
 
 def test_struct_layouts():
     import ctypes
     assert ctypes.sizeof(P.ModeSeq) == 40
+    assert ctypes.sizeof(P.PlanOpts) == 4 * 4 + 8 + 4 * 4
     assert ctypes.sizeof(P.InstanceDesc) == 4 * 4 + 8 * 16
     assert ctypes.sizeof(P.SolverOpts) == 2 * 4 + 10 * 8 + 2 * 4 + 8
