@@ -927,62 +927,78 @@ __device__ float bphase_d(BCtx& C, float beta, float D, const SolverParams& sp) 
     BSmem& S = C.S;
     const BInst<float>& P = C.P;
     const int N = C.N, Np1 = C.Np1;
-    const int a = C.tid & 7, grp = C.tid >> 3;  // 16 stage groups
-    const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
+    // Trials four at a time (thread = trial + 4 x stage group, 32 groups),
+    // largest alpha first: {1/8 .. 1/64} only when none of {1, 1/2, 1/4}
+    // passes, which leaves the accepted alpha (the largest passing) unchanged.
+    const int sub = C.tid & 3, grp = C.tid >> 2;
     const float inv2b = 0.5f / beta;
-    float phi = 0.f;
-    if (a <= sp.n_alpha) {
+    float phi0 = 0.f, slack = 0.f, acc = 0.f;
 #pragma unroll 1
-        for (int k = grp; k < N; k += 16) {
-            float x[NX], u[NU], dx[NX];
-            load_stage(C, k, alpha, x, u, dx);
-            const int mi = S.mi[k];
-            BStage<float> St;
-            stage_ctx(P, mi & 1023, x, u, St);
-            const float* lam = S.lam + 3 + NR * k;
-            for (int j = 0; j < NU; ++j) phi += rweight(P, j) * u[j] * u[j];
-            for (int r = 0; r < NR; ++r) {
-                float c, sc;
-                bool on, iq;
-                brow<float, false>(r, P, St, (mi >> 10) & 1, (mi >> 11) & 1, x, u, dx, c, nullptr, on, iq, sc);
-                if (on) phi += brow_al(iq, lam[r], beta, inv2b, c);
-            }
-            if (k == 0)
-                for (int i = 0; i < 3; ++i) {
-                    const float c = (S.xh[i * Np1] - P.start[i]) + (S.xl[i * Np1] + alpha * S.dz[i]);
-                    phi += brow_al(false, S.lam[i], beta, inv2b, c);
+    for (int batch = 0; batch < 2; ++batch) {
+        if (batch == 1 && sp.n_alpha < 4) break;
+        const int a = 4 * batch + sub;
+        const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
+        float phi = 0.f;
+        if (a <= sp.n_alpha) {
+#pragma unroll 1
+            for (int k = grp; k < N; k += 32) {
+                float x[NX], u[NU], dx[NX];
+                load_stage(C, k, alpha, x, u, dx);
+                const int mi = S.mi[k];
+                BStage<float> St;
+                stage_ctx(P, mi & 1023, x, u, St);
+                const float* lam = S.lam + 3 + NR * k;
+                for (int j = 0; j < NU; ++j) phi += rweight(P, j) * u[j] * u[j];
+                for (int r = 0; r < NR; ++r) {
+                    float c, sc;
+                    bool on, iq;
+                    brow<float, false>(r, P, St, (mi >> 10) & 1, (mi >> 11) & 1, x, u, dx, c, nullptr, on, iq, sc);
+                    if (on) phi += brow_al(iq, lam[r], beta, inv2b, c);
                 }
-            if (k == N - 1)
-                for (int i = 0; i < 3; ++i) {
-                    const float e = (S.xh[i * Np1 + N] - P.goal[i]) + (S.xl[i * Np1 + N] + alpha * S.dz[NWV * N + i]);
-                    phi += P.wT * e * e;
-                }
-        }
-    }
-    // lanes with the same alpha: xor 8, 16 inside the warp, then the warps
-    phi += __shfl_xor_sync(kFullB, phi, 8);
-    phi += __shfl_xor_sync(kFullB, phi, 16);
-    if (C.lane < 8) S.red[32 + C.warp * 8 + C.lane] = phi;
-    __syncthreads();
-    if (C.tid == 0) {
-        float ph[8];
-        for (int q = 0; q < 8; ++q) ph[q] = S.red[32 + q] + S.red[40 + q] + S.red[48 + q] + S.red[56 + q];
-        const float phi0 = ph[0];
-        const float slack = sp.ls_slack * fabsf(phi0);
-        const bool flat = fabsf(D) <= slack;
-        float acc = 0.f;
-        for (int q = 1; q <= sp.n_alpha && q < 8; ++q) {
-            const float al = ldexpf(1.f, -(q - 1));
-            if (ph[q] <= phi0 + sp.armijo_c1 * al * D || (q == 1 && flat && ph[1] <= phi0 + slack)) {
-                acc = al;
-                break;
+                if (k == 0)
+                    for (int i = 0; i < 3; ++i) {
+                        const float c = (S.xh[i * Np1] - P.start[i]) + (S.xl[i * Np1] + alpha * S.dz[i]);
+                        phi += brow_al(false, S.lam[i], beta, inv2b, c);
+                    }
+                if (k == N - 1)
+                    for (int i = 0; i < 3; ++i) {
+                        const float e =
+                            (S.xh[i * Np1 + N] - P.goal[i]) + (S.xl[i * Np1 + N] + alpha * S.dz[NWV * N + i]);
+                        phi += P.wT * e * e;
+                    }
             }
         }
-        S.red[30] = acc;
+        // threads with the same trial: xor 4, 8, 16 inside the warp, then the warps
+        phi += __shfl_xor_sync(kFullB, phi, 4);
+        phi += __shfl_xor_sync(kFullB, phi, 8);
+        phi += __shfl_xor_sync(kFullB, phi, 16);
+        if (C.lane < 4) S.red[32 + C.warp * 4 + C.lane] = phi;
+        __syncthreads();
+        if (C.tid == 0) {
+            float ph[4];
+            for (int q = 0; q < 4; ++q) ph[q] = S.red[32 + q] + S.red[36 + q] + S.red[40 + q] + S.red[44 + q];
+            if (batch == 0) {
+                phi0 = ph[0];
+                slack = sp.ls_slack * fabsf(phi0);
+            }
+            const bool flat = fabsf(D) <= slack;
+            float take = 0.f;
+            for (int q = (batch == 0) ? 1 : 0; q < 4; ++q) {
+                const int aq = 4 * batch + q;
+                if (aq > sp.n_alpha) break;
+                const float al = ldexpf(1.f, -(aq - 1));
+                if (ph[q] <= phi0 + sp.armijo_c1 * al * D || (aq == 1 && flat && ph[q] <= phi0 + slack)) {
+                    take = al;
+                    break;
+                }
+            }
+            S.red[30] = take;
+        }
+        __syncthreads();
+        acc = S.red[30];
+        __syncthreads();
+        if (acc > 0.f) break;
     }
-    __syncthreads();
-    const float acc = S.red[30];
-    __syncthreads();
     return acc;
 }
 
