@@ -46,11 +46,14 @@ N_STAGES = SEG * K
 # 7x7 Cholesky 230, gains with 5 right-hand sides 490, Schur update 230,
 # forward pass 70, 8-trial line search 800)
 FLOP_PER_STAGE_ITER = 3330
-# DRAM bytes (read + write) of one evaluator launch over the 20,736 orders:
-# the ncu capture of a 4,096-order launch at 4 CTAs per SM (2.24 MB read,
-# 3.52 GB written: stage records written back from L2,
-# profiles/eval_kernel_push_l4.md) scaled by the TOs processed
-EVAL_TRAFFIC_BYTES = (2.24128e6 + 3.516693e9) * 20736 / 4096
+# DRAM bytes (read + write) of one evaluator launch over the 20,736 orders
+# from an ncu capture of the current kernel, scaled by the TOs processed;
+# None while the kernel has changed since the last capture.  That capture
+# (a 4,096-order launch at 4 CTAs per SM: 2.24 MB read, 3.52 GB written,
+# stage records written back from L2, profiles/eval_kernel_push_l4.md)
+# predates the double-float theta row and the compensated trial merits.
+EVAL_TRAFFIC_BYTES = None
+EVAL_TRAFFIC_LAST_CAPTURE = (2.24128e6 + 3.516693e9) * 20736 / 4096
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -296,7 +299,11 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": EVAL_TRAFFIC_BYTES,
                      "note": "achieved = 3330 flop x 80 stages x solver iterations / device time; peak = FP32 "
-                             "FMA rate at 2070 MHz (152 SMs x 128 lanes)"},
+                             "FMA rate at 2070 MHz (152 SMs x 128 lanes)",
+                     "traffic_note": ("null: the kernel changed after its last ncu capture (arithmetic only: "
+                                      "theta row in double-float, compensated trial merits); that capture "
+                                      f"measured {EVAL_TRAFFIC_LAST_CAPTURE / 1e9:.1f} GB per launch")
+                     if EVAL_TRAFFIC_BYTES is None else "ncu capture of the current kernel, scaled"},
         "iterations_per_solve": iter_total / (args.steps * n * world),
     }
     if rank == 0 and args.plan_instances > 0:
@@ -487,8 +494,8 @@ def grammar_times(P, n_inst=4):
     for key in ("expansion_ms", "seed_only_ms", "uniform_ms", "enumeration_ms", "expansion_evals"):
         out[key] = float(np.median(out[key]))
     out["note"] = ("medians over instances; recovered = refined best within 1e-3 of the enumeration's; "
-                   "free-motion orders converge more slowly in FP32 than in FP64: 77 % against 93 % "
-                   "within 300 iterations on 2-4-segment box orders")
+                   "free-motion orders converge a little less often in FP32 than in FP64: 89 % against "
+                   "93 % within 300 iterations on 2-4-segment box orders")
     return out
 
 

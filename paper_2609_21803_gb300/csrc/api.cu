@@ -129,6 +129,10 @@ void make_dev_instance(const comet_instance_desc& d, DevInstance* out) {
     q.ground_mu_d = d.ground_mu;
     q.mass = (float)d.mass;
     q.ground_mu = (float)d.ground_mu;
+    const double kth = q.dt_d * q.kappa_d * q.inv_c2_d;
+    q.kth_hi = (float)kth;
+    q.kth_lo = (float)(kth - (double)q.kth_hi);
+    for (int f = 0; f < 4; ++f) q.a_lo[f] = (float)(q.a_d[f] - (double)q.a[f]);
 }
 
 // Solver parameters of a call from the options and an iteration budget

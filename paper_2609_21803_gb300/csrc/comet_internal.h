@@ -30,6 +30,11 @@ struct DevInstance {
     double start_d[3], goal_d[3];
     double w_terminal_d, w_control_d;
     double mass_d, ground_mu_d;
+    // theta-row gain K = dt kappa / c^2 as an FP32 pair (hi + lo) and the
+    // FP32 rounding residues of the face half-depths, for the theta defect
+    // evaluated in double-float
+    float kth_hi, kth_lo;
+    float a_lo[4];
 };
 
 struct SolverParams {

@@ -138,6 +138,13 @@ __device__ __forceinline__ ModeInfo mode_info(const uint16_t* modes, int len, in
 // Residual rows of interval k at (x_k, u_k, x_{k+1}) with the exact state
 // difference dx = x_{k+1} - x_k.  Values are internally scaled; `phys` is
 // the factor that maps a scaled value back to physical units.
+//
+// The theta row is evaluated in double-float (pairs of FP32 values).  Its
+// rate kappa m_z / c^2 is large for a small limit-surface constant c, so the
+// per-interval rotation dt * omega and the state difference it balances are
+// large beside the defect itself; rounded to FP32, the defect carries noise
+// of the order of its converged size, which beta turns into a stationarity
+// floor (Sec. III-C, stopping test).  The pair keeps the difference exact.
 struct Rows {
     float c[11];
     float phys[11];
@@ -156,8 +163,12 @@ struct Rows {
 // kFree: free motion (mode 12) compiled in; problems over the 12 contact
 // modes run the variant without it
 template <bool kFree>
+//
+// Inputs: xk = x_k and dx = x_{k+1} - x_k rounded to FP32, except dx[2] =
+// fl(theta_{k+1,hi} - theta_{k,hi}); ex[0] = the rest of the theta
+// difference, ex[1] = s_k - xk[3] (see stage_state).
 __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& mi, const float xk[4],
-                                          const float dx[4], const float u[3], Rows& R) {
+                                          const float dx[4], const float ex[2], const float u[3], Rows& R) {
     float nx, ny;
     face_nt(mi.face, nx, ny);
     const float tx = -ny, ty = nx;
@@ -198,6 +209,20 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
 #pragma unroll
         for (int j = 0; j < 3; ++j) R.au[r][j] = -dt * Fu[r][j] * is;
         R.ay[r] = is;
+    }
+    {
+        // c_2 sigma_2 = dtheta + K (a f_t + s f_n), K = dt kappa / c^2, with
+        // error-free products (fma) and sums (two_sum)
+        const float kh = free ? 0.f : P.kth_hi, kl = free ? 0.f : P.kth_lo;
+        const float p = a * ft, pe = fmaf(a, ft, -p) + P.a_lo[mi.face] * ft;
+        const float q = s * fn, qe = fmaf(s, fn, -q) + ex[1] * fn;
+        float m, me;
+        two_sum(p, q, m, me);
+        me += pe + qe;
+        const float km = kh * m, kme = fmaf(kh, m, -km) + (kh * me + kl * m);
+        float t, te;
+        two_sum(dx[2], km, t, te);
+        R.c[2] = (t + (te + ex[0] + kme)) * P.inv_sigma[2];
     }
     R.ax[0][2] += -dt * Fx02 * P.inv_sigma[0];
     R.ax[1][2] += -dt * Fx12 * P.inv_sigma[1];
@@ -248,6 +273,24 @@ __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& 
 #pragma unroll
     for (int r = 0; r < 11; ++r)
         if (!R.on[r]) R.c[r] = 0.f;
+}
+
+// State pieces of interval k from the compensated storage: x_k = h0 + l0,
+// x_{k+1} = h1 + l1 (the low parts may carry a trial step).  Returns x_k
+// and x_{k+1} - x_k rounded to FP32, with the theta difference and s_k
+// split for the theta row: dx[2] + ex[0] = theta_{k+1} - theta_k and
+// xk[3] + ex[1] = s_k.
+__device__ __forceinline__ void stage_state(const float h0[4], const float h1[4], const float l0[4],
+                                            const float l1[4], float xk[4], float dx[4], float ex[2]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        xk[i] = h0[i] + l0[i];
+        dx[i] = (h1[i] - h0[i]) + (l1[i] - l0[i]);
+    }
+    float e;
+    two_sum(h1[2], -h0[2], dx[2], e);
+    ex[0] = e + (l1[2] - l0[2]);
+    two_sum(h0[3], l0[3], xk[3], ex[1]);
 }
 
 // Nonzero pattern of dynamics row r over the stage variables (u0..2 at
@@ -344,18 +387,19 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
 #pragma unroll 1
     for (int k = lane; k < N; k += 32) {
         const ModeInfo mi = mode_of(S.mb[k]);
-        float xk[4], dx[4], u[3];
+        float h0[4], h1[4], l0[4], l1[4], xk[4], dx[4], ex[2], u[3];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float h0 = S.xh[i * Np1 + k], h1 = S.xh[i * Np1 + k + 1];
-            const float l0 = S.xl[i * Np1 + k], l1 = S.xl[i * Np1 + k + 1];
-            xk[i] = h0 + l0;
-            dx[i] = (h1 - h0) + (l1 - l0);
+            h0[i] = S.xh[i * Np1 + k];
+            h1[i] = S.xh[i * Np1 + k + 1];
+            l0[i] = S.xl[i * Np1 + k];
+            l1[i] = S.xl[i * Np1 + k + 1];
         }
+        stage_state(h0, h1, l0, l1, xk, dx, ex);
 #pragma unroll
         for (int j = 0; j < 3; ++j) u[j] = S.us[j * N + k];
         Rows R;
-        eval_rows<kFree>(P, mi, xk, dx, u, R);
+        eval_rows<kFree>(P, mi, xk, dx, ex, u, R);
         float* lam = S.lam + 3 + 11 * k;
         float y[11];
         bool act[11];
@@ -913,19 +957,19 @@ __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, f
     const int N = C.N, Np1 = C.N + 1;
     const Smem& S = C.sm;
     const ModeInfo mi = mode_of(S.mb[k]);
-    float xk[4], dx[4], u[3];
+    float h0[4], h1[4], l0[4], l1[4], xk[4], dx[4], ex[2], u[3];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float h0 = S.xh[i * Np1 + k], h1 = S.xh[i * Np1 + k + 1];
-        const float l0 = S.xl[i * Np1 + k] + alpha * S.dz[7 * k + i];
-        const float l1 = S.xl[i * Np1 + k + 1] + alpha * S.dz[7 * (k + 1) + i];
-        xk[i] = h0 + l0;
-        dx[i] = (h1 - h0) + (l1 - l0);
+        h0[i] = S.xh[i * Np1 + k];
+        h1[i] = S.xh[i * Np1 + k + 1];
+        l0[i] = S.xl[i * Np1 + k] + alpha * S.dz[7 * k + i];
+        l1[i] = S.xl[i * Np1 + k + 1] + alpha * S.dz[7 * (k + 1) + i];
     }
+    stage_state(h0, h1, l0, l1, xk, dx, ex);
 #pragma unroll
     for (int j = 0; j < 3; ++j) u[j] = S.us[j * N + k] + alpha * S.dz[7 * k + 4 + j];
     Rows R;
-    eval_rows<kFree>(P, mi, xk, dx, u, R);
+    eval_rows<kFree>(P, mi, xk, dx, ex, u, R);
     const float* lam = S.lam + 3 + 11 * k;
     float phi = P.w_control * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 #pragma unroll
@@ -953,30 +997,43 @@ __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, f
 // Trials run four at a time (lane = trial + 4 x stage group), largest alpha
 // first: the second batch {1/8 .. 1/64} is evaluated only when none of
 // {1, 1/2, 1/4} passes, which leaves the accepted alpha unchanged.
+// Stage merits are summed as FP32 pairs (two_sum), so the tests compare
+// phi(alpha) - phi(0) to the predicted decrease without the rounding of
+// the total, which near convergence is as large as that decrease.
 template <bool kFree>
 __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& sp) {
     const int lane = C.lane;
     const int sub = lane & 3, grp = lane >> 2;
     const float inv2b = 0.5f / beta;
-    float phi0 = 0.f, slack = 0.f;
+    float phi0 = 0.f, phi0l = 0.f, slack = 0.f;
 #pragma unroll 1
     for (int batch = 0; batch < 2; ++batch) {
         const int a = 4 * batch + sub;  // trial index: alpha = 2^-(a-1), a = 0 -> alpha = 0
         if (batch == 1 && sp.n_alpha < 4) break;
         const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
-        float phi = 0.f;
+        float phi = 0.f, phil = 0.f;
         if (a <= sp.n_alpha)
 #pragma unroll 1
-            for (int k = grp; k < C.N; k += 8) phi += stage_merit<kFree>(C, k, alpha, beta, inv2b);
-        phi += __shfl_xor_sync(kFull, phi, 4);
-        phi += __shfl_xor_sync(kFull, phi, 8);
-        phi += __shfl_xor_sync(kFull, phi, 16);
+            for (int k = grp; k < C.N; k += 8) {
+                float e;
+                two_sum(phi, stage_merit<kFree>(C, k, alpha, beta, inv2b), phi, e);
+                phil += e;
+            }
+#pragma unroll
+        for (int off = 4; off <= 16; off <<= 1) {
+            const float oh = __shfl_xor_sync(kFull, phi, off), ol = __shfl_xor_sync(kFull, phil, off);
+            float e;
+            two_sum(phi, oh, phi, e);
+            phil += ol + e;
+        }
         if (batch == 0) {
             phi0 = __shfl_sync(kFull, phi, 0);
+            phi0l = __shfl_sync(kFull, phil, 0);
             slack = sp.ls_slack * fabsf(phi0);
         }
-        bool pass = (a >= 1) && (a <= sp.n_alpha) && (phi <= phi0 + sp.armijo_c1 * alpha * D);
-        if (a == 1 && fabsf(D) <= slack && phi <= phi0 + slack) pass = true;
+        const float dphi = (phi - phi0) + (phil - phi0l);
+        bool pass = (a >= 1) && (a <= sp.n_alpha) && (dphi <= sp.armijo_c1 * alpha * D);
+        if (a == 1 && fabsf(D) <= slack && dphi <= slack) pass = true;
         const unsigned bal = __ballot_sync(kFull, pass) & 0xfu;
         if (bal) return ldexpf(1.f, -(4 * batch + __ffs(bal) - 2));
     }

@@ -414,11 +414,12 @@ def test_free_motion_closed_form_and_grammar_parity(P):
         b = t1[t][: 7 * N + 4]
         ok.append(np.max(np.abs(a - b)) <= 1e-3 * max(1.0, np.max(np.abs(b))))
     assert np.mean(ok) >= 0.99
-    # full solves.  Orders with free motion converge more slowly in FP32 than
-    # in FP64 (measured at the 300-iteration budget: 77 % against the
-    # oracle's 93 %, the same orders without free segments 98 % against
-    # 97 %): where both converge they reach the same solutions, and with a
-    # 1,500-iteration budget the GPU converges as often as the oracle at 300
+    # full solves.  Orders with free motion converge a little less often in
+    # FP32 than in FP64 (measured at the 300-iteration budget: 89 % against
+    # the oracle's 93 %; 77 % before the theta row was evaluated in
+    # double-float): where both converge they reach the same solutions, and
+    # with a 1,500-iteration budget the GPU converges as often as the oracle
+    # at 300
     g = gpu_eval(P, insts, seqs, idx, want_traj=True)
     ref, _ = oracle.solve_batch(insts, idx, modes, lens)
     cg, co, both, rel, same = compare(g, ref)
@@ -426,7 +427,7 @@ def test_free_motion_closed_form_and_grammar_parity(P):
     cl = g_long["status"] == 0
     print(f"grammar orders: converged gpu {cg.mean():.3f} (1,500 iterations {cl.mean():.3f}) "
           f"oracle {co.mean():.3f}; same {same.sum()}/{both.sum()}")
-    assert cg.mean() >= co.mean() - 0.2
+    assert cg.mean() >= co.mean() - 0.1
     assert abs(cl.mean() - co.mean()) <= 0.08
     assert same.sum() >= 0.9 * both.sum()
     for t in np.flatnonzero(cg & (g["viol"] <= 1e-5))[::4]:
