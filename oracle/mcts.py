@@ -200,7 +200,11 @@ class Mcts:
 
     def best_orders(self, k: int) -> list[int]:
         """Codes of the k evaluated orders of least (M_hat, code)."""
-        keys = sorted((merit(c, v, self.eps, self.mu), code) for code, (c, v) in self.results.items())
+        keys = []
+        for code, (c, v) in self.results.items():
+            m = merit(c, v, self.eps, self.mu)
+            keys.append((m if m == m else math.inf, code))  # a non-finite result ranks last
+        keys.sort()
         return [code for _, code in keys[:k]]
 
 

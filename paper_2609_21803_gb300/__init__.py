@@ -98,6 +98,20 @@ class GemmEpilogue(ctypes.Structure):
 
 GEMM_STORE, GEMM_BIAS_GELU, GEMM_GELU_GRAD, GEMM_ATOMIC_ADD = 0, 1, 2, 3
 
+
+class MctsOpts(ctypes.Structure):
+    _fields_ = [("n_modes", ctypes.c_int32), ("l_max", ctypes.c_int32), ("grammar", ctypes.c_int32),
+                ("reward", ctypes.c_int32), ("max_evals", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("c_uct", ctypes.c_double), ("eps_feas", ctypes.c_double), ("merit_mu", ctypes.c_double)]
+
+
+class MctsStats(ctypes.Structure):
+    _fields_ = [("evaluations", ctypes.c_int64), ("tree_nodes", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("exhausted", ctypes.c_int32), ("reserved", ctypes.c_int32), ("best", ctypes.c_double)]
+
+
+MCTS_REWARD_FEASIBLE, MCTS_REWARD_MERIT = 0, 1
+
 MODE_SEQ_DTYPE = np.dtype([("instance", "<i4"), ("len", "u1"), ("pad", "u1", (3,)), ("modes", "<u2", (MAX_SEGMENTS,))])
 MODE_SEQ_BYTES = 40
 assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == MODE_SEQ_BYTES
@@ -118,6 +132,9 @@ EXPORTS = (
     "comet_gemm_bf16", "comet_plan_learned",
     "comet_get_launch_config", "comet_set_launch_config", "comet_autotune", "comet_proposal_time_forward",
     "comet_plan_batch", "comet_frontier_create_ex", "comet_sample_orders",
+    # include/comet_mcts.h
+    "comet_mcts_default_opts", "comet_mcts_create", "comet_mcts_destroy", "comet_mcts_ask", "comet_mcts_tell",
+    "comet_mcts_get_stats", "comet_mcts_best", "comet_plan_mcts",
 )
 
 
@@ -192,6 +209,15 @@ def lib(build_if_missing: bool = False):
             L.comet_plan_learned.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), vp,
                                              ctypes.POINTER(PlanResult), vp]
             L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
+            L.comet_mcts_default_opts.argtypes = [ctypes.POINTER(MctsOpts)]
+            L.comet_mcts_create.argtypes = [ctypes.POINTER(MctsOpts), ctypes.POINTER(vp)]
+            L.comet_mcts_destroy.argtypes = [vp]
+            L.comet_mcts_ask.argtypes = [vp, i32, i64, vp, ctypes.POINTER(i64)]
+            L.comet_mcts_tell.argtypes = [vp, vp, vp, i64]
+            L.comet_mcts_get_stats.argtypes = [vp, ctypes.POINTER(MctsStats)]
+            L.comet_mcts_best.argtypes = [vp, i64, vp, vp, ctypes.POINTER(i64)]
+            L.comet_plan_mcts.argtypes = [vp, i32, ctypes.POINTER(MctsOpts), i64, ctypes.POINTER(PlanOpts),
+                                          ctypes.POINTER(PlanResult), vp]
             for name in EXPORTS:
                 if name not in ("comet_traj_stride", "comet_mode_code", "comet_last_error",
                                 "comet_default_proposal_desc", "comet_default_adamw_opts"):
@@ -420,6 +446,78 @@ def comet_sample_orders(problem, instance: int, seed: int, first: int, n: int, g
     out = np.zeros(n, dtype=MODE_SEQ_DTYPE)
     _check(lib().comet_sample_orders(problem, instance, seed, first, n, grammar, out.ctypes.data))
     return out
+
+
+def comet_mcts_default_opts(**over) -> MctsOpts:
+    o = MctsOpts()
+    _check(lib().comet_mcts_default_opts(ctypes.byref(o)))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+class Mcts:
+    """The host tree search of include/comet_mcts.h (ask / tell)."""
+
+    def __init__(self, **opts):
+        self.opts = comet_mcts_default_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().comet_mcts_create(ctypes.byref(self.opts), ctypes.byref(h)))
+        self.handle = h
+
+    def ask(self, pool: int, instance: int = 0):
+        """The next pool as a host array of packed records."""
+        out = np.zeros(pool, dtype=MODE_SEQ_DTYPE)
+        n = ctypes.c_int64()
+        _check(lib().comet_mcts_ask(self.handle, instance, pool, out.ctypes.data, ctypes.byref(n)))
+        return out[: n.value]
+
+    def tell(self, cost, viol):
+        c = np.ascontiguousarray(cost, dtype=np.float32)
+        v = np.ascontiguousarray(viol, dtype=np.float32)
+        _check(lib().comet_mcts_tell(self.handle, c.ctypes.data, v.ctypes.data, len(c)))
+
+    def stats(self) -> dict:
+        st = MctsStats()
+        _check(lib().comet_mcts_get_stats(self.handle, ctypes.byref(st)))
+        return {"evaluations": st.evaluations, "tree_nodes": st.tree_nodes, "pending": st.pending,
+                "exhausted": bool(st.exhausted), "best": st.best}
+
+    def best(self, k: int):
+        codes = np.zeros(max(k, 1), np.uint64)
+        merits = np.zeros(max(k, 1), np.float64)
+        n = ctypes.c_int64()
+        _check(lib().comet_mcts_best(self.handle, k, codes.ctypes.data, merits.ctypes.data, ctypes.byref(n)))
+        return codes[: n.value], merits[: n.value]
+
+    def close(self):
+        if self.handle:
+            lib().comet_mcts_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def comet_plan_mcts(problem, instance: int, mcts_opts=None, pool: int = 1024, opts=None, out_traj=None) -> dict:
+    """MCTS plan for one instance (comet_plan_mcts); mcts_opts: MctsOpts,
+    dict or None; opts: PlanOpts, dict or None (k_ref, ref_iters)."""
+    if mcts_opts is None or isinstance(mcts_opts, dict):
+        mcts_opts = comet_mcts_default_opts(**(mcts_opts or {}))
+    if opts is None or isinstance(opts, dict):
+        o = comet_default_plan_opts()
+        for k, v in (opts or {}).items():
+            setattr(o, k, v)
+        opts = o
+    r = PlanResult()
+    _check(lib().comet_plan_mcts(problem, int(instance), ctypes.byref(mcts_opts), int(pool), ctypes.byref(opts),
+                                 ctypes.byref(r), _ptr(out_traj)))
+    return {"best": tuple(int(r.best.modes[i]) for i in range(r.best.len)), "best_cost": r.best_cost,
+            "best_viol": r.best_viol, "best_status": r.best_status, "rounds_run": r.rounds_run,
+            "evaluations": r.evaluations, "explore_ms": r.explore_ms, "refine_ms": r.refine_ms}
 
 
 def decode_code(code: int, n_modes: int = 12):

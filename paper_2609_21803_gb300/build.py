@@ -29,8 +29,10 @@ def nvcc() -> str:
 
 
 def _flags() -> list[str]:
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                   "-I", CSRC]
+    # host code: no floating-point contraction, so that host arithmetic (the
+    # tree search's UCT scores and rewards) is plain IEEE double everywhere
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
