@@ -318,6 +318,11 @@ def run_gpu(args):
         line["bimanual"] = bimanual_times(P, per=args.bim_per)
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
+    if rank == 0 and args.mcts:
+        try:
+            line["mcts"] = mcts_times(P)
+        except Exception as e:  # a failing comparison leg must not cost the line its other figures
+            line["mcts"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     if rank == 0 and not args.no_cpu_baseline:
         conv_rate, rate, ns, cores, dt = oracle_rate(insts)
         line["cpu_baseline"] = {"value": conv_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -456,6 +461,48 @@ def batch_plan_times(P, n_inst=256, n_seq=16):
         "subset_speedup": t_one / t_sub, "subset_same_plans": same,
         "note": "device time (exploration + refinement); one-by-one = the single-instance planner per instance",
     }
+
+
+def mcts_times(P, n_inst=4, pools=(1024, 256, 64)):
+    """The MCTS comparison policy (Sec. IV-A) on the grammar leg's box
+    instances: UCT (c = 0.8) with virtual loss and random rollouts, pools of
+    P orders per evaluator launch, capped at the evaluation count of the
+    expansion (beam 64, B = 1,024, r = 2, three rounds) on the same instance,
+    then the same refinement (K_ref = 256 at t_ref = 1,500).  MCTS times are
+    wall time of the search (host tree + GPU pools) plus device time of the
+    refinement; expansion times are device time."""
+    seeds = W.admissible_push_orders(6)
+    every = W.admissible_push_orders(8)
+    ps, pe = P.pack_mode_seqs(seeds), P.pack_mode_seqs(every)
+    base = dict(k=64, batch=1024, k_ref=256, ref_iters=1500)
+    res = {q: {"ms": [], "evals": [], "pools": [], "recovered": 0, "feasible": 0} for q in pools}
+    ex_ms, ex_rec = [], 0
+    for s in range(n_inst):
+        prob = P.Problem([W.push_grammar_instance(s)])
+        ex = P.comet_plan(prob.handle, 0, ps, len(seeds), dict(base, rounds=3, radius=2, grammar=1))
+        en = P.comet_plan(prob.handle, 0, pe, len(every), dict(base, rounds=0))
+        tol = en["best_cost"] * (1 + 1e-3) + 1e-9
+        ex_ms.append(ex["explore_ms"] + ex["refine_ms"])
+        ex_rec += int(ex["best_status"] == 0 and ex["best_cost"] <= tol)
+        for q in pools:
+            mc = P.comet_plan_mcts(prob.handle, 0, dict(grammar=P.GRAMMAR_PUSH, seed=3000 + s,
+                                                        max_evals=ex["evaluations"]), q, base)
+            r = res[q]
+            r["ms"].append(mc["explore_ms"] + mc["refine_ms"])
+            r["evals"].append(mc["evaluations"])
+            r["pools"].append(mc["rounds_run"])
+            r["recovered"] += int(mc["best_status"] == 0 and mc["best_cost"] <= tol)
+            r["feasible"] += int(mc["best_status"] == 0)
+        prob.close()
+    out = {"instances": n_inst, "expansion_ms": float(np.median(ex_ms)), "expansion_recovered": ex_rec}
+    for q in pools:
+        r = res[q]
+        out[f"pool_{q}"] = {"ms": float(np.median(r["ms"])), "evaluations": float(np.median(r["evals"])),
+                            "pools": float(np.median(r["pools"])), "recovered": r["recovered"],
+                            "feasible": r["feasible"]}
+    out["note"] = ("medians over instances; recovered = refined best within 1e-3 of full enumeration's; "
+                   "MCTS capped at the expansion's evaluation count on each instance")
+    return out
 
 
 def grammar_times(P, n_inst=4):
@@ -652,6 +699,7 @@ def main():
     ap.add_argument("--grammar", type=int, default=1, help="pushing-grammar planning leg (1) or skip it (0)")
     ap.add_argument("--bim-per", type=int, default=512, help="random orders per instance in the bimanual leg")
     ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
+    ap.add_argument("--mcts", type=int, default=1, help="MCTS comparison leg (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=8,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()
