@@ -4,7 +4,7 @@
  * hands and a ground contact.  TEST INFRASTRUCTURE ONLY (see
  * comet_oracle.h); it shares no code with the CUDA library.
  *
- * The paper's bimanual task (Sec. V, Experiment 2) uses an L-shaped block
+ * The paper's bimanual task (Sec. IV-B, Experiment 2) uses an L-shaped block
  * whose geometry is not given; this is the simplified box model of the
  * hot-path scope, in the shared masked row layout of Sec. III-C:
  *
