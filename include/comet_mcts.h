@@ -87,7 +87,9 @@ typedef struct {
     double c_uct;      /* exploration constant c (0.8) */
     double eps_feas;   /* feasibility threshold on v_hat (1e-5) */
     double merit_mu;   /* mu of Eq. search_merit (100) */
-} comet_mcts_opts;     /* 56 bytes */
+    double max_ms;     /* comet_plan_mcts only: no further pool is asked for once the search has run this
+                          long (wall time, milliseconds; the pool in flight completes); 0 = no time cap */
+} comet_mcts_opts;     /* 64 bytes */
 
 typedef struct {
     int64_t evaluations; /* orders told so far */
@@ -99,13 +101,14 @@ typedef struct {
 } comet_mcts_stats;      /* 40 bytes */
 
 /* Defaults: n_modes 12, l_max 4, no grammar, feasibility reward, no budget,
- * seed 0, c = 0.8, eps_feas 1e-5, mu 100. */
+ * seed 0, c = 0.8, eps_feas 1e-5, mu 100, no time cap. */
 comet_status comet_mcts_default_opts(comet_mcts_opts* o);
 
 /* A search over the orders of 1..l_max segments.  Host memory only; no GPU
- * call.  Errors: INVALID_ARG (n_modes < 1, l_max outside 1..16, the code
- * overflow above, grammar PUSH with n_modes != 13, an unknown reward kind,
- * c_uct < 0 or not finite, max_evals < 0), OOM. */
+ * call.  Errors: INVALID_ARG (n_modes outside 1..65535, l_max outside
+ * 1..16, the code overflow above, grammar PUSH with n_modes != 13, an
+ * unknown reward kind, c_uct < 0 or not finite, max_evals < 0, max_ms < 0
+ * or not finite), OOM. */
 comet_status comet_mcts_create(const comet_mcts_opts* o, comet_mcts** out);
 comet_status comet_mcts_destroy(comet_mcts* t);
 
@@ -129,7 +132,7 @@ comet_status comet_mcts_best(const comet_mcts* t, int64_t k, uint64_t* codes, do
 
 /* MCTS plan for one instance of problem p: the search runs over that
  * instance's alphabet and segment cap (o->n_modes and o->l_max are taken
- * from the instance; o->grammar, reward, seed, c_uct and max_evals from o;
+ * from the instance; o->grammar, reward, seed, c_uct, max_evals and max_ms from o;
  * eps_feas and merit_mu from the problem's solver options), each pool is
  * evaluated with comet_eval_modes (budget t_exp), and the po->k_ref best
  * orders by merit are then refined with comet_plan (those orders as seeds,
@@ -137,9 +140,11 @@ comet_status comet_mcts_best(const comet_mcts* t, int64_t k, uint64_t* codes, do
  * search's evaluations, out->rounds_run its pools, out->explore_ms is the
  * search's wall time (host search and GPU evaluation) plus the seeds'
  * re-evaluation inside comet_plan, out->refine_ms the refinement's device
- * time.  out_traj as comet_plan.  Synchronises.  Errors: INVALID_ARG (pool
- * < 1, bad options, max_evals = 0 with more than 2^22 orders in the space),
- * and those of comet_eval_modes and comet_plan. */
+ * time.  The search stops at the first of: the budget max_evals, every
+ * order evaluated, the time cap max_ms (checked before each pool).  out_traj
+ * as comet_plan.  Synchronises.  Errors: INVALID_ARG (pool < 1, bad options,
+ * max_evals = 0 and max_ms = 0 with more than 2^22 orders in the space), and
+ * those of comet_eval_modes and comet_plan. */
 comet_status comet_plan_mcts(comet_problem* p, int32_t instance, const comet_mcts_opts* o, int64_t pool,
                              const comet_plan_opts* po, comet_plan_result* out, float* out_traj);
 

@@ -102,7 +102,8 @@ GEMM_STORE, GEMM_BIAS_GELU, GEMM_GELU_GRAD, GEMM_ATOMIC_ADD = 0, 1, 2, 3
 class MctsOpts(ctypes.Structure):
     _fields_ = [("n_modes", ctypes.c_int32), ("l_max", ctypes.c_int32), ("grammar", ctypes.c_int32),
                 ("reward", ctypes.c_int32), ("max_evals", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("c_uct", ctypes.c_double), ("eps_feas", ctypes.c_double), ("merit_mu", ctypes.c_double)]
+                ("c_uct", ctypes.c_double), ("eps_feas", ctypes.c_double), ("merit_mu", ctypes.c_double),
+                ("max_ms", ctypes.c_double)]
 
 
 class MctsStats(ctypes.Structure):

@@ -61,6 +61,9 @@ struct Node {
 
 }  // namespace
 
+static_assert(sizeof(comet_mcts_opts) == 64, "comet_mcts_opts layout");
+static_assert(sizeof(comet_mcts_stats) == 40, "comet_mcts_stats layout");
+
 struct comet_mcts {
     comet_mcts_opts o;
     std::vector<int> alpha;
@@ -239,6 +242,7 @@ comet_status check_opts(const comet_mcts_opts* o) {
         return mfail(COMET_ERR_INVALID_ARG, "mcts: unknown reward");
     if (!(o->c_uct >= 0.0) || !std::isfinite(o->c_uct)) return mfail(COMET_ERR_INVALID_ARG, "mcts: bad c_uct");
     if (o->max_evals < 0) return mfail(COMET_ERR_INVALID_ARG, "mcts: max_evals < 0");
+    if (!(o->max_ms >= 0.0) || !std::isfinite(o->max_ms)) return mfail(COMET_ERR_INVALID_ARG, "mcts: bad max_ms");
     return COMET_OK;
 }
 
@@ -258,6 +262,7 @@ comet_status comet_mcts_default_opts(comet_mcts_opts* o) {
     o->c_uct = 0.8;
     o->eps_feas = 1e-5;
     o->merit_mu = 100.0;
+    o->max_ms = 0.0;
     return COMET_OK;
 }
 
@@ -390,7 +395,7 @@ comet_status comet_plan_mcts(comet_problem* p, int32_t instance, const comet_mct
     o.merit_mu = p->opts.merit_mu;
     comet_status st = check_opts(&o);
     if (st != COMET_OK) return st;
-    if (o.max_evals == 0) {
+    if (o.max_evals == 0 && o.max_ms == 0.0) {
         // an unbounded search must end: the space has to be small
         double space = 0.0, pw = 1.0;
         for (int L = 1; L <= o.l_max; ++L) space += (pw *= (double)(o.grammar == COMET_GRAMMAR_PUSH ? 5 : o.n_modes));
@@ -417,6 +422,9 @@ comet_status comet_plan_mcts(comet_problem* p, int32_t instance, const comet_mct
     const auto t0 = std::chrono::steady_clock::now();
     int32_t pools = 0;
     for (;;) {
+        if (o.max_ms > 0.0 &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() >= o.max_ms)
+            break;
         int64_t n = 0;
         st = comet_mcts_ask(t, instance, pool, seqs.data(), &n);
         if (st != COMET_OK) return st;

@@ -109,16 +109,17 @@ def test_native_search_on_oracle_solves(lib):
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(P.MctsOpts) == 56
+    assert ctypes.sizeof(P.MctsOpts) == 64
     assert ctypes.sizeof(P.MctsStats) == 40
 
 
 def test_defaults_and_errors(lib):
     o = P.comet_mcts_default_opts()
-    assert (o.n_modes, o.l_max, o.grammar, o.reward, o.max_evals, o.c_uct, o.eps_feas, o.merit_mu) == \
-        (12, 4, 0, 0, 0, 0.8, 1e-5, 100.0)
+    assert (o.n_modes, o.l_max, o.grammar, o.reward, o.max_evals, o.c_uct, o.eps_feas, o.merit_mu, o.max_ms) == \
+        (12, 4, 0, 0, 0, 0.8, 1e-5, 100.0, 0.0)
     for bad in (dict(grammar=1), dict(l_max=17), dict(l_max=0), dict(n_modes=507, l_max=7), dict(reward=2),
-                dict(c_uct=-1.0), dict(max_evals=-1), dict(n_modes=0)):
+                dict(c_uct=-1.0), dict(max_evals=-1), dict(n_modes=0), dict(n_modes=65536, l_max=1),
+                dict(max_ms=-1.0), dict(max_ms=float("inf"))):
         with pytest.raises(P.CometError):
             P.Mcts(**bad)
     t = P.Mcts(n_modes=3, l_max=2)
