@@ -140,3 +140,17 @@ def test_defaults_and_errors(lib):
     codes, merits = t.best(6)
     assert np.isinf(merits[-2:]).all() and np.isfinite(merits[:-2]).all()
     t.close()
+
+
+def test_plan_mcts_rejects_bad_arguments_before_any_gpu_work(lib):
+    # validated on the host: no problem, no options or an empty pool
+    with pytest.raises(P.CometError):
+        P.comet_plan_mcts(None, 0, dict(seed=1), 16)
+    r = P.PlanResult()
+    o = P.comet_mcts_default_opts()
+    assert lib.comet_plan_mcts(None, 0, ctypes.byref(o), 16, None, ctypes.byref(r), None) == 1
+    assert lib.comet_plan_mcts(None, 0, None, 16, None, ctypes.byref(r), None) == 1
+    t = P.Mcts(n_modes=3, l_max=2)
+    codes, merits = t.best(0)
+    assert len(codes) == 0 and len(merits) == 0
+    t.close()
