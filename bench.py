@@ -505,13 +505,30 @@ def mcts_times(P, n_inst=4, pools=(1024, 256, 64)):
     return out
 
 
+def first_distinct(recs, n_modes, k):
+    """The first k distinct orders of a stream of packed records, in stream
+    order.  The first occurrences in a stream of independent uniform draws
+    come in uniformly random order, so the first k distinct draws are a
+    uniform sample of k orders without replacement."""
+    base = np.uint64(n_modes + 1)
+    code = recs["len"].astype(np.uint64)
+    p = base.copy()
+    for i in range(recs["modes"].shape[1]):
+        live = recs["len"] > i
+        code = code + np.where(live, (recs["modes"][:, i].astype(np.uint64) + np.uint64(1)) * p, np.uint64(0))
+        p = p * base if i + 1 < recs["modes"].shape[1] else p
+    _, first = np.unique(code, return_index=True)
+    return recs[np.sort(first)[:k]]
+
+
 def grammar_times(P, n_inst=4):
     """The paper's pushing grammar on the four-faced box (Sec. IV-A): modes
     are stick on a face or free motion, orders of at most 8 segments
     (6,297 admissible).  Seed only (the 601 admissible orders of at most 6
     segments), expansion from that seed (beam 64, B = 1,024, r = 2, three
-    rounds), uniform sampling of as many admissible orders as the expansion
-    evaluated, and full enumeration of all 6,297, each followed by the same
+    rounds), uniform sampling without replacement of as many admissible
+    orders as the expansion evaluated, and full enumeration of all 6,297,
+    each followed by the same
     refinement (K_ref = 256 at t_ref = 1,500).  Device time per instance."""
     seeds = W.admissible_push_orders(6)
     every = W.admissible_push_orders(8)
@@ -525,7 +542,10 @@ def grammar_times(P, n_inst=4):
         ex = P.comet_plan(prob.handle, 0, ps, len(seeds), dict(base, rounds=3, radius=2, grammar=1))
         so = P.comet_plan(prob.handle, 0, ps, len(seeds), dict(base, rounds=0))
         en = P.comet_plan(prob.handle, 0, pe, len(every), dict(base, rounds=0))
-        pu = P.comet_sample_orders(prob.handle, 0, 1000 + s, 0, ex["evaluations"], P.GRAMMAR_PUSH)
+        # uniform sampling without replacement (Sec. IV-B): the first distinct
+        # orders of the sampler's stream, as many as the expansion evaluated
+        pu = first_distinct(P.comet_sample_orders(prob.handle, 0, 1000 + s, 0, 4 * ex["evaluations"],
+                                                  P.GRAMMAR_PUSH), 13, ex["evaluations"])
         un = P.comet_plan(prob.handle, 0, pu, len(pu), dict(base, rounds=0))
         out["expansion_ms"].append(ex["explore_ms"] + ex["refine_ms"])
         out["seed_only_ms"].append(so["explore_ms"] + so["refine_ms"])

@@ -369,8 +369,11 @@ comet_status comet_plan_batch(comet_problem* p, int32_t n_instances, const int32
  * n_modes = 13).  Order i is the order at index draw_i mod T of the
  * (length, lexicographic) enumeration, T the number of orders and draw_i the
  * i-th output of SplitMix64 (Steele, Lea and Flood 2014) from `seed`
- * (state seed + (i + 1) * 0x9E3779B97F4A7C15).  Uniform sampling followed by
- * refinement is comet_plan with the sample as seeds and rounds = 0.  out:
+ * (state seed + (i + 1) * 0x9E3779B97F4A7C15).  The draws are independent
+ * (with replacement); the first k distinct orders of the stream are a
+ * uniform sample of k orders without replacement.  Uniform sampling
+ * followed by refinement is comet_plan with the sample as seeds and
+ * rounds = 0.  out:
  * host or device array of n records (host: synchronises).  Errors:
  * INVALID_ARG. */
 comet_status comet_sample_orders(comet_problem* p, int32_t instance, uint64_t seed, int64_t first, int64_t n,
