@@ -161,12 +161,11 @@ struct Rows {
 };
 
 // kFree: free motion (mode 12) compiled in; problems over the 12 contact
-// modes run the variant without it
-template <bool kFree>
-//
+// modes run the variant without it.
 // Inputs: xk = x_k and dx = x_{k+1} - x_k rounded to FP32, except dx[2] =
 // fl(theta_{k+1,hi} - theta_{k,hi}); ex[0] = the rest of the theta
 // difference, ex[1] = s_k - xk[3] (see stage_state).
+template <bool kFree>
 __device__ __forceinline__ void eval_rows(const DevInstance& P, const ModeInfo& mi, const float xk[4],
                                           const float dx[4], const float ex[2], const float u[3], Rows& R) {
     float nx, ny;
