@@ -194,3 +194,37 @@ def test_uct_ties_go_to_the_lowest_slot():
     t.root.untried, t.root.children, t.root.n = [], kids, 6
     t.attempt()
     assert [kids[s].n for s in (1, 2, 3)] == [3, 2, 2]
+
+
+def test_policies_on_oracle_solves_order_as_in_the_paper():
+    # every order of <= 2 segments on 16 instances solved by the FP64 oracle;
+    # each policy searches those results with the same budget, counted by the
+    # instances on which it evaluates the enumeration's feasible argmin
+    # (Eq. mode_selection).  The paper's ordering: expansion, MCTS, uniform
+    import oracle
+    import workloads as W
+    every = [(m,) for m in range(12)] + [(a, b) for a in range(12) for b in range(12)]
+    modes, lens = W.pad_sequences(every, 2)
+    found = {"expansion": [0, 0], "mcts": [0, 0], "uniform": [0, 0]}
+    for s in range(16):
+        res, _ = oracle.solve_batch([W.push_l2_instance(s)], np.zeros(len(every), np.int32), modes, lens)
+        tab = {o: (float(np.float32(res["cost"][i])), float(np.float32(res["viol"][i]))) for i, o in enumerate(every)}
+        feas = [o for o in every if tab[o][1] <= 1e-5]
+        target = min(feas, key=lambda o: (S.merit(*tab[o]), S.encode(o, 12)))
+        for j, budget in enumerate((48, 96)):
+            V, _ = S.run_expansion(lambda q: [S.merit(*tab[o]) for o in q], [(m,) for m in range(12)], 8, 12, 12,
+                                   2, 100, budget=budget)
+            found["expansion"][j] += any(seq == target for _, seq in V.values())
+            seen = []
+
+            def ev(q):
+                seen.extend(q)
+                return [tab[o][0] for o in q], [tab[o][1] for o in q]
+
+            T.run(ev, 8, n_modes=12, l_max=2, seed=s, max_evals=budget)
+            found["mcts"][j] += target in seen
+            first = list(dict.fromkeys(S.sample_orders(s, 0, 4 * budget, 12, 2)))[:budget]
+            found["uniform"][j] += target in first
+    for j in range(2):
+        assert found["expansion"][j] >= found["mcts"][j] > found["uniform"][j], found
+    assert found["mcts"][1] >= 12, found
