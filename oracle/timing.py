@@ -18,7 +18,12 @@ variables for it; the readings taken here:
     dt); free motion (mode 12) moves s at the pusher's rate for h_k;
   * the cost is that of the fixed-step problem (no term in h);
   * cold start: the fixed-step cold start, h_k = dt clipped into the bounds,
-    tau_k the running sum.
+    tau_k the running sum;
+  * the other reading, one optimised time step shared by every interval
+    (timing["shared"]): h is a fifth state held constant along the chain
+    (h_{k+1} = h_k, an equality row divided by sqrt(2)), free at k = 0, with
+    the terminal rows N h_N <= T, h_min <= h_N and h_N <= h_max; the
+    dynamics rows use h_k.
 Everything else -- the rows of each mode, the PHR augmented Lagrangian, the
 damped Newton / Gauss-Newton step with the Lagrangian curvature of the
 dynamics rows, the trial-step line search, the multiplier and penalty
@@ -118,10 +123,13 @@ class Layout:
 
     def __init__(self, N, timing):
         self.N, self.timing = N, timing is not None
-        self.nx, self.nu = (5, 4) if self.timing else (4, 3)
-        self.nr = NROW + (3 if self.timing else 0)   # timing: tau row, h_min row, h_max row
-        self.ni = 4 if self.timing else 3             # initial rows
-        self.nt = 1 if self.timing else 0             # terminal rows
+        self.shared = bool(timing and timing.get("shared"))
+        if self.shared:     # h a state: x = (x, y, theta, s, h), u = (f_n, f_t, s_dot)
+            self.nx, self.nu, self.nr, self.ni, self.nt = 5, 3, NROW + 1, 3, 3
+        elif self.timing:   # h_k a control, tau a state
+            self.nx, self.nu, self.nr, self.ni, self.nt = 5, 4, NROW + 3, 4, 1
+        else:
+            self.nx, self.nu, self.nr, self.ni, self.nt = 4, 3, NROW, 3, 0
         self.stage = self.nx + self.nu
         self.nz = N * self.stage + self.nx
         self.nl = self.ni + N * self.nr + self.nt
@@ -131,6 +139,10 @@ class Layout:
 
     def u(self, k):
         return k * self.stage + self.nx
+
+    def h_local(self):
+        """Index of the duration in the local (x_k, u_k, x_{k+1}) vector."""
+        return 4 if self.shared else self.nx + 3
 
     def local(self, k):
         """z indices of interval k's local variables (x_k, u_k, x_{k+1})."""
@@ -166,7 +178,7 @@ def interval_rows(inst, mode, smask, xk, uk, xk1, L: Layout, timing, sig):
     ineq[NEQ:NROW] = True
     J = np.zeros((nr, nloc))
     X, U, Y = 0, nx, nx + nu                      # local offsets of x_k, u_k, x_{k+1}
-    h = uk[3] if L.timing else inst["dt"]
+    h = (xk[4] if L.shared else uk[3]) if L.timing else inst["dt"]
     free = mode == MODE_FREE
     face, kind = (0, 3) if free else (mode // 3, mode % 3)
     if free:
@@ -181,7 +193,7 @@ def interval_rows(inst, mode, smask, xk, uk, xk1, L: Layout, timing, sig):
         J[i, U:U + 3] = -h * Fu[i] / sig[i]
         J[i, Y + i] = 1.0 / sig[i]
         if L.timing:
-            J[i, U + 3] = -f[i] / sig[i]
+            J[i, L.h_local()] = -f[i] / sig[i]
         scale[i] = 1.0 / sig[i]
     if smask:
         mask[3] = False
@@ -211,7 +223,11 @@ def interval_rows(inst, mode, smask, xk, uk, xk1, L: Layout, timing, sig):
         c[8], J[8, U + 0] = -fn, -1.0
         c[9], J[9, X + 3] = xk[3] - ell, 1.0
         c[10], J[10, X + 3] = -xk[3] - ell, -1.0
-    if L.timing:
+    if L.shared:
+        r2 = math.sqrt(2.0)
+        c[11] = (xk1[4] - xk[4]) / r2
+        J[11, X + 4], J[11, Y + 4], scale[11] = -1.0 / r2, 1.0 / r2, 1.0 / r2
+    elif L.timing:
         r3 = math.sqrt(3.0)
         c[11] = (xk1[4] - xk[4] - uk[3]) / r3
         J[11, X + 4], J[11, U + 3], J[11, Y + 4], scale[11] = -1.0 / r3, -1.0 / r3, 1.0 / r3, 1.0 / r3
@@ -228,7 +244,7 @@ def stage_curvature(inst, mode, xk, uk, yd, L: Layout):
     timing, h is a variable and the cross terms -yd_i df_i/dv appear."""
     nx, nu = L.nx, L.nu
     H = np.zeros((nx + nu, nx + nu))
-    h = uk[3] if L.timing else inst["dt"]
+    h = (xk[4] if L.shared else uk[3]) if L.timing else inst["dt"]
     xs, us = [0, 1, 2, 3], [nx + 0, nx + 1, nx + 2]
     idx = xs + us
     if mode != MODE_FREE:
@@ -241,7 +257,7 @@ def stage_curvature(inst, mode, xk, uk, yd, L: Layout):
         else:
             _, Fx, Fu = dynamics(inst, mode // 3, xk[:4], uk[:3])
         grad = np.concatenate([yd @ Fx, yd @ Fu])   # sum_i yd_i df_i / dv
-        hi = nx + 3
+        hi = L.h_local()
         H[hi, idx] -= grad
         H[idx, hi] -= grad
     return H
@@ -268,8 +284,8 @@ class Problem:
             for i in range(3):
                 z[L.x(k) + i] = (1.0 - a) * inst["start"][i] + a * inst["goal"][i]
             if L.timing:
-                z[L.x(k) + 4] = k * h
-        if L.timing:
+                z[L.x(k) + 4] = h if L.shared else k * h
+        if L.timing and not L.shared:
             for k in range(self.N):
                 z[L.u(k) + 3] = h
         return z
@@ -285,16 +301,22 @@ class Problem:
         L, inst = self.L, self.inst
         c = [z[L.x(0) + i] - inst["start"][i] for i in range(3)]
         idx = [L.x(0) + i for i in range(3)]
-        if L.timing:
+        if L.timing and not L.shared:
             c.append(z[L.x(0) + 4])
             idx.append(L.x(0) + 4)
         return np.array(c), idx
 
     def terminal_rows(self, z):
+        """Terminal inequality rows: values, the z index each depends on and
+        its (constant) derivative."""
         if not self.L.timing:
-            return np.zeros(0), []
+            return np.zeros(0), [], []
         i = self.L.x(self.N) + 4
-        return np.array([z[i] - self.timing["T"]]), [i]
+        if self.L.shared:
+            t = self.timing
+            return (np.array([self.N * z[i] - t["T"], t["h_min"] - z[i], z[i] - t["h_max"]]), [i, i, i],
+                    [float(self.N), -1.0, 1.0])
+        return np.array([z[i] - self.timing["T"]]), [i], [1.0]
 
     def cost(self, z):
         L, inst = self.L, self.inst
@@ -345,7 +367,7 @@ def al_merit(P: Problem, z, lam, beta):
         for r in range(L.nr):
             if mask[r]:
                 phi += row_al(ineq[r], lam[L.row(k, r)], beta, c[r])
-    ct, _ = P.terminal_rows(z)
+    ct, _, _ = P.terminal_rows(z)
     for j, c in enumerate(ct):
         phi += row_al(True, lam[L.ni + P.N * L.nr + j], beta, c)
     return phi
@@ -380,13 +402,13 @@ def measures(P: Problem, z, lam, beta):
                 comp = max(comp, abs(y[q] * c[r]))
             if y[q] != 0.0:
                 grad[loc] += y[q] * J[r]
-    ct, tidx = P.terminal_rows(z)
+    ct, tidx, tder = P.terminal_rows(z)
     for j, c in enumerate(ct):
         q = L.ni + P.N * L.nr + j
         y[q] = row_y(True, lam[q], beta, c)
         viol, vphys = max(viol, max(c, 0.0)), max(vphys, max(c, 0.0))
         comp = max(comp, abs(y[q] * c))
-        grad[tidx[j]] += y[q]
+        grad[tidx[j]] += y[q] * tder[j]
     finite &= bool(np.all(np.isfinite(grad)))
     return y, grad, dict(viol=viol, vphys=vphys, comp=comp, stat=float(np.max(np.abs(grad))), finite=finite)
 
@@ -421,12 +443,12 @@ def step(P: Problem, z, lam, beta, rho, curvature):
                            for r in range(4)])
             xu = loc[:L.nx + L.nu]
             H[np.ix_(xu, xu)] += stage_curvature(P.inst, P.mode_k[k], xk, uk, yd, L)
-    ct, tidx = P.terminal_rows(z)
+    ct, tidx, tder = P.terminal_rows(z)
     for j, c in enumerate(ct):
         q = L.ni + P.N * L.nr + j
         if lam[q] + beta * c > 0.0:
-            H[tidx[j], tidx[j]] += beta
-            g[tidx[j]] += row_y(True, lam[q], beta, c)
+            H[tidx[j], tidx[j]] += beta * tder[j] * tder[j]
+            g[tidx[j]] += row_y(True, lam[q], beta, c) * tder[j]
     H += rho * np.eye(L.nz)
     try:
         C = np.linalg.cholesky(H)
@@ -547,10 +569,10 @@ def all_rows(P: Problem, z):
             q = L.row(k, r)
             c[q], mask[q], ineq[q] = ck[r], mk[r], ik[r]
             A[q, loc] = Jk[r]
-    ct, tidx = P.terminal_rows(z)
+    ct, tidx, tder = P.terminal_rows(z)
     for j, v in enumerate(ct):
         q = L.ni + P.N * L.nr + j
-        c[q], A[q, tidx[j]], ineq[q] = v, 1.0, True
+        c[q], A[q, tidx[j]], ineq[q] = v, tder[j], True
     return c, A, ineq, mask
 
 
@@ -562,6 +584,8 @@ def durations(inst, modes, z, N=None, timing=None):
     L = Layout(N, timing)
     if not L.timing:
         return np.full(N, inst["dt"])
+    if L.shared:
+        return np.array([z[L.x(k) + 4] for k in range(N)])
     return np.array([z[L.u(k) + 3] for k in range(N)])
 
 

@@ -175,3 +175,62 @@ def test_trial_step_is_the_armijo_rule():
     # raises phi by at most ls_slack |phi(0)|, else the Armijo test applies
     assert TM.trial_step(1.0, -1e-9, lambda a: 1.0 + 5e-7 * a, 7, 1e-4, 1e-6) == 1.0
     assert TM.trial_step(1.0, -1e-9, lambda a: 1.0 + 2e-6 * a, 7, 1e-4, 1e-6) == 0.0
+
+
+# the other reading: one optimised time step shared by every interval
+
+@pytest.mark.parametrize("mode", [0, 5, 9, 12])
+def test_shared_step_rows_and_curvature_against_differences(mode):
+    inst = W.push_l2_instance(6)
+    timing = dict(shared=True, h_min=0.05, h_max=0.2, T=2.0)
+    L = TM.Layout(4, timing)
+    sig = [TM.dyn_row_scale(inst, i) for i in range(4)]
+    rng = np.random.default_rng(40 + mode)
+    v = rng.normal(size=2 * L.nx + L.nu) * 0.1
+    v[4] = v[L.nx + L.nu + 4] = 0.11
+    split = lambda w: (w[:L.nx], w[L.nx:L.nx + L.nu], w[L.nx + L.nu:])
+    J = TM.interval_rows(inst, mode, False, *split(v), L, timing, sig)[4]
+    y = rng.normal(size=4)
+    eps = 1e-6
+    Jfd = np.zeros_like(J)
+    nxu = L.nx + L.nu
+    Hfd = np.zeros((nxu, nxu))
+    for j in range(len(v)):
+        vp, vm = v.copy(), v.copy()
+        vp[j] += eps
+        vm[j] -= eps
+        Jp = TM.interval_rows(inst, mode, False, *split(vp), L, timing, sig)
+        Jm = TM.interval_rows(inst, mode, False, *split(vm), L, timing, sig)
+        Jfd[:, j] = (Jp[0] - Jm[0]) / (2 * eps)
+        if j < nxu:
+            Hfd[:, j] = (y @ Jp[4][:4] - y @ Jm[4][:4])[:nxu] / (2 * eps)
+    np.testing.assert_allclose(J, Jfd, atol=1e-7, rtol=1e-6)
+    H = TM.stage_curvature(inst, mode, *split(v)[:2], y / np.array(sig), L)
+    np.testing.assert_allclose(H, Hfd, atol=1e-6, rtol=1e-6)
+
+
+@pytest.mark.parametrize("T,h_expect", [(2.0, 2.0 / 16), (3.0, 0.15)])
+def test_straight_push_with_one_shared_step_closed_form(T, h_expect):
+    # J(h) = W R d^2 / (R + W kappa^2 N h^2) decreases in h, so the optimal
+    # shared step is min(h_max, T / N): the duration bound decides when it
+    # binds, h_max otherwise
+    d, N = 0.1, 16
+    inst = W.push_l2_straight(d)
+    Wt, R = inst["w_terminal"], inst["w_control"]
+    timing = dict(shared=True, h_min=0.05, h_max=0.15, T=T)
+    z, lam, r = TM.solve(inst, (0, 0), timing=timing, **TIGHT)
+    assert r["status"] == TM.CONVERGED
+    h = TM.durations(inst, (0, 0), z, timing=timing)
+    np.testing.assert_allclose(h, h_expect, atol=1e-9)
+    assert r["cost"] == pytest.approx(Wt * R * d * d / (R + Wt * N * h_expect ** 2), rel=1e-7)
+    # the duration bound's multiplier is positive exactly when it binds
+    assert (lam[-3] > 0.0) == (T / N < 0.15)
+
+
+def test_shared_step_pinned_at_dt_gives_the_fixed_step_solution():
+    inst = W.push_l2_instance(4)
+    z, _, r = TM.solve(inst, (0, 3), timing=dict(shared=True, h_min=inst["dt"], h_max=inst["dt"], T=5.0),
+                       **TIGHT)
+    _, _, rf = TM.solve(inst, (0, 3), **TIGHT)
+    assert r["status"] == rf["status"] == TM.CONVERGED
+    assert r["cost"] == pytest.approx(rf["cost"], rel=1e-7)
