@@ -474,8 +474,10 @@ def trial_step(phi0, D, merit_at, n_alpha, c1, ls_slack):
 
 
 def solve(inst, modes, N=None, timing=None, warm=None, **over):
-    """The method of Sec. III-C on one order; timing = None (fixed step) or
-    {"h_min", "h_max", "T"}.  Returns (z, lam, result dict); z in the
+    """The method of Sec. III-C on one order; timing = None (fixed step),
+    {"h_min", "h_max", "T"} (a duration per interval) or the same with
+    "shared": True (one step for every interval).  Options override
+    DEFAULTS (the C oracle's).  Returns (z, lam, result dict); z in the
     interleaved layout of Layout."""
     o = dict(DEFAULTS, **over)
     if N is None:
