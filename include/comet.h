@@ -201,9 +201,12 @@ comet_status comet_eval_stats(comet_problem* p, float* out_viol, float* out_meri
  *                      memory (nothing is staged; host pointers are rejected
  *                      with COMET_ERR_INVALID_ARG); the trajectory stride is
  *                      7 * N_max + 4 with N_max = max K * max_segments.
- * Asynchronous on cuda_stream.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call shares the
+ * Asynchronous on cuda_stream: the call reads no host memory on the GPU
+ * (the instance table travels as a kernel launch parameter) and does not
+ * wait for the stream.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with the current device; the first call on a device
+ * may load the library's device code there, so make that first call before
+ * any stream capture.  Every call shares the
  * array and it keeps the last call's contents (the work counter and error
  * flag are cleared by each call); calls whose kernels overlap on the GPU --
  * two streams or two host threads at once -- race on it and must be

@@ -12,16 +12,23 @@
 //
 // The array holds kNoallocScratchBytes (32 MiB) on every device that loads
 // the library, until the process exits.  Its device address is looked up
-// once per device, on the first call made with that device current.  All
-// calls share the array and it keeps the last call's contents: the work
-// counter and the error flag are cleared by every call, and calls whose
-// kernels overlap on the GPU (two streams, or two host threads) race on it.
+// (cudaGetSymbolAddress, with the device current) on every call: the lookup
+// is cheap, and an address cached across calls would go stale if the caller
+// reset the device in between.  The first call on a device may load the
+// library's device code there.  All calls share the array and it keeps the
+// last call's contents: the work counter and the error flag are cleared by
+// every call, and calls whose kernels overlap on the GPU (two streams, or two
+// host threads) race on it.
+//
+// The instance table reaches the array through a one-block kernel that takes
+// the table by value as its launch parameter, so the call never copies from
+// host memory: it does not wait for the stream to drain and holds no pointer
+// into the caller's stack.
 
 #include <cuda_runtime.h>
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "comet.h"
 #include "comet_internal.h"
@@ -30,7 +37,6 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = 32u << 20;
 constexpr int kNoallocMaxInstances = 64;
-constexpr int kMaxDevices = 64;
 
 // scratch layout: [header 256 B: work counter, error flag]
 //                 [instance table: kNoallocMaxInstances DevInstance]
@@ -41,8 +47,18 @@ constexpr size_t kHeaderBytes = 256;
 constexpr size_t kInstBytes = ((sizeof(comet::DevInstance) * kNoallocMaxInstances + 255) / 256) * 256;
 constexpr size_t kRecordBytes = kNoallocScratchBytes - kHeaderBytes - kInstBytes;
 
-std::mutex g_lock;
-unsigned char* g_addr[kMaxDevices] = {};
+// the instance table as one launch parameter (under the 32,764-byte limit of
+// kernel parameters)
+struct InstTable {
+    comet::DevInstance inst[kNoallocMaxInstances];
+};
+static_assert(sizeof(InstTable) <= 32764, "instance table too large for a kernel parameter");
+static_assert(sizeof(comet::DevInstance) % 4 == 0, "the table is copied in 4-byte words");
+
+__global__ void noalloc_table_kernel(const __grid_constant__ InstTable t, int n_words, uint32_t* dst) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&t);
+    for (int i = threadIdx.x; i < n_words; i += blockDim.x) dst[i] = src[i];
+}
 
 comet_status noalloc_fail(comet_status st, const char* msg) {
     comet::set_error(msg);
@@ -88,18 +104,16 @@ extern "C" comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst
         return noalloc_fail(COMET_ERR_INVALID_ARG,
                             "comet_eval_modes_noalloc: all arrays must be device memory (nothing is staged)");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
         return noalloc_fail(COMET_ERR_CUDA, "cudaGetDevice failed");
+    // the device address of the array on the current device (the host-side
+    // name g_noalloc_scratch is not a device address)
     unsigned char* base = nullptr;
     {
-        std::lock_guard<std::mutex> g(g_lock);
-        if (!g_addr[dev]) {
-            void* ptr = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess) return noalloc_fail(COMET_ERR_CUDA, cudaGetErrorString(e));
-            g_addr[dev] = static_cast<unsigned char*>(ptr);
-        }
-        base = g_addr[dev];
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return noalloc_fail(COMET_ERR_CUDA, cudaGetErrorString(e));
+        base = static_cast<unsigned char*>(ptr);
     }
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -123,14 +137,19 @@ extern "C" comet_status comet_eval_modes_noalloc(const comet_instance_desc* inst
     int* bad = reinterpret_cast<int*>(base + 64);
     comet::DevInstance* d_inst = reinterpret_cast<comet::DevInstance*>(base + kHeaderBytes);
     float* ws = reinterpret_cast<float*>(base + kHeaderBytes + kInstBytes);
-    comet::DevInstance h_inst[kNoallocMaxInstances];
-    for (int i = 0; i < n_instances; ++i) comet::make_dev_instance(inst[i], &h_inst[i]);
+    InstTable table;
+    memset(&table, 0, sizeof(table));
+    for (int i = 0; i < n_instances; ++i) comet::make_dev_instance(inst[i], &table.inst[i]);
     comet_solver_opts o;
     comet::merge_opts(opts, &o);
     // the counter and flag start at zero; the instance table is rewritten
+    // from the launch parameter (no host memory is read by the GPU)
     cudaError_t e = cudaMemsetAsync(base, 0, kHeaderBytes, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_inst, h_inst, sizeof(comet::DevInstance) * n_instances, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const int n_words = (int)(sizeof(comet::DevInstance) * n_instances / 4);
+        noalloc_table_kernel<<<1, 256, 0, s>>>(table, n_words, reinterpret_cast<uint32_t*>(d_inst));
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return noalloc_fail(COMET_ERR_CUDA, cudaGetErrorString(e));
 
     comet::EvalArgs a;

@@ -42,14 +42,14 @@ def _orders(seed, n, insts):
     return seqs, idx
 
 
-def _reference(P, insts, packed_dev, n, stride_expected):
+def _reference(P, insts, packed_dev, n, stride_expected, warm=None):
     # the existing, allocating entry point on the same orders
     prob = P.Problem(insts)
     assert prob.stride == stride_expected
     cost = torch.empty(n, dtype=torch.float32, device="cuda")
     status = torch.empty(n, dtype=torch.int32, device="cuda")
     traj = torch.empty((n, prob.stride), dtype=torch.float32, device="cuda")
-    P.comet_eval_modes(prob.handle, packed_dev, n, None, cost, traj, status)
+    P.comet_eval_modes(prob.handle, packed_dev, n, warm, cost, traj, status)
     torch.cuda.synchronize()
     out = cost.cpu().numpy(), status.cpu().numpy(), traj.cpu().numpy()
     prob.close()
@@ -93,3 +93,50 @@ def test_noalloc_rejects_what_it_cannot_hold(P):
         P.comet_eval_modes_noalloc([inst] * 65, None, s, d, n, None, cost, None, status)
     with pytest.raises(P.CometError, match="device memory"):
         P.comet_eval_modes_noalloc([inst], None, s, packed, n, None, cost, None, status)
+
+
+def test_noalloc_many_tos_per_warp_and_warm_starts(P):
+    """4,000 TOs at N = 80 exceed the 1,308 warps whose stage records fit the
+    fixed array, so warps take several TOs each from the work counter (the
+    launch shape only this entry point uses).  Each TO is still solved by one
+    warp with the same arithmetic, so the results equal the allocating entry
+    point's bit for bit, cold and then warm-started from the first results."""
+    insts = [W.push_l4_instance(23), W.push_l4_instance(24)]
+    stride = 7 * 80 + 4
+    n = 4000
+    seqs, idx = _orders(3, n, insts)
+    packed = P.pack_mode_seqs(seqs, idx)
+    d = torch.from_numpy(packed.view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    warm = None
+    for call in range(2):
+        cost = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+        status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        traj = torch.zeros((n, stride), dtype=torch.float32, device="cuda")
+        P.comet_eval_modes_noalloc(insts, None, s, d, n, warm, cost, traj, status)
+        torch.cuda.synchronize()
+        c, st, tr = cost.cpu().numpy(), status.cpu().numpy(), traj.cpu().numpy()
+        rc, rs, rtr = _reference(P, insts, d, n, stride, warm)
+        np.testing.assert_array_equal(st, rs, err_msg=f"call {call}")
+        np.testing.assert_array_equal(c.view(np.uint32), rc.view(np.uint32), err_msg=f"call {call}")
+        np.testing.assert_array_equal(tr.view(np.uint32), rtr.view(np.uint32), err_msg=f"call {call}")
+        assert np.mean(st == P.TO_CONVERGED) > 0.5
+        warm = traj  # the second call starts from the first call's solutions
+
+
+def test_noalloc_rejects_too_large_n_max(P):
+    """An instance whose N_max needs more shared memory per warp than a block
+    can have is rejected with INVALID_ARG before anything runs."""
+    inst = dict(W.push_l4_instance(25))
+    inst["knots_per_segment"] = 256
+    inst["max_segments"] = 16  # N_max = 4,096
+    n = 2
+    packed = P.pack_mode_seqs(np.zeros((n, 1), np.uint8))
+    d = torch.from_numpy(packed.view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
+    cost = torch.empty(n, dtype=torch.float32, device="cuda")
+    status = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(P.CometError, match="shared memory|too large"):
+        P.comet_eval_modes_noalloc([inst], None, s, d, n, None, cost, None, status)
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [-7, -7]  # nothing was launched
