@@ -27,6 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "comet_oracle.c")
 _SRC_BIM = os.path.join(_HERE, "bimanual.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libcomet_oracle.so")
+_LIB_FLOPS_PATH = os.path.join(_HERE, "_build", "libcomet_oracle_flops.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -35,18 +36,23 @@ CONVERGED, MAX_ITER, INFEASIBLE, FACTOR_FAIL, NONFINITE = range(5)
 MODE_FREE = 12
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, IEEE double, no fast-math)."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+def build(force: bool = False, count_flops: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE double, no fast-math).
+    count_flops: the separate build with the method's flop counter compiled
+    in (libcomet_oracle_flops.so), used to measure flops per stage and
+    iteration; the default build carries no counter."""
+    path = _LIB_FLOPS_PATH if count_flops else _LIB_PATH
+    os.makedirs(os.path.dirname(path), exist_ok=True)
     srcs = [_SRC, _SRC_BIM, os.path.join(_HERE, "comet_oracle.h"), os.path.join(_HERE, "bimanual.h")]
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(f) for f in srcs):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    if force or not os.path.exists(path) or os.path.getmtime(path) < max(os.path.getmtime(f) for f in srcs):
+        tmp = path + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-Wall",
-             "-o", tmp, _SRC, _SRC_BIM, "-lm", "-lpthread"]
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-Wall"]
+            + (["-DORC_COUNT_FLOPS"] if count_flops else [])
+            + ["-o", tmp, _SRC, _SRC_BIM, "-lm", "-lpthread"]
         )
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
 class Instance(ctypes.Structure):
@@ -135,6 +141,10 @@ def lib():
                                           ctypes.c_int64, _P(Opts), ctypes.c_int32, _dp, ctypes.c_int64,
                                           ctypes.c_void_p]
             L.orc_solve_batch.restype = ctypes.c_int32
+            L.orc_solve_batch_ex.argtypes = [_P(Instance), _i32p, _i32p, _u8p, ctypes.c_int32, _i32p,
+                                             ctypes.c_int64, _P(Opts), ctypes.c_int32, _dp, ctypes.c_int64,
+                                             _dp, _dp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_void_p]
+            L.orc_solve_batch_ex.restype = ctypes.c_int32
             B = _P(BimInstance)
             L.bim_interval_rows.argtypes = [B, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp, _dp,
                                             _u8p, _u8p, _dp, _dp]
@@ -153,6 +163,10 @@ def lib():
             L.bim_solve_batch.argtypes = [B, _i32p, _i32p, _u16p, ctypes.c_int32, _i32p, ctypes.c_int64, _P(Opts),
                                           ctypes.c_int32, _dp, ctypes.c_int64, ctypes.c_void_p]
             L.bim_solve_batch.restype = ctypes.c_int32
+            L.bim_solve_batch_ex.argtypes = [B, _i32p, _i32p, _u16p, ctypes.c_int32, _i32p, ctypes.c_int64,
+                                             _P(Opts), ctypes.c_int32, _dp, ctypes.c_int64, _dp, _dp,
+                                             ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_void_p]
+            L.bim_solve_batch_ex.restype = ctypes.c_int32
             _lib = L
     return _lib
 
@@ -301,6 +315,42 @@ def solve_batch(insts: list, inst_idx, seqs, lens, Ns=None, opts: Opts | None = 
     return res, tr
 
 
+def solve_batch_ex(insts: list, inst_idx, seqs, lens, warm=None, opts: Opts | None = None,
+                   nthreads: int | None = None, warm_lam=None):
+    """solve_batch with optional warm starts and the multipliers.  warm:
+    float64 [n, 7*Nmax+4], row i holding TO i's component-major trajectory
+    for its own N at the start of the row (as returned by solve_batch).
+    warm_lam: float64 [n, 3+11*Nmax] starting multipliers (row i for TO i's
+    own N), or None for zero.
+    Returns (results, trajectories [n, 7*Nmax+4], multipliers [n, 3+11*Nmax])."""
+    seqs = np.ascontiguousarray(seqs, dtype=np.uint8)
+    n, lmax = seqs.shape
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    inst_idx = np.ascontiguousarray(inst_idx, dtype=np.int32)
+    K = np.array([int(insts[i]["knots_per_segment"]) for i in range(len(insts))], dtype=np.int32)
+    Ns = np.ascontiguousarray(K[inst_idx] * lens, dtype=np.int32)
+    arr = (Instance * len(insts))(*[make_instance(d) for d in insts])
+    res = np.zeros(n, dtype=RESULT_DTYPE)
+    Nmax = int(Ns.max()) if n else 0
+    stride, lstride = traj_len(Nmax), 3 + 11 * Nmax
+    tr = np.zeros((n, stride))
+    lam = np.zeros((n, lstride))
+    w = None
+    if warm is not None:
+        w = np.ascontiguousarray(warm, dtype=np.float64)
+        assert w.shape[0] == n and w.shape[1] >= stride
+    wl = None
+    if warm_lam is not None:
+        wl = np.ascontiguousarray(warm_lam, dtype=np.float64)
+        assert wl.shape == (n, lstride)
+    o = opts if opts is not None else default_opts()
+    lib().orc_solve_batch_ex(arr, _ptr(inst_idx, _i32p), _ptr(lens, _i32p), _ptr(seqs, _u8p), lmax,
+                             _ptr(Ns, _i32p), n, ctypes.byref(o), nthreads or os.cpu_count() or 1,
+                             _ptr(w, _dp), w.shape[1] if w is not None else 0, _ptr(wl, _dp), _ptr(tr, _dp),
+                             stride, _ptr(lam, _dp), lstride, res.ctypes.data_as(ctypes.c_void_p))
+    return res, tr, lam
+
+
 # ------------------------------------------------------------- bimanual
 
 BIM_NX, BIM_NU, BIM_NROW, BIM_NMODES = 5, 12, 32, 507
@@ -432,3 +482,64 @@ def bim_solve_batch(insts: list, inst_idx, seqs, lens, opts: Opts | None = None,
                           _ptr(Ns, _i32p), n, ctypes.byref(o), nthreads or (os.cpu_count() or 1),
                           _ptr(tr, _dp), stride, res.ctypes.data)
     return res, tr
+
+
+def bim_solve_batch_ex(insts: list, inst_idx, seqs, lens, warm=None, opts: Opts | None = None,
+                       nthreads: int | None = None, warm_lam=None):
+    """bim_solve_batch with optional warm starts (float64 [n, stride], TO i's
+    trajectory for its own N at the start of row i) and the multipliers.
+    Returns (results, trajectories [n, 17*Nmax+5], multipliers [n, 3+32*Nmax])."""
+    n = len(inst_idx)
+    lmax = max(1, max((len(s) for s in seqs), default=1))
+    modes = np.zeros((n, lmax), np.uint16)
+    for i, s in enumerate(seqs):
+        modes[i, : len(s)] = s
+    lens = np.ascontiguousarray(lens, dtype=np.int32)
+    inst_idx = np.ascontiguousarray(inst_idx, dtype=np.int32)
+    Ns = np.array([insts[j]["knots_per_segment"] * int(L) for j, L in zip(inst_idx, lens)], np.int32)
+    arr = (BimInstance * len(insts))(*[bim_make_instance(d) for d in insts])
+    res = np.zeros(n, dtype=RESULT_DTYPE)
+    Nmax = int(Ns.max()) if n else 0
+    stride, lstride = bim_traj_len(Nmax), 3 + BIM_NROW * Nmax
+    tr = np.zeros((n, stride))
+    lam = np.zeros((n, lstride))
+    w = None
+    if warm is not None:
+        w = np.ascontiguousarray(warm, dtype=np.float64)
+        assert w.shape[0] == n and w.shape[1] >= stride
+    wl = None
+    if warm_lam is not None:
+        wl = np.ascontiguousarray(warm_lam, dtype=np.float64)
+        assert wl.shape == (n, lstride)
+    o = opts if opts is not None else default_opts()
+    lib().bim_solve_batch_ex(arr, _ptr(inst_idx, _i32p), _ptr(lens, _i32p), _ptr(modes, _u16p), lmax,
+                             _ptr(Ns, _i32p), n, ctypes.byref(o), nthreads or (os.cpu_count() or 1),
+                             _ptr(w, _dp), w.shape[1] if w is not None else 0, _ptr(wl, _dp), _ptr(tr, _dp),
+                             stride, _ptr(lam, _dp), lstride, res.ctypes.data_as(ctypes.c_void_p))
+    return res, tr, lam
+
+
+def flops_per_stage_iteration(insts, inst_idx, seqs, lens, opts: Opts | None = None):
+    """The method's floating-point operations per stage and solver iteration,
+    measured by the counting build of the oracle over the given orders
+    (solved one by one on the calling thread): total counted flops divided by
+    sum over the TOs of (iterations x intervals).  Returns (flops per
+    stage-iteration, total flops, sum of iterations x intervals)."""
+    L = ctypes.CDLL(build(count_flops=True))
+    L.orc_solve.argtypes = [_P(Instance), ctypes.c_int32, _u8p, ctypes.c_int32, _dp, _P(Opts), _dp, _dp, _P(Result)]
+    L.orc_flop_count.restype = ctypes.c_uint64
+    o = opts if opts is not None else default_opts()
+    seqs = np.ascontiguousarray(seqs, dtype=np.uint8)
+    L.orc_flop_reset()
+    work = 0
+    for t in range(len(inst_idx)):
+        inst = insts[int(inst_idx[t])]
+        m = np.ascontiguousarray(seqs[t][: int(lens[t])])
+        N = int(inst["knots_per_segment"]) * int(lens[t])
+        tr = np.zeros(traj_len(N))
+        r = Result()
+        L.orc_solve(ctypes.byref(make_instance(inst)), len(m), _ptr(m, _u8p), N, None, ctypes.byref(o),
+                    _ptr(tr, _dp), None, ctypes.byref(r))
+        work += r.iters * N
+    total = int(L.orc_flop_count())
+    return total / max(work, 1), total, work

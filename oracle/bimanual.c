@@ -58,7 +58,7 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         c[r] = 0.0;
         mask[r] = 1;
         ineq[r] = (r >= 11 && r <= 15) || (r >= 19 && r <= 23) || (r >= 27);
-        scale[r] = 1.0; /* v_hat in the rows' internal units (forces per m g) */
+        scale[r] = 1.0; /* physical = c / scale; set below for rows scaled by m g */
         for (int j = 0; j < NL; ++j) J[r * NL + j] = 0.0;
     }
 #define JJ(r, v) J[(r) * NL + (v)]
@@ -111,6 +111,8 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         JJ(6, j) /= mg;
         JJ(7, j) /= mg * lbar;
     }
+    scale[5] = scale[6] = 1.0 / mg; /* N */
+    scale[7] = 1.0 / (mg * lbar);   /* N m */
     /* ground */
     const double mu = in->mu_g, cg = sqrt(1.0 + mu * mu);
     const double xd = uk[0], zd = uk[1], thd = uk[2], ln = uk[ULN - 5], lt = uk[ULT - 5], pc = uk[UPC - 5];
@@ -131,6 +133,11 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         c[10] = (lt * lt - mu * mu * ln * ln) / (mg * mg);
         JJ(10, ULT) = 2.0 * lt / (mg * mg);
         JJ(10, ULN) = -2.0 * mu * mu * ln / (mg * mg);
+        /* in physical units the row is the friction force's distance from
+         * the cone edge, |lam_t| - mu |lam_n| [N] = c (m g)^2 / (|lam_t| +
+         * mu |lam_n|); both forces zero is on the edge */
+        const double den = fabs(lt) + mu * fabs(ln);
+        scale[10] = den > 0.0 ? den / (mg * mg) : 1.0;
     } else { /* pivot about the lower-left corner: its velocity is zero, the CoP is the corner */
         c[8] = xd - thd * rcz;
         JJ(8, UXD) = 1.0;
@@ -151,14 +158,17 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
         c[12] = (-lt - mu * ln) / (mg * cg);
         JJ(12, ULT) = -1.0 / (mg * cg);
         JJ(12, ULN) = -mu / (mg * cg);
+        scale[11] = scale[12] = 1.0 / (mg * cg); /* N */
     } else { /* slide: friction opposes the motion, lam_t xd <= 0 */
         c[11] = lt * xd / mg;
         JJ(11, ULT) = xd / mg;
         JJ(11, UXD) = lt / mg;
+        scale[11] = 1.0 / mg; /* W (the friction force's power) */
         mask[12] = 0;
     }
     c[13] = -ln / mg;
     JJ(13, ULN) = -1.0 / mg;
+    scale[13] = 1.0 / mg; /* N */
     if (g != 2) { /* CoP within the support half-width w(theta) */
         c[14] = pc - w;
         JJ(14, UPC) = 1.0;
@@ -183,6 +193,7 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
             JJ(b + 1, uft) = 1.0 / mg;
             c[b + 2] = sd;
             JJ(b + 2, usd) = 1.0;
+            scale[b] = scale[b + 1] = 1.0 / mg; /* N */
             for (int r = b + 3; r < b + 8; ++r) mask[r] = 0;
             continue;
         }
@@ -199,17 +210,20 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
             c[b + 4] = (-ft - muh * fn) / (mg * ch);
             JJ(b + 4, uft) = -1.0 / (mg * ch);
             JJ(b + 4, ufn) = -muh / (mg * ch);
+            scale[b + 3] = scale[b + 4] = 1.0 / (mg * ch); /* N */
         } else {
             const double sg = (kind == 1) ? -1.0 : 1.0; /* slide+: ft - mu fn = 0, sd >= 0 */
             c[b] = (ft + sg * muh * fn) / (mg * ch);
             JJ(b, uft) = 1.0 / (mg * ch);
             JJ(b, ufn) = sg * muh / (mg * ch);
+            scale[b] = 1.0 / (mg * ch); /* N */
             c[b + 3] = sg * sd;
             JJ(b + 3, usd) = sg;
             mask[b + 4] = 0;
         }
         c[b + 5] = -fn / mg;
         JJ(b + 5, ufn) = -1.0 / mg;
+        scale[b + 5] = 1.0 / mg; /* N */
         c[b + 6] = s - ell;
         JJ(b + 6, vs) = 1.0;
         c[b + 7] = -s - ell;
@@ -565,12 +579,19 @@ static void measures(const bim_instance* in, int32_t len, const uint16_t* modes,
 
 int32_t bim_solve(const bim_instance* in, int32_t len, const uint16_t* modes, int32_t N, const double* warm,
                   const orc_opts* opt, double* out_traj, double* out_lam, orc_result* res) {
+    return bim_solve_ex(in, len, modes, N, warm, NULL, opt, out_traj, out_lam, res);
+}
+
+int32_t bim_solve_ex(const bim_instance* in, int32_t len, const uint16_t* modes, int32_t N, const double* warm,
+                     const double* warm_lam, const orc_opts* opt, double* out_traj, double* out_lam,
+                     orc_result* res) {
     const int64_t nt = (int64_t)(NX + NU) * N + NX, nl = 3 + (int64_t)NR * N;
     double* z = (double*)malloc(sizeof(double) * nt);
     double* zt = (double*)malloc(sizeof(double) * nt);
     double* dz = (double*)malloc(sizeof(double) * nt);
     double* grad = (double*)malloc(sizeof(double) * nt);
     double* lam = (double*)calloc((size_t)nl, sizeof(double));
+    if (warm_lam) memcpy(lam, warm_lam, sizeof(double) * nl);
     double* y = (double*)malloc(sizeof(double) * nl);
     if (warm)
         memcpy(z, warm, sizeof(double) * nt);
@@ -585,8 +606,12 @@ int32_t bim_solve(const bim_instance* in, int32_t len, const uint16_t* modes, in
             status = ORC_NONFINITE;
             break;
         }
-        const double eps_d = opt->eps_dual * fmax(1.0, beta / opt->beta_ref);
-        if (m.viol <= opt->eps_primal && m.stat <= eps_d && m.comp <= opt->eps_comp) {
+        /* stop test as in orc_solve: scaled rows within eps_primal, rows in
+         * physical units within half eps_feas, stationarity relative to
+         * max(1, |J|) (Sec. III-C "Stopping and scoring") */
+        const double eps_d = orc_stat_tol(opt, beta, bim_cost(in, N, z));
+        if (m.viol <= opt->eps_primal && m.vphys <= 0.5 * opt->eps_feas && m.stat <= eps_d &&
+            m.comp <= opt->eps_comp) {
             memcpy(lam, y, sizeof(double) * nl);
             status = ORC_CONVERGED;
             break;
@@ -670,6 +695,11 @@ typedef struct {
     const orc_opts* opt;
     double* out_traj;
     int64_t traj_stride;
+    const double* warm;
+    int64_t warm_stride;
+    double* out_lam;
+    int64_t lam_stride;
+    const double* warm_lam;
     orc_result* res;
     int64_t next;
     pthread_mutex_t lock;
@@ -683,8 +713,11 @@ static void* bworker(void* arg) {
         pthread_mutex_unlock(&b->lock);
         if (i >= b->n) break;
         double* tr = b->out_traj ? b->out_traj + i * b->traj_stride : NULL;
-        bim_solve(&b->insts[b->inst_idx[i]], b->lens[i], b->modes + i * b->lmax, b->Ns[i], NULL, b->opt, tr, NULL,
-                  &b->res[i]);
+        const double* w = b->warm ? b->warm + i * b->warm_stride : NULL;
+        double* lam = b->out_lam ? b->out_lam + i * b->lam_stride : NULL;
+        const double* wl = b->warm_lam ? b->warm_lam + i * b->lam_stride : NULL;
+        bim_solve_ex(&b->insts[b->inst_idx[i]], b->lens[i], b->modes + i * b->lmax, b->Ns[i], w, wl, b->opt, tr,
+                     lam, &b->res[i]);
     }
     return NULL;
 }
@@ -692,7 +725,21 @@ static void* bworker(void* arg) {
 int32_t bim_solve_batch(const bim_instance* insts, const int32_t* inst_idx, const int32_t* lens,
                         const uint16_t* modes, int32_t lmax, const int32_t* Ns, int64_t n, const orc_opts* opt,
                         int32_t nthreads, double* out_traj, int64_t traj_stride, orc_result* res) {
+    return bim_solve_batch_ex(insts, inst_idx, lens, modes, lmax, Ns, n, opt, nthreads, NULL, 0, NULL, out_traj,
+                              traj_stride, NULL, 0, res);
+}
+
+int32_t bim_solve_batch_ex(const bim_instance* insts, const int32_t* inst_idx, const int32_t* lens,
+                           const uint16_t* modes, int32_t lmax, const int32_t* Ns, int64_t n, const orc_opts* opt,
+                           int32_t nthreads, const double* warm, int64_t warm_stride, const double* warm_lam,
+                           double* out_traj, int64_t traj_stride, double* out_lam, int64_t lam_stride,
+                           orc_result* res) {
     bctx b;
+    b.warm_lam = warm_lam;
+    b.warm = warm;
+    b.warm_stride = warm_stride;
+    b.out_lam = out_lam;
+    b.lam_stride = lam_stride;
     b.insts = insts;
     b.inst_idx = inst_idx;
     b.lens = lens;

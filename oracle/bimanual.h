@@ -32,10 +32,14 @@
  *   8..10 ground equalities, 11..15 ground inequalities
  *   16..18 hand L equalities, 19..23 hand L inequalities
  *   24..26 hand R equalities, 27..31 hand R inequalities
- * plus 3 initial-pose rows.  The violation v_hat (Eq. inexact_mode_value) is
- * taken in the rows' internal units: lengths in m, velocities in m/s, forces
- * relative to the weight m g, the torque relative to m g l (every scale
- * factor is 1).  Cost: w_T |pose_N - goal|^2 + sum_k u_k^T R u_k
+ * plus 3 initial-pose rows.  Internally the force rows are divided by m g
+ * and the torque row by m g l (l the larger half-side); the violation v_hat
+ * (Eq. inexact_mode_value) is taken in physical units, separately from that
+ * scaling (Sec. III-C "Stopping and scoring"): lengths in m, angles in rad,
+ * velocities in m/s, forces in N, the torque in N m, the slide-direction row
+ * as the friction force's power in W, and the slide friction row (internally
+ * (lam_t^2 - mu^2 lam_n^2) / (m g)^2) as the friction force's distance from
+ * the cone edge, |lam_t| - mu |lam_n| in N.  Cost: w_T |pose_N - goal|^2 + sum_k u_k^T R u_k
  * with R = diag(w_v (twist), w_f (forces), w_s (sliding rates), w_c (p_c)).
  */
 #ifndef COMET_BIMANUAL_ORACLE_H
@@ -105,6 +109,21 @@ int32_t bim_solve(const bim_instance* in, int32_t len, const uint16_t* modes, in
 int32_t bim_solve_batch(const bim_instance* insts, const int32_t* inst_idx, const int32_t* lens,
                         const uint16_t* modes, int32_t lmax, const int32_t* Ns, int64_t n, const orc_opts* opt,
                         int32_t nthreads, double* out_traj, int64_t traj_stride, orc_result* res);
+
+/* bim_solve_batch with optional warm starts (TO i from the trajectory at
+ * warm + i * warm_stride, in its own N, and from the multipliers at
+ * warm_lam + i * lam_stride) and optional multipliers out (3 + 32 N at
+ * out_lam + i * lam_stride). */
+int32_t bim_solve_batch_ex(const bim_instance* insts, const int32_t* inst_idx, const int32_t* lens,
+                           const uint16_t* modes, int32_t lmax, const int32_t* Ns, int64_t n, const orc_opts* opt,
+                           int32_t nthreads, const double* warm, int64_t warm_stride, const double* warm_lam,
+                           double* out_traj, int64_t traj_stride, double* out_lam, int64_t lam_stride,
+                           orc_result* res);
+
+/* bim_solve starting from the multipliers warm_lam (3 + 32 N; NULL = 0). */
+int32_t bim_solve_ex(const bim_instance* in, int32_t len, const uint16_t* modes, int32_t N, const double* warm,
+                     const double* warm_lam, const orc_opts* opt, double* out_traj, double* out_lam,
+                     orc_result* res);
 
 #ifdef __cplusplus
 }

@@ -31,6 +31,44 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Flop counter (compiled in with -DORC_COUNT_FLOPS, a separate build used
+ * to measure the method's arithmetic per stage and iteration).  It counts
+ * the floating-point operations of the method's steps: one per add,
+ * multiply, divide, square root, sine or cosine; products with structurally
+ * zero Jacobian entries are not counted, and the symmetric local model is
+ * counted on its lower triangle.  Work that only this plain implementation
+ * repeats (the constant row scales, dense zero fills) is not counted. */
+#ifdef ORC_COUNT_FLOPS
+static __thread uint64_t g_flops;
+/* what a row evaluation counts: values (trial merits need only these) and
+ * Jacobians; the step re-evaluates the rows the measures have just taken at
+ * the same point, which the method does once */
+static __thread int g_rows_on = 1, g_jac_on = 1;
+#define FLOPS(n) (g_flops += (uint64_t)(n))
+#define FLOPS_ROWS(n) (g_flops += g_rows_on ? (uint64_t)(n) : 0)
+#define FLOPS_JAC(n) (g_flops += g_jac_on ? (uint64_t)(n) : 0)
+#define COUNT_ROWS(r, j) (g_rows_on = (r), g_jac_on = (j))
+#else
+#define FLOPS(n) ((void)0)
+#define FLOPS_ROWS(n) ((void)0)
+#define FLOPS_JAC(n) ((void)0)
+#define COUNT_ROWS(r, j) ((void)0)
+#endif
+
+uint64_t orc_flop_count(void) {
+#ifdef ORC_COUNT_FLOPS
+    return g_flops;
+#else
+    return 0;
+#endif
+}
+
+void orc_flop_reset(void) {
+#ifdef ORC_COUNT_FLOPS
+    g_flops = 0;
+#endif
+}
+
 /* ---------------------------------------------------------------- model */
 
 /* Face f of the rectangular slider: inward push direction n_f in the body
@@ -67,6 +105,10 @@ void orc_dynamics(const orc_instance* in, int32_t face, const double* x, const d
     /* ellipsoidal limit surface H(w) = Fx^2 + Fy^2 + mz^2/c^2: twist ~ grad H */
     const double vx = k * Fbx, vy = k * Fby, w = k * mz / c2;
     const double ct = cos(th), st = sin(th);
+    FLOPS_ROWS(3 + 3 + 3 + 4 + 2); /* body wrench, twist, sine and cosine */
+    if (f) FLOPS_ROWS(6);
+    if (Fx) FLOPS_JAC(6 + 2);
+    if (Fu) FLOPS_JAC(16);
     if (f) {
         f[0] = ct * vx - st * vy;
         f[1] = st * vx + ct * vy;
@@ -107,6 +149,7 @@ static void dynamics_curvature(const orc_instance* in, int32_t face, const doubl
     const double vx = k * (fn * n[0] + ft * t[0]);
     const double vy = k * (fn * n[1] + ft * t[1]);
     const double f0 = ct * vx - st * vy, f1 = st * vx + ct * vy;
+    FLOPS(2 + 6 + 6 + 3 + 10 + 10 + 2);
     for (int i = 0; i < 49; ++i) Hf[i] = 0.0;
     Hf[2 * 7 + 2] = -y[0] * f0 - y[1] * f1;
     const double h_th_fn = y[0] * k * (-st * n[0] - ct * n[1]) + y[1] * k * (ct * n[0] - st * n[1]);
@@ -187,6 +230,8 @@ static void free_rows(const orc_instance* in, int32_t s_row_masked, const double
         scale[i] = 1.0 / sg;
     }
     J[3 * 11 + 6] = -in->dt / dyn_row_scale(in, 3);
+    FLOPS_ROWS(4 * 3);
+    FLOPS_JAC(1);
     if (s_row_masked) mask[3] = 0;
     c[4] = uk[0];
     J[4 * 11 + 4] = 1.0;
@@ -230,6 +275,11 @@ static void interval_rows(const orc_instance* in, int32_t mode, int32_t s_row_ma
         J[i * 11 + 7 + i] = 1.0 / sg;
         scale[i] = 1.0 / sg;
     }
+    /* defects (3 each), the nonzero Jacobian entries (x_k: diagonal and the
+     * three terms of d f / d x; u_k: seven entries of d f / d u), the mode
+     * rows' values */
+    FLOPS_ROWS(4 * 3 + 18);
+    FLOPS_JAC(4 + 3 * 2 + 7 * 2);
     if (s_row_masked) mask[3] = 0;
     /* mode equality (row 4) */
     if (kind == 0) {
@@ -354,6 +404,7 @@ static double row_al(int32_t is_ineq, double lam, double beta, double c) {
 
 static double cost_of(const orc_instance* in, int32_t N, const double* tr) {
     double J = 0.0;
+    FLOPS(3 * 4 + 3 * (int64_t)N * 3);
     for (int i = 0; i < 3; ++i) {
         const double e = CX(tr, N, N, i) - in->goal[i];
         J += in->w_terminal * e * e;
@@ -374,13 +425,18 @@ double orc_al_merit(const orc_instance* in, int32_t len, const uint8_t* modes, i
     for (int i = 0; i < 3; ++i) L += row_al(0, lam[i], beta, CX(traj, N, 0, i) - in->start[i]);
     double xk[4], uk[3], xk1[4], cc[11], sc[11], Jl[121];
     uint8_t mk[11];
+    COUNT_ROWS(1, 0);
     for (int32_t k = 0; k < N; ++k) {
         load_local(traj, N, k, xk, uk, xk1);
         interval_rows(in, mode_of_interval(modes, len, N, k), s_row_masked(modes, len, N, k),
                       xk, uk, xk1, cc, mk, sc, Jl);
         for (int r = 0; r < 11; ++r)
-            if (mk[r]) L += row_al(r >= ORC_NEQ, lam[3 + 11 * k + r], beta, cc[r]);
+            if (mk[r]) {
+                L += row_al(r >= ORC_NEQ, lam[3 + 11 * k + r], beta, cc[r]);
+                FLOPS(6);
+            }
     }
+    COUNT_ROWS(1, 1);
     return L;
 }
 
@@ -391,6 +447,7 @@ static int chol(int n, const double* A, double* L) {
     for (int j = 0; j < n; ++j) {
         double d = A[j * n + j];
         for (int p = 0; p < j; ++p) d -= L[j * n + p] * L[j * n + p];
+        FLOPS(2 * j + 1 + (n - 1 - j) * (2 * j + 1));
         if (!(d > 0.0)) return -1;
         const double ljj = sqrt(d);
         L[j * n + j] = ljj;
@@ -406,6 +463,7 @@ static int chol(int n, const double* A, double* L) {
 /* x = A^{-1} b with A = L L^T (forward then backward substitution). */
 static void chol_solve(int n, const double* L, const double* b, double* x) {
     double y[16];
+    FLOPS(2 * n * n);
     for (int i = 0; i < n; ++i) {
         double s = b[i];
         for (int p = 0; p < i; ++p) s -= L[i * n + p] * y[p];
@@ -438,6 +496,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
     double xk[4], uk[3], xk1[4], cc[11], sc[11], Jl[121];
     uint8_t mk[11];
     int32_t ok = 0;
+    COUNT_ROWS(0, 0);
     for (int32_t k = N - 1; k >= 0; --k) {
         load_local(traj, N, k, xk, uk, xk1);
         interval_rows(in, mode_of_interval(modes, len, N, k), s_row_masked(modes, len, N, k),
@@ -447,6 +506,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
          * g = cost gradient + sum y_r a_r.  Without the curvature term S_k
          * is positive definite for any rho > 0 (Gauss-Newton). */
         double H[121] = {0}, g[11] = {0};
+        FLOPS(3 * 3);
         for (int j = 0; j < 3; ++j) {
             H[(4 + j) * 11 + 4 + j] += 2.0 * in->w_control;
             g[4 + j] += 2.0 * in->w_control * uk[j];
@@ -457,6 +517,15 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
             const double l = lam[3 + 11 * k + r];
             if (ineq && !(l + beta * cc[r] > 0.0)) continue; /* inactive */
             const double y = row_y(ineq, l, beta, cc[r]);
+#ifdef ORC_COUNT_FLOPS
+            {
+                /* y, then per nonzero entry: g (2), beta a_i (1) and the
+                 * lower-triangle products of the model (2 each) */
+                int nnz = 0;
+                for (int i = 0; i < 11; ++i) nnz += Jl[r * 11 + i] != 0.0;
+                FLOPS(2 + 3 * nnz + nnz * (nnz + 1));
+            }
+#endif
             for (int i = 0; i < 11; ++i) {
                 g[i] += y * Jl[r * 11 + i];
                 for (int j = 0; j < 11; ++j) H[i * 11 + j] += beta * Jl[r * 11 + i] * Jl[r * 11 + j];
@@ -471,6 +540,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
             const int32_t mk_k = mode_of_interval(modes, len, N, k);
             if (mk_k != ORC_MODE_FREE) {  /* free motion: f is linear, no curvature */
                 dynamics_curvature(in, mk_k / 3, xk, uk, yd, Hf);
+                FLOPS(4 * 3 + 4 * 2); /* yd, and the four curvature entries into H */
                 for (int i = 0; i < 7; ++i)
                     for (int j = 0; j < 7; ++j) H[i * 11 + j] -= in->dt * Hf[i * 7 + j];
             }
@@ -491,6 +561,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
             for (int j = 0; j < 4; ++j) S[(3 + i) * 7 + 3 + j] += V[i * 4 + j];
             gw[3 + i] += v[i];
         }
+        FLOPS(7 + 10 + 4); /* rho, V_{k+1} (lower triangle), v_{k+1} */
         if (chol(7, S, L) != 0) {
             ok = -1;
             break;
@@ -505,6 +576,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
         chol_solve(7, L, gw, sol);
         for (int i = 0; i < 7; ++i) kg[7 * (int64_t)k + i] = -sol[i];
         /* V_k = H_xx - C^T S^-1 C = H_xx + C^T K_k ;  v_k = g_x + C^T k_k */
+        FLOPS(10 * 7 * 2 + 4 * 7 * 2); /* symmetric V (lower triangle) and v */
         double Vn[16], vn[4];
         for (int i = 0; i < 4; ++i) {
             for (int j = 0; j < 4; ++j) {
@@ -541,6 +613,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
             for (int i = 0; i < 4; ++i) dx[i] = -dx[i];
             /* forward pass: dw_k = K_k dx_k + k_k */
             for (int i = 0; i < 4; ++i) dz[i] = dx[i];
+            FLOPS((int64_t)N * 7 * 8);
             for (int32_t k = 0; k < N; ++k) {
                 double dw[7];
                 for (int i = 0; i < 7; ++i) {
@@ -556,6 +629,7 @@ int32_t orc_gn_step(const orc_instance* in, int32_t len, const uint8_t* modes, i
             }
         }
     }
+    COUNT_ROWS(1, 1);
     free(Kg);
     free(kg);
     return ok;
@@ -587,8 +661,13 @@ void orc_default_opts(orc_opts* o) {
     o->curv_skip = 3;
 }
 
+double orc_stat_tol(const orc_opts* opt, double beta, double cost) {
+    return opt->eps_dual * fmax(1.0, beta / opt->beta_ref) * fmax(1.0, fabs(cost));
+}
+
 /* add alpha * dz (interleaved) to a component-major trajectory */
 static void axpy_traj(int32_t N, const double* tr, double alpha, const double* dz, double* out) {
+    FLOPS(2 * (7 * (int64_t)N + 4));
     for (int32_t k = 0; k <= N; ++k)
         for (int i = 0; i < 4; ++i) out[i * (N + 1) + k] = CX(tr, N, k, i) + alpha * dz[7 * (int64_t)k + i];
     for (int32_t k = 0; k < N; ++k)
@@ -647,8 +726,15 @@ static void measures(const orc_instance* in, int32_t len, const uint8_t* modes, 
             if (v > m->viol) m->viol = v;
             if (v / sc[r] > m->vphys) m->vphys = v / sc[r];
             if (ineq && fabs(yr * cc[r]) > m->comp) m->comp = fabs(yr * cc[r]);
-            if (yr != 0.0)
+            FLOPS(2 + 2 + 2); /* y, the violation in both units, complementarity */
+            if (yr != 0.0) {
+#ifdef ORC_COUNT_FLOPS
+                int nnz = 0;
+                for (int i = 0; i < 11; ++i) nnz += Jl[r * 11 + i] != 0.0;
+                FLOPS(2 * nnz);
+#endif
                 for (int i = 0; i < 11; ++i) grad[7 * (int64_t)k + i] += yr * Jl[r * 11 + i];
+            }
         }
     }
     m->stat = 0.0;
@@ -661,12 +747,19 @@ static void measures(const orc_instance* in, int32_t len, const uint8_t* modes, 
 int32_t orc_solve(const orc_instance* in, int32_t len, const uint8_t* modes, int32_t N,
                   const double* warm, const orc_opts* opt,
                   double* out_traj, double* out_lam, orc_result* res) {
+    return orc_solve_ex(in, len, modes, N, warm, NULL, opt, out_traj, out_lam, res);
+}
+
+int32_t orc_solve_ex(const orc_instance* in, int32_t len, const uint8_t* modes, int32_t N, const double* warm,
+                     const double* warm_lam, const orc_opts* opt, double* out_traj, double* out_lam,
+                     orc_result* res) {
     const int64_t nt = 7 * (int64_t)N + 4, nl = 3 + 11 * (int64_t)N;
     double* z = (double*)malloc(sizeof(double) * nt);
     double* zt = (double*)malloc(sizeof(double) * nt);
     double* dz = (double*)malloc(sizeof(double) * nt);
     double* grad = (double*)malloc(sizeof(double) * nt);
     double* lam = (double*)calloc((size_t)nl, sizeof(double));
+    if (warm_lam) memcpy(lam, warm_lam, sizeof(double) * nl);
     double* y = (double*)malloc(sizeof(double) * nl);
     if (warm)
         memcpy(z, warm, sizeof(double) * nt);
@@ -682,9 +775,16 @@ int32_t orc_solve(const orc_instance* in, int32_t len, const uint8_t* modes, int
             status = ORC_NONFINITE;
             break;
         }
-        /* stop test (Sec. III-C "Stopping and scoring"): KKT of (z, y) */
-        const double eps_d = opt->eps_dual * fmax(1.0, beta / opt->beta_ref);
-        if (m.viol <= opt->eps_primal && m.stat <= eps_d && m.comp <= opt->eps_comp) {
+        /* stop test (Sec. III-C "Stopping and scoring"): KKT of (z, y) on
+         * the scaled problem.  Row scaling leaves grad L unchanged, so the
+         * stationarity tolerance is taken relative to the objective's size,
+         * max(1, |J|); the primal part asks for the scaled rows within
+         * eps_primal and the rows in physical units within half eps_feas,
+         * so that a converged TO is feasible by the score (Eq.
+         * inexact_mode_value) */
+        const double eps_d = orc_stat_tol(opt, beta, cost_of(in, N, z));
+        if (m.viol <= opt->eps_primal && m.vphys <= 0.5 * opt->eps_feas && m.stat <= eps_d &&
+            m.comp <= opt->eps_comp) {
             memcpy(lam, y, sizeof(double) * nl);
             status = ORC_CONVERGED;
             break;
@@ -731,6 +831,7 @@ int32_t orc_solve(const orc_instance* in, int32_t len, const uint8_t* modes, int
          * satisfying the Armijo condition */
         double D = 0.0;
         for (int64_t i = 0; i < nt; ++i) D += grad[i] * dz[i];
+        FLOPS(2 * nt);
         const double phi0 = orc_al_merit(in, len, modes, N, z, lam, beta, NULL);
         /* when the predicted decrease is below the merit's resolution
          * (|D| <= ls_slack |phi0|) the merit cannot rank the trials: the full
@@ -794,6 +895,11 @@ typedef struct {
     const orc_opts* opt;
     double* out_traj;
     int64_t traj_stride;
+    const double* warm;
+    int64_t warm_stride;
+    double* out_lam;
+    int64_t lam_stride;
+    const double* warm_lam;
     orc_result* res;
     int64_t next;
     pthread_mutex_t lock;
@@ -808,8 +914,11 @@ static void* batch_worker(void* arg) {
         if (i >= b->n) break;
         const int32_t N = b->Ns[i];
         double* tr = b->out_traj ? b->out_traj + i * b->traj_stride : NULL;
-        orc_solve(&b->insts[b->inst_idx[i]], b->lens[i], b->modes + i * b->lmax, N, NULL, b->opt,
-                  tr, NULL, &b->res[i]);
+        const double* w = b->warm ? b->warm + i * b->warm_stride : NULL;
+        double* lam = b->out_lam ? b->out_lam + i * b->lam_stride : NULL;
+        const double* wl = b->warm_lam ? b->warm_lam + i * b->lam_stride : NULL;
+        orc_solve_ex(&b->insts[b->inst_idx[i]], b->lens[i], b->modes + i * b->lmax, N, w, wl, b->opt,
+                     tr, lam, &b->res[i]);
     }
     return NULL;
 }
@@ -818,7 +927,21 @@ int32_t orc_solve_batch(const orc_instance* insts, const int32_t* inst_idx,
                         const int32_t* lens, const uint8_t* modes, int32_t lmax,
                         const int32_t* Ns, int64_t n, const orc_opts* opt, int32_t nthreads,
                         double* out_traj, int64_t traj_stride, orc_result* res) {
+    return orc_solve_batch_ex(insts, inst_idx, lens, modes, lmax, Ns, n, opt, nthreads, NULL, 0, NULL, out_traj,
+                              traj_stride, NULL, 0, res);
+}
+
+int32_t orc_solve_batch_ex(const orc_instance* insts, const int32_t* inst_idx, const int32_t* lens,
+                           const uint8_t* modes, int32_t lmax, const int32_t* Ns, int64_t n, const orc_opts* opt,
+                           int32_t nthreads, const double* warm, int64_t warm_stride, const double* warm_lam,
+                           double* out_traj, int64_t traj_stride, double* out_lam, int64_t lam_stride,
+                           orc_result* res) {
     batch_ctx b;
+    b.warm_lam = warm_lam;
+    b.warm = warm;
+    b.warm_stride = warm_stride;
+    b.out_lam = out_lam;
+    b.lam_stride = lam_stride;
     b.insts = insts;
     b.inst_idx = inst_idx;
     b.lens = lens;

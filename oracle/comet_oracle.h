@@ -70,7 +70,7 @@ typedef struct {
     double eta_ratio;         /* penalty grows if viol > eta_ratio * previous outer viol */
     double eps_feas;          /* feasibility tolerance for v_hat */
     double merit_mu;          /* mu of Eq. search_merit */
-    double beta_ref;          /* stationarity tolerance eps_dual * max(1, beta / beta_ref) */
+    double beta_ref;          /* stationarity tolerance eps_dual * max(1, beta / beta_ref) * max(1, |J|) */
     int32_t curv_skip;        /* after an indefinite Newton model, iterations that use Gauss-Newton only (3) */
     int32_t pad1;
 } orc_opts;
@@ -94,6 +94,21 @@ typedef struct {
 } orc_result;
 
 void orc_default_opts(orc_opts* o);
+
+/* Floating-point operations of the method counted on the calling thread
+ * since the last reset (the counting build, -DORC_COUNT_FLOPS, only; 0
+ * otherwise).  See comet_oracle.c for what is counted. */
+uint64_t orc_flop_count(void);
+void orc_flop_reset(void);
+
+/* Stationarity tolerance of the stop test at penalty beta and objective
+ * value `cost`: eps_dual * max(1, beta / beta_ref) * max(1, |cost|).  The
+ * paper stops on scaled feasibility, stationarity and dual-residual
+ * tolerances (Sec. III-C "Stopping and scoring"); row scaling leaves the
+ * Lagrangian gradient unchanged, so the scaling read here is the
+ * objective's: the test is relative to max(1, |J|).  The beta factor keeps
+ * the test reachable in FP32 at large penalties. */
+double orc_stat_tol(const orc_opts* opt, double beta, double cost);
 
 /* Continuous dynamics f(x,u) of the quasi-static pusher-slider on `face`
  * and its Jacobians (row-major Fx[4][4], Fu[4][3]); any output may be NULL. */
@@ -148,6 +163,21 @@ int32_t orc_solve_batch(const orc_instance* insts, const int32_t* inst_idx,
                         const int32_t* lens, const uint8_t* modes, int32_t lmax,
                         const int32_t* Ns, int64_t n, const orc_opts* opt, int32_t nthreads,
                         double* out_traj, int64_t traj_stride, orc_result* res);
+
+/* orc_solve_batch with optional warm starts (TO i starts from the
+ * component-major trajectory at warm + i * warm_stride, in its own N, and
+ * from the multipliers at warm_lam + i * lam_stride) and optional
+ * multipliers out (3 + 11 N at out_lam + i * lam_stride). */
+int32_t orc_solve_batch_ex(const orc_instance* insts, const int32_t* inst_idx, const int32_t* lens,
+                           const uint8_t* modes, int32_t lmax, const int32_t* Ns, int64_t n, const orc_opts* opt,
+                           int32_t nthreads, const double* warm, int64_t warm_stride, const double* warm_lam,
+                           double* out_traj, int64_t traj_stride, double* out_lam, int64_t lam_stride,
+                           orc_result* res);
+
+/* orc_solve starting from the multipliers warm_lam (3 + 11 N; NULL = 0). */
+int32_t orc_solve_ex(const orc_instance* in, int32_t len, const uint8_t* modes, int32_t N, const double* warm,
+                     const double* warm_lam, const orc_opts* opt, double* out_traj, double* out_lam,
+                     orc_result* res);
 
 #ifdef __cplusplus
 }

@@ -496,8 +496,12 @@ def solve(inst, modes, N=None, timing=None, warm=None, **over):
         if not m["finite"]:
             status = NONFINITE
             break
-        eps_d = o["eps_dual"] * max(1.0, beta / o["beta_ref"])
-        if m["viol"] <= o["eps_primal"] and m["stat"] <= eps_d and m["comp"] <= o["eps_comp"]:
+        # stop test of Sec. III-C as in the C oracle: stationarity relative to
+        # max(1, |J|), scaled rows within eps_primal, physical rows within
+        # half eps_feas
+        eps_d = o["eps_dual"] * max(1.0, beta / o["beta_ref"]) * max(1.0, abs(P.cost(z)))
+        if (m["viol"] <= o["eps_primal"] and m["vphys"] <= 0.5 * o["eps_feas"] and m["stat"] <= eps_d
+                and m["comp"] <= o["eps_comp"]):
             lam = y.copy()
             status = CONVERGED
             break
