@@ -41,11 +41,13 @@ UNIT = "solves/s"
 N_INSTANCES = 64
 SEG, K = 4, 20
 N_STAGES = SEG * K
-# algorithmic FP32 flops of one solver iteration per stage (dense count of
-# the method's steps: derivatives 60, row assembly and beta A^T A 1450,
-# 7x7 Cholesky 230, gains with 5 right-hand sides 490, Schur update 230,
-# forward pass 70, 8-trial line search 800)
-FLOP_PER_STAGE_ITER = 3330
+# the method's floating-point operations per stage and solver iteration on
+# this workload, counted by the oracle's counting build over a seeded sample
+# (python -m oracle.flop_count; tests/test_flop_count.py re-measures it):
+# rows and Jacobians once per iteration, the local model on its nonzero
+# pattern, the 7x7 factorisation and solves, the value function, the
+# forward pass, the sequential trial merits up to the accepted step, retries
+FLOP_PER_STAGE_ITER = 3688.7
 # DRAM bytes (read + write) of one evaluator launch over the 20,736 orders
 # from an ncu capture of the current kernel, scaled by the TOs processed;
 # None while the kernel has changed since the last capture.  That capture
@@ -54,8 +56,26 @@ FLOP_PER_STAGE_ITER = 3330
 # predates the double-float theta row and the compensated trial merits.
 EVAL_TRAFFIC_BYTES = None
 EVAL_TRAFFIC_LAST_CAPTURE = (2.24128e6 + 3.516693e9) * 20736 / 4096
-# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# nominal FP32 FMA rate at the maximum clock (152 SMs x 128 lanes x 2 flop x
+# 2070 MHz), context only: the roofline's peak is measured at run time by the
+# library's FMA microbenchmark (comet_fp32_fma_peak)
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def measure_fp32_peak(P, stream):
+    """Best of five runs of the FMA microbenchmark (about 10 ms each) on the
+    bench's stream, with the SM clock sampled around it."""
+    import torch
+
+    scratch = torch.empty(P.comet_fp32_fma_peak_threads(), dtype=torch.float32, device="cuda")
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    runs = [P.comet_fp32_fma_peak(stream.cuda_stream, 6000, scratch) for _ in range(5)]
+    c = clk.stop()
+    best = max(runs)
+    return {"tflops": best[0], "ms": best[1], "runs_tflops": [r[0] for r in runs], "sm_mhz": c.get("sm_mhz"),
+            "how": "comet_fp32_fma_peak: 8 independent fmaf chains per thread, whole waves of 256-thread "
+                   "blocks, CUDA events, best of 5"}
 
 
 def rank_env():
@@ -264,14 +284,15 @@ def run_gpu(args):
     clk = clocks.stop()
     value = conv_total / t_dev
 
-    # e2e: the C ABI with host buffers (orders in, cost/status out), copies inside
+    # e2e: the C ABI with host buffers (orders in, cost/status out), copies
+    # inside, over as many steps as the timed region
     host_seqs = packed
     h_cost = np.zeros(n, np.float32)
     h_status = np.zeros(n, np.int32)
     h_viol = np.zeros(n, np.float32)
     t0 = time.time()
     e2e_conv = 0
-    e2e_steps = max(1, min(args.steps, 4))
+    e2e_steps = max(1, args.steps)
     for s in range(e2e_steps):
         pr = probs[(args.warmup + s) % len(probs)]
         P.comet_eval_modes(pr.handle, host_seqs, n, None, h_cost, None, h_status)
@@ -282,6 +303,7 @@ def run_gpu(args):
 
     flops = FLOP_PER_STAGE_ITER * N_STAGES * iter_total
     achieved = flops / t_dev / 1e12
+    peak = measure_fp32_peak(P, stream)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -296,10 +318,12 @@ def run_gpu(args):
         # per step: the longest-first ordering (hist, scan, scatter kernels;
         # the problem holds orders of up to 4 segments) and the evaluator
         "gpu_launches": 4 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": EVAL_TRAFFIC_BYTES,
-                     "note": "achieved = 3330 flop x 80 stages x solver iterations / device time; peak = FP32 "
-                             "FMA rate at 2070 MHz (152 SMs x 128 lanes)",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peak["tflops"], "traffic": EVAL_TRAFFIC_BYTES,
+                     "peak_measured": peak, "nominal_tflops": FP32_NOMINAL_TFLOPS,
+                     "note": f"achieved = {FLOP_PER_STAGE_ITER} flop (the oracle's count of the method per "
+                             "stage and iteration) x 80 stages x solver iterations / device time; peak = "
+                             "measured FP32 FMA rate (of measured)",
                      "traffic_note": ("null: the kernel changed after its last ncu capture (arithmetic only: "
                                       "theta row in double-float, compensated trial merits); that capture "
                                       f"measured {EVAL_TRAFFIC_LAST_CAPTURE / 1e9:.1f} GB per launch")

@@ -102,8 +102,10 @@ typedef struct {
     int32_t max_iters;       /* exploration budget t_exp (default 300) */
     int32_t ref_iters;       /* refinement budget t_ref (default 1500) */
     double eps_feas;         /* feasibility tolerance on v_hat (1e-5) */
-    double eps_primal;       /* scaled primal tolerance of the stop test (1e-6) */
-    double eps_dual;         /* stationarity tolerance at beta <= beta_ref (1e-4; 1e-3 for bimanual problems) */
+    double eps_primal;       /* scaled primal tolerance of the stop test (1e-6); the stop test
+                                also holds every row within eps_feas / 2 in physical units */
+    double eps_dual;         /* stationarity tolerance (1e-4), taken relative to the objective:
+                                eps_dual * max(1, beta / beta_ref) * max(1, |J|) */
     double eps_comp;         /* complementarity tolerance (1e-6) */
     double merit_mu;         /* mu of Eq. search_merit (100) */
     double beta0, beta_max, beta_ref; /* penalty 1/mu_AL: start, cap, reference (100, 1e4, 1e3) */
@@ -384,6 +386,24 @@ comet_status comet_sample_orders(comet_problem* p, int32_t instance, uint64_t se
 
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
+
+/* ---- measurement (no paper counterpart) ------------------------------ */
+
+/* FP32 FMA throughput of the current device, the peak of the evaluator's
+ * roofline: one launch of a kernel whose threads each run 8 independent
+ * fmaf chains (a grid of whole waves of resident 256-thread blocks) is timed
+ * with CUDA events on cuda_stream after one untimed launch.  iters >= 1 is
+ * the number of 128-FMA rounds per thread (a few thousand give ~10 ms);
+ * out_scratch is device memory of comet_fp32_fma_peak_threads() floats that
+ * receives one folded value per thread.  *out_tflops = 2 x FMAs / time,
+ * *out_ms (nullable) the kernel time.  Synchronises the stream.  Errors:
+ * INVALID_ARG, CUDA. */
+comet_status comet_fp32_fma_peak(void* cuda_stream, int32_t iters, float* out_scratch, double* out_tflops,
+                                 double* out_ms);
+
+/* Threads of one comet_fp32_fma_peak launch on the current device (the
+ * scratch size in floats), or -1 on a CUDA error. */
+int32_t comet_fp32_fma_peak_threads(void);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* comet_last_error(void);

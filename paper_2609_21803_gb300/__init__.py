@@ -121,7 +121,7 @@ assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == MODE_SEQ_BYTES
 EXPORTS = (
     "comet_default_opts", "comet_problem_create", "comet_problem_destroy", "comet_traj_stride",
     "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_mode_code",
-    "comet_last_error", "comet_eval_modes_noalloc",
+    "comet_last_error", "comet_eval_modes_noalloc", "comet_fp32_fma_peak", "comet_fp32_fma_peak_threads",
     "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
     "comet_frontier_next", "comet_frontier_size", "comet_frontier_best", "comet_frontier_copy_next",
     "comet_default_plan_opts", "comet_plan",
@@ -164,6 +164,10 @@ def lib(build_if_missing: bool = False):
             L.comet_eval_modes.argtypes = [vp, vp, i64, vp, vp, vp, vp]
             L.comet_eval_modes_budget.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp]
             L.comet_eval_stats.argtypes = [vp, vp, vp, vp, vp]
+            L.comet_fp32_fma_peak.argtypes = [vp, i32, vp, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
+            L.comet_fp32_fma_peak_threads.argtypes = []
+            L.comet_fp32_fma_peak_threads.restype = i32
             L.comet_eval_modes_noalloc.argtypes = [ctypes.POINTER(InstanceDesc), i32, ctypes.POINTER(SolverOpts), vp,
                                                    vp, i64, vp, vp, vp, vp]
             L.comet_frontier_create.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(vp)]
@@ -312,6 +316,18 @@ def comet_eval_modes_budget(problem, mode_seqs, n, warm_starts, max_iters, out_c
 
 def comet_eval_stats(problem, out_viol, out_merit, out_iters, out_stat):
     _check(lib().comet_eval_stats(problem, _ptr(out_viol), _ptr(out_merit), _ptr(out_iters), _ptr(out_stat)))
+
+
+def comet_fp32_fma_peak(cuda_stream, iters: int, scratch) -> tuple[float, float]:
+    """Measured FP32 FMA throughput (TFLOP/s) and the kernel time (ms);
+    scratch: device buffer of comet_fp32_fma_peak_threads() floats."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().comet_fp32_fma_peak(cuda_stream, int(iters), _ptr(scratch), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
+
+
+def comet_fp32_fma_peak_threads() -> int:
+    return int(lib().comet_fp32_fma_peak_threads())
 
 
 def comet_eval_modes_noalloc(instances, opts, cuda_stream, mode_seqs, n, warm_starts, out_cost, out_traj,

@@ -391,10 +391,6 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
     p->stream = (cudaStream_t)cuda_stream;
     p->Nmax = Nmax;
     p->task = inst[0].task;
-    // bimanual: the force-balance rows carry FP32 rounding of about 6e-8 of
-    // m g, which the penalty (up to 1e4) lifts to a stationarity floor near
-    // 1e-3 x |J|; the default tolerance there is 1e-3 (overridable)
-    if (p->task == COMET_TASK_BIMANUAL && (!opts || !(opts->eps_dual > 0))) p->opts.eps_dual = 1e-3;
     p->stride = p->task == COMET_TASK_BIMANUAL ? 17 * (int64_t)Nmax + 5 : 7 * (int64_t)Nmax + 4;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);

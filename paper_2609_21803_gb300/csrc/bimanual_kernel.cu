@@ -190,8 +190,10 @@ __device__ void stage_ctx(const BInst<T>& P, int mode, const T* x, const T* u, B
 template <typename T, bool WJ>
 __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool mR, const T* x, const T* u,
                      const T* dx, T& c, T* J, bool& on, bool& ineq, T& scale) {
-    // v_hat is taken in the rows' internal units (forces relative to m g):
-    // every scale factor is 1
+    // internally the force rows are divided by m g and the torque row by
+    // m g l; scale maps a row back to physical units (physical = c / scale:
+    // N, N m, W, m, m/s), as v_hat is scored (Sec. III-C "Stopping and
+    // scoring")
     c = 0;
     on = true;
     ineq = (r >= 11 && r <= 15) || (r >= 19 && r <= 23) || (r >= 27);
@@ -212,6 +214,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
         if ((r == 3 && mL) || (r == 4 && mR)) on = false;
     } else if (r < 8) {
         const T sc = (r == 7) ? 1 / (mg * P.lbar) : 1 / mg;
+        scale = sc;
         if (r == 5) c = S.Fwx * sc;
         if (r == 6) c = (S.Fwz - mg) * sc;
         if (r == 7) c = S.tau * sc;
@@ -287,7 +290,13 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 if (WJ) J[UTHD] = 1;
             } else if (S.g == 1) {
                 const T s2 = 1 / (mg * mg);
-                c = (lt * lt - mu * mu * ln * ln) * s2;
+                // factored, so that the difference near the edge is formed
+                // before the product (no cancellation of two squares)
+                c = ((lt - mu * ln) * (lt + mu * ln)) * s2;
+                // physical: the friction force's distance from the cone
+                // edge, |lam_t| - mu |lam_n| [N]
+                const T den = fabs(lt) + mu * fabs(ln);
+                scale = den > (T)0 ? den * s2 : (T)1;
                 if (WJ) {
                     J[ULT] = 2 * lt * s2;
                     J[ULN] = -2 * mu * mu * ln * s2;
@@ -302,6 +311,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
         } else if (r == 11 || r == 12) {
             if (S.g != 1) {
                 const T sc = 1 / (mg * P.cg), sg = (r == 11) ? (T)1 : (T)-1;
+                scale = sc;
                 c = (sg * lt - mu * ln) * sc;
                 if (WJ) {
                     J[ULT] = sg * sc;
@@ -309,6 +319,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 }
             } else if (r == 11) {
                 const T sc = 1 / mg;
+                scale = sc;  // W
                 c = lt * xd * sc;
                 if (WJ) {
                     J[ULT] = xd * sc;
@@ -318,6 +329,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 on = false;
             }
         } else if (r == 13) {
+            scale = 1 / mg;
             c = -ln / mg;
             if (WJ) J[ULN] = -1 / mg;
         } else {
@@ -343,9 +355,11 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
         const T ell = side ? S.ell[1] : S.ell[0];
         if (h == 0) {
             if (q == 0) {
+                scale = 1 / mg;
                 c = fn / mg;
                 if (WJ) J[ufn] = 1 / mg;
             } else if (q == 1) {
+                scale = 1 / mg;
                 c = ft / mg;
                 if (WJ) J[uft] = 1 / mg;
             } else if (q == 2) {
@@ -365,6 +379,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                     if (WJ) J[usd] = 1;
                 } else {
                     const T sg = (kind == 1) ? (T)-1 : (T)1;
+                    scale = sch;
                     c = (ft + sg * muh * fn) * sch;
                     if (WJ) {
                         J[uft] = sch;
@@ -373,6 +388,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 }
             } else if (q == 3) {
                 if (kind == 0) {
+                    scale = sch;
                     c = (ft - muh * fn) * sch;
                     if (WJ) {
                         J[uft] = sch;
@@ -385,6 +401,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                 }
             } else if (q == 4) {
                 if (kind == 0) {
+                    scale = sch;
                     c = (-ft - muh * fn) * sch;
                     if (WJ) {
                         J[uft] = -sch;
@@ -394,6 +411,7 @@ __device__ void brow(int r, const BInst<T>& P, const BStage<T>& S, bool mL, bool
                     on = false;
                 }
             } else if (q == 5) {
+                scale = 1 / mg;
                 c = -fn / mg;
                 if (WJ) J[ufn] = -1 / mg;
             } else {
@@ -487,6 +505,8 @@ __device__ __forceinline__ void load_stage(const BCtx& C, int k, float alpha, fl
 
 struct BMeasures {
     float viol, stat, comp;
+    float vphys;  // violation in physical units (rows mapped back by c / scale)
+    float cost;   // objective J at the iterate (scale of the stationarity test)
     bool finite;
 };
 
@@ -500,12 +520,16 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
     float* Jw = S.Jw + warp * NR * NL;
     float* yw = S.yw + warp * NR;
     float* At = S.At + warp * NTRI;
-    float viol = 0.f, comp = 0.f;
+    float viol = 0.f, comp = 0.f, vph = 0.f, jc = 0.f;
     bool finite = true;
 #pragma unroll 1
     for (int k = warp; k < N; k += 4) {
         float x[NX], u[NU], dx[NX];
         load_stage(C, k, 0.f, x, u, dx);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NU; ++j) jc += rweight(P, j) * u[j] * u[j];
+        }
         const int mi = S.mi[k];
         BStage<float> St;
         stage_ctx(P, mi & 1023, x, u, St);
@@ -526,7 +550,9 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
         const bool act = on && (!iq || t > 0.f);
         const float y = act ? (iq ? fmaxf(t, 0.f) : t) : 0.f;
         if (on) {
-            viol = fmaxf(viol, iq ? fmaxf(c, 0.f) : fabsf(c));
+            const float vr = iq ? fmaxf(c, 0.f) : fabsf(c);
+            viol = fmaxf(viol, vr);
+            vph = fmaxf(vph, vr / sc);
             if (iq) comp = fmaxf(comp, fabsf(y * c));
             if (!isfinite(c)) finite = false;
         }
@@ -606,8 +632,14 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
             S.lam[tid] = l;
         }
         viol = fmaxf(viol, fabsf(c));
+        vph = fmaxf(vph, fabsf(c));
         if (!isfinite(c)) finite = false;
     }
+    if (tid == 0)
+        for (int i = 0; i < 3; ++i) {
+            const float e = (S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N];
+            jc += P.wT * e * e;
+        }
     __syncthreads();
     for (int k = tid; k <= N; k += kBimThreads) {
         for (int i = 0; i < NX; ++i) {
@@ -630,6 +662,8 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
     viol = bwarp_max(viol);
     stat = bwarp_max(stat);
     comp = bwarp_max(comp);
+    vph = bwarp_max(vph);
+    jc = bwarp_sum(jc);
     const bool fin = __all_sync(kFullB, finite);
     __syncthreads();
     if (C.lane == 0) {
@@ -637,6 +671,8 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
         S.red[4 + C.warp] = stat;
         S.red[8 + C.warp] = comp;
         S.red[12 + C.warp] = fin ? 1.f : 0.f;
+        S.red[24 + C.warp] = vph;
+        S.red[28 + C.warp] = jc;
     }
     __syncthreads();
     BMeasures m;
@@ -644,6 +680,8 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
     m.stat = fmaxf(fmaxf(S.red[4], S.red[5]), fmaxf(S.red[6], S.red[7]));
     m.comp = fmaxf(fmaxf(S.red[8], S.red[9]), fmaxf(S.red[10], S.red[11]));
     m.finite = S.red[12] > 0.f && S.red[13] > 0.f && S.red[14] > 0.f && S.red[15] > 0.f;
+    m.vphys = fmaxf(fmaxf(S.red[24], S.red[25]), fmaxf(S.red[26], S.red[27]));
+    m.cost = (S.red[28] + S.red[29]) + (S.red[30] + S.red[31]);
     __syncthreads();
     return m;
 }
@@ -1231,8 +1269,12 @@ __global__ void __launch_bounds__(kBimThreads, 3) bimanual_kernel(EvalArgs A) {
                         done = true;
                         break;
                     }
-                    const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
-                    if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
+                    // stop test (Sec. III-C): scaled rows within eps_primal,
+                    // rows in physical units within half eps_feas, and
+                    // stationarity relative to max(1, |J|)
+                    const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref) * fmaxf(1.f, fabsf(m.cost));
+                    if (m.viol <= sp.eps_primal && m.vphys <= 0.5f * (float)sp.eps_feas && m.stat <= eps_d &&
+                        m.comp <= sp.eps_comp) {
                         status = COMET_TO_CONVERGED;
                         done = true;
                         break;

@@ -372,6 +372,8 @@ __device__ __forceinline__ float4* rec_chunk(const Ctx& C, int q, int k) {
 // beta_old (the dual update of the outer loop).
 struct Measures {
     float viol, stat, comp;
+    float vphys;  // violation in physical units (rows mapped back by phys)
+    float cost;   // objective J at the iterate (scale of the stationarity test)
     bool finite;
 };
 
@@ -381,7 +383,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     const DevInstance& P = *C.P;
     const int N = C.N, Np1 = C.N + 1, lane = C.lane;
     Smem& S = C.sm;
-    float viol = 0.f, comp = 0.f;
+    float viol = 0.f, comp = 0.f, vph = 0.f, jc = 0.f;
     bool finite = true;
 #pragma unroll 1
     for (int k = lane; k < N; k += 32) {
@@ -417,10 +419,12 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
             if (R.on[r]) {
                 const float vr = ineq ? fmaxf(R.c[r], 0.f) : fabsf(R.c[r]);
                 viol = fmaxf(viol, vr);
+                vph = fmaxf(vph, vr * R.phys[r]);
                 if (ineq) comp = fmaxf(comp, fabsf(y[r] * R.c[r]));
                 if (!isfinite(R.c[r])) finite = false;
             }
         }
+        jc += P.w_control * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         // local AL gradient over (x_k, u_k, x_{k+1})
         float gx[4] = {0.f, 0.f, 0.f, 0.f}, gu[3], gy[4];
         const float R2 = 2.f * P.w_control;
@@ -573,8 +577,15 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
             S.lam[lane] = l;
         }
         viol = fmaxf(viol, fabsf(c));
+        vph = fmaxf(vph, fabsf(c));
         if (!isfinite(c)) finite = false;
     }
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float e = (S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N];
+            jc += P.w_terminal * e * e;
+        }
     __syncwarp();
     // combine the x parts of the gradient and take the stationarity measure
     float stat = 0.f;
@@ -606,6 +617,8 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     m.viol = warp_max(viol);
     m.stat = warp_max(stat);
     m.comp = warp_max(comp);
+    m.vphys = warp_max(vph);
+    m.cost = warp_sum(jc);
     m.finite = __all_sync(kFull, finite);
     return m;
 }
@@ -1446,8 +1459,12 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
                         done = true;
                         break;
                     }
-                    const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref);
-                    if (m.viol <= sp.eps_primal && m.stat <= eps_d && m.comp <= sp.eps_comp) {
+                    // stop test (Sec. III-C): scaled rows within eps_primal,
+                    // rows in physical units within half eps_feas, and
+                    // stationarity relative to max(1, |J|)
+                    const float eps_d = sp.eps_dual * fmaxf(1.f, beta / sp.beta_ref) * fmaxf(1.f, fabsf(m.cost));
+                    if (m.viol <= sp.eps_primal && m.vphys <= 0.5f * (float)sp.eps_feas && m.stat <= eps_d &&
+                        m.comp <= sp.eps_comp) {
                         status = COMET_TO_CONVERGED;
                         done = true;
                         break;
