@@ -1,17 +1,19 @@
 """GPU parity of the bimanual evaluator (one CTA per TO) against the FP64
 bimanual oracle, through the C ABI.
 
-Same bar as the pushing evaluator: the TO is local and non-convex and runs
-in FP32 on the GPU, so the two sides can reach different local solutions;
-checked are the first iterate (FP32 rounding), the closed forms, the
-convergence rate, cost agreement where both reach the same solution, and the
-FP64 certification of every converged GPU trajectory by the oracle's rows.
-Stationarity tolerance of the bimanual problems: 1e-3 on both sides (the
-library's default for this task; see include/comet.h).
+Same bar as the pushing evaluator (tests/_parity.py): the TO is local and
+non-convex and runs in FP32 on the GPU, so the two sides can reach different
+local solutions, which are listed and certified one by one; where both reach
+the same local solution, costs agree within 1e-4 relative plus the
+first-order allowance and knot states within 1e-3 of the exact local
+solution beyond the oracle's own distance, on the maximum.  v_hat is scored
+in physical units (N, N m, m, m/s, W) on both sides, and both use the
+library's default stop test (stationarity relative to max(1, |J|)).
 """
 import numpy as np
 import pytest
 
+import _parity as PA
 import oracle
 import workloads as W
 from oracle import search as S
@@ -49,7 +51,7 @@ def _ev(P, insts, seqs, idx=None, warm=None, want_traj=True, max_iters=0):
 
 
 def _opts(**kw):
-    return oracle.default_opts(eps_dual=1e-3, **kw)
+    return oracle.default_opts(**kw)
 
 
 def _to_oracle(traj, N, Nmax):
@@ -107,6 +109,18 @@ def test_first_iterate_matches_oracle(P):
         assert np.max(np.abs(got - tr[i])) <= 1e-4 * scale, i
 
 
+def _bim_asserts(rep, flags, n, label):
+    print(f"{label}: feasibility flags differ on {len(flags)} of {n}: {flags}")
+    print(f"{label}: different local solutions {[(d['t'], d['modes']) for d in rep['different']]}")
+    print(f"{label}: unresolved {rep['unresolved']}")
+    print(f"{label}: state bar exceeded (weakly determined; cost bar holds) {rep['state_excess']}")
+    assert not rep["vhat_fail"], rep["vhat_fail"]
+    assert not rep["cost_excess"], rep["cost_excess"]
+    assert len(rep["state_excess"]) <= max(2, rep["same"] // 100), rep["state_excess"]
+    assert all(sg != 0 or so != 0 for _, sg, so in flags)
+    assert len(rep["unresolved"]) <= max(3, rep["joint"] // 50), rep["unresolved"]
+
+
 def test_enumeration_parity_one_segment_and_mixed(P):
     insts = [W.bimanual_instance(s) for s in range(2)]
     rng = np.random.default_rng(0)
@@ -114,32 +128,22 @@ def test_enumeration_parity_one_segment_and_mixed(P):
                                              for _ in range(120)]
     idx = np.concatenate([np.repeat([0, 1], 507), rng.integers(0, 2, 120)]).astype(np.int32)
     lens = np.array([len(s) for s in seqs], np.int32)
+    Ns = 15 * lens
     g = _ev(P, insts, seqs, idx)
-    ref, _ = oracle.bim_solve_batch(insts, idx, seqs, lens, opts=_opts())
-    cg, co = g["status"] == 0, ref["status"] == 0
-    both = cg & co
-    rel = np.abs(g["cost"].astype(np.float64) - ref["cost"]) / np.abs(ref["cost"])
-    same = both & (rel < 1e-2)
-    print(f"bimanual: conv gpu {cg.mean():.3f} oracle {co.mean():.3f}; same {same.sum() / both.sum():.3f}; "
-          f"rel<1e-4 {np.mean(rel[both] < 1e-4):.3f}")
-    assert abs(cg.mean() - co.mean()) <= 0.08
-    assert same.sum() >= 0.97 * both.sum()
-    assert np.mean(rel[same] <= 1e-4 + 2e-4) >= 0.97
-    # feasibility flags agree
-    assert np.mean((g["viol"] <= 1e-5) == (ref["viol"] <= 1e-5)) >= 0.9
-    # every converged GPU trajectory is certified by the oracle's FP64 rows
-    for t in np.flatnonzero(cg)[::17]:
-        N = 15 * len(seqs[t])
-        v = _certify(insts[idx[t]], seqs[t], N, _to_oracle(g["traj"][t], N, 90))
-        assert v <= 1e-5, (t, v)
+    g["traj_nmax"] = 90
+    ref, rtr, _ = oracle.bim_solve_batch_ex(insts, idx, seqs, lens, opts=_opts())
+    cg, co = (g["status"] == 0) & (g["viol"] <= 1e-5), (ref["status"] == 0) & (ref["viol"] <= 1e-5)
+    print(f"bimanual: feasible gpu {cg.mean():.3f} oracle {co.mean():.3f}")
+    T = PA.Task(True)
+    rep = PA.compare(T, insts, idx, seqs, lens, Ns, g, ref, rtr)
+    flags = PA.flag_disagreements(g, ref)
+    _bim_asserts(rep, flags, len(seqs), "bimanual 1-3 segments")
+    assert len(flags) <= max(3, 5 * len(seqs) // 100), len(flags)
+    assert not PA.certify_different(T, insts, idx, seqs, lens, Ns, g, rep)
     # the enumeration argmin over the one-segment orders of each instance
-    for i in range(2):
-        sl = slice(507 * i, 507 * (i + 1))
-        ag = S.enumeration_argmin(g["cost"][sl], g["viol"][sl])
-        ao = S.enumeration_argmin(ref["cost"][sl], ref["viol"][sl])
-        if ag != ao:
-            # a near tie: the oracle's own costs of the two picks agree
-            assert ref["cost"][sl][ag] <= ref["cost"][sl][ao] * (1 + 1e-3) or not co[sl][ag]
+    out, bad = PA.argmin_parity(T, insts, [slice(507 * i, 507 * (i + 1)) for i in range(2)], idx, seqs, lens, Ns,
+                                g, ref, rtr)
+    assert not bad, bad
 
 
 def test_warm_start_and_malformed_orders(P):
@@ -209,9 +213,9 @@ def test_bimanual_plan(P):
 
 
 def test_long_orders_convergence_matches_oracle(P):
-    # random orders of 1..6 segments (N up to 90): the GPU's converged
-    # fraction tracks the FP64 oracle's on the same orders, and converged GPU
-    # trajectories are certified by the oracle's rows
+    # random orders of 1..6 segments (N up to 90): the GPU's feasible
+    # fraction tracks the FP64 oracle's on the same orders; the per-TO bar
+    # holds where both are feasible
     insts = [W.bimanual_instance(s) for s in range(8)]
     rng = np.random.default_rng(11)
     seqs, idx = [], []
@@ -223,14 +227,14 @@ def test_long_orders_convergence_matches_oracle(P):
     idx = np.array(idx, np.int32)
     lens = np.array([len(s) for s in seqs], np.int32)
     g = _ev(P, insts, seqs, idx)
-    ref, _ = oracle.bim_solve_batch(insts, idx, seqs, lens, opts=_opts())
+    g["traj_nmax"] = 90
+    ref, rtr, _ = oracle.bim_solve_batch_ex(insts, idx, seqs, lens, opts=_opts())
     cg = (g["status"] == 0) & (g["viol"] <= 1e-5)
     co = (ref["status"] == 0) & (ref["viol"] <= 1e-5)
     print(f"1..6 segments: converged gpu {cg.mean():.3f} oracle {co.mean():.3f}")
     assert abs(cg.mean() - co.mean()) <= 0.08
-    both = cg & co
-    rel = np.abs(g["cost"].astype(np.float64) - ref["cost"]) / np.abs(ref["cost"])
-    assert np.mean(rel[both] <= 1e-2) >= 0.9
-    for t in np.flatnonzero(cg)[::7]:
-        N = 15 * len(seqs[t])
-        assert _certify(insts[idx[t]], seqs[t], N, _to_oracle(g["traj"][t], N, 90)) <= 1e-5, t
+    T = PA.Task(True)
+    rep = PA.compare(T, insts, idx, seqs, lens, 15 * lens, g, ref, rtr)
+    flags = PA.flag_disagreements(g, ref)
+    _bim_asserts(rep, flags, len(seqs), "bimanual 1-6 segments")
+    assert not PA.certify_different(T, insts, idx, seqs, lens, 15 * lens, g, rep)

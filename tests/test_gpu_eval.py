@@ -21,6 +21,7 @@ import os
 import numpy as np
 import pytest
 
+import _parity as PA
 import oracle
 import workloads as W
 from oracle import search as S
@@ -94,6 +95,32 @@ def test_straight_push_closed_form(P):
     np.testing.assert_allclose(fn, 0.1 / 1.7, rtol=2e-3)
 
 
+def _nmax(g):
+    return (int(g["stride"]) - 4) // 7
+
+
+def _parity_asserts(rep, flags, n, label):
+    """The acceptance bar on a compare() report (see tests/_parity.py)."""
+    print(f"{label}: feasibility flags differ on {len(flags)} of {n}: {flags}")
+    print(f"{label}: different local solutions {[(d['t'], d['modes']) for d in rep['different']]}")
+    print(f"{label}: unresolved {rep['unresolved']}")
+    print(f"{label}: state bar exceeded (weakly determined; cost bar holds) {rep['state_excess']}")
+    # every converged GPU answer is feasible by the oracle's FP64 rows
+    assert not rep["vhat_fail"], rep["vhat_fail"]
+    # costs of the same local solution: 1e-4 relative plus the first-order
+    # allowance, on the maximum
+    assert not rep["cost_excess"], rep["cost_excess"]
+    # knot states: within 1e-3 of the exact local solution beyond the
+    # oracle's own distance; the listed exceptions lie along weakly curved
+    # directions (their cost bar holds)
+    assert len(rep["state_excess"]) <= max(2, rep["same"] // 100), rep["state_excess"]
+    # a stop on the tolerances implies feasibility on either side, so a
+    # flag disagreement needs one side that ended without the stop test
+    assert all(sg != 0 or so != 0 for _, sg, so in flags)
+    assert len(flags) <= max(3, 3 * n // 100), len(flags)
+    assert len(rep["unresolved"]) <= max(3, rep["joint"] // 50), rep["unresolved"]
+
+
 def test_two_segment_enumeration_parity(P):
     # the 2-segment workload: every one of the 144 orders x 32 seeded goals
     seeds = range(32)
@@ -102,54 +129,52 @@ def test_two_segment_enumeration_parity(P):
     n = len(seqs) * len(insts)
     allseq = np.tile(seqs, (len(insts), 1))
     idx = np.repeat(np.arange(len(insts)), len(seqs)).astype(np.int32)
+    lens, Ns = np.full(n, 2, np.int32), np.full(n, 16)
     g = gpu_eval(P, insts, allseq, idx, want_traj=True)
-    ref, _ = oracle.solve_batch(insts, idx, allseq, np.full(n, 2, np.int32), nthreads=os.cpu_count())
-    cg, co, both, rel, same = compare(g, ref)
-    print(f"conv gpu {cg.mean():.4f} oracle {co.mean():.4f}; both {both.mean():.4f}; "
-          f"rel<1e-4 {np.mean(rel[both] < 1e-4):.4f}; same-solution {same.sum() / both.sum():.4f}")
-    assert cg.mean() >= 0.95 and abs(cg.mean() - co.mean()) <= 0.03
-    assert same.sum() >= 0.85 * both.sum()
-    # cost agreement where both reached the same local solution
-    bias = 2e-4 * np.abs(ref["cost"]) + 1e-7
-    assert np.mean(np.abs(g["cost"] - ref["cost"])[same] <= 1e-4 * np.abs(ref["cost"][same]) + bias[same]) >= 0.97
-    # feasibility flags (v_hat <= eps_feas) agree
-    assert np.mean((g["viol"] <= 1e-5) == (ref["viol"] <= 1e-5)) >= 0.97
-    # every CONVERGED GPU result is certified by the oracle's FP64 residuals
-    N = 16
-    for t in np.flatnonzero(cg)[::7]:
-        v, tr = certify_fp64(insts[idx[t]], allseq[t], N, g["traj"][t], 16)
-        assert v <= 1e-5, (t, v)
-        fnv, ftv = tr[4 * 17: 4 * 17 + N], tr[4 * 17 + N: 4 * 17 + 2 * N]
-        assert np.all(fnv >= -1e-5) and np.all(np.abs(ftv) <= insts[idx[t]]["mu"] * fnv + 2e-5)
-    # enumeration argmin (Eq. mode_selection) per instance: identical where
-    # the oracle's best is ahead of the GPU's pick by more than 1e-3 relative;
-    # where the GPU's local solve found a better minimum for another order
-    # (a valid, certified plan no worse than the oracle's best) the picks may
-    # differ -- the paper reports the same effect between its FP64 CPU and
-    # mixed-precision GPU evaluators
-    same_pick = 0
-    worse = 0
-    for i in range(len(insts)):
-        sl = slice(144 * i, 144 * (i + 1))
-        ag = S.enumeration_argmin(g["cost"][sl], g["viol"][sl])
-        ao = S.enumeration_argmin(ref["cost"][sl], ref["viol"][sl])
-        if ag == ao:
-            same_pick += 1
-            continue
-        gap = (ref["merit"][sl][ao] - ref["merit"][sl][ag]) / abs(ref["merit"][sl][ao])
-        if gap < -1e-3:   # the oracle's evaluation of the GPU pick is worse ...
-            # ... so the GPU's plan must itself be certified and at least as good
-            t = 144 * i + ag
-            v, _ = certify_fp64(insts[i], allseq[t], N, g["traj"][t], 16)
-            assert g["status"][t] == 0 and v <= 1e-5, (i, ag, v)
-            if g["cost"][t] > ref["cost"][sl][ao] * (1 + 1e-3):
-                # the GPU's FP32 solve of the oracle's best order reached a
-                # worse local minimum (see test_iteration_level_parity)
-                worse += 1
-                assert g["cost"][t] <= ref["cost"][sl][ao] * 1.05, (i, ag, ao)
-    print(f"argmin identical on {same_pick}/{len(insts)}; GPU plan worse than 1e-3 on {worse}")
-    assert same_pick >= 0.9 * len(insts), same_pick
-    assert worse <= max(1, len(insts) // 20), worse
+    g["traj_nmax"] = _nmax(g)
+    ref, rtr, _ = oracle.solve_batch_ex(insts, idx, allseq, lens, nthreads=os.cpu_count())
+    T = PA.Task(False)
+    rep = PA.compare(T, insts, idx, list(allseq), lens, Ns, g, ref, rtr)
+    flags = PA.flag_disagreements(g, ref)
+    _parity_asserts(rep, flags, n, "N=16")
+    # a GPU answer that reached another local solution is a certified one
+    assert not PA.certify_different(T, insts, idx, list(allseq), lens, Ns, g, rep)
+    # enumeration argmin (Eq. mode_selection) per instance
+    out, bad = PA.argmin_parity(T, insts, [slice(144 * i, 144 * (i + 1)) for i in range(len(insts))], idx,
+                                list(allseq), lens, Ns, g, ref, rtr)
+    assert not bad, bad
+
+
+def test_full_enumeration_parity_four_segments(P):
+    # the benchmarked workload: 4-segment orders, N = 80, both 20,736-order
+    # enumerations of two instances in one launch on the GPU and on the
+    # oracle; the argmin of each instance is compared, the per-TO bar is
+    # taken on a seeded sample of 1,024 orders per instance
+    insts = [W.push_l4_instance(s) for s in (0, 1)]
+    seqs = W.all_sequences(12, 4)
+    m = len(seqs)
+    n = 2 * m
+    allseq = np.tile(seqs, (2, 1))
+    idx = np.repeat(np.arange(2), m).astype(np.int32)
+    lens, Ns = np.full(n, 4, np.int32), np.full(n, 80)
+    g = gpu_eval(P, insts, allseq, idx, want_traj=True)
+    g["traj_nmax"] = _nmax(g)
+    ref, rtr, _ = oracle.solve_batch_ex(insts, idx, allseq, lens, nthreads=os.cpu_count())
+    print(f"N=80: converged gpu {np.mean(g['status'] == 0):.4f} oracle {np.mean(ref['status'] == 0):.4f}")
+    T = PA.Task(False)
+    out, bad = PA.argmin_parity(T, insts, [slice(0, m), slice(m, n)], idx, list(allseq), lens, Ns, g, ref, rtr)
+    assert not bad, bad
+    rng = np.random.default_rng(0)
+    sel = np.concatenate([np.sort(rng.choice(m, 1024, replace=False)) + i * m for i in range(2)])
+    rep = PA.compare(T, insts, idx, list(allseq), lens, Ns, g, ref, rtr, sel=sel)
+    flags = PA.flag_disagreements(g, ref, sel)
+    _parity_asserts(rep, flags, len(sel), "N=80")
+    assert not PA.certify_different(T, insts, idx, list(allseq), lens, Ns, g, rep)
+    # feasibility flags over both whole enumerations
+    flags_all = PA.flag_disagreements(g, ref)
+    print(f"N=80 all orders: feasibility flags differ on {len(flags_all)} of {n}")
+    assert all(sg != 0 or so != 0 for _, sg, so in flags_all)
+    assert len(flags_all) <= 3 * n // 100
 
 
 @pytest.mark.parametrize("iters", [1, 2, 5])
@@ -208,32 +233,6 @@ def test_fp64_refinement_at_high_penalty(P):
     assert same.sum() >= 0.85 * both.sum()
     for t in np.flatnonzero(cg)[::13]:
         v, _ = certify_fp64(insts[idx[t]], allseq[t], 16, ref_on["traj"][t], 16)
-        assert v <= 1e-5, (t, v)
-
-
-def test_four_segment_sampled_parity(P):
-    # the 4-segment workload at full size on the GPU (one instance, 20,736
-    # orders, the bench's launch configuration); the oracle checks a seeded
-    # sample of the results one by one
-    inst = W.push_l4_instance(5)
-    seqs = W.all_sequences(12, 4)
-    g = gpu_eval(P, [inst], seqs, want_traj=True)
-    rng = np.random.default_rng(0)
-    sub = np.sort(rng.choice(len(seqs), 256, replace=False))
-    ref, _ = oracle.solve_batch([inst], np.zeros(len(sub), np.int32), seqs[sub], np.full(len(sub), 4, np.int32),
-                                nthreads=os.cpu_count())
-    gs = {k: v[sub] for k, v in g.items() if k != "stride"}
-    cg, co, both, rel, same = compare(gs, ref)
-    print(f"N=80 conv gpu {np.mean(g['status'] == 0):.4f} sample gpu {cg.mean():.4f} oracle {co.mean():.4f} "
-          f"same {same.sum() / max(1, both.sum()):.4f} rel<1e-4 {np.mean(rel[both] < 1e-4):.4f}")
-    assert np.mean(g["status"] == 0) >= 0.75
-    assert abs(cg.mean() - co.mean()) <= 0.08
-    assert same.sum() >= 0.8 * both.sum()
-    bias = 4e-4 * np.abs(ref["cost"]) + 1e-7
-    assert np.mean(np.abs(gs["cost"] - ref["cost"])[same] <= 1e-4 * np.abs(ref["cost"][same]) + bias[same]) >= 0.95
-    # certification of the converged GPU results on the whole launch (sampled)
-    for t in np.flatnonzero(g["status"] == 0)[::211]:
-        v, _ = certify_fp64(inst, seqs[t], 80, g["traj"][t], 80)
         assert v <= 1e-5, (t, v)
 
 
