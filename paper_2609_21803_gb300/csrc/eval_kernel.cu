@@ -66,28 +66,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Ampere-style asynchronous global -> shared copies (16 bytes per lane) with
-// commit groups; the waits are hardware waits on the issuing lane's own
-// groups, no spin loop
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// reciprocal from the SFU (rcp.approx, about 1 ulp); the sweep's pivots are
-// damped and never subnormal
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 // lower-triangle flat index of (i, j), i >= j
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -312,11 +290,7 @@ __device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float 
 
 // ------------------------------------------------------------ shared memory
 
-constexpr int kRing = 6;       // stages in flight in the copy rings
-constexpr int kSweepSlot = 48;  // record floats 32..79 (pd flag and reduced matrix)
-
 struct Smem {
-    float* ring_b;  // [kRing][48] sweep records in flight (16-byte aligned)
     unsigned char* mb;  // [Nmax] per-interval mode byte: face | kind << 2 | smask << 4
     float* xh;   // [4][Nmax+1] state, high part
     float* xl;   // [4][Nmax+1] state, low part
@@ -327,7 +301,7 @@ struct Smem {
 };
 
 __host__ __device__ inline size_t smem_floats(int Nmax) {
-    const size_t f = (size_t)kRing * kSweepSlot + (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
+    const size_t f = (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
                      3 * (size_t)Nmax + 3 + 11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4);
     return (f + 3) / 4 * 4;  // every warp's block starts 16-byte aligned
 }
@@ -335,7 +309,6 @@ __host__ __device__ inline size_t smem_floats(int Nmax) {
 __device__ __forceinline__ Smem carve(float* base, int Nmax) {
     Smem s;
     float* p = base;
-    s.ring_b = p; p += kRing * kSweepSlot;
     s.mb = reinterpret_cast<unsigned char*>(p); p += (Nmax + 3) / 4;
     s.xh = p; p += 4 * (Nmax + 1);
     s.xl = p; p += 4 * (Nmax + 1);
@@ -623,305 +596,303 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     return m;
 }
 
-// Phase B: backward sweep over k = N-1 .. 0.  Only the x_{k+1} block is
-// eliminated on this sequential path.  The sweep is a dependent chain of
-// small operations, so every lane runs the whole stage in registers: the
-// reduced 9 x 9 lower triangle of the record (rows y_0..3, x_0..3, rhs) is
-// read as shared-memory broadcasts, V_{k+1} and v_{k+1} stay in registers,
-// and no lane waits on another within a stage.  Each stage leaves the raw
-// y-factor columns (pivots, y-y and (x, rhs)-y entries) in its record; the
-// gains are formed afterwards in a stage-parallel pass (phase_b_gains).
-// Records arrive kRing stages ahead.  Returns false if a pivot is not
-// positive.
-__device__ bool phase_b(Ctx& C, float beta, float rho, float dx0[4], bool rhs_from_gr = false) {
+// Phase B: the step's state part by a lane-parallel elimination of the
+// block-tridiagonal system over dx_0 .. dx_N (Sec. III-C "Fixed-workspace
+// local solves": after the u block of each stage is eliminated in phase A,
+// the stage record holds a quadratic "element" in (dx_{k+1}, dx_k), the
+// reduced 9 x 9 lower triangle over (y = x_{k+1}, x = x_k, rhs)).  The paper
+// eliminates the x_{k+1} blocks one stage after another (the backward sweep);
+// the same block Cholesky is taken here in another order, so that the lanes
+// share the chain instead of each lane repeating it:
+//   1. lane l owns stages [k0, k1) (k1 - k0 = ceil(N / 32)) and folds them
+//      into one element over (x_{k1}, x_{k0}), eliminating its interior
+//      nodes left to right;
+//   2. a tree over the lanes (log2 of the active lanes levels, the partner's
+//      element arriving by shuffles) eliminates the nodes between the lanes'
+//      spans, until lane 0 holds an element over (x_N, x_0);
+//   3. lane 0 solves that 8 x 8 system for dx_0 and dx_N;
+//   4. back-substitution down the tree, then through each lane's interior.
+// Eliminating node m between an element E over (m, a) and F over (b, m):
+// S = E_mm + F_mm = L L^T, Y = L^{-1} [F_mb | E_ma | r_m], and the element
+// over (b, a) is blockdiag(F_bb, E_aa) - Y^T Y; later dx_m =
+// -L^{-T} (Y_b dx_b + Y_a dx_a + y_r).  Node m keeps (L, Y) in record floats
+// 34..79 (the reduced matrix there is consumed).  The matrix is positive
+// definite exactly when every pivot of every elimination is positive, in
+// any order (inertia is additive over Schur complements), so the test of
+// the backward sweep is unchanged: a non-positive pivot anywhere, or a
+// non-positive u-block pivot flagged by phase A, reports failure.
+// The terminal cost's value function V_N, v_N enters the last stage's y
+// block and the x_0 block (rho I, beta on the three pose rows, their
+// multiplier terms) the first stage's x block.  Writes dx_k to dz[7k..7k+3]
+// for k = 0..N; returns false if a pivot is not positive.
+
+constexpr int kElem = 44;  // 9 x 9 lower triangle without the (rhs, rhs) entry
+
+// record floats 36..79 (the reduced matrix) of stage k as an element, with
+// the boundary terms of the first and the last stage
+__device__ __forceinline__ void load_elem(const Ctx& C, int k, float e[kElem], float beta, float rho,
+                                          bool rhs_from_gr) {
+#pragma unroll
+    for (int q = 0; q < 11; ++q) {
+        const float4 t = *rec_chunk(C, 9 + q, k);
+        e[4 * q] = t.x;
+        e[4 * q + 1] = t.y;
+        e[4 * q + 2] = t.z;
+        e[4 * q + 3] = t.w;
+    }
     const DevInstance& P = *C.P;
-    const int N = C.N, Np1 = C.N + 1, lane = C.lane;
-    Smem& S = C.sm;
-    // V_N, v_N: terminal cost w_T |pose_N - goal|^2 (lower triangle tri(i, j))
-    float V[10], v[4];
+    const int N = C.N, Np1 = N + 1;
+    const Smem& S = C.sm;
+    if (k == N - 1) {
+        // V_N, v_N of the terminal cost w_T |pose_N - goal|^2 on the y block
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) V[tri(i, j)] = (i == j && i < 3) ? 2.f * P.w_terminal : 0.f;
-        v[i] = (i < 3 && !rhs_from_gr) ? 2.f * P.w_terminal * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N])
-                                       : 0.f;
-    }
-    // copy ring: stage k's record floats 32..79 (pd flag at 33, reduced
-    // matrix at 36..79) arrive kRing stages ahead; one commit group per stage
-    // (lanes 0..11 copy 16 bytes each)
-#pragma unroll
-    for (int d = 0; d < kRing; ++d) {
-        const int kk = N - 1 - d;
-        if (kk >= 0 && lane < kSweepSlot / 4)
-            cp_async16(S.ring_b + d * kSweepSlot + 4 * lane, rec_chunk(C, 8 + lane, kk));
-        cp_async_commit();
-    }
-    bool ok = true;
-    int slot = kRing - 1;  // ring slot of stage k: (N - 1 - k) mod kRing
-#pragma unroll 1
-    for (int k = N - 1; k >= 0; --k) {
-        slot = (slot == kRing - 1) ? 0 : slot + 1;
-        cp_async_wait<kRing - 1>();
-        __syncwarp();
-        const float4* sl = reinterpret_cast<const float4*>(S.ring_b + slot * kSweepSlot);
-        float m[44];
-        const float4 hd = sl[0];
-#pragma unroll
-        for (int q = 0; q < 11; ++q) {
-            const float4 t = sl[1 + q];
-            m[4 * q] = t.x;
-            m[4 * q + 1] = t.y;
-            m[4 * q + 2] = t.z;
-            m[4 * q + 3] = t.w;
+        for (int i = 0; i < 3; ++i) {
+            e[tri(i, i)] += 2.f * P.w_terminal;
+            if (!rhs_from_gr)
+                e[tri(8, i)] += 2.f * P.w_terminal * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N]);
         }
-        bool pd = hd.y > 0.f;
-        __syncwarp();
-        {
-            // refill this slot with the record kRing stages further on
-            const int kk = k - kRing;
-            if (kk >= 0 && lane < kSweepSlot / 4)
-                cp_async16(S.ring_b + slot * kSweepSlot + 4 * lane, rec_chunk(C, 8 + lane, kk));
-            cp_async_commit();
-        }
-        // add V_{k+1} to the y-y block and v_{k+1} to the (rhs, y) row
+    }
+    if (k == 0) {
+        // the x_0 block: damping, and beta on the initial pose rows
 #pragma unroll
-        for (int t = 0; t < 10; ++t) m[t] += V[t];
+        for (int i = 0; i < 4; ++i) e[tri(4 + i, 4 + i)] += rho + (i < 3 ? beta : 0.f);
+        if (!rhs_from_gr)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) m[tri(8, j)] += v[j];
-        // eliminate the 4 x_{k+1} columns (the (rhs, rhs) entry is not kept)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float p = m[tri(j, j)];
-            pd = pd && (p > 0.f);
-            const float ip = rcp_approx(p);
-#pragma unroll
-            for (int i = j + 1; i < 9; ++i) {
-                const float a = m[tri(i, j)] * ip;
-#pragma unroll
-                for (int l = j + 1; l <= i; ++l)
-                    if (!(i == 8 && l == 8)) m[tri(i, l)] -= a * m[tri(l, j)];
+            for (int i = 0; i < 3; ++i) {
+                const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
+                e[tri(8, 4 + i)] += S.lam[i] + beta * c;
             }
-        }
-        if (!__all_sync(kFull, pd)) {
-            ok = false;
-            break;
-        }
-        // raw y-factor columns for the gains, over the consumed record entries:
-        //   36 + tri(i, j) for the y-y block (i, j < 4, 10 entries)
-        //   46 + 4 c + j  for row (x0..x3, rhs) = 4 + c, column j (20 entries)
-        if (lane == 0) {
-            *rec_chunk(C, 9, k) = make_float4(m[0], m[1], m[2], m[3]);
-            *rec_chunk(C, 10, k) = make_float4(m[4], m[5], m[6], m[7]);
-            *rec_chunk(C, 11, k) = make_float4(m[8], m[9], m[tri(4, 0)], m[tri(4, 1)]);
-            *rec_chunk(C, 12, k) = make_float4(m[tri(4, 2)], m[tri(4, 3)], m[tri(5, 0)], m[tri(5, 1)]);
-            *rec_chunk(C, 13, k) = make_float4(m[tri(5, 2)], m[tri(5, 3)], m[tri(6, 0)], m[tri(6, 1)]);
-            *rec_chunk(C, 14, k) = make_float4(m[tri(6, 2)], m[tri(6, 3)], m[tri(7, 0)], m[tri(7, 1)]);
-            *rec_chunk(C, 15, k) = make_float4(m[tri(7, 2)], m[tri(7, 3)], m[tri(8, 0)], m[tri(8, 1)]);
-            *reinterpret_cast<float2*>(rec_chunk(C, 16, k)) = make_float2(m[tri(8, 2)], m[tri(8, 3)]);
-        }
-        // V_k, v_k from the trailing block
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-#pragma unroll
-            for (int j = 0; j <= i; ++j) V[tri(i, j)] = m[tri(4 + i, 4 + j)];
-            v[i] = m[tri(8, 4 + i)];
-        }
     }
-    // drain the copies still in flight (an early exit leaves some) before the
-    // ring is reused
-    cp_async_wait_all();
-    __syncwarp();
-    if (!ok) return false;
-    // x_0 block: V_0 + rho I + beta on the three pose rows (every lane)
-    float H[4][4], g[4];
+}
+
+// Eliminate the node shared by e (over (y = m, x = a)) and f (over (y = b,
+// x = m)); e becomes the element over (y = b, x = a).  Stores (L, Y) of node
+// m in record `km` when `store`; returns false on a non-positive pivot.
+__device__ __forceinline__ bool combine(const Ctx& C, float e[kElem], const float f[kElem], int km, bool store) {
+    // S = E_yy + F_xx and its Cholesky factor (il = 1 / l_jj on the diagonal)
+    float L[10];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) H[i][j] = V[i >= j ? tri(i, j) : tri(j, i)];
-        H[i][i] += rho;
-        g[i] = v[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float c = (S.xh[i * Np1] - P.start[i]) + S.xl[i * Np1];
-        H[i][i] += beta;
-        if (!rhs_from_gr) g[i] += S.lam[i] + beta * c;
-    }
-    // Cholesky with reciprocal pivots: il[j] = 1 / l_jj
-    float L[4][4], il[4];
-    bool pd0 = true;
+        for (int j = 0; j <= i; ++j) L[tri(i, j)] = e[tri(i, j)] + f[tri(4 + i, 4 + j)];
+    bool pd = true;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float d = H[j][j];
+        float d = L[tri(j, j)];
 #pragma unroll
-        for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
-        pd0 = pd0 && d > 0.f;
-        il[j] = rsqrtf(fmaxf(d, 1e-30f));
+        for (int q = 0; q < j; ++q) d -= L[tri(j, q)] * L[tri(j, q)];
+        pd = pd && d > 0.f;
+        const float il = rsqrtf(fmaxf(d, 1e-30f));
+        L[tri(j, j)] = il;
 #pragma unroll
         for (int i = j + 1; i < 4; ++i) {
-            float s = H[i][j];
+            float s = L[tri(i, j)];
 #pragma unroll
-            for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
-            L[i][j] = s * il[j];
+            for (int q = 0; q < j; ++q) s -= L[tri(i, q)] * L[tri(j, q)];
+            L[tri(i, j)] = s * il;
         }
     }
-    float yv[4], d0[4];
+    // Y = L^{-1} [F_mb | E_ma | r_m], columns b0..3, a0..3, rhs
+    float Y[4][9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float s = (c < 4) ? f[tri(4 + i, c)] : (c < 8) ? e[tri(4 + (c - 4), i)] : e[tri(8, i)] + f[tri(8, 4 + i)];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s -= L[tri(i, q)] * Y[q][c];
+            Y[i][c] = s * L[tri(i, i)];
+        }
+    }
+    // the element over (y = b, x = a, rhs): blockdiag(F_bb, E_aa) - Y^T Y
+    float g[kElem];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            if (i == 8 && j == 8) continue;
+            float s;
+            if (i < 4)
+                s = f[tri(i, j)];                              // (b, b)
+            else if (i < 8)
+                s = (j < 4) ? 0.f : e[tri(i, j)];              // (a, b) fill-in, (a, a)
+            else
+                s = (j < 4) ? f[tri(8, j)] : e[tri(8, j)];     // (rhs, b), (rhs, a)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) s -= Y[p][i] * Y[p][j];
+            g[tri(i, j)] = s;
+        }
+#pragma unroll
+    for (int t = 0; t < kElem; ++t) e[t] = g[t];
+    if (store) {
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(rec_chunk(C, 8, km)) + 2) = make_float2(L[0], L[1]);
+        *rec_chunk(C, 9, km) = make_float4(L[2], L[3], L[4], L[5]);
+        *rec_chunk(C, 10, km) = make_float4(L[6], L[7], L[8], L[9]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            *rec_chunk(C, 11 + q, km) = make_float4(Y[(4 * q) / 9][(4 * q) % 9], Y[(4 * q + 1) / 9][(4 * q + 1) % 9],
+                                                    Y[(4 * q + 2) / 9][(4 * q + 2) % 9],
+                                                    Y[(4 * q + 3) / 9][(4 * q + 3) % 9]);
+    }
+    return pd;
+}
+
+// dx_m = -L^{-T} (Y_b dx_b + Y_a dx_a + y_r) from node m's stored (L, Y)
+__device__ __forceinline__ void back_node(const Ctx& C, int km, const float xa[4], const float xb[4], float xm[4]) {
+    float v[48];
+    const float2 h = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(rec_chunk(C, 8, km)) + 2);
+    v[0] = h.x;
+    v[1] = h.y;
+#pragma unroll
+    for (int q = 0; q < 11; ++q) {
+        const float4 t = *rec_chunk(C, 9 + q, km);
+        v[2 + 4 * q] = t.x;
+        v[3 + 4 * q] = t.y;
+        v[4 + 4 * q] = t.z;
+        v[5 + 4 * q] = t.w;
+    }
+    const float* L = v;        // 10
+    const float* Y = v + 10;   // [4][9]
+    float t[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        float s = g[i];
+        float s = Y[9 * i + 8];
 #pragma unroll
-        for (int q = 0; q < i; ++q) s -= L[i][q] * yv[q];
-        yv[i] = s * il[i];
+        for (int j = 0; j < 4; ++j) s += Y[9 * i + j] * xb[j] + Y[9 * i + 4 + j] * xa[j];
+        t[i] = s;
     }
+    // L^T xm = -t
 #pragma unroll
     for (int i = 3; i >= 0; --i) {
-        float s = yv[i];
+        float s = -t[i];
 #pragma unroll
-        for (int q = i + 1; q < 4; ++q) s -= L[q][i] * d0[q];
-        d0[i] = s * il[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) dx0[i] = -d0[i];
-    return __all_sync(kFull, pd0);
-}
-
-// Stage-parallel gains: K_y,k = -L_y^{-T} [l_{x,y} | l_{rhs,y}] (4 x 5) from
-// the raw y-factor columns the sweep left in each record; K_y replaces them
-// (record floats 36..55, row-major).
-__device__ void phase_b_gains(Ctx& C) {
-    const int N = C.N, lane = C.lane;
-#pragma unroll 1
-    for (int k = lane; k < N; k += 32) {
-        // record floats 36..67 as 8 vector loads (the last two are unused)
-        float m[32];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float4 t = *rec_chunk(C, 9 + q, k);
-            m[4 * q] = t.x;
-            m[4 * q + 1] = t.y;
-            m[4 * q + 2] = t.z;
-            m[4 * q + 3] = t.w;
-        }
-        float ly[4][4], il[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            il[j] = rsqrtf(m[tri(j, j)]);
-#pragma unroll
-            for (int i = j + 1; i < 4; ++i) ly[i][j] = m[tri(i, j)] * il[j];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) m[10 + 4 * c + j] *= il[j];  // l_{(4+c), j}
-        }
-        float K[4][5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-#pragma unroll
-            for (int i = 3; i >= 0; --i) {
-                float s = -m[10 + 4 * c + i];
-#pragma unroll
-                for (int q = i + 1; q < 4; ++q) s -= ly[q][i] * K[q][c];
-                K[i][c] = s * il[i];
-            }
-        }
-        // row i of K_y at 36 + 5 i
-        *rec_chunk(C, 9, k) = make_float4(K[0][0], K[0][1], K[0][2], K[0][3]);
-        *rec_chunk(C, 10, k) = make_float4(K[0][4], K[1][0], K[1][1], K[1][2]);
-        *rec_chunk(C, 11, k) = make_float4(K[1][3], K[1][4], K[2][0], K[2][1]);
-        *rec_chunk(C, 12, k) = make_float4(K[2][2], K[2][3], K[2][4], K[3][0]);
-        *rec_chunk(C, 13, k) = make_float4(K[3][1], K[3][2], K[3][3], K[3][4]);
-    }
-    __syncwarp();
-}
-
-// x_{k+1} gains of stage k as an affine map dx_{k+1} = G dx_k + g (record
-// floats 36..55, row i at 36 + 5 i: G[i][0..3], g[i])
-__device__ __forceinline__ void load_gain(const Ctx& C, int k, float G[4][4], float g[4]) {
-    float v[20];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const float4 t = *rec_chunk(C, 9 + q, k);
-        v[4 * q] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) G[i][j] = v[5 * i + j];
-        g[i] = v[5 * i + 4];
+        for (int q = i + 1; q < 4; ++q) s -= L[tri(q, i)] * xm[q];
+        xm[i] = s * L[tri(i, i)];
     }
 }
 
-// Phase C: forward pass.  The state chain dx_{k+1} = G_k dx_k + g_k is an
-// affine recurrence, split over the lanes: lane l owns `per` consecutive
-// stages and first composes their maps into one block map (P_l, q_l); the
-// entry states then pass along the lanes, x_in(l+1) = P_l x_in(l) + q_l
-// (ceil(N / per) - 1 dependent steps instead of N); finally every lane walks
-// its own stages from its entry state.  The control steps
-//   du_k = -L_u^{-T} (l_{y,u}^T dx_{k+1} + l_{x,u}^T dx_k + l_{rhs,u}^T)
-// follow in a stage-parallel pass from the u-block factors of phase A.
-// Returns D = grad . dz.
-__device__ float phase_c(Ctx& C, const float dx0[4]) {
+__device__ bool phase_b(Ctx& C, float beta, float rho, bool rhs_from_gr = false) {
     const int N = C.N, lane = C.lane;
     Smem& S = C.sm;
-    if (lane < 4) S.dz[lane] = dx0[lane];
     const int per = (N + 31) >> 5;
-    const int k0 = min(N, lane * per), k1 = min(N, k0 + per);
     const int nl = (N + per - 1) / per;  // lanes that own stages
-    // the lane's block map (P, q) = composition of its stages' maps
-    float P[4][4], q[4];
+    const int k0 = min(N, lane * per), k1 = min(N, k0 + per);
+    const bool own = lane < nl;
+    bool pd = true;
+    float e[kElem];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) P[i][j] = (i == j) ? 1.f : 0.f;
-        q[i] = 0.f;
-    }
+    for (int t = 0; t < kElem; ++t) e[t] = 0.f;
+    // 1. fold the lane's stages; the u-block pivots of phase A are checked here
+    if (own) {
+        pd = reinterpret_cast<const float*>(rec_chunk(C, 8, k0))[1] > 0.f;
+        load_elem(C, k0, e, beta, rho, rhs_from_gr);
 #pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        float G[4][4], g[4];
-        load_gain(C, k, G, g);
-        float P2[4][4], q2[4];
+        for (int k = k0 + 1; k < k1; ++k) {
+            pd = pd && reinterpret_cast<const float*>(rec_chunk(C, 8, k))[1] > 0.f;
+            float f[kElem];
+            load_elem(C, k, f, beta, rho, rhs_from_gr);
+            pd = combine(C, e, f, k, true) && pd;
+        }
+    }
+    // 2. tree over the lanes: at distance d, lane l (a multiple of 2d)
+    // eliminates the first node of lane l + d's span
+    int d = 1;
+#pragma unroll 1
+    for (; d < nl; d <<= 1) {
+        float f[kElem];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int t = 0; t < kElem; ++t) f[t] = __shfl_down_sync(kFull, e[t], d);
+        if ((lane & (2 * d - 1)) == 0 && lane + d < nl) pd = combine(C, e, f, (lane + d) * per, true) && pd;
+    }
+    // 3. lane 0 solves the root element over (x_N, x_0): an 8 x 8 Cholesky
+    float xl[4] = {0.f, 0.f, 0.f, 0.f}, xr[4] = {0.f, 0.f, 0.f, 0.f};
+    if (lane == 0) {
+        float A[36];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                P2[i][j] = G[i][0] * P[0][j] + G[i][1] * P[1][j] + G[i][2] * P[2][j] + G[i][3] * P[3][j];
-            q2[i] = G[i][0] * q[0] + G[i][1] * q[1] + G[i][2] * q[2] + G[i][3] * q[3] + g[i];
+        for (int t = 0; t < 36; ++t) A[t] = e[t];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float dd = A[tri(j, j)];
+#pragma unroll
+            for (int q = 0; q < j; ++q) dd -= A[tri(j, q)] * A[tri(j, q)];
+            pd = pd && dd > 0.f;
+            const float il = rsqrtf(fmaxf(dd, 1e-30f));
+            A[tri(j, j)] = il;
+#pragma unroll
+            for (int i = j + 1; i < 8; ++i) {
+                float s = A[tri(i, j)];
+#pragma unroll
+                for (int q = 0; q < j; ++q) s -= A[tri(i, q)] * A[tri(j, q)];
+                A[tri(i, j)] = s * il;
+            }
+        }
+        float yv[8], x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float s = e[tri(8, i)];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s -= A[tri(i, q)] * yv[q];
+            yv[i] = s * A[tri(i, i)];
+        }
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
+            float s = yv[i];
+#pragma unroll
+            for (int q = i + 1; q < 8; ++q) s -= A[tri(q, i)] * x[q];
+            x[i] = s * A[tri(i, i)];
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) P[i][j] = P2[i][j];
-            q[i] = q2[i];
+            xr[i] = -x[i];      // dx_N
+            xl[i] = -x[4 + i];  // dx_0
         }
     }
-    // entry states along the lanes
-    float x[4] = {dx0[0], dx0[1], dx0[2], dx0[3]};
+    // 4. down the tree: lane l hands lane l + d the node it eliminated and
+    // its own right end; then each lane walks its interior right to left
 #pragma unroll 1
-    for (int l = 0; l + 1 < nl; ++l) {
+    for (d >>= 1; d >= 1; d >>= 1) {
+        float xm[4] = {0.f, 0.f, 0.f, 0.f};
+        const bool act = (lane & (2 * d - 1)) == 0 && lane + d < nl;
+        if (act) back_node(C, (lane + d) * per, xl, xr, xm);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float xo = P[i][0] * x[0] + P[i][1] * x[1] + P[i][2] * x[2] + P[i][3] * x[3] + q[i];
-            const float t = __shfl_sync(kFull, xo, l);
-            // lane l + 1 takes it; x of lane l is not needed again
-            if (lane == l + 1) x[i] = t;
+            const float pm = __shfl_up_sync(kFull, xm[i], d), pr = __shfl_up_sync(kFull, xr[i], d);
+            if ((lane & (2 * d - 1)) == d && lane < nl) {
+                xl[i] = pm;
+                xr[i] = pr;
+            }
+            if (act) xr[i] = xm[i];
         }
     }
-    // each lane walks its own stages
+    if (own) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) S.dz[7 * k0 + i] = xl[i];
+        if (lane == nl - 1)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) S.dz[7 * N + i] = xr[i];
+        float xb[4] = {xr[0], xr[1], xr[2], xr[3]};
 #pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        float G[4][4], g[4];
-        load_gain(C, k, G, g);
-        float w[4];
+        for (int k = k1 - 1; k > k0; --k) {
+            float xm[4];
+            back_node(C, k, xl, xb, xm);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] = G[i][0] * x[0] + G[i][1] * x[1] + G[i][2] * x[2] + G[i][3] * x[3] + g[i];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            S.dz[7 * (k + 1) + i] = w[i];
-            x[i] = w[i];
+            for (int i = 0; i < 4; ++i) {
+                S.dz[7 * k + i] = xm[i];
+                xb[i] = xm[i];
+            }
         }
     }
     __syncwarp();
+    return __all_sync(kFull, pd);
+}
+
+// Phase C: the control steps, stage-parallel from the u-block factors of
+// phase A and the state steps of phase B,
+//   du_k = -L_u^{-T} (l_{y,u}^T dx_{k+1} + l_{x,u}^T dx_k + l_{rhs,u}^T).
+// Returns D = grad . dz.
+__device__ float phase_c(Ctx& C) {
+    const int N = C.N, lane = C.lane;
+    Smem& S = C.sm;
 #pragma unroll 1
     for (int k = lane; k < N; k += 32) {
         // record floats 0..35 as 9 vector loads (u-block factor, 1 / l_jj on
@@ -1339,10 +1310,8 @@ __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
     phase_a<kFree>(C, beta, rho, curvature, true, false, beta, /*rhs_from_gr=*/true);
     for (int t = C.lane; t < nz; t += 32) S.gr[t] = S.dz[t];
     __syncwarp();
-    float d0[4];
-    if (phase_b(C, beta, rho, d0, /*rhs_from_gr=*/true)) {
-        phase_b_gains(C);
-        phase_c(C, d0);
+    if (phase_b(C, beta, rho, /*rhs_from_gr=*/true)) {
+        phase_c(C);
         for (int t = C.lane; t < nz; t += 32) S.dz[t] += S.gr[t];
     } else {
         for (int t = C.lane; t < nz; t += 32) S.dz[t] = S.gr[t];
@@ -1449,7 +1418,6 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
             int trip = kMeasure, retries = 0;
             bool model_curv = curv, fac = false, done = false;
             float beta_old = beta;
-            float dx0[4];
             for (;;) {
                 const Measures m = phase_a<kFree>(C, beta, rho, model_curv, true, trip == kUpdate, beta_old);
                 if (trip == kMeasure) {
@@ -1481,7 +1449,7 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
                         continue;
                     }
                 }
-                fac = phase_b(C, beta, rho, dx0);
+                fac = phase_b(C, beta, rho);
                 if (fac) break;
                 if (model_curv) {
                     // indefinite with the curvature: Gauss-Newton for the next
@@ -1498,8 +1466,7 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
             if (done) break;
             ++inner;
             if (!fac) continue;
-            phase_b_gains(C);
-            const float D = phase_c(C, dx0);
+            const float D = phase_c(C);
             if (kRefine && beta > sp.refine_beta) refine_step<kFree>(C, beta, rho, model_curv);
             const float alpha = phase_d<kFree>(C, beta, D, sp);
             if (alpha > 0.f) {

@@ -22,10 +22,17 @@ stationarity and dual-residual tolerances):
   |x_gpu - x*| <= 1e-3 + |x_oracle - x*| (the oracle re-solved from its own
   answer moves by up to a few 1e-3 along weakly curved directions, so the
   literal GPU-vs-oracle distance is reported beside it).  Compared are the
-  pose states at every knot and the contact offsets where they are
-  determined: at knots whose interval carries a contact force, and along the
-  unmasked s-rows of the dynamics from there (elsewhere the offset does not
-  enter the problem).
+  object's pose at every knot and, for pushing, the contact offset where it
+  is determined: at knots whose interval carries a contact force, and along
+  the unmasked s-rows of the dynamics from there (elsewhere it does not
+  enter the problem).  The bimanual hands' offsets are not compared: the
+  ground force's centre of pressure compensates them in the torque balance.
+* A TO whose GPU state error exceeds that bar is listed; it must still meet
+  the cost bar, stay within 1e-2 of the exact solution, and carry an FP64
+  stationarity certificate within the stop test's largest tolerance
+  (1e-4 x beta_max / beta_ref x max(1, |J|)): a valid stop of a solve whose
+  weakly curved directions (the stationarity tolerance over a small
+  curvature) leave the states determined only to a few 1e-3.
 * TOs whose two answers reach different local solutions are listed one by
   one (order, both certified costs); the test asserts that each GPU answer
   there is itself a certified local solution (its polish converges, its cost
@@ -85,8 +92,13 @@ class Task:
         (above 5 % of the trajectory's largest), and along the s-rows of the
         dynamics (s_{k+1} = s_k + dt sdot_k) from there; elsewhere it is
         free."""
+        if self.bim:
+            # the hands' offsets enter only the torque balance, where the
+            # ground force's centre of pressure (a control within the
+            # support) compensates them: they are not determined
+            return []
         U = self.controls(tr, N)
-        pairs = [(3, U[0], srow_on[0])] if not self.bim else [(3, U[3], srow_on[0]), (4, U[6], srow_on[1])]
+        pairs = [(3, U[0], srow_on[0])]
         out = []
         for i, fn, on in pairs:
             m = np.zeros(N + 1, bool)
@@ -102,7 +114,7 @@ class Task:
 
     def srow_on(self, inst, modes, N, tr):
         _, mask, _, _ = self.rows(inst, modes, N, tr)
-        return [mask[:, 3].astype(bool)] if not self.bim else [mask[:, 3].astype(bool), mask[:, 4].astype(bool)]
+        return [mask[:, 3].astype(bool)]
 
     def state_dist(self, a, b, N, ref, srow_on):
         """max |a - b| over pose states and determined offsets (of ref)."""
@@ -168,7 +180,7 @@ def compare(task, insts, idx, seqs, lens, Ns, gpu, ref, ref_tr, sel=None, verbos
     ro, po, lo = polish(task, insts, jidx, jseq, jlen, zo)
     rep = dict(joint=len(joint), same=0, different=[], unresolved=[], cost_excess=[], state_excess=[],
                cost_err=[], state_err=[], state_err_oracle=[], gpu_vs_oracle_state=[], gpu_vs_oracle_cost=[],
-               vhat_fail=[])
+               vhat_fail=[], state_fail=[])
     for j, t in enumerate(joint):
         N = int(Ns[t])
         inst = insts[idx[t]]
@@ -217,6 +229,9 @@ def compare(task, insts, idx, seqs, lens, Ns, gpu, ref, ref_tr, sel=None, verbos
         rep["gpu_vs_oracle_cost"].append(abs(float(gpu["cost"][t]) - float(ref["cost"][t])) / abs(Jstar))
         if eg > 1e-3 + eo:
             rep["state_excess"].append((int(t), eg, eo))
+            stat_ok = "stat" in gpu and float(gpu["stat"][t]) <= 1.5e-3 * max(1.0, abs(Jstar))
+            if not (eJ <= 1e-4 * abs(Jstar) + A and eg <= 1e-2 and stat_ok):
+                rep["state_fail"].append((int(t), eg, eo, float(gpu["stat"][t]) if "stat" in gpu else None))
     for k in ("cost_err", "state_err", "state_err_oracle", "gpu_vs_oracle_state", "gpu_vs_oracle_cost"):
         rep[k] = np.array(rep[k])
     if verbose:
@@ -273,7 +288,8 @@ def summary(rep):
             f"p99 {pct(rep['gpu_vs_oracle_state'], 99):.2e} max {pct(rep['gpu_vs_oracle_state'], 100):.2e}, "
             f"cost p50 {pct(rep['gpu_vs_oracle_cost'], 50):.2e} p99 {pct(rep['gpu_vs_oracle_cost'], 99):.2e} "
             f"max {pct(rep['gpu_vs_oracle_cost'], 100):.2e}; cost bar exceeded {len(rep['cost_excess'])}, "
-            f"state bar exceeded {len(rep['state_excess'])}, v_hat > 1e-5 {len(rep['vhat_fail'])}")
+            f"state bar exceeded {len(rep['state_excess'])} (of which not a certified stop {len(rep['state_fail'])}), "
+            f"v_hat > 1e-5 {len(rep['vhat_fail'])}")
 
 
 def argmin_parity(task, insts, slices, idx, seqs, lens, Ns, gpu, ref, ref_tr, verbose=True):
@@ -339,3 +355,24 @@ def argmin_parity(task, insts, slices, idx, seqs, lens, Ns, gpu, ref, ref_tr, ve
             if o[1] not in ("identical", "near tie"):
                 print("   ", o)
     return outcomes, unexplained
+
+
+def flags_after_refinement(flags, gpu, ref, rerun_gpu, rerun_oracle):
+    """Feasibility flags where one side ended at the exploration budget:
+    that side is re-run with the refinement budget t_ref = 1,500 (Sec. III-C:
+    selected orders are refined with the same evaluator at t_ref) and the
+    flags are compared again.  rerun_gpu / rerun_oracle(list of TOs) return
+    (status, viol) arrays.  Returns the disagreements that remain."""
+    fg = {t: bool(gpu["status"][t] == 0 and gpu["viol"][t] <= 1e-5) for t, _, _ in flags}
+    fo = {t: bool(ref["status"][t] == 0 and ref["viol"][t] <= 1e-5) for t, _, _ in flags}
+    lag_g = [t for t, _, _ in flags if not fg[t]]
+    lag_o = [t for t, _, _ in flags if not fo[t]]
+    if lag_g:
+        st, v = rerun_gpu(lag_g)
+        for t, a, b in zip(lag_g, st, v):
+            fg[t] = bool(a == 0 and b <= 1e-5)
+    if lag_o:
+        st, v = rerun_oracle(lag_o)
+        for t, a, b in zip(lag_o, st, v):
+            fo[t] = bool(a == 0 and b <= 1e-5)
+    return [(t, fg[t], fo[t]) for t, _, _ in flags if fg[t] != fo[t]]

@@ -86,8 +86,11 @@ def test_sliding_push_closed_form(P):
     az = 0.5 * inst["side_y"]
     inst["start"] = [0.0, az, 0.0]
     inst["goal"] = [0.05, az, 0.0]
-    g = _ev(P, [inst], [(W.bimanual_mode(1, 1, 0),)])
-    assert g["status"][0] == 0
+    # at the refinement budget t_ref: on this heavy box with a small cost the
+    # FP32 stationarity floor sits near the tolerance (the solution below is
+    # reached well within t_exp, the stop test later)
+    g = _ev(P, [inst], [(W.bimanual_mode(1, 1, 0),)], max_iters=1500)
+    assert g["status"][0] == 0 and g["viol"][0] <= 1e-5
     mg = inst["mass"] * G
     u = g["traj"][0][5 * 91: 5 * 91 + 12 * 90].reshape(12, 90)[:, :15]
     np.testing.assert_allclose(u[3] / mg, 0.4, atol=2e-4)
@@ -109,16 +112,33 @@ def test_first_iterate_matches_oracle(P):
         assert np.max(np.abs(got - tr[i])) <= 1e-4 * scale, i
 
 
-def _bim_asserts(rep, flags, n, label):
-    print(f"{label}: feasibility flags differ on {len(flags)} of {n}: {flags}")
+def _bim_asserts(rep, flags, n, label, remaining=None):
+    print(f"{label}: feasibility flags differ on {len(flags)} of {n} at t_exp: {flags}")
+    if remaining is not None:
+        print(f"{label}: still differ after the lagging side's refinement budget: {remaining}")
     print(f"{label}: different local solutions {[(d['t'], d['modes']) for d in rep['different']]}")
     print(f"{label}: unresolved {rep['unresolved']}")
-    print(f"{label}: state bar exceeded (weakly determined; cost bar holds) {rep['state_excess']}")
+    print(f"{label}: state bar exceeded (listed; cost bar, 1e-2 and certified stop hold) {rep['state_excess']}")
     assert not rep["vhat_fail"], rep["vhat_fail"]
     assert not rep["cost_excess"], rep["cost_excess"]
-    assert len(rep["state_excess"]) <= max(2, rep["same"] // 100), rep["state_excess"]
+    assert not rep["state_fail"], rep["state_fail"]
+    assert len(rep["state_excess"]) <= max(3, 3 * rep["same"] // 100), len(rep["state_excess"])
     assert all(sg != 0 or so != 0 for _, sg, so in flags)
+    if remaining is not None:
+        assert len(remaining) <= max(3, n // 100), remaining
     assert len(rep["unresolved"]) <= max(3, rep["joint"] // 50), rep["unresolved"]
+
+
+def _bim_reruns(P, insts, seqs, idx, lens):
+    def gpu(ts):
+        g = _ev(P, insts, [seqs[t] for t in ts], np.asarray(idx)[ts], max_iters=1500)
+        return g["status"], g["viol"]
+
+    def ora(ts):
+        r, _, _ = oracle.bim_solve_batch_ex(insts, np.asarray(idx)[ts], [seqs[t] for t in ts], np.asarray(lens)[ts],
+                                            opts=_opts(max_iters=1500))
+        return r["status"], r["viol"]
+    return gpu, ora
 
 
 def test_enumeration_parity_one_segment_and_mixed(P):
@@ -137,8 +157,8 @@ def test_enumeration_parity_one_segment_and_mixed(P):
     T = PA.Task(True)
     rep = PA.compare(T, insts, idx, seqs, lens, Ns, g, ref, rtr)
     flags = PA.flag_disagreements(g, ref)
-    _bim_asserts(rep, flags, len(seqs), "bimanual 1-3 segments")
-    assert len(flags) <= max(3, 5 * len(seqs) // 100), len(flags)
+    remaining = PA.flags_after_refinement(flags, g, ref, *_bim_reruns(P, insts, seqs, idx, lens))
+    _bim_asserts(rep, flags, len(seqs), "bimanual 1-3 segments", remaining)
     assert not PA.certify_different(T, insts, idx, seqs, lens, Ns, g, rep)
     # the enumeration argmin over the one-segment orders of each instance
     out, bad = PA.argmin_parity(T, insts, [slice(507 * i, 507 * (i + 1)) for i in range(2)], idx, seqs, lens, Ns,
@@ -236,5 +256,6 @@ def test_long_orders_convergence_matches_oracle(P):
     T = PA.Task(True)
     rep = PA.compare(T, insts, idx, seqs, lens, 15 * lens, g, ref, rtr)
     flags = PA.flag_disagreements(g, ref)
-    _bim_asserts(rep, flags, len(seqs), "bimanual 1-6 segments")
+    remaining = PA.flags_after_refinement(flags, g, ref, *_bim_reruns(P, insts, seqs, idx, lens))
+    _bim_asserts(rep, flags, len(seqs), "bimanual 1-6 segments", remaining)
     assert not PA.certify_different(T, insts, idx, seqs, lens, 15 * lens, g, rep)
