@@ -48,14 +48,11 @@ N_STAGES = SEG * K
 # pattern, the 7x7 factorisation and solves, the value function, the
 # forward pass, the sequential trial merits up to the accepted step, retries
 FLOP_PER_STAGE_ITER = 3688.7
-# DRAM bytes (read + write) of one evaluator launch over the 20,736 orders
-# from an ncu capture of the current kernel, scaled by the TOs processed;
-# None while the kernel has changed since the last capture.  That capture
-# (a 4,096-order launch at 4 CTAs per SM: 2.24 MB read, 3.52 GB written,
-# stage records written back from L2, profiles/eval_kernel_push_l4.md)
-# predates the double-float theta row and the compensated trial merits.
-EVAL_TRAFFIC_BYTES = None
-EVAL_TRAFFIC_LAST_CAPTURE = (2.24128e6 + 3.516693e9) * 20736 / 4096
+# DRAM bytes (read + write) of one evaluator launch over the 20,736 orders,
+# from the ncu capture of the current kernel on the 4,096-order case (8.42 MB
+# read, 1.033 GB written: spills and stage records written back from L2;
+# profiles/eval_kernel_push_l4.md), scaled by the TOs processed
+EVAL_TRAFFIC_BYTES = (8.415744e6 + 1.03254e9) * 20736 / 4096
 # nominal FP32 FMA rate at the maximum clock (152 SMs x 128 lanes x 2 flop x
 # 2070 MHz), context only: the roofline's peak is measured at run time by the
 # library's FMA microbenchmark (comet_fp32_fma_peak)
@@ -324,10 +321,8 @@ def run_gpu(args):
                      "note": f"achieved = {FLOP_PER_STAGE_ITER} flop (the oracle's count of the method per "
                              "stage and iteration) x 80 stages x solver iterations / device time; peak = "
                              "measured FP32 FMA rate (of measured)",
-                     "traffic_note": ("null: the kernel changed after its last ncu capture (arithmetic only: "
-                                      "theta row in double-float, compensated trial merits); that capture "
-                                      f"measured {EVAL_TRAFFIC_LAST_CAPTURE / 1e9:.1f} GB per launch")
-                     if EVAL_TRAFFIC_BYTES is None else "ncu capture of the current kernel, scaled"},
+                     "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel on a "
+                                     "4,096-order launch (same workload), scaled by the TOs processed to 20,736"},
         "iterations_per_solve": iter_total / (args.steps * n * world),
     }
     if rank == 0 and args.plan_instances > 0:
@@ -339,7 +334,7 @@ def run_gpu(args):
     if rank == 0 and args.grammar:
         line["grammar"] = grammar_times(P)
     if rank == 0 and args.bimanual:
-        line["bimanual"] = bimanual_times(P, per=args.bim_per)
+        line["bimanual"] = bimanual_times(P, per=args.bim_per, fp32_peak=peak["tflops"])
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and args.mcts:
@@ -449,25 +444,32 @@ def hetero_times(P, n_inst=256, per=512, n_split=32):
 
 
 def batch_plan_times(P, n_inst=256, n_seq=16):
-    """Algorithm 1 on the mixed workload for many instances at once: every
-    instance seeded with its one-segment orders and a fifth of its
-    two-segment ones, beam 16, B = 256 per instance, three rounds, K_ref = 16
-    refined with t_ref = 600.  All instances through the batched planner (one
-    evaluator launch per round for all of them) against the single-instance
-    planner called once per instance on the first `n_seq` instances.  Device
-    time of exploration + refinement, plans per second."""
+    """Algorithm 1 on the mixed workload as configured: 256 instances
+    (rectangular sliders, 1-6 segments, 10-30 knots per segment), each seeded
+    with all its orders of at most two segments (156), beam k = 64, batch
+    B = 1,024 per instance, three rounds, an evaluation budget of 2e5 per
+    instance, the K_ref = 64 best refined with t_ref = 1,500.  All instances
+    through the batched planner (one persistent evaluator launch per round
+    for all of them, the round captured as a CUDA graph, the launch shape
+    autotuned) against the single-instance planner called once per instance
+    on the first `n_seq` instances.  Device time of exploration +
+    refinement."""
     insts = [W.push_mixed_instance(s) for s in range(n_inst)]
 
     def seeds(inst):
         two = [(a, b) for a in range(12) for b in range(12)] if inst["max_segments"] >= 2 else []
-        return [(m,) for m in range(12)] + two[::5]
+        return [(m,) for m in range(12)] + two
 
     sd = [seeds(i) for i in insts]
-    opts = dict(k=16, batch=256, rounds=3, k_ref=16, ref_iters=600)
+    opts = dict(k=64, batch=1024, rounds=3, k_ref=64, ref_iters=1500, budget=200000)
     prob = P.Problem(insts)
+    sample = P.pack_mode_seqs([s for i in range(n_seq) for s in sd[i]],
+                              np.concatenate([np.full(len(sd[i]), i, np.int32) for i in range(n_seq)]))
+    P.comet_autotune(prob.handle, sample, len(sample), 60)
     P.comet_plan_batch(prob.handle, list(range(n_seq)), sd[:n_seq], opts)  # warm
     rb = P.comet_plan_batch(prob.handle, list(range(n_inst)), sd, opts)
     t_all = (rb[0]["explore_ms"] + rb[0]["refine_ms"]) / 1e3
+    t_explore = rb[0]["explore_ms"] / 1e3
     rs = P.comet_plan_batch(prob.handle, list(range(n_seq)), sd[:n_seq], opts)
     t_sub = (rs[0]["explore_ms"] + rs[0]["refine_ms"]) / 1e3
     t_one, same = 0.0, 0
@@ -478,12 +480,16 @@ def batch_plan_times(P, n_inst=256, n_seq=16):
         same += int(r["best"] == rs[i]["best"] and r["best_cost"] == rs[i]["best_cost"])
     prob.close()
     feas = sum(int(r["best_status"] == 0) for r in rb)
+    evals = [r["evaluations"] for r in rb]
     return {
-        "instances": n_inst, "batched_ms": t_all * 1e3, "batched_plans_per_s": n_inst / t_all,
-        "feasible_plans": feas, "evaluations_median": float(np.median([r["evaluations"] for r in rb])),
+        "instances": n_inst, "config": "beam 64, B 1024, 3 rounds, budget 2e5/instance, seeds 156, K_ref 64 at 1500",
+        "batched_ms": t_all * 1e3, "plan_ms_per_instance": t_all * 1e3 / n_inst, "batched_plans_per_s": n_inst / t_all,
+        "explore_solves_per_s": float(np.sum(evals)) / t_explore, "feasible_plans": feas,
+        "evaluations_median": float(np.median(evals)), "evaluations_max": int(np.max(evals)),
         "subset": n_seq, "subset_batched_ms": t_sub * 1e3, "subset_one_by_one_ms": t_one * 1e3,
         "subset_speedup": t_one / t_sub, "subset_same_plans": same,
-        "note": "device time (exploration + refinement); one-by-one = the single-instance planner per instance",
+        "note": "device time (exploration + refinement); one-by-one = the single-instance planner per instance; "
+                "explore_solves_per_s = evaluations of all instances / exploration time",
     }
 
 
@@ -590,7 +596,13 @@ def grammar_times(P, n_inst=4):
     return out
 
 
-def bimanual_times(P, n_inst=8, per=512, n_plan=2):
+# the bimanual method's floating-point operations per stage and iteration,
+# counted by the oracle's counting build on random 1..6-segment orders of
+# the bimanual workload (python -m oracle.flop_count; tests/test_flop_count.py)
+BIM_FLOP_PER_STAGE_ITER = 8185.0
+
+
+def bimanual_times(P, n_inst=8, per=512, n_plan=2, fp32_peak=None):
     """The bimanual variant (box flipped by two point hands on a ground
     contact, 507 modes per segment, 15 knots per segment, one CTA per TO):
     random orders of 1..6 segments (512 per instance, 8 instances) in one
@@ -619,6 +631,9 @@ def bimanual_times(P, n_inst=8, per=512, n_plan=2):
     t = e0.elapsed_time(e1) / 1e3
     conv = int(((r["status"] == 0) & (r["viol"] < 1e-5)).sum())
     iters = float(r["iters"].float().mean())
+    # stage-iterations of the launch: iterations x intervals (15 per segment)
+    lens = torch.tensor([len(q) for q in seqs], dtype=torch.float64, device="cuda")
+    stage_iters = float((r["iters"].double() * 15.0 * lens).sum())
     cfg = P.comet_get_launch_config(prob.handle)
     prob.close()
     plans = []
@@ -630,10 +645,15 @@ def bimanual_times(P, n_inst=8, per=512, n_plan=2):
                       "best_len": len(res["best"]), "best_cost": res["best_cost"],
                       "feasible": bool(res["best_status"] == 0 and res["best_viol"] <= 1e-5)})
         pr.close()
+    achieved = BIM_FLOP_PER_STAGE_ITER * stage_iters / t / 1e12
+    roof = {"kernel": "bimanual_kernel (one CTA per TO)", "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
+            "peak": fp32_peak, "frac": achieved / fp32_peak if fp32_peak else None,
+            "note": f"achieved = {BIM_FLOP_PER_STAGE_ITER} flop (the oracle's count per stage and iteration) x "
+                    "stage-iterations of the launch / device time; peak = measured FP32 FMA rate (of measured)"}
     return {"orders": len(seqs), "converged_solves_per_s": conv / t, "solves_per_s": len(seqs) / t,
             "converged_fraction": conv / len(seqs), "iterations_per_solve": iters, "ms": t * 1e3,
-            "ctas_per_sm": cfg["blocks_per_sm"], "plans": plans,
-            "note": "one CTA (128 threads) per TO; device time"}
+            "ctas_per_sm": cfg["blocks_per_sm"], "plans": plans, "roofline": roof,
+            "note": "one CTA (128 threads) per TO; device time; v_hat in physical units"}
 
 
 def measured_peak(key, fallback):
@@ -699,9 +719,10 @@ def learned_times(P, insts, n_eval):
     # the ablation on held-out instances
     seeds = [(m,) for m in range(12)] + [tuple(s) for s in W.all_sequences(12, 2)]
     ps = P.pack_mode_seqs(seeds)
-    same, pl_ms, le_ms, pl_ev, le_ev = 0, [], [], [], []
+    same, pl_ms, le_ms, pl_ev, le_ev, gaps = 0, [], [], [], [], []
     for i in range(48, 48 + n_eval):
-        pr = P.Problem([insts[i % len(insts)]])
+        # held-out instances: seeds 48.. (the training set uses seeds 1000..1511)
+        pr = P.Problem([W.push_l4_instance(i)])
         a = P.comet_plan(pr.handle, 0, ps, len(ps), dict(k=64, batch=4096, rounds=3, k_ref=256))
         qq = P.comet_proposal_create(pr.handle)
         P.comet_proposal_set_params(qq, flat)
@@ -709,6 +730,7 @@ def learned_times(P, insts, n_eval):
         P.comet_proposal_destroy(qq)
         pr.close()
         same += b["best_cost"] <= a["best_cost"] * (1 + 1e-3) + 1e-9
+        gaps.append((b["best_cost"] - a["best_cost"]) / abs(a["best_cost"]))
         pl_ms.append(a["explore_ms"] + a["refine_ms"])
         le_ms.append(b["explore_ms"] + b["refine_ms"])
         pl_ev.append(a["evaluations"])
@@ -725,7 +747,12 @@ def learned_times(P, insts, n_eval):
         "plain_ms": float(np.median(pl_ms)), "learned_ms": float(np.median(le_ms)),
         "plain_evals": float(np.median(pl_ev)), "learned_evals": float(np.median(le_ev)),
         "plan_speedup": float(np.median(pl_ms) / np.median(le_ms)),
-        "note": "plan times are device time (medians); same_best = learned plan within 1e-3 of plain expansion's",
+        "cost_gap": {"p10": float(np.percentile(gaps, 10)), "p50": float(np.median(gaps)),
+                     "p90": float(np.percentile(gaps, 90)), "max": float(np.max(gaps)), "min": float(np.min(gaps)),
+                     "learned_better_by_1e-3": int(np.sum(np.array(gaps) < -1e-3)),
+                     "learned_worse_by_1e-3": int(np.sum(np.array(gaps) > 1e-3))},
+        "note": "plan times are device time (medians); same_best = learned plan within 1e-3 of plain expansion's; "
+                "cost_gap = (J_learned - J_plain) / J_plain of the returned plans over the held-out instances",
     }
 
 
@@ -744,7 +771,7 @@ def main():
     ap.add_argument("--bim-per", type=int, default=512, help="random orders per instance in the bimanual leg")
     ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
     ap.add_argument("--mcts", type=int, default=1, help="MCTS comparison leg (1) or skip it (0)")
-    ap.add_argument("--learned-instances", type=int, default=8,
+    ap.add_argument("--learned-instances", type=int, default=32,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -43,7 +43,8 @@ def build(force: bool = False, count_flops: bool = False) -> str:
     iteration; the default build carries no counter."""
     path = _LIB_FLOPS_PATH if count_flops else _LIB_PATH
     os.makedirs(os.path.dirname(path), exist_ok=True)
-    srcs = [_SRC, _SRC_BIM, os.path.join(_HERE, "comet_oracle.h"), os.path.join(_HERE, "bimanual.h")]
+    srcs = [_SRC, _SRC_BIM, os.path.join(_HERE, "comet_oracle.h"), os.path.join(_HERE, "bimanual.h"),
+            os.path.join(_HERE, "flops.h")]
     if force or not os.path.exists(path) or os.path.getmtime(path) < max(os.path.getmtime(f) for f in srcs):
         tmp = path + f".tmp{os.getpid()}"
         subprocess.check_call(
@@ -539,6 +540,29 @@ def flops_per_stage_iteration(insts, inst_idx, seqs, lens, opts: Opts | None = N
         tr = np.zeros(traj_len(N))
         r = Result()
         L.orc_solve(ctypes.byref(make_instance(inst)), len(m), _ptr(m, _u8p), N, None, ctypes.byref(o),
+                    _ptr(tr, _dp), None, ctypes.byref(r))
+        work += r.iters * N
+    total = int(L.orc_flop_count())
+    return total / max(work, 1), total, work
+
+
+def bim_flops_per_stage_iteration(insts, inst_idx, seqs, lens, opts: Opts | None = None):
+    """flops_per_stage_iteration for the bimanual task (counting build of the
+    bimanual oracle, orders solved one by one on the calling thread)."""
+    L = ctypes.CDLL(build(count_flops=True))
+    L.bim_solve.argtypes = [_P(BimInstance), ctypes.c_int32, _u16p, ctypes.c_int32, _dp, _P(Opts), _dp, _dp,
+                            _P(Result)]
+    L.orc_flop_count.restype = ctypes.c_uint64
+    o = opts if opts is not None else default_opts()
+    L.orc_flop_reset()
+    work = 0
+    for t in range(len(inst_idx)):
+        inst = insts[int(inst_idx[t])]
+        m = np.ascontiguousarray(seqs[t][: int(lens[t])], dtype=np.uint16)
+        N = int(inst["knots_per_segment"]) * int(lens[t])
+        tr = np.zeros(bim_traj_len(N))
+        r = Result()
+        L.bim_solve(ctypes.byref(bim_make_instance(inst)), len(m), _ptr(m, _u16p), N, None, ctypes.byref(o),
                     _ptr(tr, _dp), None, ctypes.byref(r))
         work += r.iters * N
     total = int(L.orc_flop_count())

@@ -9,6 +9,7 @@
  * search_merit.  All arithmetic is IEEE double.
  */
 #include "bimanual.h"
+#include "flops.h"
 
 #include <math.h>
 #include <pthread.h>
@@ -54,6 +55,11 @@ void bim_interval_rows(const bim_instance* in, int32_t mode, int32_t mask_sL, in
     const int32_t g = mode / 169, hL = (mode / 13) % 13, hR = mode % 13;
     const double mg = in->mass * in->grav, lbar = in->ax > in->az ? in->ax : in->az;
     const double th = xk[2], cth = cos(th), sth = sin(th);
+    /* values: kinematic defects 15, wrench sums 6 + 2 x 14 + scaling 3,
+     * sine and cosine 2, ground rows 10, hand rows 2 x 8; Jacobians: wrench
+     * entries 2 x 12 + 4 + scaling 24, ground 10, hands 2 x 6 */
+    FLOPS_ROWS(15 + 6 + 28 + 3 + 2 + 10 + 16);
+    FLOPS_JAC(24 + 4 + 24 + 10 + 12);
     for (int r = 0; r < NR; ++r) {
         c[r] = 0.0;
         mask[r] = 1;
@@ -312,6 +318,7 @@ void bim_cold_start(const bim_instance* in, int32_t N, double* traj) {
 
 double bim_cost(const bim_instance* in, int32_t N, const double* tr) {
     double R[NU], J = 0.0;
+    FLOPS(3 * 4 + (int64_t)NU * N * 3);
     control_weights(in, R);
     for (int i = 0; i < 3; ++i) {
         const double e = CXb(tr, N, N, i) - in->goal[i];
@@ -344,11 +351,16 @@ double bim_al_merit(const bim_instance* in, int32_t len, const uint16_t* modes, 
     for (int i = 0; i < 3; ++i) L += row_al(0, lam[i], beta, CXb(traj, N, 0, i) - in->start[i]);
     double cc[NR], sc[NR], J[NR * NL];
     uint8_t mk[NR], iq[NR];
+    COUNT_ROWS(1, 0);
     for (int32_t k = 0; k < N; ++k) {
         rows_at(in, modes, len, N, traj, k, cc, mk, iq, sc, J);
         for (int r = 0; r < NR; ++r)
-            if (mk[r]) L += row_al(iq[r], lam[3 + NR * k + r], beta, cc[r]);
+            if (mk[r]) {
+                L += row_al(iq[r], lam[3 + NR * k + r], beta, cc[r]);
+                FLOPS(6);
+            }
     }
+    COUNT_ROWS(1, 1);
     return L;
 }
 
@@ -357,6 +369,7 @@ static int chol(int n, const double* A, double* L) {
     for (int j = 0; j < n; ++j) {
         double d = A[j * n + j];
         for (int p = 0; p < j; ++p) d -= L[j * n + p] * L[j * n + p];
+        FLOPS(2 * j + 1 + (n - 1 - j) * (2 * j + 1));
         if (!(d > 0.0)) return -1;
         const double ljj = sqrt(d);
         L[j * n + j] = ljj;
@@ -371,6 +384,7 @@ static int chol(int n, const double* A, double* L) {
 
 static void chol_solve(int n, const double* L, const double* b, double* x) {
     double y[NW];
+    FLOPS(2 * n * n);
     for (int i = 0; i < n; ++i) {
         double s = b[i];
         for (int p = 0; p < i; ++p) s -= L[i * n + p] * y[p];
@@ -401,12 +415,14 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
     double cc[NR], sc[NR], Jl[NR * NL];
     uint8_t mk[NR], iq[NR];
     int32_t ok = 0;
+    COUNT_ROWS(0, 0);
     for (int32_t k = N - 1; k >= 0; --k) {
         rows_at(in, modes, len, N, traj, k, cc, mk, iq, sc, Jl);
         /* local Gauss-Newton model of the AL over (x_k, u_k, x_{k+1}) */
         double H[NL * NL], g[NL];
         memset(H, 0, sizeof(H));
         memset(g, 0, sizeof(g));
+        FLOPS(NU * 3);
         for (int j = 0; j < NU; ++j) {
             H[(NX + j) * NL + NX + j] += 2.0 * R[j];
             g[NX + j] += 2.0 * R[j] * CUb(traj, N, k, j);
@@ -416,6 +432,13 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
             const double l = lam[3 + NR * (int64_t)k + r];
             if (iq[r] && !(l + beta * cc[r] > 0.0)) continue;
             const double y = row_y(iq[r], l, beta, cc[r]);
+#ifdef ORC_COUNT_FLOPS
+            {
+                int nnz = 0;
+                for (int i = 0; i < NL; ++i) nnz += Jl[r * NL + i] != 0.0;
+                FLOPS(2 + 3 * nnz + nnz * (nnz + 1));
+            }
+#endif
             for (int i = 0; i < NL; ++i) {
                 if (Jl[r * NL + i] == 0.0) continue;
                 g[i] += y * Jl[r * NL + i];
@@ -437,6 +460,7 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
             for (int j = 0; j < NX; ++j) S[(NU + i) * NW + NU + j] += V[i * NX + j];
             gw[NU + i] += v[i];
         }
+        FLOPS(NW + 15 + NX); /* rho, V_{k+1} (lower triangle), v_{k+1} */
         if (chol(NW, S, L) != 0) {
             ok = -1;
             break;
@@ -450,6 +474,7 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
         chol_solve(NW, L, gw, sol);
         for (int i = 0; i < NW; ++i) kg[(int64_t)NW * k + i] = -sol[i];
         double Vn[NX * NX], vn[NX];
+        FLOPS(15 * NW * 2 + NX * NW * 2); /* symmetric V (lower triangle) and v */
         for (int i = 0; i < NX; ++i) {
             for (int j = 0; j < NX; ++j) {
                 double s = H[i * NL + j];
@@ -494,6 +519,7 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
             }
             for (int i = 0; i < NX; ++i) dx[i] = -dx[i];
             for (int i = 0; i < NX; ++i) dz[i] = dx[i];
+            FLOPS((int64_t)N * NW * 2 * NX);
             for (int32_t k = 0; k < N; ++k) {
                 double dw[NW];
                 for (int i = 0; i < NW; ++i) {
@@ -509,6 +535,7 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
             }
         }
     }
+    COUNT_ROWS(1, 1);
     free(Kg);
     free(kg);
     return ok;
@@ -516,6 +543,7 @@ int32_t bim_gn_step(const bim_instance* in, int32_t len, const uint16_t* modes, 
 
 static void axpy_traj(int32_t N, const double* tr, double alpha, const double* dz, double* out) {
     const int32_t NZ = NX + NU;
+    FLOPS(2 * ((int64_t)NZ * N + NX));
     for (int32_t k = 0; k <= N; ++k)
         for (int i = 0; i < NX; ++i) out[i * (N + 1) + k] = CXb(tr, N, k, i) + alpha * dz[(int64_t)NZ * k + i];
     for (int32_t k = 0; k < N; ++k)
@@ -562,6 +590,14 @@ static void measures(const bim_instance* in, int32_t len, const uint16_t* modes,
             if (!isfinite(cc[r])) m->finite = 0;
             const double yr = row_y(iq[r], lam[idx], beta, cc[r]);
             y[idx] = yr;
+            FLOPS(6);
+#ifdef ORC_COUNT_FLOPS
+            if (yr != 0.0) {
+                int nnz = 0;
+                for (int i = 0; i < NL; ++i) nnz += Jl[r * NL + i] != 0.0;
+                FLOPS(2 * nnz);
+            }
+#endif
             const double vv = iq[r] ? (cc[r] > 0.0 ? cc[r] : 0.0) : fabs(cc[r]);
             if (vv > m->viol) m->viol = vv;
             if (vv / sc[r] > m->vphys) m->vphys = vv / sc[r];
@@ -638,6 +674,7 @@ int32_t bim_solve_ex(const bim_instance* in, int32_t len, const uint16_t* modes,
         }
         double D = 0.0;
         for (int64_t i = 0; i < nt; ++i) D += grad[i] * dz[i];
+        FLOPS(2 * nt);
         const double phi0 = bim_al_merit(in, len, modes, N, z, lam, beta);
         const double slack = opt->ls_slack * fabs(phi0);
         const int32_t flat = fabs(D) <= slack;

@@ -31,33 +31,16 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* Flop counter (compiled in with -DORC_COUNT_FLOPS, a separate build used
- * to measure the method's arithmetic per stage and iteration).  It counts
- * the floating-point operations of the method's steps: one per add,
- * multiply, divide, square root, sine or cosine; products with structurally
- * zero Jacobian entries are not counted, and the symmetric local model is
- * counted on its lower triangle.  Work that only this plain implementation
- * repeats (the constant row scales, dense zero fills) is not counted. */
+#include "flops.h"
+
 #ifdef ORC_COUNT_FLOPS
-static __thread uint64_t g_flops;
-/* what a row evaluation counts: values (trial merits need only these) and
- * Jacobians; the step re-evaluates the rows the measures have just taken at
- * the same point, which the method does once */
-static __thread int g_rows_on = 1, g_jac_on = 1;
-#define FLOPS(n) (g_flops += (uint64_t)(n))
-#define FLOPS_ROWS(n) (g_flops += g_rows_on ? (uint64_t)(n) : 0)
-#define FLOPS_JAC(n) (g_flops += g_jac_on ? (uint64_t)(n) : 0)
-#define COUNT_ROWS(r, j) (g_rows_on = (r), g_jac_on = (j))
-#else
-#define FLOPS(n) ((void)0)
-#define FLOPS_ROWS(n) ((void)0)
-#define FLOPS_JAC(n) ((void)0)
-#define COUNT_ROWS(r, j) ((void)0)
+__thread uint64_t orc_g_flops;
+__thread int orc_g_rows_on = 1, orc_g_jac_on = 1;
 #endif
 
 uint64_t orc_flop_count(void) {
 #ifdef ORC_COUNT_FLOPS
-    return g_flops;
+    return orc_g_flops;
 #else
     return 0;
 #endif
@@ -65,7 +48,7 @@ uint64_t orc_flop_count(void) {
 
 void orc_flop_reset(void) {
 #ifdef ORC_COUNT_FLOPS
-    g_flops = 0;
+    orc_g_flops = 0;
 #endif
 }
 

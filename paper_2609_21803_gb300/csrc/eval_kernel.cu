@@ -778,31 +778,40 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, bool rhs_from_gr = false)
     const int nl = (N + per - 1) / per;  // lanes that own stages
     const int k0 = min(N, lane * per), k1 = min(N, k0 + per);
     const bool own = lane < nl;
+    const int nlev = nl > 1 ? 32 - __clz(nl - 1) : 0;  // tree levels, ceil(log2 nl)
+    const int nsteps = (per - 1) + nlev;
     bool pd = true;
     float e[kElem];
 #pragma unroll
     for (int t = 0; t < kElem; ++t) e[t] = 0.f;
-    // 1. fold the lane's stages; the u-block pivots of phase A are checked here
     if (own) {
         pd = reinterpret_cast<const float*>(rec_chunk(C, 8, k0))[1] > 0.f;
         load_elem(C, k0, e, beta, rho, rhs_from_gr);
-#pragma unroll 1
-        for (int k = k0 + 1; k < k1; ++k) {
-            pd = pd && reinterpret_cast<const float*>(rec_chunk(C, 8, k))[1] > 0.f;
-            float f[kElem];
-            load_elem(C, k, f, beta, rho, rhs_from_gr);
-            pd = combine(C, e, f, k, true) && pd;
-        }
     }
-    // 2. tree over the lanes: at distance d, lane l (a multiple of 2d)
-    // eliminates the first node of lane l + d's span
-    int d = 1;
+    // 1-2. one loop, one elimination call site: steps 0 .. per-2 fold the
+    // lane's next stage (the u-block pivot flag of phase A checked on the
+    // way), the remaining steps are the tree levels d = 1, 2, 4, ...: lane l
+    // (a multiple of 2d) eliminates the first node of lane l + d's span
 #pragma unroll 1
-    for (; d < nl; d <<= 1) {
+    for (int st = 0; st < nsteps; ++st) {
         float f[kElem];
+        bool act;
+        int km;
+        if (st < per - 1) {  // warp-uniform
+            km = k0 + 1 + st;
+            act = own && km < k1;
+            if (act) {
+                pd = pd && reinterpret_cast<const float*>(rec_chunk(C, 8, km))[1] > 0.f;
+                load_elem(C, km, f, beta, rho, rhs_from_gr);
+            }
+        } else {
+            const int d = 1 << (st - (per - 1));
 #pragma unroll
-        for (int t = 0; t < kElem; ++t) f[t] = __shfl_down_sync(kFull, e[t], d);
-        if ((lane & (2 * d - 1)) == 0 && lane + d < nl) pd = combine(C, e, f, (lane + d) * per, true) && pd;
+            for (int t = 0; t < kElem; ++t) f[t] = __shfl_down_sync(kFull, e[t], d);
+            act = (lane & (2 * d - 1)) == 0 && lane + d < nl;
+            km = (lane + d) * per;
+        }
+        if (act) pd = combine(C, e, f, km, true) && pd;
     }
     // 3. lane 0 solves the root element over (x_N, x_0): an 8 x 8 Cholesky
     float xl[4] = {0.f, 0.f, 0.f, 0.f}, xr[4] = {0.f, 0.f, 0.f, 0.f};
@@ -847,21 +856,37 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, bool rhs_from_gr = false)
             xl[i] = -x[4 + i];  // dx_0
         }
     }
-    // 4. down the tree: lane l hands lane l + d the node it eliminated and
-    // its own right end; then each lane walks its interior right to left
+    // 4. back-substitution, one call site: the tree levels top-down (lane l
+    // hands lane l + d the node it eliminated and its own right end), then
+    // each lane's interior right to left
+    float xc[4];  // dx of the node right of the current interior node
 #pragma unroll 1
-    for (d >>= 1; d >= 1; d >>= 1) {
-        float xm[4] = {0.f, 0.f, 0.f, 0.f};
-        const bool act = (lane & (2 * d - 1)) == 0 && lane + d < nl;
-        if (act) back_node(C, (lane + d) * per, xl, xr, xm);
+    for (int st = nsteps - 1; st >= 0; --st) {
+        const bool tree = st >= per - 1;  // warp-uniform
+        const int d = tree ? 1 << (st - (per - 1)) : 0;
+        if (st == per - 2)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float pm = __shfl_up_sync(kFull, xm[i], d), pr = __shfl_up_sync(kFull, xr[i], d);
-            if ((lane & (2 * d - 1)) == d && lane < nl) {
-                xl[i] = pm;
-                xr[i] = pr;
+            for (int i = 0; i < 4; ++i) xc[i] = xr[i];
+        const bool act = tree ? ((lane & (2 * d - 1)) == 0 && lane + d < nl) : (own && k0 + 1 + st < k1);
+        const int km = tree ? (lane + d) * per : k0 + 1 + st;
+        float xm[4] = {0.f, 0.f, 0.f, 0.f};
+        if (act) back_node(C, km, xl, tree ? xr : xc, xm);
+        if (tree) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float pm = __shfl_up_sync(kFull, xm[i], d), pr = __shfl_up_sync(kFull, xr[i], d);
+                if ((lane & (2 * d - 1)) == d && lane < nl) {
+                    xl[i] = pm;
+                    xr[i] = pr;
+                }
+                if (act) xr[i] = xm[i];
             }
-            if (act) xr[i] = xm[i];
+        } else if (act) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                S.dz[7 * km + i] = xm[i];
+                xc[i] = xm[i];
+            }
         }
     }
     if (own) {
@@ -870,17 +895,6 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, bool rhs_from_gr = false)
         if (lane == nl - 1)
 #pragma unroll
             for (int i = 0; i < 4; ++i) S.dz[7 * N + i] = xr[i];
-        float xb[4] = {xr[0], xr[1], xr[2], xr[3]};
-#pragma unroll 1
-        for (int k = k1 - 1; k > k0; --k) {
-            float xm[4];
-            back_node(C, k, xl, xb, xm);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                S.dz[7 * k + i] = xm[i];
-                xb[i] = xm[i];
-            }
-        }
     }
     __syncwarp();
     return __all_sync(kFull, pd);
@@ -1324,8 +1338,13 @@ __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
 // kRefine: the variant with the FP64 refinement step compiled in; the
 // launch picks it only when the penalty can exceed refine_beta, so the
 // default kernel carries none of that code (a smaller instruction footprint).
+// At most 3 resident CTAs of 4 warps per SM: the register cap is then 168,
+// where the elimination of phase B and the assembly of phase A run without
+// most of the local-memory spills a 128-register cap costs (12 warps per SM
+// at 168 registers were 7 % faster than 16 at 128 on the 4-segment
+// enumeration, with DRAM write-back 7 times lower).
 template <bool kRefine, bool kFree>
-__global__ void __launch_bounds__(128, 4) eval_kernel(EvalArgs A) {
+__global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
     extern __shared__ float smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;

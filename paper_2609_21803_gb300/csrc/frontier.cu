@@ -675,7 +675,10 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
     const int32_t batch = po.batch;
     for (int i = 0; i < n_inst; ++i) {
         const int64_t n0 = seed_offsets[i + 1] - seed_offsets[i];
-        const int64_t cap = po.budget > 0 ? std::max<int64_t>(po.budget, n0) : n0 + (int64_t)po.rounds * batch;
+        // V never holds more than the seeds and `rounds` batches, nor more
+        // than the budget
+        const int64_t reach = n0 + (int64_t)po.rounds * batch;
+        const int64_t cap = po.budget > 0 ? std::max<int64_t>(std::min<int64_t>(po.budget, reach), n0) : reach;
         const comet_status st =
             comet_frontier_create_ex(p, instances[i], cap, (int32_t)std::min<int64_t>(batch, cap),
                                      std::max(po.k, po.k_ref), po.radius, po.grammar, &fr[i]);

@@ -32,3 +32,10 @@ def test_counter_matches_hand_counts():
     chol7 = sum(2 * j + 1 + (6 - j) * (2 * j + 1) for j in range(7))
     assert total >= chol7 + 5 * 2 * 49
     assert total < 20000
+
+
+def test_bench_bimanual_constant_is_the_oracle_count():
+    import bench
+
+    f, total, work = flop_count.measure_bimanual()
+    assert f == pytest.approx(bench.BIM_FLOP_PER_STAGE_ITER, rel=1e-3)
