@@ -387,6 +387,47 @@ comet_status comet_sample_orders(comet_problem* p, int32_t instance, uint64_t se
 /* Mode code of an order (see the conventions above); 0 if invalid. */
 uint64_t comet_mode_code(const comet_mode_seq* seq, int32_t n_modes);
 
+/* ---- timing optimisation (Sec. III-C, Sec. IV-A) --------------------- */
+
+/* Bounds of the interval durations when timing is optimised. */
+typedef struct {
+    double h_min, h_max; /* bounds of every interval's duration h_k [s], 0 < h_min <= h_max */
+    double T_max;        /* duration bound: sum_k h_k <= T_max [s], T_max > 0 */
+} comet_timing_opts;
+
+/* Solve the mode-conditioned TO of each order of a pushing problem with the
+ * interval durations among the controls (Sec. III-C: with timing optimised
+ * the interval durations join the controls; Sec. IV-A: an optimised time
+ * step under the benchmark's duration bound).  Readings: interval k lasts
+ * h_k, a fourth control bounded by h_min <= h_k <= h_max; the elapsed time
+ * tau, a fifth state, carries the duration bound (tau_{k+1} = tau_k + h_k,
+ * tau_0 = 0, tau_N <= T_max), which keeps the problem stage-wise; the
+ * dynamics rows are (x_{k+1} - x_k - h_k f(x_k, u_k)) / sigma_i with the
+ * fixed-step row scales; the cost is the fixed-step one (no term in h).
+ * The method (PHR augmented Lagrangian, Newton step with the dynamics
+ * curvature including the h cross terms and the Gauss-Newton fallback,
+ * backward sweep, trial merits, multiplier and penalty updates, stop test,
+ * FP64 certificate) is that of comet_eval_modes.
+ *   mode_seqs, n: orders as in comet_eval_modes; malformed orders get
+ *       COMET_TO_NONFINITE and a NaN cost;
+ *   warm_starts: NULL (cold start: the fixed-step cold start, h_k = dt
+ *       clipped into the bounds, tau_k = k h_0) or n records of
+ *       9 N_max + 5 floats: x, y, theta, s, tau [N_max + 1] each, then
+ *       f_n, f_t, sdot, h [N_max] each;
+ *   max_iters: iteration budget (0 = the problem's max_iters);
+ *   out_cost, out_status: [n]; out_traj: NULL or n records in the
+ *       warm-start layout.
+ * Every array must be device memory of the problem's device (host pointers
+ * are rejected with INVALID_ARG); the call is asynchronous on the problem's
+ * stream.  Per-TO diagnostics are then read with comet_eval_stats.  The
+ * per-warp state lives in shared memory (about 1.2 + 0.19 N_max KB);
+ * problems whose N_max does not fit are rejected with INVALID_ARG.
+ * Errors: INVALID_ARG (NULL problem or timing, a bimanual problem, bounds
+ * out of order, n < 0, host arrays, N_max too large), OOM / CUDA. */
+comet_status comet_eval_modes_timed(comet_problem* p, const comet_timing_opts* timing,
+                                    const comet_mode_seq* mode_seqs, int64_t n, const float* warm_starts,
+                                    int32_t max_iters, float* out_cost, float* out_traj, int32_t* out_status);
+
 /* ---- measurement (no paper counterpart) ------------------------------ */
 
 /* FP32 FMA throughput of the current device, the peak of the evaluator's

@@ -99,6 +99,10 @@ class GemmEpilogue(ctypes.Structure):
 GEMM_STORE, GEMM_BIAS_GELU, GEMM_GELU_GRAD, GEMM_ATOMIC_ADD = 0, 1, 2, 3
 
 
+class TimingOpts(ctypes.Structure):
+    _fields_ = [("h_min", ctypes.c_double), ("h_max", ctypes.c_double), ("T_max", ctypes.c_double)]
+
+
 class MctsOpts(ctypes.Structure):
     _fields_ = [("n_modes", ctypes.c_int32), ("l_max", ctypes.c_int32), ("grammar", ctypes.c_int32),
                 ("reward", ctypes.c_int32), ("max_evals", ctypes.c_int64), ("seed", ctypes.c_uint64),
@@ -121,6 +125,7 @@ assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == MODE_SEQ_BYTES
 EXPORTS = (
     "comet_default_opts", "comet_problem_create", "comet_problem_destroy", "comet_traj_stride",
     "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_mode_code",
+    "comet_eval_modes_timed",
     "comet_last_error", "comet_eval_modes_noalloc", "comet_fp32_fma_peak", "comet_fp32_fma_peak_threads",
     "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
     "comet_frontier_next", "comet_frontier_size", "comet_frontier_best", "comet_frontier_copy_next",
@@ -164,6 +169,7 @@ def lib(build_if_missing: bool = False):
             L.comet_eval_modes.argtypes = [vp, vp, i64, vp, vp, vp, vp]
             L.comet_eval_modes_budget.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp]
             L.comet_eval_stats.argtypes = [vp, vp, vp, vp, vp]
+            L.comet_eval_modes_timed.argtypes = [vp, ctypes.POINTER(TimingOpts), vp, i64, vp, i32, vp, vp, vp]
             L.comet_fp32_fma_peak.argtypes = [vp, i32, vp, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double)]
             L.comet_fp32_fma_peak_threads.argtypes = []
@@ -316,6 +322,17 @@ def comet_eval_modes_budget(problem, mode_seqs, n, warm_starts, max_iters, out_c
 
 def comet_eval_stats(problem, out_viol, out_merit, out_iters, out_stat):
     _check(lib().comet_eval_stats(problem, _ptr(out_viol), _ptr(out_merit), _ptr(out_iters), _ptr(out_stat)))
+
+
+def comet_eval_modes_timed(problem, timing: dict, mode_seqs, n, warm_starts, max_iters, out_cost, out_traj,
+                           out_status):
+    """Timing optimisation (comet_eval_modes_timed); timing: {"h_min",
+    "h_max", "T_max"}; every array device memory; trajectory records of
+    9 N_max + 5 floats (x, y, theta, s, tau [N_max + 1], f_n, f_t, sdot, h
+    [N_max])."""
+    t = TimingOpts(float(timing["h_min"]), float(timing["h_max"]), float(timing["T_max"]))
+    _check(lib().comet_eval_modes_timed(problem, ctypes.byref(t), _ptr(mode_seqs), int(n), _ptr(warm_starts),
+                                        int(max_iters), _ptr(out_cost), _ptr(out_traj), _ptr(out_status)))
 
 
 def comet_fp32_fma_peak(cuda_stream, iters: int, scratch) -> tuple[float, float]:

@@ -133,6 +133,9 @@ void make_dev_instance(const comet_instance_desc& d, DevInstance* out) {
     q.kth_hi = (float)kth;
     q.kth_lo = (float)(kth - (double)q.kth_hi);
     for (int f = 0; f < 4; ++f) q.a_lo[f] = (float)(q.a_d[f] - (double)q.a[f]);
+    const double kc = q.kappa_d * q.inv_c2_d;
+    q.kc_hi = (float)kc;
+    q.kc_lo = (float)(kc - (double)q.kc_hi);
 }
 
 // Solver parameters of a call from the options and an iteration budget
@@ -447,6 +450,7 @@ comet_status comet_problem_destroy(comet_problem* p) {
     cudaFree(p->d_queue);
     cudaFree(p->d_bad);
     cudaFree(p->d_ws);
+    cudaFree(p->d_tws);
     cudaFree(p->d_viol);
     cudaFree(p->d_merit);
     cudaFree(p->d_iters);
@@ -560,6 +564,82 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* seq
 comet_status comet_eval_modes(comet_problem* p, const comet_mode_seq* seqs, int64_t n, const float* warm,
                               float* out_cost, float* out_traj, int32_t* out_status) {
     return comet_eval_modes_budget(p, seqs, n, warm, 0, out_cost, out_traj, out_status);
+}
+
+comet_status comet_eval_modes_timed(comet_problem* p, const comet_timing_opts* timing,
+                                    const comet_mode_seq* mode_seqs, int64_t n, const float* warm_starts,
+                                    int32_t max_iters, float* out_cost, float* out_traj, int32_t* out_status) {
+    if (!p || !timing) return fail(COMET_ERR_INVALID_ARG, "problem and timing are required");
+    if (p->task != COMET_TASK_PUSHER_SLIDER)
+        return fail(COMET_ERR_INVALID_ARG, "timing optimisation is defined for pushing problems");
+    if (!(timing->h_min > 0.0 && timing->h_min <= timing->h_max && timing->T_max > 0.0))
+        return fail(COMET_ERR_INVALID_ARG, "timing bounds: need 0 < h_min <= h_max and T_max > 0");
+    if (n < 0 || n > 0xffffffffLL) return fail(COMET_ERR_INVALID_ARG, "n out of range");
+    if (max_iters < 0) return fail(COMET_ERR_INVALID_ARG, "max_iters < 0");
+    if (n == 0) {
+        p->last_n = 0;
+        return COMET_OK;
+    }
+    if (!mode_seqs || !out_cost || !out_status)
+        return fail(COMET_ERR_INVALID_ARG, "mode_seqs, out_cost and out_status are required");
+    if (!is_device_ptr(mode_seqs) || !is_device_ptr(out_cost) || !is_device_ptr(out_status) ||
+        (warm_starts && !is_device_ptr(warm_starts)) || (out_traj && !is_device_ptr(out_traj)))
+        return fail(COMET_ERR_INVALID_ARG, "comet_eval_modes_timed takes device arrays only");
+    CUDA_TRY(cudaSetDevice(p->device), "cudaSetDevice");
+    int smem_optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device),
+             "shared memory limit");
+    const size_t per_warp = comet::timing_smem_per_warp_bytes(p->Nmax);
+    int wpb = 4;
+    while (wpb > 1 && per_warp * wpb > (size_t)smem_optin) --wpb;
+    if (per_warp * wpb > (size_t)smem_optin)
+        return fail(COMET_ERR_INVALID_ARG, "N_max = %d does not fit the timing kernel's shared memory", p->Nmax);
+    {
+        const comet_status st = comet::reserve_eval(p, n);
+        if (st != COMET_OK) return st;
+    }
+    const int bps = comet::timing_blocks_per_sm(wpb, p->Nmax);
+    if (bps < 1) return fail(COMET_ERR_CUDA, "timing kernel: no resident block");
+    const int64_t resident = (int64_t)p->num_sms * bps * wpb;
+    const int64_t warps = ((std::min<int64_t>(resident, n) + wpb - 1) / wpb) * wpb;
+    const int64_t ws_floats = comet::timing_ws_per_warp_floats(p->Nmax) * warps;
+    if (p->tws_floats < ws_floats) {
+        cudaFree(p->d_tws);
+        p->d_tws = nullptr;
+        p->tws_floats = 0;
+        CUDA_TRY(cudaMalloc(&p->d_tws, sizeof(float) * (size_t)ws_floats), "timing workspace");
+        p->tws_floats = ws_floats;
+    }
+    cudaStream_t s = p->stream;
+    CUDA_TRY(cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned int), s), "queue reset");
+    CUDA_TRY(cudaMemsetAsync(p->d_bad, 0, sizeof(int), s), "flag reset");
+    comet::TimingArgs a;
+    memset(&a, 0, sizeof(a));
+    a.e.inst = p->d_inst;
+    a.e.n_inst = (int)p->inst.size();
+    a.e.seqs = mode_seqs;
+    a.e.n = n;
+    a.e.warm = warm_starts;
+    a.e.stride = 9 * (int64_t)p->Nmax + 5;
+    a.e.Nmax = p->Nmax;
+    a.e.out_cost = out_cost;
+    a.e.out_traj = out_traj;
+    a.e.out_status = out_status;
+    a.e.out_viol = p->d_viol;
+    a.e.out_merit = p->d_merit;
+    a.e.out_iters = p->d_iters;
+    a.e.out_stat = p->d_stat;
+    a.e.ws = p->d_tws;
+    a.e.ws_per_warp = comet::timing_ws_per_warp_floats(p->Nmax);
+    a.e.queue = p->d_queue;
+    a.e.bad_input = p->d_bad;
+    a.e.sp = comet::make_params(p->opts, max_iters);
+    a.h_min = (float)timing->h_min;
+    a.h_max = (float)timing->h_max;
+    a.T = (float)timing->T_max;
+    p->last_n = n;
+    CUDA_TRY(comet::launch_timing(a, (int)warps, wpb, s), "timing kernel launch");
+    return COMET_OK;
 }
 
 comet_status comet_eval_stats(comet_problem* p, float* out_viol, float* out_merit, int32_t* out_iters,

@@ -35,6 +35,9 @@ struct DevInstance {
     // evaluated in double-float
     float kth_hi, kth_lo;
     float a_lo[4];
+    // kappa / c^2 as an FP32 pair, for the theta row with a variable
+    // interval duration (timing optimisation)
+    float kc_hi, kc_lo;
 };
 
 struct SolverParams {
@@ -87,6 +90,18 @@ constexpr int kBimThreads = 128;
 size_t bim_smem_bytes(int Nmax);
 int bim_blocks_per_sm(int Nmax);
 cudaError_t launch_bimanual(const EvalArgs& a, int n_ctas, cudaStream_t s);
+
+// Timing optimisation of the pushing TO (timing_kernel.cu): the arguments
+// of the evaluator plus the duration bounds; per-warp workspace of
+// timing_ws_per_warp_floats(N_max) floats.
+struct TimingArgs {
+    EvalArgs e;
+    float h_min, h_max, T;
+};
+size_t timing_smem_per_warp_bytes(int Nmax);
+int64_t timing_ws_per_warp_floats(int Nmax);
+int timing_blocks_per_sm(int warps_per_block, int Nmax);
+cudaError_t launch_timing(const TimingArgs& a, int total_warps, int warps_per_block, cudaStream_t s);
 
 // Launch shape cached by the autotuner for (device, N_max) (autotune.cu).
 bool cached_launch_shape(int device, int nmax, int* wpb, int* bps);

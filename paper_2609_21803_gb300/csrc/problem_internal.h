@@ -24,6 +24,9 @@ struct comet_problem {
     int blocks_per_sm = 0;
     float* d_ws = nullptr;
     int64_t ws_warps = 0;
+    // per-warp workspace of the timing-optimisation kernel
+    float* d_tws = nullptr;
+    int64_t tws_floats = 0;
     unsigned int* d_queue = nullptr;
     int* d_bad = nullptr;
     // per-TO diagnostics of the last call
