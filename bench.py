@@ -335,6 +335,8 @@ def run_gpu(args):
         line["grammar"] = grammar_times(P)
     if rank == 0 and args.bimanual:
         line["bimanual"] = bimanual_times(P, per=args.bim_per, fp32_peak=peak["tflops"])
+    if rank == 0 and args.timing:
+        line["timing"] = timing_times(P)
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and args.mcts:
@@ -656,6 +658,54 @@ def bimanual_times(P, n_inst=8, per=512, n_plan=2, fp32_peak=None):
             "note": "one CTA (128 threads) per TO; device time; v_hat in physical units"}
 
 
+def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=1500):
+    """Timing optimisation (interval durations among the controls, the
+    elapsed time tau carrying the duration bound): the 2-segment
+    enumerations (144 orders, N = 16) of the listed instances and the
+    4-segment enumeration (20,736 orders, N = 80) of one instance, each under
+    a bound with room (h in [dt/2, 2 dt], T twice the fixed schedule's
+    length) and a binding one (h in [dt/5, 3 dt], T = 3/4 of it); one launch
+    each after a warm-up launch, device time."""
+    import torch
+
+    out = {}
+    stream = torch.cuda.current_stream()
+    work = [("l2", [W.push_l2_instance(s) for s in per_inst], 2), ("l4", [W.push_l4_instance(l4_inst)], 4)]
+    for name, insts, L in work:
+        orders = [tuple(int(v) for v in q) for q in W.all_sequences(12, L)]
+        seqs = [q for _ in insts for q in orders]
+        idx = np.repeat(np.arange(len(insts), dtype=np.int32), len(orders))
+        n = len(seqs)
+        d = torch.from_numpy(P.pack_mode_seqs(seqs, idx).view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
+        dt, nint = insts[0]["dt"], insts[0]["knots_per_segment"] * L
+        bounds = {"slack": dict(h_min=0.5 * dt, h_max=2.0 * dt, T_max=2.0 * nint * dt),
+                  "binding": dict(h_min=0.2 * dt, h_max=3.0 * dt, T_max=0.75 * nint * dt)}
+        prob = P.Problem(insts)
+        cost = torch.empty(n, dtype=torch.float32, device="cuda")
+        status = torch.empty(n, dtype=torch.int32, device="cuda")
+        viol = torch.empty(n, dtype=torch.float32, device="cuda")
+        iters = torch.empty(n, dtype=torch.int32, device="cuda")
+        for bname, tm in bounds.items():
+            nw = min(n, 256)
+            P.comet_eval_modes_timed(prob.handle, tm, d[:nw], nw, None, max_iters, cost, None, status)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.comet_eval_modes_timed(prob.handle, tm, d, n, None, max_iters, cost, None, status)
+            e1.record(stream)
+            P.comet_eval_stats(prob.handle, viol, None, iters, None)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            conv = int(((status == 0) & (viol <= 1e-5)).sum())
+            out[f"{name}_{bname}"] = {
+                "orders": n, "intervals": nint, "bounds": tm, "ms": t * 1e3,
+                "converged_solves_per_s": conv / t, "converged_fraction": conv / n,
+                "iterations_per_solve": float(iters.float().mean()), "max_iters": max_iters}
+        prob.close()
+    out["note"] = ("timing_kernel: one warp per TO, state (x, y, theta, s, tau), control (f_n, f_t, sdot, h); "
+                   "cold start h_k = dt clipped into the bounds; device time of one launch")
+    return out
+
+
 def measured_peak(key, fallback):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -771,6 +821,7 @@ def main():
     ap.add_argument("--bim-per", type=int, default=512, help="random orders per instance in the bimanual leg")
     ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
     ap.add_argument("--mcts", type=int, default=1, help="MCTS comparison leg (1) or skip it (0)")
+    ap.add_argument("--timing", type=int, default=1, help="timing-optimisation leg (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=32,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()
