@@ -20,6 +20,18 @@
  * 13-way one-hot (entries 0..11 = mode m_i, entry 12 = blank when i >= L).
  * out_dim = 1 + 3 N_max rounded up to a multiple of 16.
  *
+ * Bimanual problems (COMET_TASK_BIMANUAL): the mode m = 169 g + 13 h_L +
+ * h_R enters as a factored one-hot of 30 entries per slot (ground g at
+ * 0..2, left hand at 3..15, right hand at 16..28, blank at 29), so in_dim =
+ * 12 + 30 L_max rounded up to 64; the instance part is the start pose
+ * (x, z, theta), the goal pose, 10 side_x, 10 side_y, 3 (x_g - x_s),
+ * 3 (z_g - z_s), theta_g - theta_s and the mass.  The outputs are log M_hat
+ * and the 12 controls of every interval, y[1 + c N_max + k] for c = xd, zd,
+ * thd, fn_L, ft_L, sd_L, fn_R, ft_R, sd_R, lam_n, lam_t, p_c, with the six
+ * forces in units of the box's weight m g (g = 9.81 m/s^2); out_dim = 1 +
+ * 12 N_max rounded up to 16.  Warm starts take the cold start's poses (hand
+ * offsets 0) with the predicted controls (warm_mode 0 is read as 1).
+ *
  * Parameters (flat FP32 vector, the optimiser's master copy):
  *   [W_1 (width x in_dim), b_1, W_2 (width x width), b_2, W_3, b_3,
  *    W_4 (out_dim x width), b_4], W row-major [out][in].
@@ -52,7 +64,7 @@ typedef struct {
     int32_t rows_cap;      /* rows of one forward / training batch held at once (4096); grown by calls */
     int64_t dataset_cap;   /* samples the proposal's training set can hold (0 = none) */
     uint64_t seed;         /* weight initialisation: U(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases */
-    double lambda_w;       /* weight of the control loss (1.0): Omega = lambda_w / (3 N) per control */
+    double lambda_w;       /* weight of the control loss (1.0): Omega = lambda_w / (n_u N) per control */
     int32_t warm_mode;     /* warm-start states: 0 = Euler rollout of the predicted controls from
                               the start pose (s reset to 0 at a face change), 1 = the cold start's
                               poses (1; fewer solver iterations in measurements) */
@@ -66,9 +78,10 @@ typedef struct {
 void comet_default_proposal_desc(comet_proposal_desc* d);
 void comet_default_adamw_opts(comet_adamw_opts* o);
 
-/* Create a proposal for problem p's instances (n_modes 12, L_max and N_max
- * of the problem).  The problem must outlive it.  Errors: INVALID_ARG for a
- * bad descriptor, CUDA / OOM from the runtime. */
+/* Create a proposal for problem p's instances (pushing: n_modes 12 or 13;
+ * bimanual: 507; L_max and N_max of the problem).  The problem must outlive
+ * it.  Errors: INVALID_ARG for a bad descriptor, CUDA / OOM from the
+ * runtime. */
 comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* d, comet_proposal** out);
 comet_status comet_proposal_destroy(comet_proposal* q);
 
@@ -113,8 +126,9 @@ comet_status comet_proposal_train_batch(comet_proposal* q, const uint16_t* x, co
  * host): orders, and comet_eval_modes' cost, status and trajectory with
  * comet_eval_stats' v_hat.  Targets: T_0 = log max(M_hat, 1e-12) with
  * M_hat = J_hat + merit_mu max(v_hat - eps_feas, 0), weight 1 unless the TO
- * is NONFINITE; controls of CONVERGED TOs with weight lambda_w / (3 N), all
- * other weights 0.  Errors: BUDGET when the set is full. */
+ * is NONFINITE; controls of CONVERGED TOs with weight lambda_w / (n_u N)
+ * (n_u = 3 pushing, 12 bimanual, forces in units of m g), all other weights
+ * 0.  Errors: BUDGET when the set is full. */
 comet_status comet_proposal_add_samples(comet_proposal* q, const comet_mode_seq* seqs, int64_t n,
                                         const float* cost, const float* viol, const int32_t* status,
                                         const float* traj);

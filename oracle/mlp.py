@@ -35,6 +35,15 @@ i < L_max (entries 0..11 = the mode m_i, entry 12 = blank for i >= L).
 Output layout (out_dim = 1 + 3 N_max, padded to a multiple of 16): entry 0
 is log M_hat; entry 1 + c N_max + k is control component c (f_n, f_t, s_dot)
 of interval k.
+
+Bimanual task (``bim_dims``, ``bim_features``, ``bim_targets``, ``bim_warm``):
+the 507 modes m = 169 g + 13 h_L + h_R (ground g, hands h_L, h_R) enter as a
+factored one-hot of 30 entries per slot (g at 0..2, h_L at 3..15, h_R at
+16..28, blank at 29); the instance part is the start pose (x, z, theta), the
+goal pose, 10 side_x, 10 side_y, 3 (x_g - x_s), 3 (z_g - z_s), theta_g -
+theta_s and the mass.  Outputs: log M_hat, then the 12 controls (xd, zd,
+thd, fn_L, ft_L, sd_L, fn_R, ft_R, sd_R, lam_n, lam_t, p_c) of every
+interval, the forces in units of the box's weight m g (g = 9.81).
 """
 from __future__ import annotations
 
@@ -204,3 +213,74 @@ def targets(cost, viol, status, traj_controls, N, n_max, out_dim, lambda_w=1.0, 
                 T[1 + c * n_max + k] = traj_controls[c][k]
                 Om[1 + c * n_max + k] = lambda_w / (3.0 * N)
     return T, Om
+
+
+# ------------------------------------------------------------ bimanual task
+
+GRAV = 9.81
+BIM_SLOT = 30
+BIM_FORCES = (3, 4, 6, 7, 9, 10)   # fn_L, ft_L, fn_R, ft_R, lam_n, lam_t
+
+
+def bim_dims(l_max: int, n_max: int, width: int = 256):
+    """(in_dim, width, out_dim) of the proposal for a bimanual family."""
+    return pad_to(12 + BIM_SLOT * l_max, 64), width, pad_to(1 + 12 * n_max, 16)
+
+
+def bim_features(inst: dict, modes, l_max: int, in_dim: int) -> np.ndarray:
+    s, g = np.asarray(inst["start"], float), np.asarray(inst["goal"], float)
+    x = np.zeros(in_dim)
+    x[0:3] = s
+    x[3:6] = g
+    x[6] = 10.0 * inst["side_x"]
+    x[7] = 10.0 * inst["side_y"]
+    x[8] = 3.0 * (g[0] - s[0])
+    x[9] = 3.0 * (g[1] - s[1])
+    x[10] = g[2] - s[2]
+    x[11] = inst["mass"]
+    for i in range(l_max):
+        base = 12 + BIM_SLOT * i
+        if i < len(modes):
+            m = int(modes[i])
+            x[base + m // 169] = 1.0
+            x[base + 3 + (m // 13) % 13] = 1.0
+            x[base + 16 + m % 13] = 1.0
+        else:
+            x[base + BIM_SLOT - 1] = 1.0
+    return x
+
+
+def bim_targets(cost, viol, status, traj_controls, N, n_max, out_dim, mass, lambda_w=1.0, merit_mu=100.0,
+                eps_feas=1e-5):
+    """As ``targets`` for the 12 bimanual controls (traj_controls[c][k]),
+    forces divided by m g, control weights lambda_w / (12 N)."""
+    T = np.zeros(out_dim)
+    Om = np.zeros(out_dim)
+    m = cost + merit_mu * max(viol - eps_feas, 0.0)
+    if status != 4 and np.isfinite(m):
+        T[0] = np.log(max(m, 1e-12))
+        Om[0] = 1.0
+    if status == 0:
+        for c in range(12):
+            scale = 1.0 / (mass * GRAV) if c in BIM_FORCES else 1.0
+            for k in range(N):
+                T[1 + c * n_max + k] = traj_controls[c][k] * scale
+                Om[1 + c * n_max + k] = lambda_w / (12.0 * N)
+    return T, Om
+
+
+def bim_warm(inst: dict, N: int, n_max: int, y) -> np.ndarray:
+    """Warm start of a bimanual order from the outputs y: the cold start's
+    poses (linear from start to goal, hand offsets 0) and the predicted
+    controls, forces times m g; trajectory layout x[5][n_max+1], u[12][n_max]."""
+    w = np.zeros(5 * (n_max + 1) + 12 * n_max)
+    s, g = np.asarray(inst["start"], float), np.asarray(inst["goal"], float)
+    for k in range(N + 1):
+        a = k / N
+        for c in range(3):
+            w[c * (n_max + 1) + k] = (1.0 - a) * s[c] + a * g[c]
+    mg = inst["mass"] * GRAV
+    for c in range(12):
+        for k in range(N):
+            w[5 * (n_max + 1) + c * n_max + k] = y[1 + c * n_max + k] * (mg if c in BIM_FORCES else 1.0)
+    return w

@@ -30,6 +30,12 @@ namespace {
 
 constexpr int kLayers = 4;
 constexpr int kInstFeat = 12;  // per-instance features ahead of the one-hot slots
+constexpr int kBimSlot = 30;   // bimanual slot: ground 3 + left hand 13 + right hand 13 + blank
+constexpr float kGrav = 9.81f;
+
+// bimanual controls (xd, zd, thd, fn_L, ft_L, sd_L, fn_R, ft_R, sd_R, lam_n,
+// lam_t, p_c): the forces, which the proposal predicts in units of m g
+__host__ __device__ inline bool bim_force(int j) { return j == 3 || j == 4 || j == 6 || j == 7 || j == 9 || j == 10; }
 
 }  // namespace
 
@@ -37,6 +43,8 @@ struct comet_proposal {
     comet_problem* p = nullptr;
     comet_proposal_desc desc;
     int in_dim = 0, width = 0, out_dim = 0, l_max = 0, n_max = 0, n_modes = 0, n_inst = 0;
+    // task layout: bimanual (factored one-hot, 12 controls on 5 states) or pushing
+    int bim = 0, nx = 4, n_ctrl = 3, slot_w = 13;
     int64_t n_params = 0;
     int64_t w_off[kLayers], b_off[kLayers];
     int din[kLayers], dout[kLayers];
@@ -226,7 +234,8 @@ __global__ void adamw_kernel(float* p, const float* g, float* m, float* v, int64
 // and orders of another instance range give zero rows
 __global__ void features_kernel(const comet_mode_seq* seqs, int64_t n_rows, const int64_t* d_n, const float* fi,
                                 int n_inst, int l_max, int n_modes, int in_dim, uint16_t* X, uint16_t* Xt,
-                                int64_t ld_t) {
+                                int64_t ld_t, int bim) {
+    const int slot_w = bim ? kBimSlot : n_modes + 1;
     const int64_t nn = d_n ? min(*d_n, n_rows) : n_rows;
     const int64_t total = n_rows * in_dim;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -238,10 +247,17 @@ __global__ void features_kernel(const comet_mode_seq* seqs, int64_t n_rows, cons
             if (s.instance >= 0 && s.instance < n_inst && s.len >= 1 && s.len <= l_max) {
                 if (c < kInstFeat) {
                     x = fi[s.instance * kInstFeat + c];
-                } else if (c < kInstFeat + (n_modes + 1) * l_max) {
-                    const int slot = (c - kInstFeat) / (n_modes + 1), e = (c - kInstFeat) % (n_modes + 1);
-                    const int want = slot < s.len ? (int)s.modes[slot] : n_modes;
-                    x = (e == want) ? 1.f : 0.f;
+                } else if (c < kInstFeat + slot_w * l_max) {
+                    const int slot = (c - kInstFeat) / slot_w, e = (c - kInstFeat) % slot_w;
+                    if (bim) {
+                        // mode m = 169 g + 13 h_L + h_R: one-hots of g, h_L, h_R
+                        const int m = slot < s.len ? (int)s.modes[slot] : -1;
+                        x = (m < 0) ? (e == kBimSlot - 1 ? 1.f : 0.f)
+                                    : ((e == m / 169 || e == 3 + (m / 13) % 13 || e == 16 + m % 13) ? 1.f : 0.f);
+                    } else {
+                        const int want = slot < s.len ? (int)s.modes[slot] : n_modes;
+                        x = (e == want) ? 1.f : 0.f;
+                    }
                 }
             }
         }
@@ -255,7 +271,7 @@ __global__ void features_kernel(const comet_mode_seq* seqs, int64_t n_rows, cons
 __global__ void targets_kernel(const comet_mode_seq* seqs, int64_t n, const float* cost, const float* viol,
                                const int32_t* status, const float* traj, int64_t stride, const int* Kseg,
                                int n_inst, int n_max, int out_dim, float merit_mu, float eps_feas, float lambda_w,
-                               float* T, float* Om) {
+                               float* T, float* Om, int nx, int n_ctrl, int bim, const comet::DevInstance* inst) {
     const int64_t total = n * out_dim;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / out_dim;
@@ -270,12 +286,13 @@ __global__ void targets_kernel(const comet_mode_seq* seqs, int64_t n, const floa
                 tv = logf(fmaxf(m, 1e-12f));
                 w = 1.f;
             }
-        } else if (c <= 3 * n_max && valid_inst && st == COMET_TO_CONVERGED) {
+        } else if (c <= n_ctrl * n_max && valid_inst && st == COMET_TO_CONVERGED) {
             const int comp = (c - 1) / n_max, k = (c - 1) % n_max;
             const int N = Kseg[s.instance] * s.len;
             if (k < N) {
-                tv = traj[i * stride + 4 * (int64_t)(n_max + 1) + (int64_t)comp * n_max + k];
-                w = lambda_w / (3.f * (float)N);
+                tv = traj[i * stride + nx * (int64_t)(n_max + 1) + (int64_t)comp * n_max + k];
+                if (bim && bim_force(comp)) tv /= inst[s.instance].mass * kGrav;
+                w = lambda_w / ((float)n_ctrl * (float)N);
             }
         }
         T[t] = tv;
@@ -356,7 +373,7 @@ __global__ void bias_grad_kernel(const uint16_t* Gt, int64_t ld_t, int64_t M, fl
 // (s_0 = 0, s reset to 0 after a face change), or the cold-start poses
 __global__ void predict_post_kernel(const float* Y, int out_dim, const comet_mode_seq* seqs, const int* row_of,
                                     int64_t n_rows, const int64_t* d_n, const comet::DevInstance* inst, int n_inst,
-                                    int n_max, int warm_mode, float* merit, float* warm, int64_t stride) {
+                                    int n_max, int warm_mode, float* merit, float* warm, int64_t stride, int bim) {
     const int64_t nn = d_n ? min(*d_n, n_rows) : n_rows;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = row_of ? (int64_t)row_of[i] : i;
@@ -371,6 +388,20 @@ __global__ void predict_post_kernel(const float* Y, int out_dim, const comet_mod
         }
         const comet::DevInstance& P = inst[s.instance];
         const int L = s.len, N = P.K * L, Nm1 = n_max + 1;
+        if (bim) {
+            // bimanual: the cold start's poses (hand offsets 0) and the
+            // predicted controls, forces back from units of m g
+            const float mg = P.mass * kGrav;
+            for (int k = 0; k <= n_max; ++k) {
+                const float al = (float)k / (float)N;
+                for (int c = 0; c < 5; ++c)
+                    w[c * Nm1 + k] = (k <= N && c < 3) ? (1.f - al) * P.start[c] + al * P.goal[c] : 0.f;
+            }
+            for (int c = 0; c < 12; ++c)
+                for (int k = 0; k < n_max; ++k)
+                    w[5 * Nm1 + c * n_max + k] = (k < N) ? y[1 + c * n_max + k] * (bim_force(c) ? mg : 1.f) : 0.f;
+            continue;
+        }
         float x[4] = {P.start[0], P.start[1], P.start[2], 0.f};
         for (int k = 0; k <= N; ++k) {
             if (warm_mode == 1 && k > 0) {
@@ -637,7 +668,7 @@ comet_status proposal_prune_device(comet_proposal* q, comet_frontier* f, int kee
     FrontierDev& F = f->d;
     const int64_t cap = f->batch;
     features_kernel<<<grid_for(cap * q->in_dim), 256, 0, s>>>(F.next, cap, F.n_next, q->feat_inst, q->n_inst,
-                                                              q->l_max, q->n_modes, q->in_dim, q->X, nullptr, 0);
+                                                              q->l_max, q->n_modes, q->in_dim, q->X, nullptr, 0, q->bim);
     QTRY(cudaGetLastError(), "features");
     QTRY(forward(q, cap, false, s), "forward");
     encode_kernel<<<grid_for(cap), 256, 0, s>>>(F.next, cap, F.n_next, q->n_modes, q->pr_codes);
@@ -661,7 +692,8 @@ comet_status proposal_prune_device(comet_proposal* q, comet_frontier* f, int kee
     if (warm) {
         predict_post_kernel<<<grid_for(keep, 128), 128, 0, s>>>(q->Y, q->out_dim, F.next, row_scratch, keep, F.n_next,
                                                                 q->p->d_inst, q->n_inst, q->n_max,
-                                                                q->desc.warm_mode, nullptr, warm, q->p->stride);
+                                                                q->desc.warm_mode, nullptr, warm, q->p->stride,
+                                                                q->bim);
         QTRY(cudaGetLastError(), "warm starts");
     }
     return COMET_OK;
@@ -679,12 +711,12 @@ comet_status proposal_predict_device(comet_proposal* q, const comet_mode_seq* se
                                      float* warm, cudaStream_t s) {
     QTRY(ensure_rows(q, n), "proposal activations");
     features_kernel<<<grid_for(n * q->in_dim), 256, 0, s>>>(seqs, n, nullptr, q->feat_inst, q->n_inst, q->l_max,
-                                                            q->n_modes, q->in_dim, q->X, nullptr, 0);
+                                                            q->n_modes, q->in_dim, q->X, nullptr, 0, q->bim);
     QTRY(cudaGetLastError(), "features");
     QTRY(forward(q, n, false, s), "forward");
     predict_post_kernel<<<grid_for(n, 128), 128, 0, s>>>(q->Y, q->out_dim, seqs, nullptr, n, nullptr, q->p->d_inst,
                                                          q->n_inst, q->n_max, q->desc.warm_mode, merit, warm,
-                                                         q->p->stride);
+                                                         q->p->stride, q->bim);
     QTRY(cudaGetLastError(), "predict");
     return COMET_OK;
 }
@@ -716,8 +748,6 @@ void comet_default_adamw_opts(comet_adamw_opts* o) {
 comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* d_in, comet_proposal** out) {
     if (!p || !out) return qfail(COMET_ERR_INVALID_ARG, "problem and out are required");
     *out = nullptr;
-    if (p->task != COMET_TASK_PUSHER_SLIDER)
-        return qfail(COMET_ERR_INVALID_ARG, "the learned proposal is built for the pushing task");
     comet_proposal_desc d;
     if (d_in)
         d = *d_in;
@@ -745,9 +775,13 @@ comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* 
     q->n_modes = n_modes;
     q->n_max = p->Nmax;
     q->n_inst = (int)p->inst.size();
-    q->in_dim = (int)pad_to(kInstFeat + (int64_t)(n_modes + 1) * l_max, 64);
+    q->bim = p->task == COMET_TASK_BIMANUAL ? 1 : 0;
+    q->nx = q->bim ? 5 : 4;
+    q->n_ctrl = q->bim ? 12 : 3;
+    q->slot_w = q->bim ? kBimSlot : n_modes + 1;
+    q->in_dim = (int)pad_to(kInstFeat + (int64_t)q->slot_w * l_max, 64);
     q->width = d.width;
-    q->out_dim = (int)pad_to(1 + 3 * (int64_t)p->Nmax, 16);
+    q->out_dim = (int)pad_to(1 + (int64_t)q->n_ctrl * p->Nmax, 16);
     const int dims[kLayers + 1] = {q->in_dim, q->width, q->width, q->width, q->out_dim};
     int64_t off = 0;
     for (int l = 0; l < kLayers; ++l) {
@@ -793,6 +827,15 @@ comet_status comet_proposal_create(comet_problem* p, const comet_proposal_desc* 
         }
         f[6] = (float)(10.0 * D.side_x);
         f[7] = (float)(10.0 * D.side_y);
+        if (q->bim) {
+            // the box in the vertical plane: 3 (g - s) for x and z (gravity
+            // fixes the frame), dtheta, and the mass
+            f[8] = (float)(3.0 * (D.goal[0] - D.start[0]));
+            f[9] = (float)(3.0 * (D.goal[1] - D.start[1]));
+            f[10] = (float)(D.goal[2] - D.start[2]);
+            f[11] = (float)D.mass;
+            continue;
+        }
         // the goal in the start frame: 3 R(-theta_s)(g - s), dtheta
         const double dx = D.goal[0] - D.start[0], dy = D.goal[1] - D.start[1];
         const double c = cos(D.start[2]), sn = sin(D.start[2]);
@@ -872,7 +915,7 @@ comet_status comet_proposal_features(comet_proposal* q, const comet_mode_seq* se
         d = (const comet_mode_seq*)tmp;
     }
     features_kernel<<<grid_for(n * q->in_dim), 256, 0, s>>>(d, n, nullptr, q->feat_inst, q->n_inst, q->l_max,
-                                                            q->n_modes, q->in_dim, out_x, nullptr, 0);
+                                                            q->n_modes, q->in_dim, out_x, nullptr, 0, q->bim);
     cudaError_t e = cudaGetLastError();
     if (tmp) {
         cudaStreamSynchronize(s);
@@ -982,11 +1025,11 @@ comet_status comet_proposal_add_samples(comet_proposal* q, const comet_mode_seq*
     if (e == cudaSuccess) {
         features_kernel<<<grid_for(n * q->in_dim), 256, 0, s>>>(ds, n, nullptr, q->feat_inst, q->n_inst, q->l_max,
                                                                 q->n_modes, q->in_dim,
-                                                                q->ds_X + q->ds_n * q->in_dim, nullptr, 0);
+                                                                q->ds_X + q->ds_n * q->in_dim, nullptr, 0, q->bim);
         targets_kernel<<<grid_for(n * q->out_dim), 256, 0, s>>>(
             ds, n, dc, dv, dst, dt, stride, dK, q->n_inst, q->n_max, q->out_dim, (float)q->p->opts.merit_mu,
             (float)q->p->opts.eps_feas, (float)q->desc.lambda_w, q->ds_T + q->ds_n * q->out_dim,
-            q->ds_Om + q->ds_n * q->out_dim);
+            q->ds_Om + q->ds_n * q->out_dim, q->nx, q->n_ctrl, q->bim, q->p->d_inst);
         e = cudaGetLastError();
     }
     cudaStreamSynchronize(s);

@@ -155,3 +155,52 @@ def test_features_layout():
              "side_x": 0.09, "side_y": 0.12}
     np.testing.assert_allclose(mlp.features(moved, (3, 11), 4, din)[8:11], mlp.features(inst, (3, 11), 4, din)[8:11],
                                atol=1e-12)
+
+
+def test_bimanual_features_layout():
+    # mode m = 169 g + 13 h_L + h_R: three hand-decoded cases, a blank slot,
+    # the instance part, and a bijection of the 507 modes onto 3 x 13 x 13
+    inst = {"start": [0.0, 0.05, 0.0], "goal": [0.1, 0.05, 1.7], "side_x": 0.2, "side_y": 0.1, "mass": 1.5}
+    din, width, dout = mlp.bim_dims(6, 90)
+    assert (din, width, dout) == (192, 256, 1088)
+    x = mlp.bim_features(inst, (0, 506, 200), 6, din)
+    np.testing.assert_allclose(x[:12], [0.0, 0.05, 0.0, 0.1, 0.05, 1.7, 2.0, 1.0, 0.3, 0.0, 1.7, 1.5], atol=1e-12)
+    slots = x[12:12 + 30 * 6].reshape(6, 30)
+    assert list(np.nonzero(slots[0])[0]) == [0, 3, 16]            # g 0, h_L 0, h_R 0
+    assert list(np.nonzero(slots[1])[0]) == [2, 15, 28]           # 506 = 2*169 + 12*13 + 12
+    assert list(np.nonzero(slots[2])[0]) == [1, 5, 21]            # 200 = 169 + 2*13 + 5
+    for i in range(3, 6):
+        assert list(np.nonzero(slots[i])[0]) == [29]
+    assert np.all(x[12 + 30 * 6:] == 0)
+    seen = set()
+    for m in range(507):
+        nz = tuple(np.nonzero(mlp.bim_features(inst, (m,), 1, din)[12:42])[0])
+        assert len(nz) == 3 and nz[0] < 3 and 3 <= nz[1] < 16 and 16 <= nz[2] < 29
+        seen.add(nz)
+    assert len(seen) == 507
+
+
+def test_bimanual_targets_and_warm_start_scale_the_forces():
+    n_max, N, mass = 30, 15, 2.0
+    _, _, dout = mlp.bim_dims(2, n_max)
+    rng = np.random.default_rng(3)
+    ctrl = rng.normal(size=(12, n_max))
+    T, Om = mlp.bim_targets(0.5, 0.0, 0, ctrl, N, n_max, dout, mass)
+    assert T[0] == pytest.approx(np.log(0.5)) and Om[0] == 1.0
+    for c in range(12):
+        want = ctrl[c, :N] / (mass * 9.81) if c in (3, 4, 6, 7, 9, 10) else ctrl[c, :N]
+        np.testing.assert_allclose(T[1 + c * n_max:1 + c * n_max + N], want, rtol=1e-15)
+        assert np.all(T[1 + c * n_max + N:1 + (c + 1) * n_max] == 0)
+        np.testing.assert_allclose(Om[1 + c * n_max:1 + c * n_max + N], 1.0 / (12 * N))
+    # not converged: only the merit entry carries weight
+    T2, Om2 = mlp.bim_targets(0.5, 1e-3, 1, ctrl, N, n_max, dout, mass)
+    assert Om2[0] == 1.0 and np.all(Om2[1:] == 0)
+    assert T2[0] == pytest.approx(np.log(0.5 + 100.0 * (1e-3 - 1e-5)))
+    # the warm start undoes the force scaling: targets in, controls out
+    inst = {"start": [0.0, 0.1, 0.0], "goal": [0.2, 0.1, 1.6], "mass": mass}
+    w = mlp.bim_warm(inst, N, n_max, T)
+    u = w[5 * (n_max + 1):].reshape(12, n_max)
+    np.testing.assert_allclose(u[:, :N], ctrl[:, :N], rtol=1e-12)
+    xs = w[:5 * (n_max + 1)].reshape(5, n_max + 1)
+    np.testing.assert_allclose(xs[2, :N + 1], np.linspace(0.0, 1.6, N + 1), atol=1e-12)
+    assert np.all(xs[3:] == 0) and np.all(xs[:, N + 1:] == 0)
