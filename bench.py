@@ -335,6 +335,8 @@ def run_gpu(args):
         line["grammar"] = grammar_times(P)
     if rank == 0 and args.bimanual:
         line["bimanual"] = bimanual_times(P, per=args.bim_per, fp32_peak=peak["tflops"])
+    if rank == 0 and args.cfg5:
+        line["cfg5"] = cfg5_times(P)
     if rank == 0 and args.timing:
         line["timing"] = timing_times(P)
     if rank == 0 and args.learned_instances > 0:
@@ -706,6 +708,91 @@ def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=150
     return out
 
 
+def cfg5_times(P, n_inst=128, n_train=64, per_train=768):
+    """Bimanual flipping at the configured scale: 128 seeded instances (seeds
+    0..127), Algorithm 1 from the 507 one-segment seeds (beam 16, s_max = 3,
+    K_ref = 64 at t_ref, budget 1e6 evaluations per instance), FP32 solves
+    with FP64 certification, all instances in one batched planner call:
+    plain (B = 1,024) and with the learned proposal (the 256 best of each
+    round's whole neighbourhood by predicted merit, warm-started).  The proposal is trained first on evaluator results
+    of separate instances (seeds 1000.., 768 random orders of 1..4 segments
+    each)."""
+    import torch
+
+    budget = 1000000
+    rng = np.random.default_rng(2)
+    tr = [W.bimanual_instance(1000 + s) for s in range(n_train)]
+    prob = P.Problem(tr)
+    q = P.comet_proposal_create(prob.handle, {"dataset_cap": n_train * per_train})
+    seqs = [tuple(int(m) for m in rng.integers(0, 507, rng.integers(1, 5))) for _ in range(n_train * per_train)]
+    packed = P.pack_mode_seqs(seqs, np.repeat(np.arange(n_train, dtype=np.int32), per_train))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for a in range(0, len(packed), 16384):
+        d = torch.from_numpy(packed[a:a + 16384].view(np.uint8).reshape(-1, P.MODE_SEQ_BYTES)).cuda()
+        r = prob.eval(d, want_traj=True)
+        P.comet_proposal_add_samples(q, d, len(d), r["cost"], r["viol"], r["status"], r["traj"])
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    t0 = time.time()
+    losses = np.concatenate([P.comet_proposal_train(q, 600, 2048, {"lr": 1e-3}, seed=1),
+                             P.comet_proposal_train(q, 400, 2048, {"lr": 3e-4}, seed=2)])
+    t_train = time.time() - t0
+    _, _, _, npar = P.comet_proposal_dims(q)
+    flat = np.zeros(npar, np.float32)
+    P.comet_proposal_get_params(q, flat)
+    P.comet_proposal_destroy(q)
+    prob.close()
+    insts = [W.bimanual_instance(s) for s in range(n_inst)]
+    one = [(m,) for m in range(507)]
+    prob = P.Problem(insts)
+    plain_opts = dict(k=16, batch=1024, rounds=3, k_ref=64, budget=budget)
+    t0 = time.time()
+    plain = P.comet_plan_batch(prob.handle, list(range(n_inst)), [one] * n_inst, plain_opts)
+    t_plain_wall = time.time() - t0
+    t_plain = (plain[0]["explore_ms"] + plain[0]["refine_ms"]) / 1e3
+    q = P.comet_proposal_create(prob.handle)
+    P.comet_proposal_set_params(q, flat)
+    t0 = time.time()
+    learned = P.comet_plan_batch(prob.handle, list(range(n_inst)), [one] * n_inst,
+                                 dict(k=16, batch=256, rounds=3, k_ref=64, budget=budget), proposal=q)
+    t_learned_wall = time.time() - t0
+    t_learned = (learned[0]["explore_ms"] + learned[0]["refine_ms"]) / 1e3
+    P.comet_proposal_destroy(q)
+    prob.close()
+    ok = lambda r: bool(r["best_status"] == 0 and r["best_viol"] <= 1e-5)
+    feas_p = [ok(r) for r in plain]
+    feas_l = [ok(r) for r in learned]
+    both = [i for i in range(n_inst) if feas_p[i] and feas_l[i]]
+    gaps = np.array([(learned[i]["best_cost"] - plain[i]["best_cost"]) / abs(plain[i]["best_cost"]) for i in both])
+    ev_p = [r["evaluations"] for r in plain]
+    ev_l = [r["evaluations"] for r in learned]
+    return {
+        "instances": n_inst, "budget_per_instance": budget,
+        "config": "bimanual box flip, 507 modes, 15 knots/segment, L <= 6; beam 16, 3 rounds, K_ref 64 at t_ref 1500",
+        "train": {"instances": n_train, "samples": n_train * per_train, "dataset_s": t_data, "train_s": t_train,
+                  "steps": 1000, "batch": 2048, "loss_first": float(losses[:10].mean()),
+                  "loss_last": float(losses[-50:].mean())},
+        "plain": {"feasible_plans": int(sum(feas_p)), "evaluations_total": int(np.sum(ev_p)),
+                  "evaluations_median": float(np.median(ev_p)), "batched_ms": t_plain * 1e3,
+                  "ms_per_instance": t_plain * 1e3 / n_inst, "wall_s": t_plain_wall,
+                  "best_len_median": float(np.median([len(r["best"]) for r in plain])), "batch": 1024},
+        "learned": {"feasible_plans": int(sum(feas_l)), "evaluations_total": int(np.sum(ev_l)),
+                    "evaluations_median": float(np.median(ev_l)), "batched_ms": t_learned * 1e3,
+                    "ms_per_instance": t_learned * 1e3 / n_inst, "wall_s": t_learned_wall,
+                    "best_len_median": float(np.median([len(r["best"]) for r in learned])), "batch": 256},
+        "plan_time_ratio_plain_over_learned": t_plain / t_learned,
+        "evaluations_saved": 1.0 - float(np.sum(ev_l)) / float(np.sum(ev_p)),
+        "cost_gap_learned_vs_plain": {"n": len(both), "p10": float(np.percentile(gaps, 10)) if len(both) else None,
+                                      "p50": float(np.median(gaps)) if len(both) else None,
+                                      "p90": float(np.percentile(gaps, 90)) if len(both) else None,
+                                      "learned_better_by_1e-3": int(np.sum(gaps < -1e-3)),
+                                      "learned_worse_by_1e-3": int(np.sum(gaps > 1e-3))},
+        "note": "feasible = certified plan (FP64 v_hat <= 1e-5); plan times are device time of one batched "
+                "planner call over all instances (exploration + refinement)",
+    }
+
+
 def measured_peak(key, fallback):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -822,6 +909,8 @@ def main():
     ap.add_argument("--bimanual", type=int, default=1, help="bimanual leg (1) or skip it (0)")
     ap.add_argument("--mcts", type=int, default=1, help="MCTS comparison leg (1) or skip it (0)")
     ap.add_argument("--timing", type=int, default=1, help="timing-optimisation leg (1) or skip it (0)")
+    ap.add_argument("--cfg5", type=int, default=1,
+                    help="bimanual planning at scale with the learned proposal (1) or skip it (0)")
     ap.add_argument("--learned-instances", type=int, default=32,
                     help="held-out instances of the learned-planner ablation (0 = skip training and ablation)")
     args = ap.parse_args()

@@ -172,6 +172,17 @@ comet_status comet_plan_learned(comet_problem* p, int32_t instance, const comet_
                                 const comet_plan_opts* opts, comet_proposal* q, comet_plan_result* out,
                                 float* out_traj);
 
+/* comet_plan_batch (comet.h) with the proposal: Algorithm 1 over several
+ * instances of p, each round's evaluations of all instances in one launch;
+ * every instance's seeds are warm-started by the proposal, and in every
+ * round each instance's whole one-edit neighbourhood of its k best orders
+ * is ranked by predicted merit and the opts->batch (<= 4096) best are kept
+ * and warm-started, as in comet_plan_learned.  The proposal must have been
+ * created for p.  Outputs and synchronisation as comet_plan_batch. */
+comet_status comet_plan_batch_learned(comet_problem* p, int32_t n_instances, const int32_t* instances,
+                                      const comet_mode_seq* seeds, const int64_t* seed_offsets,
+                                      const comet_plan_opts* opts, comet_proposal* q, comet_plan_result* out);
+
 /* ---- raw BF16 tensor-core GEMM (device pointers) --------------------------
  * D[M][N] = A[M][K] B[N][K]^T with A, B row-major BF16 (leading dimensions
  * lda, ldb in elements, multiples of 8, 16-byte aligned bases), FP32

@@ -137,7 +137,7 @@ EXPORTS = (
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
     "comet_get_launch_config", "comet_set_launch_config", "comet_autotune", "comet_proposal_time_forward",
-    "comet_plan_batch", "comet_frontier_create_ex", "comet_sample_orders",
+    "comet_plan_batch", "comet_plan_batch_learned", "comet_frontier_create_ex", "comet_sample_orders",
     # include/comet_mcts.h
     "comet_mcts_default_opts", "comet_mcts_create", "comet_mcts_destroy", "comet_mcts_ask", "comet_mcts_tell",
     "comet_mcts_get_stats", "comet_mcts_best", "comet_plan_mcts",
@@ -217,6 +217,7 @@ def lib(build_if_missing: bool = False):
                                          ctypes.POINTER(i32)]
             L.comet_proposal_time_forward.argtypes = [vp, vp, i64, i32, ctypes.POINTER(ctypes.c_float)]
             L.comet_plan_batch.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(PlanOpts), vp]
+            L.comet_plan_batch_learned.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(PlanOpts), vp, vp]
             L.comet_plan_learned.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), vp,
                                              ctypes.POINTER(PlanResult), vp]
             L.comet_gemm_bf16.argtypes = [vp, i64, vp, i64, i64, i32, i32, ctypes.POINTER(GemmEpilogue), vp]
@@ -447,8 +448,9 @@ def comet_plan(problem, instance: int, seeds, n_seeds: int, opts=None, out_traj=
             "refine_ms": r.refine_ms}
 
 
-def comet_plan_batch(problem, instances, seeds_per_instance, opts=None) -> list:
-    """Algorithm 1 for several instances at once (comet_plan_batch);
+def comet_plan_batch(problem, instances, seeds_per_instance, opts=None, proposal=None) -> list:
+    """Algorithm 1 for several instances at once (comet_plan_batch; with
+    `proposal`, comet_plan_batch_learned of include/comet_proposal.h);
     seeds_per_instance: a list (one per instance) of lists of mode tuples."""
     if opts is None or isinstance(opts, dict):
         o = comet_default_plan_opts()
@@ -464,8 +466,12 @@ def comet_plan_batch(problem, instances, seeds_per_instance, opts=None) -> list:
         offs[i + 1] = offs[i] + len(seeds)
     packed = pack_mode_seqs(allseq, np.array(idx, np.int32))
     res = (PlanResult * len(inst))()
-    _check(lib().comet_plan_batch(problem, len(inst), inst.ctypes.data, packed.ctypes.data, offs.ctypes.data,
-                                  ctypes.byref(opts), res))
+    if proposal is None:
+        _check(lib().comet_plan_batch(problem, len(inst), inst.ctypes.data, packed.ctypes.data, offs.ctypes.data,
+                                      ctypes.byref(opts), res))
+    else:
+        _check(lib().comet_plan_batch_learned(problem, len(inst), inst.ctypes.data, packed.ctypes.data,
+                                              offs.ctypes.data, ctypes.byref(opts), proposal, res))
     out = []
     for r in res:
         out.append({"best": tuple(int(r.best.modes[i]) for i in range(r.best.len)), "best_cost": r.best_cost,

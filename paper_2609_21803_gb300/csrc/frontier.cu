@@ -390,10 +390,13 @@ comet_status plan_impl(comet_problem* p, int32_t instance, const comet_mode_seq*
     const comet_instance_desc& di = p->inst[instance];
     const int64_t slots =
         comet::edit_slots(di.max_segments, po.grammar == COMET_GRAMMAR_PUSH ? 5 : di.n_modes, po.radius);
-    const int32_t cand = q ? (int32_t)std::min<int64_t>((int64_t)po.k * slots, capacity) : batch;
+    const int64_t cand = q ? std::max<int64_t>((int64_t)po.k * slots, batch) : batch;
+    if (cand > INT32_MAX) return ffail(COMET_ERR_INVALID_ARG, "neighbourhood too large");
+    // the next batch holds the whole neighbourhood, so the frontier's
+    // capacity covers it even where the evaluations stay far below it
     comet_frontier* f = nullptr;
-    comet_status st = comet_frontier_create_ex(p, instance, capacity, std::max(cand, batch), std::max(po.k, po.k_ref),
-                                               po.radius, po.grammar, &f);
+    comet_status st = comet_frontier_create_ex(p, instance, std::max<int64_t>(capacity, cand), (int32_t)cand,
+                                               std::max(po.k, po.k_ref), po.radius, po.grammar, &f);
     if (st != COMET_OK) return st;
     struct Guard {
         comet_frontier* f;
@@ -564,6 +567,7 @@ extern "C" comet_status comet_plan_learned(comet_problem* p, int32_t instance, c
                                            int64_t n_seeds, const comet_plan_opts* opts, comet_proposal* q,
                                            comet_plan_result* out, float* out_traj) {
     if (!q) return ffail(COMET_ERR_INVALID_ARG, "proposal is required");
+    if (comet::proposal_problem(q) != p) return ffail(COMET_ERR_INVALID_ARG, "the proposal belongs to another problem");
     return comet::plan_impl(p, instance, seeds, n_seeds, opts, q, out, out_traj);
 }
 
@@ -617,11 +621,19 @@ __global__ void decode_top_kernel(const comet::TopKey* top, int k, const unsigne
 
 }  // namespace
 
-extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const int32_t* instances,
-                                         const comet_mode_seq* seeds, const int64_t* seed_offsets,
-                                         const comet_plan_opts* po_in, comet_plan_result* out) {
+namespace {
+
+// Algorithm 1 over several instances, rounds shared by all of them; with a
+// proposal q each frontier's whole neighbourhood is ranked and pruned to
+// `batch` by predicted merit and the kept orders (and the seeds) are
+// warm-started from its predicted controls.
+comet_status plan_batch_impl(comet_problem* p, int32_t n_inst, const int32_t* instances,
+                             const comet_mode_seq* seeds, const int64_t* seed_offsets, const comet_plan_opts* po_in,
+                             comet_proposal* q, comet_plan_result* out) {
     if (!p || n_inst < 1 || !instances || !seeds || !seed_offsets || !out)
         return ffail(COMET_ERR_INVALID_ARG, "problem, instances, seeds, offsets and out are required");
+    if (q && comet::proposal_problem(q) != p)
+        return ffail(COMET_ERR_INVALID_ARG, "the proposal belongs to another problem");
     comet_plan_opts po;
     if (po_in)
         po = *po_in;
@@ -629,6 +641,7 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
         comet_default_plan_opts(&po);
     if (po.k < 1 || po.batch < 1 || po.rounds < 0 || po.k_ref < 1 || po.k_ref > comet::kChunk)
         return ffail(COMET_ERR_INVALID_ARG, "bad planner options");
+    if (q && po.batch > comet::kChunk) return ffail(COMET_ERR_INVALID_ARG, "a learned plan keeps at most 4096 per round");
     for (int i = 0; i < n_inst; ++i) {
         if (instances[i] < 0 || instances[i] >= (int)p->inst.size())
             return ffail(COMET_ERR_INVALID_ARG, "instance out of range");
@@ -679,9 +692,16 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
         // than the budget
         const int64_t reach = n0 + (int64_t)po.rounds * batch;
         const int64_t cap = po.budget > 0 ? std::max<int64_t>(std::min<int64_t>(po.budget, reach), n0) : reach;
-        const comet_status st =
-            comet_frontier_create_ex(p, instances[i], cap, (int32_t)std::min<int64_t>(batch, cap),
-                                     std::max(po.k, po.k_ref), po.radius, po.grammar, &fr[i]);
+        // with a proposal the next batch holds the beam's whole neighbourhood
+        const comet_instance_desc& di = p->inst[instances[i]];
+        const int64_t slots =
+            comet::edit_slots(di.max_segments, po.grammar == COMET_GRAMMAR_PUSH ? 5 : di.n_modes, po.radius);
+        const int64_t cand = q ? std::max<int64_t>((int64_t)po.k * slots, batch) : std::min<int64_t>(batch, cap);
+        if (cand > INT32_MAX) return ffail(COMET_ERR_INVALID_ARG, "neighbourhood too large");
+        // a frontier's next batch never exceeds its capacity
+        const int64_t cap_i = std::max<int64_t>(cap, cand);
+        const comet_status st = comet_frontier_create_ex(p, instances[i], cap_i, (int32_t)cand,
+                                                         std::max(po.k, po.k_ref), po.radius, po.grammar, &fr[i]);
         if (st != COMET_OK) return st;
     }
     const int64_t n_round = (int64_t)n_inst * batch, n_ref_all = (int64_t)n_inst * po.k_ref;
@@ -698,6 +718,20 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
     float* d_cost = (float*)(bp + b_seq);
     int32_t* d_status = (int32_t*)(bp + b_seq + b_f);
     SlotSrc* d_src = (SlotSrc*)(bp + b_seq + 2 * b_f);
+    DevBuf warm_buf, rows_buf;
+    float* d_warm = nullptr;
+    int* d_rows = nullptr;
+    if (q) {
+        int64_t cand_max = 0;
+        for (int i = 0; i < n_inst; ++i) cand_max = std::max<int64_t>(cand_max, fr[i]->batch);
+        st = comet::proposal_reserve_prune(q, std::max<int64_t>(cand_max, S), batch);
+        if (st != COMET_OK) return st;
+        FTRY(cudaMalloc(&warm_buf.p, sizeof(float) * (size_t)p->stride * (size_t)std::max<int64_t>(S, n_round)),
+             "warm starts");
+        FTRY(cudaMalloc(&rows_buf.p, sizeof(int) * (size_t)n_round), "rows");
+        d_warm = (float*)warm_buf.p;
+        d_rows = (int*)rows_buf.p;
+    }
     {
         std::vector<SlotSrc> h(n_inst);
         for (int i = 0; i < n_inst; ++i) h[i] = SlotSrc{fr[i]->d.next, fr[i]->d.n_next};
@@ -716,7 +750,11 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
     FTRY(cudaEventRecord(ev[0], s), "event");
     // seed batches of every instance in one launch
     FTRY(cudaMemcpyAsync(d_seqs, seeds, sizeof(comet_mode_seq) * S, cudaMemcpyDefault, s), "copy seeds");
-    st = comet::launch_eval_device(p, d_seqs, S, nullptr, nullptr, 0, d_cost, nullptr, d_status);
+    if (q) {
+        st = comet::proposal_predict_device(q, d_seqs, S, nullptr, d_warm, s);
+        if (st != COMET_OK) return st;
+    }
+    st = comet::launch_eval_device(p, d_seqs, S, nullptr, d_warm, 0, d_cost, nullptr, d_status);
     if (st != COMET_OK) return st;
     for (int i = 0; i < n_inst; ++i) {
         const int64_t o = seed_offsets[i], n = seed_offsets[i + 1] - o;
@@ -729,11 +767,18 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
         for (int i = 0; i < n_inst; ++i) {
             const cudaError_t e = comet::launch_expand(fr[i]->d, po.k, fr[i]->batch, po.budget, s);
             if (e != cudaSuccess) return fcuda(e, "expand");
+            if (q) {
+                // rank the whole neighbourhood, keep `batch` in order; the
+                // warm starts land in the frontier's slots
+                const comet_status r = comet::proposal_prune_device(
+                    q, fr[i], batch, d_warm + (int64_t)i * batch * p->stride, d_rows + (int64_t)i * batch, s);
+                if (r != COMET_OK) return r;
+            }
         }
         gather_next_kernel<<<(unsigned)std::min<int64_t>((n_round + 255) / 256, 4096), 256, 0, s>>>(d_src, n_inst,
                                                                                                    batch, d_seqs);
         FTRY(cudaGetLastError(), "gather");
-        comet_status r = comet::launch_eval_device(p, d_seqs, n_round, nullptr, nullptr, 0, d_cost, nullptr, d_status);
+        comet_status r = comet::launch_eval_device(p, d_seqs, n_round, nullptr, d_warm, 0, d_cost, nullptr, d_status);
         if (r != COMET_OK) return r;
         for (int i = 0; i < n_inst; ++i) {
             comet::FrontierDev Fa = fr[i]->d;
@@ -824,6 +869,22 @@ extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const
         }
     }
     return COMET_OK;
+}
+
+}  // namespace
+
+extern "C" comet_status comet_plan_batch(comet_problem* p, int32_t n_inst, const int32_t* instances,
+                                         const comet_mode_seq* seeds, const int64_t* seed_offsets,
+                                         const comet_plan_opts* opts, comet_plan_result* out) {
+    return plan_batch_impl(p, n_inst, instances, seeds, seed_offsets, opts, nullptr, out);
+}
+
+extern "C" comet_status comet_plan_batch_learned(comet_problem* p, int32_t n_inst, const int32_t* instances,
+                                                 const comet_mode_seq* seeds, const int64_t* seed_offsets,
+                                                 const comet_plan_opts* opts, comet_proposal* q,
+                                                 comet_plan_result* out) {
+    if (!q) return ffail(COMET_ERR_INVALID_ARG, "proposal is required");
+    return plan_batch_impl(p, n_inst, instances, seeds, seed_offsets, opts, q, out);
 }
 
 // ------------------------------------------------ uniform sampling of orders

@@ -706,6 +706,8 @@ comet_status proposal_reserve_prune(comet_proposal* q, int64_t cap, int keep) {
     return COMET_OK;
 }
 
+comet_problem* proposal_problem(const comet_proposal* q) { return q ? q->p : nullptr; }
+
 // warm starts of the seed orders (device), rows in order
 comet_status proposal_predict_device(comet_proposal* q, const comet_mode_seq* seqs, int64_t n, float* merit,
                                      float* warm, cudaStream_t s) {

@@ -73,5 +73,7 @@ comet_status proposal_prune_device(comet_proposal* q, comet_frontier* f, int kee
                                    cudaStream_t s);
 comet_status proposal_predict_device(comet_proposal* q, const comet_mode_seq* seqs, int64_t n, float* merit,
                                      float* warm, cudaStream_t s);
+// The problem a proposal was created for.
+comet_problem* proposal_problem(const comet_proposal* q);
 
 }  // namespace comet

@@ -194,3 +194,22 @@ def test_bimanual_learned_planner(P, trained):
     rows = np.array(rows, dtype=float)
     assert np.all(rows[:, 5] >= rows[:, 4])          # a certified plan wherever plain expansion finds one
     assert np.all(rows[:, 3] < 0.6 * rows[:, 2])     # from far fewer evaluations
+
+
+def test_batched_learned_planner_equals_one_instance_at_a_time(P, trained):
+    # the batched planner runs the same algorithm: per instance the same
+    # evaluated set, plan and cost as the single-instance learned planner
+    flat, _ = trained
+    insts = [W.bimanual_instance(s) for s in range(44, 48)]
+    prob = P.Problem(insts)
+    q = P.comet_proposal_create(prob.handle)
+    P.comet_proposal_set_params(q, flat)
+    one = [(m,) for m in range(507)]
+    opts = dict(k=16, batch=256, rounds=3, k_ref=64)
+    batched = P.comet_plan_batch(prob.handle, list(range(4)), [one] * 4, opts, proposal=q)
+    for i in range(4):
+        r = P.comet_plan(prob.handle, i, P.pack_mode_seqs(one, np.full(507, i, np.int32)), 507, opts, proposal=q)
+        assert r["evaluations"] == batched[i]["evaluations"]
+        assert r["best"] == batched[i]["best"] and r["best_cost"] == batched[i]["best_cost"]
+    P.comet_proposal_destroy(q)
+    prob.close()
