@@ -14,7 +14,8 @@
 // Work per iteration:
 //   A  a warp per stage, a lane per constraint row (32 rows): rows and their
 //      Jacobians from one stage context, the AL model over (u, x_{k+1}, x_k)
-//      as 276 lane-parallel dot products, elimination of the 12 u columns;
+//      as 276 lane-parallel dot products, then the 12 u columns eliminated
+//      in registers (a model row per lane, shuffles for the pivot column);
 //      records to the CTA's workspace (L2-resident)
 //   B  one warp: the sequential sweep eliminating the 5 x_{k+1} columns, the
 //      next stage's record prefetched into registers
@@ -587,34 +588,42 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
                 At[tt] = h;
             }
             __syncwarp();
-            // eliminate the u block (12 Cholesky columns); a non-positive
-            // pivot marks the record
+            // eliminate the u block (12 Cholesky columns) in registers: lane
+            // i < 23 holds row i of the lower triangle (entries 0..i); the
+            // pivot comes from lane j and the column entry L_cj from lane c
+            // by shuffles.  A non-positive pivot marks the record.
+            float row[NE];
+#pragma unroll
+            for (int cc = 0; cc < NE; ++cc) row[cc] = (cc <= lane && lane < NE) ? At[tri(lane, cc)] : 0.f;
             bool pd = true;
+#pragma unroll
             for (int j = 0; j < 12; ++j) {
-                const float d = At[tri(j, j)];
+                const float d = __shfl_sync(kFullB, row[j], j);
                 pd = pd && (d > 0.f);
                 const float l = sqrtf(fmaxf(d, 1e-30f));
                 const float il = 1.f / l;
-                __syncwarp();
-                if (lane == 0) At[tri(j, j)] = l;
-                for (int i = j + 1 + lane; i < NE; i += 32) At[tri(i, j)] *= il;
-                __syncwarp();
-                // entries of columns > j (flat index >= tri(j + 1, j + 1))
-                for (int tt = tri(j + 1, j + 1) + lane; tt < NTRI; tt += 32) {
-                    const int i = C.tab[tt] >> 8, cc = C.tab[tt] & 255;
-                    if (cc > j) At[tt] -= At[tri(i, j)] * At[tri(cc, j)];
+                if (lane == j) row[j] = l;
+                if (lane > j) row[j] *= il;
+#pragma unroll
+                for (int cc = j + 1; cc < NE; ++cc) {
+                    const float lcj = __shfl_sync(kFullB, row[j], cc);
+                    if (lane >= cc) row[cc] -= row[j] * lcj;
                 }
-                __syncwarp();
             }
+            // records from the rows: the u factor (rows 0..11), the coupling
+            // rows (12..22) x u columns, the reduced (y, x, rhs) block
             float* rec = C.rec + (size_t)k * kBimRec;
-            for (int tt = lane; tt < 78; tt += 32) rec[R_LUU + tt] = At[tt];
-            for (int q = lane; q < 132; q += 32) {
-                const int p = q / 12, j = q % 12;
-                rec[R_CPL + q] = At[tri(12 + p, j)];
-            }
-            for (int q = lane; q < NTRI_RED; q += 32) {
-                const int i = C.tab[q] >> 8, j = C.tab[q] & 255;
-                rec[R_RED + q] = At[tri(12 + i, 12 + j)];
+            if (lane < 12) {
+#pragma unroll
+                for (int cc = 0; cc < 12; ++cc)
+                    if (cc <= lane) rec[R_LUU + tri(lane, cc)] = row[cc];
+            } else if (lane < NE) {
+                const int p = lane - 12;
+#pragma unroll
+                for (int cc = 0; cc < 12; ++cc) rec[R_CPL + 12 * p + cc] = row[cc];
+#pragma unroll
+                for (int cc = 12; cc < NE; ++cc)
+                    if (cc <= lane) rec[R_RED + tri(p, cc - 12)] = row[cc];
             }
             if (lane == 0) rec[R_PD] = pd ? 1.f : -1.f;
         }
