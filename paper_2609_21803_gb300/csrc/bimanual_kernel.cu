@@ -13,10 +13,10 @@
 //
 // Work per iteration:
 //   A  a warp per stage, a lane per constraint row (32 rows): rows and their
-//      Jacobians from one stage context, the AL model over (u, x_{k+1}, x_k)
-//      as 276 lane-parallel dot products, then the 12 u columns eliminated
-//      in registers (a model row per lane, shuffles for the pivot column);
-//      records to the CTA's workspace (L2-resident)
+//      Jacobians from one stage context; the AL model over (u, x_{k+1}, x_k)
+//      built in registers, a model row per lane, from each row's nonzero
+//      pattern; the 12 u columns eliminated there (shuffles for the pivot
+//      column); records to the CTA's workspace (L2-resident)
 //   B  one warp: the sequential sweep eliminating the 5 x_{k+1} columns, the
 //      next stage's record prefetched into registers
 //   gains and control steps stage-parallel, the forward chain on 5 lanes
@@ -36,7 +36,6 @@ namespace {
 constexpr unsigned kFullB = 0xffffffffu;
 constexpr int NX = 5, NU = 12, NR = 32, NL = 22, NWV = 17;
 constexpr int NE = 23;               // elimination order (u 12, y 5, x 5, rhs)
-constexpr int NTRI = NE * (NE + 1) / 2;  // 276
 constexpr int NRED = 11;             // reduced block (y 5, x 5, rhs)
 constexpr int NTRI_RED = NRED * (NRED + 1) / 2;  // 66
 // record layout (floats)
@@ -78,16 +77,10 @@ __device__ __forceinline__ float brcp_approx(float x) {
 }
 
 // elimination position of local variable v; rhs = 22
-__device__ __forceinline__ int epos(int v) { return v >= 17 ? v - 5 : (v >= 5 ? v - 5 : v + 17); }
+__host__ __device__ constexpr int epos(int v) { return v >= 17 ? v - 5 : (v >= 5 ? v - 5 : v + 17); }
 // local variable of elimination position e (e < 22)
-__device__ __forceinline__ int evar(int e) { return e < 12 ? e + 5 : (e < 17 ? e + 5 : e - 17); }
+__host__ __device__ constexpr int evar(int e) { return e < 17 ? e + 5 : e - 17; }
 
-__device__ __forceinline__ void untri(int t, int& i, int& j) {
-    i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-    while (tri(i + 1, 0) <= t) ++i;
-    while (tri(i, 0) > t) --i;
-    j = t - tri(i, 0);
-}
 
 template <typename T>
 struct BInst {
@@ -182,6 +175,39 @@ __device__ void stage_ctx(const BInst<T>& P, int mode, const T* x, const T* u, B
     S.rcz = -P.ax * sth - P.az * cth;
     S.w = P.ax * cth * cth + P.az * sth * sth;
     S.dw = 2 * sth * cth * (P.az - P.ax);
+}
+
+// hand rows of one side (q = 0..7): force, sliding rate and offset
+__host__ __device__ constexpr int bnz_hand(bool right, int q, int a) {
+    return (q == 0 || q == 3) ? (a == 0 ? (right ? UFNR : UFNL) : a == 1 ? (right ? UFTR : UFTL)
+                                 : a == 2 ? (right ? USDR : USDL) : -1)
+         : q == 1 ? (a == 0 ? (right ? UFTR : UFTL) : -1)
+         : q == 2 ? (a == 0 ? (right ? USDR : USDL) : -1)
+         : q == 4 ? (a == 0 ? (right ? UFNR : UFNL) : a == 1 ? (right ? UFTR : UFTL) : -1)
+         : q == 5 ? (a == 0 ? (right ? UFNR : UFNL) : -1)
+                  : (a == 0 ? (right ? VSR : VSL) : -1);
+}
+
+// Local variables that row r can depend on, over all modes (a superset of
+// the nonzeros brow writes), ascending; -1 pads.  Kinematic rows: x_k,r,
+// the rate and x_{k+1},r; wrench rows: the force components, the angle and
+// (torque) z, the hands' offsets and the centre of pressure; ground rows:
+// the twist, the ground force and p_c, the angle where the pivot enters;
+// hand rows: that hand's force, sliding rate and offset.
+__host__ __device__ constexpr int bnz(int r, int a) {
+    return r < 5 ? (a == 0 ? r : a == 1 ? (r < 3 ? UXD + r : (r == 3 ? USDL : USDR)) : a == 2 ? VX1 + r : -1)
+         : r == 5 ? (a == 0 ? VTH : a == 1 ? UFNL : a == 2 ? UFTL : a == 3 ? UFNR : a == 4 ? UFTR : a == 5 ? ULT : -1)
+         : r == 6 ? (a == 0 ? VTH : a == 1 ? UFNL : a == 2 ? UFTL : a == 3 ? UFNR : a == 4 ? UFTR : a == 5 ? ULN : -1)
+         : r == 7 ? (a == 0 ? VZ : a == 1 ? VSL : a == 2 ? VSR : a == 3 ? UFNL : a == 4 ? UFTL : a == 5 ? UFNR
+                     : a == 6 ? UFTR : a == 7 ? ULN : a == 8 ? ULT : a == 9 ? UPC : -1)
+         : r == 8 ? (a == 0 ? VTH : a == 1 ? UXD : a == 2 ? UZD : a == 3 ? UTHD : -1)
+         : r == 9 ? (a == 0 ? VTH : a == 1 ? UZD : a == 2 ? UTHD : -1)
+         : r == 10 ? (a == 0 ? VTH : a == 1 ? UTHD : a == 2 ? ULN : a == 3 ? ULT : a == 4 ? UPC : -1)
+         : r == 11 ? (a == 0 ? UXD : a == 1 ? ULN : a == 2 ? ULT : -1)
+         : r == 12 ? (a == 0 ? ULN : a == 1 ? ULT : -1)
+         : r == 13 ? (a == 0 ? ULN : -1)
+         : r <= 15 ? (a == 0 ? VTH : a == 1 ? UPC : -1)
+         : bnz_hand(r >= 24, r - (r >= 24 ? 24 : 16), a);
 }
 
 // Row r of an interval: scaled value c, presence, inequality flag, the
@@ -447,14 +473,14 @@ __device__ __forceinline__ void two_sum_b(float a, float b, float& s, float& e) 
 struct BSmem {
     float *xh, *xl, *us, *lam, *dz, *gr;
     int* mi;     // per interval: mode | maskL << 10 | maskR << 11
-    float *Jw, *yw, *At;  // per warp: [32][22], [32], [276]
+    float *Jw, *yw;       // per warp: [32][22], [32]
     float* ring;          // sweep copy ring [kBRing][kBSlot] (16-byte aligned)
     float* red;           // reductions / broadcasts [64]
 };
 
 __host__ __device__ inline size_t bsmem_floats(int Nmax) {
     const size_t f = (size_t)10 * (Nmax + 1) + (size_t)NU * Nmax + 3 + (size_t)NR * Nmax +
-                     2 * ((size_t)NWV * Nmax + NX) + (size_t)Nmax + 4 * (NR * NL + NR + NTRI) + kBRing * kBSlot + 64;
+                     2 * ((size_t)NWV * Nmax + NX) + (size_t)Nmax + 4 * (NR * NL + NR) + kBRing * kBSlot + 64;
     return (f + 3) / 4 * 4;
 }
 
@@ -470,13 +496,11 @@ __device__ BSmem bcarve(float* p, int Nmax) {
     s.mi = reinterpret_cast<int*>(p); p += Nmax;
     s.Jw = p; p += 4 * NR * NL;
     s.yw = p; p += 4 * NR;
-    s.At = p; p += 4 * NTRI;
     s.red = p;
     return s;
 }
 
 struct BCtx {
-    const unsigned short* tab;  // (i << 8 | j) of the flat lower-triangle index t < 276
     const DevInstance* D;
     BInst<float> P;
     BSmem S;
@@ -520,7 +544,6 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
     const int N = C.N, lane = C.lane, warp = C.warp;
     float* Jw = S.Jw + warp * NR * NL;
     float* yw = S.yw + warp * NR;
-    float* At = S.At + warp * NTRI;
     float viol = 0.f, comp = 0.f, vph = 0.f, jc = 0.f;
     bool finite = true;
 #pragma unroll 1
@@ -562,6 +585,7 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
         yw[lane] = y;
         __syncwarp();
         // AL gradient over the local variables (lane = variable)
+        float gval = 0.f;
         if (lane < NL) {
             float g = 0.f;
             for (int r = 0; r < NR; ++r) g += yw[r] * Jw[r * NL + lane];
@@ -570,31 +594,47 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
                 S.gr[NWV * k + lane] = g;
             else
                 S.dz[NWV * (k + 1) + lane - 17] = g;
-            if (assemble) At[tri(22, epos(lane))] = g;
+            gval = g;
         }
         if (assemble) {
-            // lower triangle of beta sum_r J J^T + cost + rho over (u, y, x); the
-            // rhs row was written above
-            for (int tt = lane; tt < tri(22, 0); tt += 32) {
-                const int i = C.tab[tt] >> 8, j = C.tab[tt] & 255;
-                const int vi = evar(i), vj = evar(j);
-                float h = 0.f;
-                for (int r = 0; r < NR; ++r) h += Jw[r * NL + vi] * Jw[r * NL + vj];
-                h *= beta;
-                if (i == j) {
-                    if (i < 12) h += 2.f * rweight(P, i) + rho;
-                    else if (i < 17) h += rho;
+            // the model in registers, a row per lane: lane i < 22 holds row i
+            // of the lower triangle over (u, y, x) in elimination order (and
+            // lane 22 the rhs row).  Row i = sum_r J_r[v_i] J_r over the
+            // active rows in row order; for row r only the columns of its
+            // pattern (bnz) are added, the others being exact zeros: the
+            // lane's own entry times a broadcast Jacobian value
+            const int vi = lane < NL ? evar(lane) : 0;
+            float row[NE];
+#pragma unroll
+            for (int cc = 0; cc < NE; ++cc) row[cc] = 0.f;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float a = lane < NL ? Jw[r * NL + vi] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    if (bnz(r, q) < 0) break;
+                    row[epos(bnz(r, q))] += a * Jw[r * NL + bnz(r, q)];
                 }
-                At[tt] = h;
             }
-            __syncwarp();
+            // beta, then the cost and damping on the diagonal (u: cost +
+            // rho, x_{k+1}: rho); the gradient as the rhs row (lane 22)
+#pragma unroll
+            for (int cc = 0; cc < NE - 1; ++cc) {
+                row[cc] *= beta;
+                if (lane == cc) {
+                    if (cc < 12) row[cc] += 2.f * rweight(P, cc) + rho;
+                    else if (cc < 17) row[cc] += rho;
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < NE - 1; ++cc) {
+                const float gv = __shfl_sync(kFullB, gval, evar(cc));
+                if (lane == NE - 1) row[cc] = gv;
+            }
             // eliminate the u block (12 Cholesky columns) in registers: lane
             // i < 23 holds row i of the lower triangle (entries 0..i); the
             // pivot comes from lane j and the column entry L_cj from lane c
             // by shuffles.  A non-positive pivot marks the record.
-            float row[NE];
-#pragma unroll
-            for (int cc = 0; cc < NE; ++cc) row[cc] = (cc <= lane && lane < NE) ? At[tri(lane, cc)] : 0.f;
             bool pd = true;
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
@@ -1176,14 +1216,6 @@ __global__ void __launch_bounds__(kBimThreads, 3) bimanual_kernel(EvalArgs A) {
     const SolverParams& sp = A.sp;
     const int64_t n_tos = A.d_n ? min(*A.d_n, A.n) : A.n;
     __shared__ unsigned int s_t;
-    __shared__ unsigned short s_tab[NTRI];
-    for (int t = C.tid; t < NTRI; t += kBimThreads) {
-        int i, j;
-        untri(t, i, j);
-        s_tab[t] = (unsigned short)(i << 8 | j);
-    }
-    C.tab = s_tab;
-    __syncthreads();
     for (;;) {
         if (C.tid == 0) s_t = atomicAdd(A.queue, 1u);
         __syncthreads();
