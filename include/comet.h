@@ -331,25 +331,30 @@ typedef struct {
     int32_t warps_per_block;    /* TOs per CTA (one warp per TO): 1..4 (default 4) */
     int32_t blocks_per_sm;      /* resident CTAs per SM the grid is sized for */
     int32_t max_blocks_per_sm;  /* occupancy limit of warps_per_block (get only) */
-    int32_t reserved;
+    int32_t unroll;             /* stages per trip of the evaluator's stage-parallel loops:
+                                   1 or 2 (0 reads as 1) */
 } comet_launch_config;
 
 /* The problem's current launch shape. */
 comet_status comet_get_launch_config(comet_problem* p, comet_launch_config* out);
 
 /* Set the launch shape (warps_per_block in 1..4, blocks_per_sm in 1..the
- * occupancy limit; INVALID_ARG otherwise).  Results never depend on it: every
- * shape solves each TO in one warp with the same arithmetic.  Synchronises. */
+ * occupancy limit, unroll 0, 1 or 2; INVALID_ARG otherwise).  Results never
+ * depend on warps_per_block and blocks_per_sm: every shape solves each TO in
+ * one warp with the same arithmetic.  The unrolled build of the stage loops
+ * is the same solver compiled with other multiply-add contractions, so its
+ * FP32 rounding differs.  Synchronises. */
 comet_status comet_set_launch_config(comet_problem* p, const comet_launch_config* cfg);
 
 /* Autotuner (no paper counterpart; the paper sizes its worker pool by hand):
  * times the evaluator on the n orders of `sample` (host or device) with an
  * iteration budget max_iters (0 = the solver's) under every candidate shape
  * -- 1..4 TOs per CTA, each at its occupancy limit and at three quarters of
- * it -- keeps the fastest for p and caches it per (device, N_max) for
- * problems created later in the process.  out (nullable) receives the pick,
- * out_ms (nullable, >= 8 floats) the time of each candidate in order, and
- * n_candidates (nullable) their number.  Synchronises. */
+ * it, each with the stage loops unrolled 1 and 2 times -- keeps the fastest
+ * for p and caches it per (device, N_max) for problems created later in the
+ * process.  out (nullable) receives the pick, out_ms (nullable, >= 16
+ * floats) the time of each candidate in order, and n_candidates (nullable)
+ * their number.  Synchronises. */
 comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int64_t n, int32_t max_iters,
                             comet_launch_config* out, float* out_ms, int32_t* n_candidates);
 

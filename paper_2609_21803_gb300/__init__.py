@@ -74,7 +74,7 @@ class PlanResult(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("max_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_blocks_per_sm", ctypes.c_int32), ("unroll", ctypes.c_int32)]
 
 
 class ProposalDesc(ctypes.Structure):
@@ -773,11 +773,11 @@ def comet_get_launch_config(problem) -> dict:
     c = LaunchConfig()
     _check(lib().comet_get_launch_config(problem, ctypes.byref(c)))
     return {"warps_per_block": c.warps_per_block, "blocks_per_sm": c.blocks_per_sm,
-            "max_blocks_per_sm": c.max_blocks_per_sm}
+            "max_blocks_per_sm": c.max_blocks_per_sm, "unroll": c.unroll}
 
 
-def comet_set_launch_config(problem, warps_per_block: int, blocks_per_sm: int):
-    c = LaunchConfig(warps_per_block, blocks_per_sm, 0, 0)
+def comet_set_launch_config(problem, warps_per_block: int, blocks_per_sm: int, unroll: int = 1):
+    c = LaunchConfig(warps_per_block, blocks_per_sm, 0, unroll)
     _check(lib().comet_set_launch_config(problem, ctypes.byref(c)))
 
 
@@ -789,4 +789,4 @@ def comet_autotune(problem, sample, n: int, max_iters: int = 0):
     _check(lib().comet_autotune(problem, _ptr(sample), n, max_iters, ctypes.byref(c), ms.ctypes.data,
                                 ctypes.byref(nc)))
     return ({"warps_per_block": c.warps_per_block, "blocks_per_sm": c.blocks_per_sm,
-             "max_blocks_per_sm": c.max_blocks_per_sm}, [float(x) for x in ms[: nc.value]])
+             "max_blocks_per_sm": c.max_blocks_per_sm, "unroll": c.unroll}, [float(x) for x in ms[: nc.value]])

@@ -325,6 +325,7 @@ comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, 
     a.ws_per_warp = ws_unit_floats(p);
     a.queue = p->d_queue;
     a.bad_input = p->d_bad;
+    a.unroll = p->unroll;
     a.sp = make_params(p->opts, max_iters);
     for (const comet_instance_desc& d : p->inst) a.sp.free_motion |= d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes == 13;
     if (p->task == COMET_TASK_BIMANUAL)
@@ -426,12 +427,13 @@ comet_status comet_problem_create(const comet_instance_desc* inst, int32_t n_ins
     p->blocks_per_sm = comet::eval_blocks_per_sm(p->warps_per_block, smem);
     {
         // a shape the autotuner picked for this device and N_max
-        int w = 0, b = 0;
-        if (p->blocks_per_sm >= 1 && comet::cached_launch_shape(p->device, Nmax, &w, &b)) {
+        int w = 0, b = 0, un = 1;
+        if (p->blocks_per_sm >= 1 && comet::cached_launch_shape(p->device, Nmax, &w, &b, &un)) {
             const int occ = comet::eval_blocks_per_sm(w, comet::smem_per_warp_bytes(Nmax) * w);
             if (occ >= b && b >= 1) {
                 p->warps_per_block = w;
                 p->blocks_per_sm = b;
+                p->unroll = un;
             }
         }
     }

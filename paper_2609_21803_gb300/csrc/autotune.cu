@@ -1,11 +1,14 @@
 // autotune.cu -- launch shape of the persistent evaluator: TOs per CTA (one
-// warp per TO, 1..4) and resident CTAs per SM.  comet_autotune times the
-// evaluator on a sample of the caller's orders under every candidate shape
-// and keeps the fastest; the pick is cached per (device, N_max) for the
-// process, and problems created later with the same key start from it.
+// warp per TO, 1..4), resident CTAs per SM and the unrolling of the stage
+// loops (1 or 2 stages per trip).  comet_autotune times the evaluator on a
+// sample of the caller's orders under every candidate shape and keeps the
+// fastest; the pick is cached per (device, N_max) for the process, and
+// problems created later with the same key start from it.
 //
-// Every shape solves each TO in one warp with the same arithmetic, so the
-// results do not depend on the shape, only the time does.
+// Every (TOs per CTA, CTAs per SM) shape solves each TO in one warp with the
+// same arithmetic, so the results do not depend on it, only the time does;
+// the unrolled build of the stage loops is compiled with other multiply-add
+// contractions, so its FP32 rounding differs.
 
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -24,7 +27,10 @@
 namespace {
 
 std::mutex g_mu;
-std::map<std::pair<int, int>, std::pair<int, int>> g_cache;  // (device, N_max) -> (warps/CTA, CTAs/SM)
+struct Shape {
+    int wpb, bps, unroll;
+};
+std::map<std::pair<int, int>, Shape> g_cache;  // (device, N_max) -> shape
 
 comet_status tfail(comet_status st, const char* msg) {
     comet::set_error(msg);
@@ -47,12 +53,13 @@ int occupancy(const comet_problem* p, int wpb) {
 namespace comet {
 
 // launch shape cached for this device and N_max, if any
-bool cached_launch_shape(int device, int nmax, int* wpb, int* bps) {
+bool cached_launch_shape(int device, int nmax, int* wpb, int* bps, int* unroll) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find({device, nmax});
     if (it == g_cache.end()) return false;
-    *wpb = it->second.first;
-    *bps = it->second.second;
+    *wpb = it->second.wpb;
+    *bps = it->second.bps;
+    *unroll = it->second.unroll;
     return true;
 }
 
@@ -65,7 +72,7 @@ comet_status comet_get_launch_config(comet_problem* p, comet_launch_config* out)
     out->warps_per_block = p->warps_per_block;
     out->blocks_per_sm = p->blocks_per_sm;
     out->max_blocks_per_sm = p->task == COMET_TASK_PUSHER_SLIDER ? occupancy(p, p->warps_per_block) : p->blocks_per_sm;
-    out->reserved = 0;
+    out->unroll = p->unroll;
     return COMET_OK;
 }
 
@@ -79,9 +86,11 @@ comet_status comet_set_launch_config(comet_problem* p, const comet_launch_config
     if (occ < 1) return tfail(COMET_ERR_INVALID_ARG, "this shape does not fit on an SM");
     if (c->blocks_per_sm < 1 || c->blocks_per_sm > occ)
         return tfail(COMET_ERR_INVALID_ARG, "blocks_per_sm must be in 1..the occupancy limit");
+    if (c->unroll < 0 || c->unroll > 2) return tfail(COMET_ERR_INVALID_ARG, "unroll must be 0, 1 or 2");
     if (p->stream) cudaStreamSynchronize(p->stream);
     p->warps_per_block = c->warps_per_block;
     p->blocks_per_sm = c->blocks_per_sm;
+    p->unroll = c->unroll == 2 ? 2 : 1;
     return COMET_OK;
 }
 
@@ -92,14 +101,17 @@ comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int6
         return tfail(COMET_ERR_INVALID_ARG, "the bimanual evaluator runs one CTA per TO; its shape is fixed");
     cudaStream_t s = p->stream;
     // candidate shapes: 1..4 TOs per CTA, each at its occupancy limit and at
-    // three quarters of it (fewer resident warps, less contention)
-    std::vector<std::pair<int, int>> cand;
+    // three quarters of it (fewer resident warps, less contention), each
+    // with the stage loops unrolled once and twice
+    std::vector<Shape> cand;
     for (int w = 1; w <= 4; ++w) {
         const int occ = occupancy(p, w);
         if (occ < 1) continue;
-        cand.push_back({w, occ});
         const int q = std::max(1, (occ * 3) / 4);
-        if (q != occ) cand.push_back({w, q});
+        for (int un = 1; un <= 2; ++un) {
+            cand.push_back({w, occ, un});
+            if (q != occ) cand.push_back({w, q, un});
+        }
     }
     if (cand.empty()) return tfail(COMET_ERR_INVALID_ARG, "no launch shape fits");
     // device copies of the sample and outputs
@@ -123,13 +135,14 @@ comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int6
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int w0 = p->warps_per_block, b0 = p->blocks_per_sm;
+    const int w0 = p->warps_per_block, b0 = p->blocks_per_sm, u0 = p->unroll;
     float best_ms = 0.f;
     int best = -1;
     comet_status st = COMET_OK;
     for (size_t c = 0; c < cand.size() && e == cudaSuccess && st == COMET_OK; ++c) {
-        p->warps_per_block = cand[c].first;
-        p->blocks_per_sm = cand[c].second;
+        p->warps_per_block = cand[c].wpb;
+        p->blocks_per_sm = cand[c].bps;
+        p->unroll = cand[c].unroll;
         st = comet::reserve_eval(p, n);
         if (st != COMET_OK) break;
         // one untimed launch (attributes, caches), then the timed one
@@ -156,11 +169,13 @@ comet_status comet_autotune(comet_problem* p, const comet_mode_seq* sample, int6
     if (st != COMET_OK || e != cudaSuccess || best < 0) {
         p->warps_per_block = w0;
         p->blocks_per_sm = b0;
+        p->unroll = u0;
         if (st != COMET_OK) return st;
         return tcuda(e, "autotune");
     }
-    p->warps_per_block = cand[best].first;
-    p->blocks_per_sm = cand[best].second;
+    p->warps_per_block = cand[best].wpb;
+    p->blocks_per_sm = cand[best].bps;
+    p->unroll = cand[best].unroll;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_cache[{p->device, p->Nmax}] = cand[best];

@@ -73,6 +73,7 @@ struct EvalArgs {
     int64_t ws_per_warp;     // floats
     unsigned int* queue;     // work counter (next TO index)
     int* bad_input;          // set when a malformed order is met
+    int unroll;              // stages per trip of the stage loops (1 or 2)
     SolverParams sp;
 };
 
@@ -104,7 +105,7 @@ int timing_blocks_per_sm(int warps_per_block, int Nmax);
 cudaError_t launch_timing(const TimingArgs& a, int total_warps, int warps_per_block, cudaStream_t s);
 
 // Launch shape cached by the autotuner for (device, N_max) (autotune.cu).
-bool cached_launch_shape(int device, int nmax, int* wpb, int* bps);
+bool cached_launch_shape(int device, int nmax, int* wpb, int* bps, int* unroll);
 
 // Longest-first order of a batch (schedule.cu): perm[0..n) lists the TOs by
 // decreasing interval count; scratch holds lpt_scratch_bytes().

@@ -350,7 +350,7 @@ struct Measures {
     bool finite;
 };
 
-template <bool kFree>
+template <bool kFree, int kUnr = 1>
 __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool assemble, bool update,
                             float beta_old, bool rhs_from_gr = false) {
     const DevInstance& P = *C.P;
@@ -358,7 +358,7 @@ __device__ Measures phase_a(Ctx& C, float beta, float rho, bool curvature, bool 
     Smem& S = C.sm;
     float viol = 0.f, comp = 0.f, vph = 0.f, jc = 0.f;
     bool finite = true;
-#pragma unroll 1
+#pragma unroll (kUnr)
     for (int k = lane; k < N; k += 32) {
         const ModeInfo mi = mode_of(S.mb[k]);
         float h0[4], h1[4], l0[4], l1[4], xk[4], dx[4], ex[2], u[3];
@@ -904,10 +904,11 @@ __device__ bool phase_b(Ctx& C, float beta, float rho, bool rhs_from_gr = false)
 // phase A and the state steps of phase B,
 //   du_k = -L_u^{-T} (l_{y,u}^T dx_{k+1} + l_{x,u}^T dx_k + l_{rhs,u}^T).
 // Returns D = grad . dz.
+template <int kUnr = 1>
 __device__ float phase_c(Ctx& C) {
     const int N = C.N, lane = C.lane;
     Smem& S = C.sm;
-#pragma unroll 1
+#pragma unroll (kUnr)
     for (int k = lane; k < N; k += 32) {
         // record floats 0..35 as 9 vector loads (u-block factor, 1 / l_jj on
         // its diagonal, and the coupling columns)
@@ -997,7 +998,7 @@ __device__ __forceinline__ float stage_merit(const Ctx& C, int k, float alpha, f
 // Stage merits are summed as FP32 pairs (two_sum), so the tests compare
 // phi(alpha) - phi(0) to the predicted decrease without the rounding of
 // the total, which near convergence is as large as that decrease.
-template <bool kFree>
+template <bool kFree, int kUnr = 1>
 __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& sp) {
     const int lane = C.lane;
     const int sub = lane & 3, grp = lane >> 2;
@@ -1010,7 +1011,7 @@ __device__ float phase_d(const Ctx& C, float beta, float D, const SolverParams& 
         const float alpha = (a == 0) ? 0.f : ldexpf(1.f, -(a - 1));
         float phi = 0.f, phil = 0.f;
         if (a <= sp.n_alpha)
-#pragma unroll 1
+#pragma unroll (kUnr)
             for (int k = grp; k < C.N; k += 8) {
                 float e;
                 two_sum(phi, stage_merit<kFree>(C, k, alpha, beta, inv2b), phi, e);
@@ -1343,7 +1344,9 @@ __device__ void refine_step(Ctx& C, float beta, float rho, bool curvature) {
 // most of the local-memory spills a 128-register cap costs (12 warps per SM
 // at 168 registers were 7 % faster than 16 at 128 on the 4-segment
 // enumeration, with DRAM write-back 7 times lower).
-template <bool kRefine, bool kFree>
+// kUnr: stages per trip of the stage-parallel loops (phases A, C and D
+// unrolled 1 or 2 times; the autotuner picks it with the launch shape).
+template <bool kRefine, bool kFree, int kUnr = 1>
 __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
     extern __shared__ float smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1438,7 +1441,7 @@ __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
             bool model_curv = curv, fac = false, done = false;
             float beta_old = beta;
             for (;;) {
-                const Measures m = phase_a<kFree>(C, beta, rho, model_curv, true, trip == kUpdate, beta_old);
+                const Measures m = phase_a<kFree, kUnr>(C, beta, rho, model_curv, true, trip == kUpdate, beta_old);
                 if (trip == kMeasure) {
                     if (!m.finite) {
                         status = COMET_TO_NONFINITE;
@@ -1485,9 +1488,9 @@ __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
             if (done) break;
             ++inner;
             if (!fac) continue;
-            const float D = phase_c(C);
+            const float D = phase_c<kUnr>(C);
             if (kRefine && beta > sp.refine_beta) refine_step<kFree>(C, beta, rho, model_curv);
-            const float alpha = phase_d<kFree>(C, beta, D, sp);
+            const float alpha = phase_d<kFree, kUnr>(C, beta, D, sp);
             if (alpha > 0.f) {
                 phase_e(C, alpha);
                 rho = fmaxf(sp.rho_min, rho / 10.f);
@@ -1528,15 +1531,17 @@ __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
 size_t smem_per_warp_bytes(int Nmax) { return smem_floats(Nmax) * sizeof(float); }
 
 namespace {
-// every instantiation of the evaluator: (refinement, free motion)
+// every instantiation of the evaluator: (refinement, free motion, unroll;
+// the refinement variants run unrolled once)
 cudaError_t set_smem_all(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(eval_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(eval_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(eval_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(eval_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int b = (int)smem;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(eval_kernel<false, false, 1>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel<true, false, 1>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel<false, true, 1>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel<true, true, 1>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel<false, false, 2>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel<false, true, 2>, at, b);
     return e;
 }
 }  // namespace
@@ -1549,7 +1554,7 @@ int eval_blocks_per_sm(int warps_per_block, size_t smem_per_block) {
     }
     // the variants share the register cap and shared memory, so one
     // occupancy query serves all
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<false, false>, warps_per_block * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<false, false, 1>, warps_per_block * 32,
                                                       smem_per_block) != cudaSuccess)
         return 0;
     return nb;
@@ -1571,17 +1576,22 @@ cudaError_t launch_eval(const EvalArgs& a, int total_warps, int warps_per_block,
     }
     const int blocks = (total_warps + warps_per_block - 1) / warps_per_block;
     const bool refine = a.sp.refine && a.sp.refine_beta < a.sp.beta_max;
+    const bool unr2 = a.unroll == 2 && !refine;
     const unsigned threads = warps_per_block * 32;
     if (a.sp.free_motion) {
         if (refine)
-            eval_kernel<true, true><<<blocks, threads, smem, s>>>(a);
+            eval_kernel<true, true, 1><<<blocks, threads, smem, s>>>(a);
+        else if (unr2)
+            eval_kernel<false, true, 2><<<blocks, threads, smem, s>>>(a);
         else
-            eval_kernel<false, true><<<blocks, threads, smem, s>>>(a);
+            eval_kernel<false, true, 1><<<blocks, threads, smem, s>>>(a);
     } else {
         if (refine)
-            eval_kernel<true, false><<<blocks, threads, smem, s>>>(a);
+            eval_kernel<true, false, 1><<<blocks, threads, smem, s>>>(a);
+        else if (unr2)
+            eval_kernel<false, false, 2><<<blocks, threads, smem, s>>>(a);
         else
-            eval_kernel<false, false><<<blocks, threads, smem, s>>>(a);
+            eval_kernel<false, false, 1><<<blocks, threads, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

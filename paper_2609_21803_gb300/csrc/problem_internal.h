@@ -22,6 +22,7 @@ struct comet_problem {
     int num_sms = 0;
     int warps_per_block = 4;
     int blocks_per_sm = 0;
+    int unroll = 1;  // stages per trip of the evaluator's stage loops
     float* d_ws = nullptr;
     int64_t ws_warps = 0;
     // per-warp workspace of the timing-optimisation kernel
