@@ -69,6 +69,43 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // lower-triangle flat index of (i, j), i >= j
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Warm-start staging: one bulk copy (cp.async.bulk, the untiled TMA path)
+// completing on the warp's mbarrier.  Waits are bounded (about one second
+// of clock cycles) and report whether the phase completed.
+constexpr long long kStageWaitCycles = 2000000000ll;
+__device__ __forceinline__ uint32_t ek_smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool ek_mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool ek_mbar_wait(uint32_t bar, uint32_t parity) {
+    if (ek_mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (ek_mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kStageWaitCycles) return false;
+    }
+}
+// dst (shared) and src (global) 16-byte aligned, bytes a positive multiple of 16
+__device__ __forceinline__ void ek_bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // face geometry: inward normal n, tangent t = rot90(n)
 __device__ __forceinline__ void face_nt(int face, float& nx, float& ny) {
     nx = (face == 0) ? 1.f : ((face == 2) ? -1.f : 0.f);
@@ -291,6 +328,7 @@ __device__ __forceinline__ float row_al(bool ineq, float lam, float beta, float 
 // ------------------------------------------------------------ shared memory
 
 struct Smem {
+    unsigned long long* mbar;  // the warp's mbarrier (warm-start staging), 16 bytes reserved
     unsigned char* mb;  // [Nmax] per-interval mode byte: face | kind << 2 | smask << 4
     float* xh;   // [4][Nmax+1] state, high part
     float* xl;   // [4][Nmax+1] state, low part
@@ -301,7 +339,7 @@ struct Smem {
 };
 
 __host__ __device__ inline size_t smem_floats(int Nmax) {
-    const size_t f = (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
+    const size_t f = 4 + (size_t)(Nmax + 3) / 4 + (size_t)8 * (Nmax + 1) +
                      3 * (size_t)Nmax + 3 + 11 * (size_t)Nmax + 2 * (7 * (size_t)Nmax + 4);
     return (f + 3) / 4 * 4;  // every warp's block starts 16-byte aligned
 }
@@ -309,6 +347,7 @@ __host__ __device__ inline size_t smem_floats(int Nmax) {
 __device__ __forceinline__ Smem carve(float* base, int Nmax) {
     Smem s;
     float* p = base;
+    s.mbar = reinterpret_cast<unsigned long long*>(p); p += 4;
     s.mb = reinterpret_cast<unsigned char*>(p); p += (Nmax + 3) / 4;
     s.xh = p; p += 4 * (Nmax + 1);
     s.xl = p; p += 4 * (Nmax + 1);
@@ -1360,6 +1399,15 @@ __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
     C.rec = A.ws + (size_t)warp_global * A.ws_per_warp;
     const SolverParams& sp = A.sp;
     const int64_t n_tos = A.d_n ? min(*A.d_n, A.n) : A.n;
+    const uint32_t wbar = ek_smem_u32(C.sm.mbar);
+    uint32_t wphase = 0;  // parity of the warp's next staging phase
+    if (A.warm) {
+        if (lane == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(wbar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+    }
 
     for (;;) {
         unsigned int t = 0;
@@ -1396,6 +1444,44 @@ __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
         // ---- initial iterate: warm start or the cold start
         const float* warm = A.warm ? A.warm + ti * A.stride : nullptr;
         const int Nm1 = A.Nmax + 1;
+        if (warm) {
+            // stage the record in the step / gradient buffers (free until
+            // the first iteration): float j at stg[j], with stg congruent to
+            // the record modulo 16 bytes, so that its 16-byte aligned
+            // interior arrives by one bulk copy; the head and tail (at most
+            // 3 floats each) by plain loads
+            const uintptr_t src = reinterpret_cast<uintptr_t>(warm);
+            const int nrec = (int)A.stride;
+            const uintptr_t a0 = (src + 15) & ~(uintptr_t)15, a1 = (src + 4 * (uintptr_t)nrec) & ~(uintptr_t)15;
+            const bool bulk = a1 > a0;
+            float* stg = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(S.dz) + 15) & ~(uintptr_t)15) +
+                         ((src & 15) >> 2);
+            const int h_end = bulk ? (int)((a0 - src) >> 2) : nrec, t_begin = bulk ? (int)((a1 - src) >> 2) : nrec;
+            __syncwarp();
+            if (bulk && lane == 0)
+                ek_bulk_copy(ek_smem_u32(stg) + (uint32_t)(a0 - src), reinterpret_cast<const void*>(a0),
+                             (uint32_t)(a1 - a0), wbar);
+            for (int j = lane; j < h_end; j += 32) stg[j] = warm[j];
+            for (int j = t_begin + lane; j < nrec; j += 32) stg[j] = warm[j];
+            bool ok = true;
+            if (bulk) {
+                ok = ek_mbar_wait(wbar, wphase);
+                wphase ^= 1u;
+            }
+            if (!__all_sync(kFull, ok)) {
+                // the copy did not complete: flag it, give the copy a second
+                // bounded wait, and leave
+                if (lane == 0) {
+                    atomicExch(A.bad_input, 2);
+                    A.out_status[ti] = COMET_TO_NONFINITE;
+                    A.out_cost[ti] = __int_as_float(0x7fc00000);
+                }
+                ek_mbar_wait(wbar, wphase ^ 1u);
+                return;
+            }
+            __syncwarp();
+            warm = stg;
+        }
         for (int q = lane; q < 4 * Np1; q += 32) {
             const int i = q / Np1, k = q - i * Np1;
             float x;
