@@ -140,8 +140,29 @@ def test_straight_push_with_free_durations_closed_form(P):
 @pytest.mark.parametrize("timing", [SLACK, BIND], ids=["slack", "binding"])
 def test_converged_answers_against_the_exact_local_solutions(P, timing):
     seqs, idx = workload()
+    _converged_parity(P, seqs, idx, timing, [TJ.instance(i) for i in range(5)])
+
+
+def test_free_motion_orders(P):
+    # the free-motion mode (12) inside timed orders: the pusher off the
+    # slider, the slider at rest, the offset moving at the pusher's rate for
+    # h_k; first iterate and converged answers as above
+    orders = [(12, 0), (0, 12), (12, 3), (7, 12), (12, 12), (12, 9)]
+    seqs = [q for _ in range(4) for q in orders]
+    idx = np.repeat(np.arange(4, dtype=np.int32), len(orders))
+    insts = [dict(TJ.instance(i), n_modes=13) for i in range(4)]
+    g = gpu_timed(P, seqs, idx, SLACK, 1, insts=insts)
+    ref = TJ.run([(int(i), q, SLACK, 1, None, None) for q, i in zip(seqs, idx)])
+    worst = max(np.abs(TJ.to_interleaved(g["traj"][t]) - z).max() / max(1.0, np.abs(z).max())
+                for t, (z, _, _) in enumerate(ref))
+    print(f"free motion, first iterate: max scaled difference {worst:.2e}")
+    assert worst <= 1e-4
+    _converged_parity(P, seqs, idx, SLACK, insts)
+
+
+def _converged_parity(P, seqs, idx, timing, insts):
     n = len(seqs)
-    g = gpu_timed(P, seqs, idx, timing, 1500)
+    g = gpu_timed(P, seqs, idx, timing, 1500, insts=insts)
     ref = TJ.run([(int(i), q, timing, 1500, None, None) for q, i in zip(seqs, idx)])
     conv_g = g["status"] == TM.CONVERGED
     conv_o = np.array([r["status"] == TM.CONVERGED for _, _, r in ref])
@@ -151,7 +172,7 @@ def test_converged_answers_against_the_exact_local_solutions(P, timing):
     # the host's floating-point library); after it none may remain
     lag = np.nonzero(conv_o & ~conv_g)[0]
     if len(lag):
-        r2 = gpu_timed(P, [seqs[t] for t in lag], idx[lag], timing, 1500, warm=g["traj"][lag])
+        r2 = gpu_timed(P, [seqs[t] for t in lag], idx[lag], timing, 1500, warm=g["traj"][lag], insts=insts)
         for j, t in enumerate(lag):
             for k in ("cost", "status", "traj", "viol", "iters"):
                 g[k][t] = r2[k][j]
