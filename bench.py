@@ -47,7 +47,11 @@ N_STAGES = SEG * K
 # rows and Jacobians once per iteration, the local model on its nonzero
 # pattern, the 7x7 factorisation and solves, the value function, the
 # forward pass, the sequential trial merits up to the accepted step, retries
-FLOP_PER_STAGE_ITER = 3688.7
+FLOP_PER_STAGE_ITER = 1989.2
+# the same for timing optimisation (state x, y, theta, s, tau; control f_n,
+# f_t, sdot, h), counted by the numpy oracle over 48 two-segment orders
+# under each of the timing leg's bounds
+TIMING_FLOP_PER_STAGE_ITER = {"slack": 3362.3, "binding": 3555.3}
 # DRAM bytes (read + write) of one evaluator launch over the 20,736 orders,
 # from the ncu capture of the current kernel on the 4,096-order case (8.42 MB
 # read, 1.033 GB written: spills and stage records written back from L2;
@@ -334,11 +338,13 @@ def run_gpu(args):
     if rank == 0 and args.grammar:
         line["grammar"] = grammar_times(P)
     if rank == 0 and args.bimanual:
-        line["bimanual"] = bimanual_times(P, per=args.bim_per, fp32_peak=peak["tflops"])
+        line["bimanual"] = bimanual_times(P, per=args.bim_per, fp32_peak=peak["tflops"],
+                                          oracle_s=0.0 if args.no_cpu_baseline else 10.0)
     if rank == 0 and args.cfg5:
         line["cfg5"] = cfg5_times(P)
     if rank == 0 and args.timing:
-        line["timing"] = timing_times(P)
+        line["timing"] = timing_times(P, fp32_peak=peak["tflops"],
+                                      oracle_n=None if args.no_cpu_baseline else 2 * (os.cpu_count() or 1))
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and args.mcts:
@@ -606,7 +612,28 @@ def grammar_times(P, n_inst=4):
 BIM_FLOP_PER_STAGE_ITER = 8185.0
 
 
-def bimanual_times(P, n_inst=8, per=512, n_plan=2, fp32_peak=None):
+def bim_oracle_rate(insts, seqs, idx, seconds_target=10.0):
+    """The bimanual FP64 C oracle as it stands on the leg's orders (in the
+    leg's order), one TO per host thread on every core, over a sample grown
+    to about `seconds_target` seconds.  Returns (converged solves/s, sample
+    size, cores, seconds)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    n = min(len(seqs), 4 * cores)
+    while True:
+        t0 = time.time()
+        res, _ = oracle.bim_solve_batch(insts, idx[:n], seqs[:n], [len(q) for q in seqs[:n]], nthreads=cores)
+        dt = time.time() - t0
+        n2 = int(min(len(seqs), n * seconds_target / max(dt, 1e-3)))
+        if n2 <= 1.5 * n or n >= len(seqs):
+            break
+        n = n2
+    conv = int(np.sum((res["status"] == 0) & (res["viol"] < 1e-5)))
+    return conv / dt, n, cores, dt
+
+
+def bimanual_times(P, n_inst=8, per=512, n_plan=2, fp32_peak=None, oracle_s=10.0):
     """The bimanual variant (box flipped by two point hands on a ground
     contact, 507 modes per segment, 15 knots per segment, one CTA per TO):
     random orders of 1..6 segments (512 per instance, 8 instances) in one
@@ -654,13 +681,57 @@ def bimanual_times(P, n_inst=8, per=512, n_plan=2, fp32_peak=None):
             "peak": fp32_peak, "frac": achieved / fp32_peak if fp32_peak else None,
             "note": f"achieved = {BIM_FLOP_PER_STAGE_ITER} flop (the oracle's count per stage and iteration) x "
                     "stage-iterations of the launch / device time; peak = measured FP32 FMA rate (of measured)"}
-    return {"orders": len(seqs), "converged_solves_per_s": conv / t, "solves_per_s": len(seqs) / t,
-            "converged_fraction": conv / len(seqs), "iterations_per_solve": iters, "ms": t * 1e3,
-            "ctas_per_sm": cfg["blocks_per_sm"], "plans": plans, "roofline": roof,
-            "note": "one CTA (128 threads) per TO; device time; v_hat in physical units"}
+    out = {"orders": len(seqs), "converged_solves_per_s": conv / t, "solves_per_s": len(seqs) / t,
+           "converged_fraction": conv / len(seqs), "iterations_per_solve": iters, "ms": t * 1e3,
+           "ctas_per_sm": cfg["blocks_per_sm"], "plans": plans, "roofline": roof,
+           "note": "one CTA (128 threads) per TO; device time; v_hat in physical units"}
+    if oracle_s > 0:
+        rate, ns, cores, dt = bim_oracle_rate(insts, seqs, np.array(idx, np.int32), oracle_s)
+        out["oracle"] = {"converged_solves_per_s": rate, "cores": cores, "kind": "oracle",
+                         "sample": f"first {ns} orders of the leg ({dt:.1f} s), FP64 C oracle, one TO per thread"}
+    return out
 
 
-def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=1500):
+def _timing_oracle_job(job):
+    from oracle import timing as TM
+
+    inst, modes, tm, max_iters = job
+    _, _, r = TM.solve(inst, modes, timing=tm, max_iters=max_iters)
+    return r["status"], r["viol"]
+
+
+def timing_oracle_rate(insts, orders, idx, tm, max_iters, n):
+    """The numpy FP64 timing oracle as it stands on the first `n` orders of
+    the leg, one TO per spawned worker (one BLAS thread each) on every core.
+    Returns (converged solves/s, seconds, cores)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    cores = os.cpu_count() or 1
+    tmo = dict(h_min=tm["h_min"], h_max=tm["h_max"], T=tm["T_max"])
+    jobs = [(insts[int(idx[i])], orders[i], tmo, max_iters) for i in range(n)]
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with ProcessPoolExecutor(min(cores, n), mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_timing_oracle_job, jobs[:1]))  # workers up (numpy imported) before the clock
+            t0 = time.time()
+            res = list(ex.map(_timing_oracle_job, jobs))
+            dt = time.time() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    conv = sum(1 for st, v in res if st == 0 and v < 1e-5)
+    return conv / dt, dt, cores
+
+
+def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=1500, fp32_peak=None,
+                 oracle_n=None):
     """Timing optimisation (interval durations among the controls, the
     elapsed time tau carrying the duration bound): the 2-segment
     enumerations (144 orders, N = 16) of the listed instances and the
@@ -698,13 +769,25 @@ def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=150
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) / 1e3
             conv = int(((status == 0) & (viol <= 1e-5)).sum())
-            out[f"{name}_{bname}"] = {
-                "orders": n, "intervals": nint, "bounds": tm, "ms": t * 1e3,
-                "converged_solves_per_s": conv / t, "converged_fraction": conv / n,
-                "iterations_per_solve": float(iters.float().mean()), "max_iters": max_iters}
+            it_sum = float(iters.double().sum())
+            achieved = TIMING_FLOP_PER_STAGE_ITER[bname] * it_sum * nint / t / 1e12
+            leg = {"orders": n, "intervals": nint, "bounds": tm, "ms": t * 1e3,
+                   "converged_solves_per_s": conv / t, "converged_fraction": conv / n,
+                   "iterations_per_solve": it_sum / n, "max_iters": max_iters,
+                   "roofline": {"bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "peak": fp32_peak,
+                                "frac": achieved / fp32_peak if fp32_peak else None}}
+            if name == "l2" and oracle_n:
+                seqs_i = [tuple(q) for q in seqs]
+                rate, dt_o, cores = timing_oracle_rate(insts, seqs_i, idx, tm, max_iters, min(oracle_n, n))
+                leg["oracle"] = {"converged_solves_per_s": rate, "cores": cores, "kind": "oracle",
+                                 "sample": f"first {min(oracle_n, n)} orders of the leg ({dt_o:.1f} s), numpy FP64 "
+                                           "oracle, one TO per spawned worker"}
+            out[f"{name}_{bname}"] = leg
         prob.close()
     out["note"] = ("timing_kernel: one warp per TO, state (x, y, theta, s, tau), control (f_n, f_t, sdot, h); "
-                   "cold start h_k = dt clipped into the bounds; device time of one launch")
+                   "cold start h_k = dt clipped into the bounds; device time of one launch; roofline achieved = "
+                   f"{TIMING_FLOP_PER_STAGE_ITER} flop per stage-iteration (the numpy oracle's count under each "
+                   "bound) x iterations x intervals / device time, peak = measured FP32 FMA rate (of measured)")
     return out
 
 

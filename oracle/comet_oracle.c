@@ -169,6 +169,12 @@ void orc_cold_start(const orc_instance* in, int32_t N, double* traj) {
 static double dyn_row_scale(const orc_instance* in, int32_t i) {
     double nrm[4];
     const double x0[4] = {0.0, 0.0, 0.0, 0.0}, u0[3] = {0.0, 0.0, 0.0};
+#ifdef ORC_COUNT_FLOPS
+    /* a constant of the instance that this plain implementation recomputes
+     * at every row evaluation: not the method's work */
+    const int rows_on = orc_g_rows_on, jac_on = orc_g_jac_on;
+    COUNT_ROWS(0, 0);
+#endif
     for (int32_t face = 0; face < 4; ++face) {
         double Fx[16], Fu[12], s2 = 1.0; /* the x_{k+1} entry */
         orc_dynamics(in, face, x0, u0, NULL, Fx, Fu);
@@ -187,6 +193,9 @@ static double dyn_row_scale(const orc_instance* in, int32_t i) {
                 nrm[a] = nrm[b];
                 nrm[b] = t;
             }
+#ifdef ORC_COUNT_FLOPS
+    COUNT_ROWS(rows_on, jac_on);
+#endif
     return 0.5 * (nrm[1] + nrm[2]);
 }
 

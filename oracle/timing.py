@@ -53,6 +53,75 @@ DEFAULTS = dict(max_iters=300, max_factor_retries=8, n_alpha=7, max_inner=40, be
                 merit_mu=100.0, beta_ref=1e3, curv_skip=3)
 
 
+# ---------------------------------------------------------- flop counting
+# The method's arithmetic per stage and iteration, counted the way the C
+# oracle's counting build counts it (flops.h): one per add, multiply,
+# divide, square root, sine or cosine; products with structurally zero
+# Jacobian entries are not counted; the symmetric model on its lower
+# triangle; rows that the step re-evaluates at the point the measures have
+# just taken are not counted, nor are Jacobians for merit values.  The
+# step is counted as the backward sweep over w_k = (u_k, x_{k+1}) that the
+# method prescribes (Sec. III-C), not as this module's dense factorisation,
+# and a failed factorisation as a whole sweep.  Off unless count_flops()
+# is active.
+_FLOPS = None
+
+
+def _flops(n):
+    global _FLOPS
+    if _FLOPS is not None:
+        _FLOPS += int(n)
+
+
+def count_flops(on: bool):
+    """Start (on=True, counter at 0) or stop counting; returns the count."""
+    global _FLOPS
+    got = _FLOPS or 0
+    _FLOPS = 0 if on else None
+    return got
+
+
+def _rows_flops(L, free, jac):
+    """Values (and with `jac` the nonzero Jacobian entries) of one interval's
+    rows: dynamics f (21: body wrench, twist, sine, cosine, f) and its
+    Jacobians (24), the four defects (12) and their Jacobian entries (24),
+    the mode rows (18); free motion only the defects (12) and d(s)/d(sdot)
+    (1).  With timing: the duration column of the defects (one per nonzero
+    f_i) and the tau row and the two duration bounds (5), or for the shared
+    step the h row (2)."""
+    v = 12 if free else 21 + 12 + 18
+    j = 1 if free else 24 + 24
+    if L.timing:
+        v += 2 if L.shared else 5
+        j += 1 if free else 4
+    return v + (j if jac else 0)
+
+
+def _curv_flops(L, free):
+    """The dynamics rows' Lagrangian curvature on one interval: the second
+    derivatives of f (39), yd (12) and the four entries times h (8); with
+    timing also the cross terms sum_i yd_i df_i/dv (6 + 14 nonzero products)
+    and their 7 entries; free motion only yd and its one cross term."""
+    c = 0 if free else 39 + 12 + 8
+    if L.timing:
+        c += 12 + 3 if free else 6 + 14 + 7
+    return c
+
+
+def _chol_flops(n):
+    return sum((2 * j + 1) * (n - j) for j in range(n))
+
+
+def _sweep_stage_flops(nx, nu):
+    """One stage of the backward sweep over w = (u_k, x_{k+1}), n = nu + nx:
+    S = H_ww + rho I + V_{k+1} (n + nx(nx+1)/2 + nx), its Cholesky factor,
+    the gains for the nx columns of H_wx and the rhs (2 n^2 each), and
+    V_k, v_k (lower triangle and vector, 2 n each entry)."""
+    n = nu + nx
+    return (n + nx * (nx + 1) // 2 + nx + _chol_flops(n) + (nx + 1) * 2 * n * n
+            + nx * (nx + 1) // 2 * n * 2 + nx * n * 2)
+
+
 # ------------------------------------------------------------------ model
 
 def face_frame(inst, face):
@@ -359,11 +428,13 @@ def row_al(ineq, lam, beta, c):
 def al_merit(P: Problem, z, lam, beta):
     L = P.L
     phi = P.cost(z)
+    _flops(3 * 4 + 3 * P.N * 3)
     ci, _ = P.initial_rows(z)
     for i, c in enumerate(ci):
         phi += row_al(False, lam[i], beta, c)
     for k in range(P.N):
         *_, (c, mask, _, ineq, _) = P.stage(z, k)
+        _flops(_rows_flops(L, P.mode_k[k] == MODE_FREE, False) + 6 * int(np.count_nonzero(mask)))
         for r in range(L.nr):
             if mask[r]:
                 phi += row_al(ineq[r], lam[L.row(k, r)], beta, c[r])
@@ -390,10 +461,12 @@ def measures(P: Problem, z, lam, beta):
     for k in range(P.N):
         *_, (c, mask, scale, ineq, J) = P.stage(z, k)
         loc = L.local(k)
+        _flops(_rows_flops(L, P.mode_k[k] == MODE_FREE, True))
         for r in range(L.nr):
             q = L.row(k, r)
             if not mask[r]:
                 continue
+            _flops(6 + (2 * np.count_nonzero(J[r]) if row_y(ineq[r], lam[q], beta, c[r]) != 0.0 else 0))
             finite &= math.isfinite(c[r])
             y[q] = row_y(ineq[r], lam[q], beta, c[r])
             v = max(c[r], 0.0) if ineq[r] else abs(c[r])
@@ -426,6 +499,7 @@ def step(P: Problem, z, lam, beta, rho, curvature):
         yv = row_y(False, lam[i], beta, c)
         H[idx[i], idx[i]] += beta
         g[idx[i]] += yv
+    mflops = [9] * P.N  # the local model's arithmetic per stage
     for k in range(P.N):
         xk, uk, _, (c, mask, _, ineq, J) = P.stage(z, k)
         loc = L.local(k)
@@ -435,10 +509,13 @@ def step(P: Problem, z, lam, beta, rho, curvature):
             q = L.row(k, r)
             if ineq[r] and not (lam[q] + beta * c[r] > 0.0):
                 continue
+            nnz = np.count_nonzero(J[r])
+            mflops[k] += 2 + 3 * nnz + nnz * (nnz + 1)
             yv = row_y(ineq[r], lam[q], beta, c[r])
             g[loc] += yv * J[r]
             H[np.ix_(loc, loc)] += beta * np.outer(J[r], J[r])
         if curvature:
+            mflops[k] += _curv_flops(L, P.mode_k[k] == MODE_FREE)
             yd = np.array([row_y(False, lam[L.row(k, r)], beta, c[r]) / P.sig[r] if mask[r] else 0.0
                            for r in range(4)])
             xu = loc[:L.nx + L.nu]
@@ -453,9 +530,38 @@ def step(P: Problem, z, lam, beta, rho, curvature):
     try:
         C = np.linalg.cholesky(H)
     except np.linalg.LinAlgError:
+        if _FLOPS is not None:
+            _flops(_failed_sweep_flops(P, H, mflops))
         return None, g
+    _flops(sum(mflops) + P.N * (_sweep_stage_flops(L.nx, L.nu) + (L.nu + L.nx) * 2 * L.nx)
+           + _chol_flops(L.nx) + 2 * L.nx * L.nx)
     dz = -np.linalg.solve(C.T, np.linalg.solve(C, g))
     return dz, g
+
+
+def _failed_sweep_flops(P: Problem, H, mflops):
+    """What the backward sweep counts before it meets the non-positive pivot:
+    the sweep is the Cholesky factorisation of H + rho I with the variables
+    in the order w_{N-1}, ..., w_0, x_0 (w_k = (u_k, x_{k+1})), so LAPACK's
+    dpotrf on that ordering finds the same pivot; the stages before it are
+    counted whole, the failing one up to and including that column."""
+    from scipy.linalg import lapack
+
+    L = P.L
+    n = L.nu + L.nx
+    order = []
+    for k in range(P.N - 1, -1, -1):
+        order += list(range(L.u(k), L.u(k) + L.nu)) + list(range(L.x(k + 1), L.x(k + 1) + L.nx))
+    order += list(range(L.x(0), L.x(0) + L.nx))
+    _, info = lapack.dpotrf(H[np.ix_(order, order)], lower=1)
+    p = int(info) - 1
+    b, j = divmod(p, n)
+    part = lambda m, jj: sum((2 * q + 1) * (m - q) for q in range(jj + 1))  # noqa: E731
+    full = _sweep_stage_flops(L.nx, L.nu)
+    if b < P.N:  # stage k = N - 1 - b: model, S, its factor up to column j
+        done = sum(mflops[P.N - 1 - i] for i in range(b + 1))
+        return done + b * full + n + L.nx * (L.nx + 1) // 2 + L.nx + part(n, j)
+    return sum(mflops) + P.N * full + part(L.nx, p - P.N * n)
 
 
 def trial_step(phi0, D, merit_at, n_alpha, c1, ls_slack):
@@ -499,6 +605,7 @@ def solve(inst, modes, N=None, timing=None, warm=None, **over):
         # stop test of Sec. III-C as in the C oracle: stationarity relative to
         # max(1, |J|), scaled rows within eps_primal, physical rows within
         # half eps_feas
+        _flops(3 * 4 + 3 * N * 3)
         eps_d = o["eps_dual"] * max(1.0, beta / o["beta_ref"]) * max(1.0, abs(P.cost(z)))
         if (m["viol"] <= o["eps_primal"] and m["vphys"] <= 0.5 * o["eps_feas"] and m["stat"] <= eps_d
                 and m["comp"] <= o["eps_comp"]):
@@ -533,10 +640,16 @@ def solve(inst, modes, N=None, timing=None, warm=None, **over):
             n_rej += 1
             continue
         D = float(np.dot(g, dz))
+        _flops(2 * L.nz)
         phi0 = al_merit(P, z, lam, beta)
-        alpha = trial_step(phi0, D, lambda a: al_merit(P, z + a * dz, lam, beta), o["n_alpha"], o["armijo_c1"],
-                           o["ls_slack"])
+
+        def merit_at(a):
+            _flops(2 * L.nz)  # the trial point z + a dz
+            return al_merit(P, z + a * dz, lam, beta)
+
+        alpha = trial_step(phi0, D, merit_at, o["n_alpha"], o["armijo_c1"], o["ls_slack"])
         if alpha > 0.0:
+            _flops(2 * L.nz)
             z = z + alpha * dz
             rho = max(o["rho_min"], rho / 10.0)
         else:
@@ -546,6 +659,7 @@ def solve(inst, modes, N=None, timing=None, warm=None, **over):
         it = o["max_iters"]
     if status != CONVERGED:
         y, grad, m = measures(P, z, lam, beta)
+    _flops(3 * 4 + 3 * N * 3)
     cost = P.cost(z)
     if not math.isfinite(cost) or not m["finite"]:
         status = NONFINITE
@@ -606,3 +720,20 @@ def interleave_c_traj(tr, N):
         for j in range(3):
             z[7 * k + 4 + j] = tr[4 * (N + 1) + j * N + k]
     return z
+
+
+def flops_per_stage_iteration(insts, orders, timing, **over):
+    """(flops per stage-iteration, total flops, stage-iterations) of the
+    method over the given (instance index, modes) orders solved with these
+    options: the count above divided by the sum over the orders of
+    iterations x intervals."""
+    total = work = 0
+    for i, modes in orders:
+        count_flops(True)
+        try:
+            _, _, r = solve(insts[i], modes, timing=timing, **over)
+        finally:
+            f = count_flops(False)
+        total += f
+        work += r["iters"] * int(insts[i]["knots_per_segment"]) * len(modes)
+    return total / max(work, 1), total, work
