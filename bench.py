@@ -344,7 +344,8 @@ def run_gpu(args):
         line["cfg5"] = cfg5_times(P)
     if rank == 0 and args.timing:
         line["timing"] = timing_times(P, fp32_peak=peak["tflops"],
-                                      oracle_n=None if args.no_cpu_baseline else 2 * (os.cpu_count() or 1))
+                                      oracle_n=None if args.no_cpu_baseline else 2 * (os.cpu_count() or 1),
+                                      l4_orders=args.orders)
     if rank == 0 and args.learned_instances > 0:
         line["learned"] = learned_times(P, insts, args.learned_instances)
     if rank == 0 and args.mcts:
@@ -731,7 +732,7 @@ def timing_oracle_rate(insts, orders, idx, tm, max_iters, n):
 
 
 def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=1500, fp32_peak=None,
-                 oracle_n=None):
+                 oracle_n=None, l4_orders=0):
     """Timing optimisation (interval durations among the controls, the
     elapsed time tau carrying the duration bound): the 2-segment
     enumerations (144 orders, N = 16) of the listed instances and the
@@ -746,6 +747,8 @@ def timing_times(P, per_inst=(3, 4, 5, 6, 7, 8, 9, 10), l4_inst=3, max_iters=150
     work = [("l2", [W.push_l2_instance(s) for s in per_inst], 2), ("l4", [W.push_l4_instance(l4_inst)], 4)]
     for name, insts, L in work:
         orders = [tuple(int(v) for v in q) for q in W.all_sequences(12, L)]
+        if L == 4 and l4_orders:
+            orders = orders[:l4_orders]  # profiling: a prefix of the enumeration
         seqs = [q for _ in insts for q in orders]
         idx = np.repeat(np.arange(len(insts), dtype=np.int32), len(orders))
         n = len(seqs)

@@ -21,9 +21,10 @@
 // One iteration (the method of Sec. III-C, as in eval_kernel.cu):
 //   A  stage-parallel: rows, PHR multiplier estimates, measures, the local
 //      AL model over (u_k, x_{k+1}, x_k) and the elimination of its u block;
-//   B  backward sweep over the 5 x_{k+1} columns (every lane runs the chain
-//      on a broadcast copy of the stage record), the x_0 block last;
-//   C  gains, forward pass, control steps;
+//   B  the state steps by the lane-parallel elimination of the
+//      block-tridiagonal system (lanes fold their stages, a shuffle tree
+//      over the lanes, a 10 x 10 root solve, back-substitution);
+//   C  the control steps, stage-parallel;
 //   D  trial merits of alpha in {1, 1/2, ..., 1/64};
 //   E  compensated update.
 
@@ -57,14 +58,12 @@ constexpr int LU = 0, LY = 4, LX = 9, LR = 14;
 //   R_UF  0..9    u-block Cholesky factor (lower triangle, 1/l_jj on the diagonal)
 //   R_CP  10..53  coupling columns: local row 4 + c (c = 0..10) x u column j at 10 + 4c + j
 //   R_PD  54      +1 / -1: the u block was positive definite
-//   R_RED 56..120 reduced lower triangle over local rows 4..14 (no (rhs, rhs) entry);
-//                 after the sweep the raw y-factor columns, after the gains pass
-//                 the gain rows K[i][0..5] at 56 + 6i
+//   R_RED 56..120 reduced lower triangle over local rows 4..14 (no (rhs, rhs) entry):
+//                 the stage's element in (dx_{k+1}, dx_k); once the elimination of
+//                 phase B has taken a stage's node, floats 56..125 hold that node's
+//                 factor and solved columns
 constexpr int kTRec = 128;
 constexpr int R_UF = 0, R_CP = 10, R_PD = 54, R_RED = 56;
-constexpr int kTRing = 4;          // stages in flight in the sweep's copy ring
-constexpr int kTSlot = 72;         // record floats 52..123 (chunks 13..30)
-constexpr int kTSlotChunk0 = 13;
 
 __device__ __forceinline__ float twarp_sum(float v) {
 #pragma unroll
@@ -93,17 +92,6 @@ __device__ __forceinline__ void two_sum_t(float a, float b, float& s, float& e) 
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-
-__device__ __forceinline__ void tcp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void tcp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void tcp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void tcp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __host__ __device__ constexpr int ttri(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -277,7 +265,6 @@ __device__ __forceinline__ float trow_al(bool ineq, float lam, float beta, float
 // ------------------------------------------------------------ shared memory
 
 struct TSmem {
-    float* ring;        // [kTRing][kTSlot] sweep records in flight
     unsigned char* mb;  // [Nmax] mode byte: face | kind << 2 | smask << 4
     float* xh;          // [5][N+1] state, high part
     float* xl;          // [5][N+1] state, low part
@@ -288,7 +275,7 @@ struct TSmem {
 };
 
 __host__ __device__ inline size_t tsmem_floats(int Nmax) {
-    const size_t f = (size_t)kTRing * kTSlot + (size_t)(Nmax + 3) / 4 + (size_t)2 * TX * (Nmax + 1) +
+    const size_t f = (size_t)(Nmax + 3) / 4 + (size_t)2 * TX * (Nmax + 1) +
                      (size_t)TU * Nmax + 5 + (size_t)TR * Nmax + 2 * ((size_t)TW * Nmax + TX);
     return (f + 3) / 4 * 4;
 }
@@ -296,7 +283,6 @@ __host__ __device__ inline size_t tsmem_floats(int Nmax) {
 __device__ __forceinline__ TSmem tcarve(float* base, int Nmax) {
     TSmem s;
     float* p = base;
-    s.ring = p; p += kTRing * kTSlot;
     s.mb = reinterpret_cast<unsigned char*>(p); p += (Nmax + 3) / 4;
     s.xh = p; p += TX * (Nmax + 1);
     s.xl = p; p += TX * (Nmax + 1);
@@ -620,299 +606,313 @@ __device__ TMeasures tphase_a(TCtx& C, float beta, float rho, bool curvature, bo
     return m;
 }
 
-// Phase B: backward sweep k = N-1 .. 0 over the 5 x_{k+1} columns of the
-// reduced 11 x 11 stage matrices (rows y 0..4, x 0..4, rhs), then the x_0
-// block.  Every lane runs the chain on a broadcast copy of the record; the
-// records arrive kTRing stages ahead through a cp.async ring.  Each stage
-// leaves its raw y-factor columns in its record.  Returns false if a pivot
-// is not positive.
-__device__ bool tphase_b(TCtx& C, float beta, float rho, float dx0[TX]) {
-    const DevInstance& P = *C.P;
-    const int N = C.N, Np1 = N + 1, lane = C.lane;
-    TSmem& S = C.sm;
-    constexpr int NRED = TM - TU;  // 11
-    float V[15], v[TX];
-#pragma unroll
-    for (int i = 0; i < TX; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) V[ttri(i, j)] = (i == j && i < 3) ? 2.f * P.w_terminal : 0.f;
-        v[i] = (i < 3) ? 2.f * P.w_terminal * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N]) : 0.f;
-    }
-    {
-        // the terminal row tau_N - T <= 0 while active
-        const float t = S.lam[4 + TR * N] + beta * tterm_row(C, 0.f);
-        if (t > 0.f) {
-            V[ttri(4, 4)] += beta;
-            v[4] += t;
-        }
-    }
-    constexpr int kLanesCopy = kTSlot / 4;  // 18
-#pragma unroll
-    for (int d = 0; d < kTRing; ++d) {
-        const int kk = N - 1 - d;
-        if (kk >= 0 && lane < kLanesCopy) tcp_async16(S.ring + d * kTSlot + 4 * lane, trec(C, kTSlotChunk0 + lane, kk));
-        tcp_async_commit();
-    }
-    bool ok = true;
-    int slot = kTRing - 1;
-#pragma unroll 1
-    for (int k = N - 1; k >= 0; --k) {
-        slot = (slot == kTRing - 1) ? 0 : slot + 1;
-        tcp_async_wait<kTRing - 1>();
-        __syncwarp();
-        const float* sl = S.ring + slot * kTSlot;
-        bool pd = sl[R_PD - 4 * kTSlotChunk0] > 0.f;
-        float m[66];
-#pragma unroll
-        for (int t = 0; t < 65; ++t) m[t] = sl[R_RED - 4 * kTSlotChunk0 + t];
-        m[65] = 0.f;
-        __syncwarp();
-        {
-            const int kk = k - kTRing;
-            if (kk >= 0 && lane < kLanesCopy)
-                tcp_async16(S.ring + slot * kTSlot + 4 * lane, trec(C, kTSlotChunk0 + lane, kk));
-            tcp_async_commit();
-        }
-#pragma unroll
-        for (int t = 0; t < 15; ++t) m[t] += V[t];
-#pragma unroll
-        for (int j = 0; j < TX; ++j) m[ttri(NRED - 1, j)] += v[j];
-#pragma unroll
-        for (int j = 0; j < TX; ++j) {
-            const float p = m[ttri(j, j)];
-            pd = pd && (p > 0.f);
-            const float ip = 1.f / p;
-#pragma unroll
-            for (int i = j + 1; i < NRED; ++i) {
-                const float a = m[ttri(i, j)] * ip;
-#pragma unroll
-                for (int l = j + 1; l <= i; ++l)
-                    if (!(i == NRED - 1 && l == NRED - 1)) m[ttri(i, l)] -= a * m[ttri(l, j)];
-            }
-        }
-        if (!__all_sync(kFullT, pd)) {
-            ok = false;
-            break;
-        }
-        // raw y-factor columns: y-y block (15) then rows (x 0..4, rhs) x columns y 0..4 (30)
-        if (lane == 0) {
-            float o[48];
-#pragma unroll
-            for (int t = 0; t < 15; ++t) o[t] = m[t];
-#pragma unroll
-            for (int c = 0; c < 6; ++c)
-#pragma unroll
-                for (int j = 0; j < TX; ++j) o[15 + 5 * c + j] = m[ttri(TX + c, j)];
-            o[45] = o[46] = o[47] = 0.f;
-#pragma unroll
-            for (int q = 0; q < 12; ++q)
-                *trec(C, R_RED / 4 + q, k) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-        }
-#pragma unroll
-        for (int i = 0; i < TX; ++i) {
-#pragma unroll
-            for (int j = 0; j <= i; ++j) V[ttri(i, j)] = m[ttri(TX + i, TX + j)];
-            v[i] = m[ttri(NRED - 1, TX + i)];
-        }
-    }
-    tcp_async_wait_all();
-    __syncwarp();
-    if (!ok) return false;
-    // x_0 block: V_0 + rho I + beta on the four initial rows
-    float H[15], g[TX];
-#pragma unroll
-    for (int t = 0; t < 15; ++t) H[t] = V[t];
-#pragma unroll
-    for (int i = 0; i < TX; ++i) {
-        H[ttri(i, i)] += rho;
-        g[i] = v[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int q = tinit_comp(i);
-        H[ttri(q, q)] += beta;
-        g[q] += S.lam[i] + beta * tinit_row(C, i, 0.f);
-    }
-    float L[15], il[TX];
-    bool pd0 = true;
-#pragma unroll
-    for (int j = 0; j < TX; ++j) {
-        float d = H[ttri(j, j)];
-#pragma unroll
-        for (int q = 0; q < j; ++q) d -= L[ttri(j, q)] * L[ttri(j, q)];
-        pd0 = pd0 && d > 0.f;
-        il[j] = rsqrtf(fmaxf(d, 1e-30f));
-#pragma unroll
-        for (int i = j + 1; i < TX; ++i) {
-            float s = H[ttri(i, j)];
-#pragma unroll
-            for (int q = 0; q < j; ++q) s -= L[ttri(i, q)] * L[ttri(j, q)];
-            L[ttri(i, j)] = s * il[j];
-        }
-    }
-    float yv[TX], d0[TX];
-#pragma unroll
-    for (int i = 0; i < TX; ++i) {
-        float s = g[i];
-#pragma unroll
-        for (int q = 0; q < i; ++q) s -= L[ttri(i, q)] * yv[q];
-        yv[i] = s * il[i];
-    }
-#pragma unroll
-    for (int i = TX - 1; i >= 0; --i) {
-        float s = yv[i];
-#pragma unroll
-        for (int q = i + 1; q < TX; ++q) s -= L[ttri(q, i)] * d0[q];
-        d0[i] = s * il[i];
-    }
-#pragma unroll
-    for (int i = 0; i < TX; ++i) dx0[i] = -d0[i];
-    return __all_sync(kFullT, pd0);
-}
+// Phase B: the step's state part by a lane-parallel elimination of the
+// block-tridiagonal system over dx_0 .. dx_N (Sec. III-C "Fixed-workspace
+// local solves"), the order the fixed-step evaluator uses, here with 5 x 5
+// blocks.  After phase A each stage record holds a quadratic element in
+// (dx_{k+1}, dx_k): the reduced lower triangle over (y = x_{k+1}, x = x_k,
+// rhs).  Lane l folds the elements of its stages [k0, k1) into one over
+// (x_{k1}, x_{k0}); a tree over the lanes (the partner's element by
+// shuffles) eliminates the nodes between the spans until lane 0 holds an
+// element over (x_N, x_0) and solves that 10 x 10 system; the node steps
+// follow by back-substitution down the tree and through each lane's span.
+// Eliminating node m between E over (m, a) and F over (b, m):
+// S = E_mm + F_mm = L L^T, Y = L^{-1} [F_mb | E_ma | r_m], the element over
+// (b, a) is blockdiag(F_bb, E_aa) - Y^T Y, and later
+// dx_m = -L^{-T} (Y_b dx_b + Y_a dx_a + y_r).  The same block Cholesky as
+// the backward sweep, in another order: the matrix is positive definite
+// exactly when every pivot is positive, in any order, so a non-positive
+// pivot (or a u-block pivot flagged by phase A) reports failure.  Writes
+// dx_k to dz[9k .. 9k+4], k = 0..N.
 
-// Stage-parallel gains: K = -L_y^{-T} [l_{x,y} | l_{rhs,y}] (5 x 6) from
-// the raw y-factor columns; row i of K at record float 56 + 6 i.
-__device__ void tphase_gains(TCtx& C) {
-    const int N = C.N, lane = C.lane;
-#pragma unroll 1
-    for (int k = lane; k < N; k += 32) {
-        float m[48];
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            const float4 t = *trec(C, R_RED / 4 + q, k);
-            m[4 * q] = t.x;
-            m[4 * q + 1] = t.y;
-            m[4 * q + 2] = t.z;
-            m[4 * q + 3] = t.w;
-        }
-        float ly[15], il[TX];
-#pragma unroll
-        for (int j = 0; j < TX; ++j) {
-            il[j] = rsqrtf(m[ttri(j, j)]);
-#pragma unroll
-            for (int i = j + 1; i < TX; ++i) ly[ttri(i, j)] = m[ttri(i, j)] * il[j];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) m[15 + 5 * c + j] *= il[j];
-        }
-        float K[TX][6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int i = TX - 1; i >= 0; --i) {
-                float s = -m[15 + 5 * c + i];
-#pragma unroll
-                for (int q = i + 1; q < TX; ++q) s -= ly[ttri(q, i)] * K[q][c];
-                K[i][c] = s * il[i];
-            }
-        float o[32];
-#pragma unroll
-        for (int i = 0; i < TX; ++i)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) o[6 * i + c] = K[i][c];
-        o[30] = o[31] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            *trec(C, R_RED / 4 + q, k) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-    }
-    __syncwarp();
-}
+constexpr int kTElem = 65;  // 11 x 11 lower triangle without the (rhs, rhs) entry
+constexpr int kTElemChunk0 = R_RED / 4;  // 14: element and node floats start here
 
-__device__ __forceinline__ void tload_gain(const TCtx& C, int k, float G[TX][TX], float g[TX]) {
-    float v[32];
+// record floats 56..120 of stage k as an element, with the boundary terms:
+// the terminal cost and the active terminal row on the last stage's y
+// block, damping and the four initial rows on the first stage's x block
+__device__ __forceinline__ void tload_elem(const TCtx& C, int k, float e[kTElem], float beta, float rho) {
+    float v[68];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float4 t = *trec(C, R_RED / 4 + q, k);
+    for (int q = 0; q < 17; ++q) {
+        const float4 t = *trec(C, kTElemChunk0 + q, k);
         v[4 * q] = t.x;
         v[4 * q + 1] = t.y;
         v[4 * q + 2] = t.z;
         v[4 * q + 3] = t.w;
     }
 #pragma unroll
-    for (int i = 0; i < TX; ++i) {
+    for (int t = 0; t < kTElem; ++t) e[t] = v[t];
+    const DevInstance& P = *C.P;
+    const int N = C.N, Np1 = N + 1;
+    const TSmem& S = C.sm;
+    if (k == N - 1) {
 #pragma unroll
-        for (int j = 0; j < TX; ++j) G[i][j] = v[6 * i + j];
-        g[i] = v[6 * i + 5];
+        for (int i = 0; i < 3; ++i) {
+            e[ttri(i, i)] += 2.f * P.w_terminal;
+            e[ttri(10, i)] += 2.f * P.w_terminal * ((S.xh[i * Np1 + N] - P.goal[i]) + S.xl[i * Np1 + N]);
+        }
+        const float t = S.lam[4 + TR * N] + beta * tterm_row(C, 0.f);  // tau_N - T <= 0 while active
+        if (t > 0.f) {
+            e[ttri(4, 4)] += beta;
+            e[ttri(10, 4)] += t;
+        }
+    }
+    if (k == 0) {
+#pragma unroll
+        for (int i = 0; i < TX; ++i) e[ttri(5 + i, 5 + i)] += rho;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int q = tinit_comp(i);
+            e[ttri(5 + q, 5 + q)] += beta;
+            e[ttri(10, 5 + q)] += S.lam[i] + beta * tinit_row(C, i, 0.f);
+        }
     }
 }
 
-// Phase C: forward pass dx_{k+1} = G_k dx_k + g_k split over the lanes
-// (each lane composes its stages' affine maps, the entry states pass along
-// the lanes, then each lane walks its stages), then the control steps
-// du_k = -L_u^{-T} (coupling^T [dx_{k+1}; dx_k; 1]).  Returns D = grad . dz.
-__device__ float tphase_c(TCtx& C, const float dx0[TX]) {
-    const int N = C.N, lane = C.lane;
-    TSmem& S = C.sm;
-    if (lane < TX) S.dz[lane] = (lane == 0) ? dx0[0] : (lane == 1) ? dx0[1] : (lane == 2) ? dx0[2]
-                                                      : (lane == 3) ? dx0[3] : dx0[4];
-    const int per = (N + 31) >> 5;
-    const int k0 = min(N, lane * per), k1 = min(N, k0 + per);
-    const int nl = (N + per - 1) / per;
-    float Pm[TX][TX], q[TX];
+// Eliminate the node shared by e (over (y = m, x = a)) and f (over (y = b,
+// x = m)); e becomes the element over (y = b, x = a).  Stores node m's
+// (L, Y) in record `km` when `store`; false on a non-positive pivot.
+__device__ __forceinline__ bool tcombine(const TCtx& C, float e[kTElem], const float f[kTElem], int km, bool store) {
+    float L[15];
+#pragma unroll
+    for (int i = 0; i < TX; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) L[ttri(i, j)] = e[ttri(i, j)] + f[ttri(TX + i, TX + j)];
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < TX; ++j) {
+        float d = L[ttri(j, j)];
+#pragma unroll
+        for (int q = 0; q < j; ++q) d -= L[ttri(j, q)] * L[ttri(j, q)];
+        pd = pd && d > 0.f;
+        const float il = rsqrtf(fmaxf(d, 1e-30f));
+        L[ttri(j, j)] = il;
+#pragma unroll
+        for (int i = j + 1; i < TX; ++i) {
+            float s = L[ttri(i, j)];
+#pragma unroll
+            for (int q = 0; q < j; ++q) s -= L[ttri(i, q)] * L[ttri(j, q)];
+            L[ttri(i, j)] = s * il;
+        }
+    }
+    // Y = L^{-1} [F_mb | E_ma | r_m]: columns b 0..4, a 0..4, rhs
+    float Y[TX][11];
+#pragma unroll
+    for (int c = 0; c < 11; ++c)
+#pragma unroll
+        for (int i = 0; i < TX; ++i) {
+            float s = (c < TX) ? f[ttri(TX + i, c)]
+                               : (c < 2 * TX) ? e[ttri(TX + (c - TX), i)] : e[ttri(10, i)] + f[ttri(10, TX + i)];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s -= L[ttri(i, q)] * Y[q][c];
+            Y[i][c] = s * L[ttri(i, i)];
+        }
+    // the element over (y = b, x = a, rhs): blockdiag(F_bb, E_aa) - Y^T Y
+    float g[kTElem];
+#pragma unroll
+    for (int i = 0; i < 11; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            if (i == 10 && j == 10) continue;
+            float s;
+            if (i < TX)
+                s = f[ttri(i, j)];                                   // (b, b)
+            else if (i < 2 * TX)
+                s = (j < TX) ? 0.f : e[ttri(i, j)];                  // (a, b) fill-in, (a, a)
+            else
+                s = (j < TX) ? f[ttri(10, j)] : e[ttri(10, j)];      // (rhs, b), (rhs, a)
+#pragma unroll
+            for (int p = 0; p < TX; ++p) s -= Y[p][i] * Y[p][j];
+            g[ttri(i, j)] = s;
+        }
+#pragma unroll
+    for (int t = 0; t < kTElem; ++t) e[t] = g[t];
+    if (store) {
+        float o[72];
+#pragma unroll
+        for (int t = 0; t < 15; ++t) o[t] = L[t];
+#pragma unroll
+        for (int i = 0; i < TX; ++i)
+#pragma unroll
+            for (int c = 0; c < 11; ++c) o[15 + 11 * i + c] = Y[i][c];
+        o[70] = o[71] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 18; ++q)
+            *trec(C, kTElemChunk0 + q, km) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    }
+    return pd;
+}
+
+// dx_m = -L^{-T} (Y_b dx_b + Y_a dx_a + y_r) from node m's stored (L, Y)
+__device__ __forceinline__ void tback_node(const TCtx& C, int km, const float xa[TX], const float xb[TX],
+                                           float xm[TX]) {
+    float v[72];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        const float4 t = *trec(C, kTElemChunk0 + q, km);
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+    const float* L = v;
+    const float* Y = v + 15;  // [5][11]
+    float t[TX];
 #pragma unroll
     for (int i = 0; i < TX; ++i) {
+        float s = Y[11 * i + 10];
 #pragma unroll
-        for (int j = 0; j < TX; ++j) Pm[i][j] = (i == j) ? 1.f : 0.f;
-        q[i] = 0.f;
+        for (int j = 0; j < TX; ++j) s += Y[11 * i + j] * xb[j] + Y[11 * i + TX + j] * xa[j];
+        t[i] = s;
     }
+#pragma unroll
+    for (int i = TX - 1; i >= 0; --i) {
+        float s = -t[i];
+#pragma unroll
+        for (int q = i + 1; q < TX; ++q) s -= L[ttri(q, i)] * xm[q];
+        xm[i] = s * L[ttri(i, i)];
+    }
+}
+
+__device__ bool tphase_b(TCtx& C, float beta, float rho) {
+    const int N = C.N, lane = C.lane;
+    TSmem& S = C.sm;
+    const int per = (N + 31) >> 5;
+    const int nl = (N + per - 1) / per;  // lanes that own stages
+    const int k0 = min(N, lane * per), k1 = min(N, k0 + per);
+    const bool own = lane < nl;
+    const int nlev = nl > 1 ? 32 - __clz(nl - 1) : 0;  // tree levels, ceil(log2 nl)
+    const int nsteps = (per - 1) + nlev;
+    bool pd = true;
+    float e[kTElem];
+#pragma unroll
+    for (int t = 0; t < kTElem; ++t) e[t] = 0.f;
+    if (own) {
+        pd = reinterpret_cast<const float*>(trec(C, R_PD / 4, k0))[R_PD % 4] > 0.f;
+        tload_elem(C, k0, e, beta, rho);
+    }
+    // folds of the lane's next stages, then the tree levels d = 1, 2, 4, ...:
+    // lane l (a multiple of 2d) eliminates the first node of lane l + d's span
 #pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        float G[TX][TX], g[TX];
-        tload_gain(C, k, G, g);
-        float P2[TX][TX], q2[TX];
-#pragma unroll
-        for (int i = 0; i < TX; ++i) {
-#pragma unroll
-            for (int j = 0; j < TX; ++j) {
-                float s = 0.f;
-#pragma unroll
-                for (int l = 0; l < TX; ++l) s += G[i][l] * Pm[l][j];
-                P2[i][j] = s;
+    for (int st = 0; st < nsteps; ++st) {
+        float f[kTElem];
+        bool act;
+        int km;
+        if (st < per - 1) {  // warp-uniform
+            km = k0 + 1 + st;
+            act = own && km < k1;
+            if (act) {
+                pd = pd && reinterpret_cast<const float*>(trec(C, R_PD / 4, km))[R_PD % 4] > 0.f;
+                tload_elem(C, km, f, beta, rho);
             }
-            float s = g[i];
+        } else {
+            const int d = 1 << (st - (per - 1));
 #pragma unroll
-            for (int l = 0; l < TX; ++l) s += G[i][l] * q[l];
-            q2[i] = s;
+            for (int t = 0; t < kTElem; ++t) f[t] = __shfl_down_sync(kFullT, e[t], d);
+            act = (lane & (2 * d - 1)) == 0 && lane + d < nl;
+            km = (lane + d) * per;
+        }
+        if (act) pd = tcombine(C, e, f, km, true) && pd;
+    }
+    // lane 0 solves the root element over (x_N, x_0): a 10 x 10 Cholesky
+    float xl[TX], xr[TX];
+#pragma unroll
+    for (int i = 0; i < TX; ++i) xl[i] = xr[i] = 0.f;
+    if (lane == 0) {
+        float A[55];
+#pragma unroll
+        for (int t = 0; t < 55; ++t) A[t] = e[t];
+#pragma unroll
+        for (int j = 0; j < 2 * TX; ++j) {
+            float dd = A[ttri(j, j)];
+#pragma unroll
+            for (int q = 0; q < j; ++q) dd -= A[ttri(j, q)] * A[ttri(j, q)];
+            pd = pd && dd > 0.f;
+            const float il = rsqrtf(fmaxf(dd, 1e-30f));
+            A[ttri(j, j)] = il;
+#pragma unroll
+            for (int i = j + 1; i < 2 * TX; ++i) {
+                float s = A[ttri(i, j)];
+#pragma unroll
+                for (int q = 0; q < j; ++q) s -= A[ttri(i, q)] * A[ttri(j, q)];
+                A[ttri(i, j)] = s * il;
+            }
+        }
+        float yv[2 * TX], x[2 * TX];
+#pragma unroll
+        for (int i = 0; i < 2 * TX; ++i) {
+            float s = e[ttri(10, i)];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s -= A[ttri(i, q)] * yv[q];
+            yv[i] = s * A[ttri(i, i)];
+        }
+#pragma unroll
+        for (int i = 2 * TX - 1; i >= 0; --i) {
+            float s = yv[i];
+#pragma unroll
+            for (int q = i + 1; q < 2 * TX; ++q) s -= A[ttri(q, i)] * x[q];
+            x[i] = s * A[ttri(i, i)];
         }
 #pragma unroll
         for (int i = 0; i < TX; ++i) {
-#pragma unroll
-            for (int j = 0; j < TX; ++j) Pm[i][j] = P2[i][j];
-            q[i] = q2[i];
+            xr[i] = -x[i];       // dx_N
+            xl[i] = -x[TX + i];  // dx_0
         }
     }
-    float x[TX];
-#pragma unroll
-    for (int i = 0; i < TX; ++i) x[i] = dx0[i];
+    // back-substitution: the tree levels top-down (lane l hands lane l + d
+    // the node it eliminated and its own right end), then each lane's span
+    // right to left
+    float xc[TX];  // dx of the node right of the current interior node
 #pragma unroll 1
-    for (int l = 0; l + 1 < nl; ++l) {
+    for (int st = nsteps - 1; st >= 0; --st) {
+        const bool tree = st >= per - 1;  // warp-uniform
+        const int d = tree ? 1 << (st - (per - 1)) : 0;
+        if (st == per - 2)
 #pragma unroll
-        for (int i = 0; i < TX; ++i) {
-            float xo = q[i];
+            for (int i = 0; i < TX; ++i) xc[i] = xr[i];
+        const bool act = tree ? ((lane & (2 * d - 1)) == 0 && lane + d < nl) : (own && k0 + 1 + st < k1);
+        const int km = tree ? (lane + d) * per : k0 + 1 + st;
+        float xm[TX];
 #pragma unroll
-            for (int j = 0; j < TX; ++j) xo += Pm[i][j] * x[j];
-            const float t = __shfl_sync(kFullT, xo, l);
-            if (lane == l + 1) x[i] = t;
+        for (int i = 0; i < TX; ++i) xm[i] = 0.f;
+        if (act) tback_node(C, km, xl, tree ? xr : xc, xm);
+        if (tree) {
+#pragma unroll
+            for (int i = 0; i < TX; ++i) {
+                const float pm = __shfl_up_sync(kFullT, xm[i], d), pr = __shfl_up_sync(kFullT, xr[i], d);
+                if ((lane & (2 * d - 1)) == d && lane < nl) {
+                    xl[i] = pm;
+                    xr[i] = pr;
+                }
+                if (act) xr[i] = xm[i];
+            }
+        } else if (act) {
+#pragma unroll
+            for (int i = 0; i < TX; ++i) {
+                S.dz[TW * km + i] = xm[i];
+                xc[i] = xm[i];
+            }
         }
     }
-#pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        float G[TX][TX], g[TX];
-        tload_gain(C, k, G, g);
-        float w[TX];
+    if (own) {
 #pragma unroll
-        for (int i = 0; i < TX; ++i) {
-            float s = g[i];
+        for (int i = 0; i < TX; ++i) S.dz[TW * k0 + i] = xl[i];
+        if (lane == nl - 1)
 #pragma unroll
-            for (int j = 0; j < TX; ++j) s += G[i][j] * x[j];
-            w[i] = s;
-        }
-#pragma unroll
-        for (int i = 0; i < TX; ++i) {
-            S.dz[TW * (k + 1) + i] = w[i];
-            x[i] = w[i];
-        }
+            for (int i = 0; i < TX; ++i) S.dz[TW * N + i] = xr[i];
     }
     __syncwarp();
+    return __all_sync(kFullT, pd);
+}
+
+// Phase C: the control steps, stage-parallel from the u-block factors of
+// phase A and the state steps of phase B,
+//   du_k = -L_u^{-T} (coupling^T [dx_{k+1}; dx_k; 1]).
+// Returns D = grad . dz.
+__device__ float tphase_c(TCtx& C) {
+    const int N = C.N, lane = C.lane;
+    TSmem& S = C.sm;
 #pragma unroll 1
     for (int k = lane; k < N; k += 32) {
         float f[56];
@@ -1323,7 +1323,6 @@ __global__ void __launch_bounds__(128, 3) timing_kernel(const TimingArgs A) {
             int trip = kMeasure, retries = 0;
             bool model_curv = curv, fac = false, done = false;
             float beta_old = beta;
-            float dx0[TX];
             for (;;) {
                 const TMeasures m = tphase_a(C, beta, rho, model_curv, trip == kUpdate, beta_old);
                 if (trip == kMeasure) {
@@ -1353,7 +1352,7 @@ __global__ void __launch_bounds__(128, 3) timing_kernel(const TimingArgs A) {
                         continue;
                     }
                 }
-                fac = tphase_b(C, beta, rho, dx0);
+                fac = tphase_b(C, beta, rho);
                 if (fac) break;
                 if (model_curv) {
                     curv_hold = sp.curv_skip;
@@ -1368,8 +1367,7 @@ __global__ void __launch_bounds__(128, 3) timing_kernel(const TimingArgs A) {
             if (done) break;
             ++inner;
             if (!fac) continue;
-            tphase_gains(C);
-            const float D = tphase_c(C, dx0);
+            const float D = tphase_c(C);
             const float alpha = tphase_d(C, beta, D, sp);
             if (alpha > 0.f) {
                 tphase_e(C, alpha);
