@@ -24,12 +24,19 @@ def instance(i: int) -> dict:
 
 
 def solve(job):
-    """job = (inst_index, modes, timing, max_iters, warm or None, extra opts)."""
+    """job = (inst_index, modes, timing, max_iters, warm or None, extra opts);
+    an inst_index of the form ("l4", seed) names a push_l4 instance (N = 20
+    knots per segment) instead."""
     i, modes, timing, max_iters, warm, extra = job
     opts = dict(extra or {})
     if max_iters is not None:
         opts["max_iters"] = max_iters
-    z, lam, r = TM.solve(instance(i), tuple(modes), N, timing=timing, warm=warm, **opts)
+    if isinstance(i, tuple):
+        inst = W.push_l4_instance(i[1])
+        n = int(inst["knots_per_segment"]) * len(modes)
+    else:
+        inst, n = instance(i), N
+    z, lam, r = TM.solve(inst, tuple(modes), n, timing=timing, warm=warm, **opts)
     return z, lam, r
 
 
@@ -53,14 +60,16 @@ def run(jobs, workers=None):
                 os.environ[k] = v
 
 
-def to_interleaved(tr: np.ndarray, Nmax: int = N) -> np.ndarray:
+def to_interleaved(tr: np.ndarray, Nmax: int = N, n: int | None = None) -> np.ndarray:
     """GPU record (x, y, theta, s, tau [Nmax+1]; f_n, f_t, sdot, h [Nmax])
-    -> the oracle's interleaved z of an N-interval TO."""
+    -> the oracle's interleaved z of an n-interval TO (n = Nmax unless
+    given)."""
+    n = Nmax if n is None else n
     x = tr[: 5 * (Nmax + 1)].reshape(5, Nmax + 1)
     u = tr[5 * (Nmax + 1): 5 * (Nmax + 1) + 4 * Nmax].reshape(4, Nmax)
-    z = np.zeros(9 * N + 5)
-    for k in range(N + 1):
+    z = np.zeros(9 * n + 5)
+    for k in range(n + 1):
         z[9 * k: 9 * k + 5] = x[:, k]
-    for k in range(N):
+    for k in range(n):
         z[9 * k + 5: 9 * k + 9] = u[:, k]
     return z
