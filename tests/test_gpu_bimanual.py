@@ -264,3 +264,36 @@ def test_long_orders_convergence_matches_oracle(P):
     assert len(remaining) <= max(3, 2 * len(seqs) // 100), remaining
     _bim_asserts(rep, flags, len(seqs), "bimanual 1-6 segments")
     assert not PA.certify_different(T, insts, idx, seqs, lens, 15 * lens, g, rep)
+
+
+def test_full_size_launch_sampled(P):
+    # the bench's bimanual launch as timed: 512 random orders of 1..6
+    # segments on each of 8 instances (4,096 TOs, N up to 90) in one launch;
+    # 64 seeded samples of its outputs against the oracle's solves of the
+    # same orders, on the bar of the tests above
+    insts = [W.bimanual_instance(s) for s in range(8)]
+    rng = np.random.default_rng(11)
+    seqs, idx = [], []
+    for i in range(8):
+        for _ in range(512):
+            L = int(rng.integers(1, 7))
+            seqs.append(tuple(int(m) for m in rng.integers(0, 507, L)))
+            idx.append(i)
+    n = len(seqs)
+    idx = np.array(idx, np.int32)
+    g = _ev(P, insts, seqs, idx)
+    conv = (g["status"] == 0) & (g["viol"] <= 1e-5)
+    print(f"full launch: {int(conv.sum())} of {n} converged ({conv.mean():.3f})")
+    picks = np.sort(np.random.default_rng(5).choice(n, 64, replace=False))
+    ss = [seqs[t] for t in picks]
+    si = idx[picks]
+    sl = np.array([len(q) for q in ss], np.int32)
+    gs = {k: (v[picks] if isinstance(v, np.ndarray) and v.shape[:1] == (n,) else v) for k, v in g.items()}
+    gs["traj_nmax"] = 90
+    ref, rtr, _ = oracle.bim_solve_batch_ex(insts, si, ss, sl, opts=_opts())
+    T = PA.Task(True)
+    rep = PA.compare(T, insts, si, ss, sl, 15 * sl, gs, ref, rtr)
+    flags = PA.flag_disagreements(gs, ref)
+    remaining = PA.flags_after_refinement(flags, gs, ref, *_bim_reruns(P, insts, ss, si, sl))
+    _bim_asserts(rep, flags, len(ss), "bimanual full launch, sampled", remaining)
+    assert not PA.certify_different(T, insts, si, ss, sl, 15 * sl, gs, rep)
