@@ -184,7 +184,7 @@ def compare(task, insts, idx, seqs, lens, Ns, gpu, ref, ref_tr, sel=None, verbos
     for j, t in enumerate(joint):
         N = int(Ns[t])
         inst = insts[idx[t]]
-        m = seqs[t]
+        m = tuple(seqs[t])[: int(lens[t])]  # the order at its own length (seqs may be padded)
         a, b, c = zg[j, : task.traj_len(N)], zo[j, : task.traj_len(N)], po[j, : task.traj_len(N)]
         pgj = pg[j, : task.traj_len(N)]
         # every converged GPU answer is feasible by the oracle's own rows
@@ -248,8 +248,8 @@ def certify_different(task, insts, idx, seqs, lens, Ns, gpu, rep):
         t = d["t"]
         N = int(Ns[t])
         a = task.gpu_to_oracle(gpu["traj"][t], N, gpu["traj_nmax"])
-        m = seqs[t]
-        mm = np.asarray([m], np.uint8) if not task.bim else [m]
+        m = tuple(seqs[t])[: int(lens[t])]
+        mm = np.asarray([seqs[t]], np.uint8) if not task.bim else [m]
         r, p, lam = polish(task, insts, idx[t: t + 1], mm, lens[t: t + 1], a[None, :])
         if r["status"][0] != 0:
             bad.append((t, "polish not converged"))

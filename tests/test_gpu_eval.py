@@ -276,6 +276,68 @@ def test_mixed_lengths_and_instances_one_launch(P):
     assert np.all(g["iters"] <= 300)
 
 
+def test_mixed_workload_full_launch_sampled(P):
+    # the bench's mixed workload as timed: 256 rectangular sliders (length
+    # caps 1..6, 10..30 knots per segment, N up to 180) with 512 random
+    # orders each, 131,072 TOs in one launch at the autotuned shape; 64
+    # seeded samples of its outputs against the oracle.  Trajectories of the
+    # sample come from a second launch of those orders alone, which must give
+    # the same outputs bit for bit (each TO's arithmetic does not depend on
+    # its launch)
+    insts = [W.push_mixed_instance(s) for s in range(256)]
+    rng = np.random.default_rng(7)
+    seqs, idx = [], []
+    for i, inst in enumerate(insts):
+        for _ in range(512):
+            L = int(rng.integers(1, inst["max_segments"] + 1))
+            seqs.append(tuple(int(m) for m in rng.integers(0, 12, L)))
+            idx.append(i)
+    n = len(seqs)
+    idx = np.array(idx, np.int32)
+    prob = P.Problem(insts)
+    d = torch.from_numpy(P.pack_mode_seqs(seqs, idx).view(np.uint8).reshape(n, P.MODE_SEQ_BYTES)).cuda()
+    P.comet_autotune(prob.handle, d[:8192], 8192, 40)
+    r = prob.eval(d)
+    torch.cuda.synchronize()
+    full = {k: v.cpu().numpy() for k, v in r.items()}
+    prob.close()
+    conv = (full["status"] == 0) & (full["viol"] <= 1e-5)
+    print(f"mixed workload, one launch: {int(conv.sum())} of {n} converged ({conv.mean():.3f})")
+    picks = np.sort(np.random.default_rng(5).choice(n, 64, replace=False))
+    ss = [seqs[t] for t in picks]
+    si = idx[picks]
+    g = gpu_eval(P, insts, ss, si, want_traj=True)
+    g["traj_nmax"] = _nmax(g)
+    for k in ("status", "cost", "viol", "iters"):
+        np.testing.assert_array_equal(g[k], full[k][picks])
+    modes, lens = W.pad_sequences(ss, 6)
+    Ns = np.array([int(insts[i]["knots_per_segment"]) * int(L) for i, L in zip(si, lens)])
+    ref, rtr, _ = oracle.solve_batch_ex(insts, si, modes, lens, nthreads=os.cpu_count())
+    T = PA.Task(False)
+    rep = PA.compare(T, insts, si, list(modes), lens, Ns, g, ref, rtr)
+    flags = PA.flag_disagreements(g, ref)
+    # re-runs of the lagging side with each order at its own length (the
+    # padded mode array is the oracle's layout)
+    _, rerun_oracle = _reruns(P, insts, modes, si, lens)
+
+    def rerun_gpu(ts):
+        r2 = gpu_eval(P, insts, [ss[t] for t in ts], si[ts], max_iters=1500)
+        return r2["status"], r2["viol"]
+
+    remaining = PA.flags_after_refinement(flags, g, ref, rerun_gpu, rerun_oracle)
+    # on these sliders (aspect up to 3, mu up to 0.6, c down to 0.015 m) the
+    # FP64 oracle itself often stops at stationary points that are not local
+    # minima (its polish descends far), where no exact local solution is
+    # attached to compare the GPU with: those are listed, and the GPU is held
+    # to the bar wherever the oracle's answer is a local solution
+    oracle_nonlocal = [u for u in rep["unresolved"] if not u["oracle_local"]]
+    print(f"oracle stops at non-minimum stationary points: "
+          f"{[(u['t'], u['modes'], u['gpu_local']) for u in oracle_nonlocal]}")
+    rep_gpu = dict(rep, unresolved=[u for u in rep["unresolved"] if u["oracle_local"]])
+    _parity_asserts(rep_gpu, flags, len(ss), "mixed workload, sampled", remaining)
+    assert not PA.certify_different(T, insts, si, list(modes), lens, Ns, g, rep)
+
+
 def test_warm_start_at_oracle_solution(P):
     inst = W.push_l2_instance(4)
     seqs = W.all_sequences(12, 2)[::13]
