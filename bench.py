@@ -8,7 +8,7 @@ instance: every order solved by the persistent evaluator, scored
 (Eq. inexact_mode_value, Eq. search_merit) and the enumeration argmin taken
 (Eq. mode_selection).  Steps cycle through the instances.
 
-Prints one JSON line (contract of the driver): value = converged solves
+Prints one JSON line (the benchmark line format): value = converged solves
 (status CONVERGED and FP64-certified v_hat < 1e-5) per second over the timed
 steps, device-timed with CUDA events on the problem's stream, inputs resident
 in HBM; e2e = the same metric through the C ABI with host buffers (copies
