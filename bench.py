@@ -347,7 +347,7 @@ def run_gpu(args):
                                       oracle_n=None if args.no_cpu_baseline else 2 * (os.cpu_count() or 1),
                                       l4_orders=args.orders)
     if rank == 0 and args.learned_instances > 0:
-        line["learned"] = learned_times(P, insts, args.learned_instances)
+        line["learned"] = learned_times(P, insts, args.learned_instances, oracle_on=not args.no_cpu_baseline)
     if rank == 0 and args.mcts:
         try:
             line["mcts"] = mcts_times(P)
@@ -891,7 +891,7 @@ def measured_peak(key, fallback):
 MLP_MACS = 64 * 256 + 2 * 256 * 256 + 256 * 256
 
 
-def learned_times(P, insts, n_eval):
+def learned_times(P, insts, n_eval, oracle_on=True):
     """The learned proposal on the same workload family: a training set of
     about 1M evaluator results (512 random 4-segment instances, seeds
     1000..1511, 2,048 random orders each, solved by the GPU evaluator), 3,000
@@ -933,6 +933,23 @@ def learned_times(P, insts, n_eval):
     P.comet_proposal_features(q, torch.from_numpy(packed[:rows].view(np.uint8).reshape(-1, P.MODE_SEQ_BYTES)).cuda(), rows, x)
     # device time of the fused forward kernel, events on its own stream
     fwd_s = P.comet_proposal_time_forward(q, x, rows, 50) / 1e3
+    din, width, dout, _ = P.comet_proposal_dims(q)
+    oracle_fwd = None
+    if oracle_on:
+        # the FP64 oracle's forward on the host over the same features
+        # (numpy, its BLAS on the host cores), repeated for about a second
+        from oracle import mlp as OM
+
+        bits = x.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+        X = bits.view(np.float32).astype(np.float64)
+        params = OM.unflatten(flat.astype(np.float64), din, width, dout)
+        nr, done, t0 = 4096, 0, time.time()
+        while time.time() - t0 < 1.0:
+            OM.forward(params, X[:nr])
+            done += nr
+        dt_o = time.time() - t0
+        oracle_fwd = {"rows_per_s": done / dt_o, "cores": os.cpu_count() or 1, "kind": "oracle",
+                      "sample": f"{done} rows of the enumeration's features in {dt_o:.1f} s, numpy FP64 forward"}
     P.comet_proposal_destroy(q)
     prob.close()
     peak, kind = measured_peak("bf16_tflops", 1900.0)
@@ -962,7 +979,8 @@ def learned_times(P, insts, n_eval):
         "dataset_samples": n_inst * per, "dataset_s": t_data, "train_steps": steps, "train_batch": 4096,
         "train_s": t_train, "train_samples_per_s": steps * 4096 / t_train,
         "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-100:].mean()),
-        "forward_rows": rows, "forward_ms": fwd_s * 1e3,
+        "forward_rows": rows, "forward_ms": fwd_s * 1e3, "forward_rows_per_s": rows / fwd_s,
+        "oracle_forward": oracle_fwd,
         "roofline": {"kernel": "mlp_fused_forward_kernel (4 tcgen05 layers chained through TMEM)", "bound": "tensor",
                      "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tflops / peak,
                      "peak_kind": f"{kind} bf16 (burst)", "train_step_tflops": train_tflops},
