@@ -24,6 +24,7 @@
 //   E  compensated state update
 
 #include <cuda_runtime.h>
+#include <cuda/annotated_ptr>
 #include <math.h>
 #include <stdint.h>
 
@@ -652,7 +653,9 @@ __device__ BMeasures bphase_a(BCtx& C, float beta, float rho, bool assemble, boo
             }
             // records from the rows: the u factor (rows 0..11), the coupling
             // rows (12..22) x u columns, the reduced (y, x, rhs) block
-            float* rec = C.rec + (size_t)k * kBimRec;
+            // record stores with the persisting (evict-last) L2 priority: the
+            // CTAs' workspaces fit in L2 and are rewritten every iteration
+            cuda::annotated_ptr<float, cuda::access_property::persisting> rec(C.rec + (size_t)k * kBimRec);
             if (lane < 12) {
 #pragma unroll
                 for (int cc = 0; cc < 12; ++cc)
@@ -820,7 +823,8 @@ __device__ bool bphase_b(BCtx& C, float beta, float rho) {
 #pragma unroll
                     for (int j = 0; j < 5; ++j) o[15 + 5 * c + j] = m[tri(5 + c, j)];
                 o[45] = o[46] = o[47] = 0.f;
-                float4* r4 = reinterpret_cast<float4*>(C.rec + (size_t)k * kBimRec + R_YF);
+                cuda::annotated_ptr<float4, cuda::access_property::persisting> r4(
+                    reinterpret_cast<float4*>(C.rec + (size_t)k * kBimRec + R_YF));
 #pragma unroll
                 for (int q = 0; q < 12; ++q) r4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
             }
@@ -931,7 +935,7 @@ __device__ void bphase_gains(BCtx& C) {
             }
         }
         o[30] = o[31] = 0.f;
-        float4* w4 = reinterpret_cast<float4*>(rec + R_YF);
+        cuda::annotated_ptr<float4, cuda::access_property::persisting> w4(reinterpret_cast<float4*>(rec + R_YF));
 #pragma unroll
         for (int q = 0; q < 8; ++q) w4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
     }

@@ -29,6 +29,7 @@
 //   E  compensated update.
 
 #include <cuda_runtime.h>
+#include <cuda/annotated_ptr>
 #include <math.h>
 #include <stdint.h>
 
@@ -305,6 +306,14 @@ __device__ __forceinline__ float4* trec(const TCtx& C, int q, int k) {
     return reinterpret_cast<float4*>(C.rec + 4 * ((size_t)q * C.Nmax + k));
 }
 
+// record stores with the persisting (evict-last) L2 priority: the resident
+// warps' records fit in L2 and are rewritten every iteration (as in
+// eval_kernel.cu)
+__device__ __forceinline__ void trec_st(const TCtx& C, int q, int k, float4 v) {
+    cuda::annotated_ptr<float4, cuda::access_property::persisting> p(trec(C, q, k));
+    *p = v;
+}
+
 // states of interval k from the compensated storage, the low parts moved by
 // alpha dz (alpha = 0: the iterate; dz is not read then, since it may hold
 // the gradient's parked pieces or nothing yet)
@@ -535,7 +544,7 @@ __device__ TMeasures tphase_a(TCtx& C, float beta, float rho, bool curvature, bo
                 if (!(i == TM - TU - 1 && j == i)) rec[R_RED + ttri(i, j)] = A[ttri(TU + i, TU + j)];
 #pragma unroll
         for (int q = 0; q < kTRec / 4; ++q)
-            *trec(C, q, k) = make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
+            trec_st(C, q, k, make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]));
     }
     __syncwarp();
     // initial rows (pose and tau_0 = 0) and the terminal row tau_N <= T
@@ -739,7 +748,7 @@ __device__ __forceinline__ bool tcombine(const TCtx& C, float e[kTElem], const f
         o[70] = o[71] = 0.f;
 #pragma unroll
         for (int q = 0; q < 18; ++q)
-            *trec(C, kTElemChunk0 + q, km) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            trec_st(C, kTElemChunk0 + q, km, make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
     }
     return pd;
 }
