@@ -56,7 +56,7 @@ TIMING_FLOP_PER_STAGE_ITER = {"slack": 3362.3, "binding": 3555.3}
 # from the ncu capture of the current kernel on the 4,096-order case (8.42 MB
 # read, 1.033 GB written: spills and stage records written back from L2;
 # profiles/eval_kernel_push_l4.md), scaled by the TOs processed
-EVAL_TRAFFIC_BYTES = (9.974016e6 + 1.099579e9) * 20736 / 4096
+EVAL_TRAFFIC_BYTES = (9.287168e6 + 37.679872e6) * 20736 / 4096
 # nominal FP32 FMA rate at the maximum clock (152 SMs x 128 lanes x 2 flop x
 # 2070 MHz), context only: the roofline's peak is measured at run time by the
 # library's FMA microbenchmark (comet_fp32_fma_peak)
