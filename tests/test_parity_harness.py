@@ -60,3 +60,34 @@ def test_planted_errors_are_caught():
     rep = PA.compare(T, insts, idx, list(allseq), lens, Ns, other, ref, rtr, sel=np.array(same), verbose=False)
     assert {e[0] for e in rep["cost_excess"]} >= set(a)
     assert {e[0] for e in rep["state_excess"]} >= set(b)
+
+
+def test_padded_orders_of_mixed_lengths():
+    # orders of 1..4 segments passed as a zero-padded mode array with their
+    # lengths: every order is compared at its own length (a padded order read
+    # whole would be another order, with other rows and v_hat)
+    insts = [W.push_l4_instance(s) for s in (0, 1)]
+    rng = np.random.default_rng(4)
+    seqs = [tuple(int(m) for m in rng.integers(0, 12, 1 + t % 4)) for t in range(24)]
+    idx = (np.arange(24) % 2).astype(np.int32)
+    modes, lens = W.pad_sequences(seqs, 4)
+    Ns = 20 * lens
+    ref, rtr, _ = oracle.solve_batch_ex(insts, idx, modes, lens, nthreads=os.cpu_count())
+    g, gtr, _ = oracle.solve_batch_ex(insts, idx, modes, lens, opts=oracle.default_opts(beta0=300.0),
+                                      nthreads=os.cpu_count())
+    # the answers in the GPU's layout, padded to the longest order (N = 80)
+    Nm = int(Ns.max())
+    tr = np.zeros((24, 7 * Nm + 4))
+    for t in range(24):
+        N = int(Ns[t])
+        for i in range(4):
+            tr[t, i * (Nm + 1): i * (Nm + 1) + N + 1] = gtr[t][i * (N + 1): (i + 1) * (N + 1)]
+        for j in range(3):
+            tr[t, 4 * (Nm + 1) + j * Nm: 4 * (Nm + 1) + j * Nm + N] = gtr[t][4 * (N + 1) + j * N: 4 * (N + 1) + (j + 1) * N]
+    other = dict(status=g["status"], cost=g["cost"], viol=g["viol"], traj=tr, traj_nmax=Nm)
+    T = PA.Task(False)
+    rep = PA.compare(T, insts, idx, list(modes), lens, Ns, other, ref, rtr, verbose=False)
+    assert rep["joint"] >= 12
+    assert not rep["vhat_fail"], rep["vhat_fail"]
+    assert not rep["cost_excess"], rep["cost_excess"]
+    assert not PA.certify_different(T, insts, idx, list(modes), lens, Ns, other, rep)
