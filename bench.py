@@ -305,6 +305,7 @@ def run_gpu(args):
     flops = FLOP_PER_STAGE_ITER * N_STAGES * iter_total
     achieved = flops / t_dev / 1e12
     peak = measure_fp32_peak(P, stream)
+    hbm_peak, hbm_kind = measured_peak("hbm_gbs", 6800.0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -321,6 +322,10 @@ def run_gpu(args):
         "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
                      "frac": achieved / peak["tflops"], "traffic": EVAL_TRAFFIC_BYTES,
+                     "hbm": {"achieved_gbs": EVAL_TRAFFIC_BYTES * args.steps / t_dev / 1e9, "peak_gbs": hbm_peak,
+                             "frac": EVAL_TRAFFIC_BYTES * args.steps / t_dev / 1e9 / hbm_peak,
+                             "peak_kind": f"of {hbm_kind} (STREAM-style copy; 6.8 TB/s when no measured figure is present)",
+                             "note": "the captured DRAM traffic per launch x launches / device time"},
                      "peak_measured": peak, "nominal_tflops": FP32_NOMINAL_TFLOPS,
                      "note": f"achieved = {FLOP_PER_STAGE_ITER} flop (the oracle's count of the method per "
                              "stage and iteration) x 80 stages x solver iterations / device time; peak = "
