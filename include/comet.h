@@ -183,6 +183,25 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* mod
 comet_status comet_eval_stats(comet_problem* p, float* out_viol, float* out_merit,
                               int32_t* out_iters, float* out_stat);
 
+/* Failure report of the last evaluator launch on this problem (an addition
+ * of this library, for callers that pass device arrays, where
+ * comet_eval_modes returns before the launch ends).  Synchronises the
+ * problem's stream and reads the launch's device flag into *out_flag
+ * (nullable): 0 = nothing to report; 1 = a malformed order was met (its TO
+ * carries COMET_TO_NONFINITE); 2 = a bounded device wait gave up (the
+ * warm-start staging copy did not complete within about a second; the TO
+ * carries COMET_TO_NONFINITE and NaN cost), in which case the call returns
+ * COMET_ERR_TIMEOUT.  Device waits never hang: each gives up after its
+ * bound and leaves the context usable.  comet_eval_modes with host arrays
+ * makes the same check itself and returns COMET_ERR_TIMEOUT. */
+comet_status comet_eval_check(comet_problem* p, int32_t* out_flag);
+
+/* Test hook: with on != 0, the evaluator's launches on this problem do not
+ * issue the warm-start staging copy, so the bounded wait for it runs out
+ * (failure detection is tested on a wait that nothing completes; no copy is
+ * left in flight).  Off by default; no production path sets it. */
+comet_status comet_debug_stall_staging(comet_problem* p, int32_t on);
+
 /* Solve one mode-conditioned TO per order without allocating any memory.
  * (An addition of this library; the paper has no counterpart.)
  *

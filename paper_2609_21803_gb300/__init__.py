@@ -124,7 +124,8 @@ assert MODE_SEQ_DTYPE.itemsize == ctypes.sizeof(ModeSeq) == MODE_SEQ_BYTES
 # exported symbols of include/comet.h
 EXPORTS = (
     "comet_default_opts", "comet_problem_create", "comet_problem_destroy", "comet_traj_stride",
-    "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_mode_code",
+    "comet_eval_modes", "comet_eval_modes_budget", "comet_eval_stats", "comet_eval_check",
+    "comet_debug_stall_staging", "comet_mode_code",
     "comet_eval_modes_timed",
     "comet_last_error", "comet_eval_modes_noalloc", "comet_fp32_fma_peak", "comet_fp32_fma_peak_threads",
     "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
@@ -169,6 +170,8 @@ def lib(build_if_missing: bool = False):
             L.comet_eval_modes.argtypes = [vp, vp, i64, vp, vp, vp, vp]
             L.comet_eval_modes_budget.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp]
             L.comet_eval_stats.argtypes = [vp, vp, vp, vp, vp]
+            L.comet_eval_check.argtypes = [vp, vp]
+            L.comet_debug_stall_staging.argtypes = [vp, i32]
             L.comet_eval_modes_timed.argtypes = [vp, ctypes.POINTER(TimingOpts), vp, i64, vp, i32, vp, vp, vp]
             L.comet_fp32_fma_peak.argtypes = [vp, i32, vp, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double)]
@@ -323,6 +326,20 @@ def comet_eval_modes_budget(problem, mode_seqs, n, warm_starts, max_iters, out_c
 
 def comet_eval_stats(problem, out_viol, out_merit, out_iters, out_stat):
     _check(lib().comet_eval_stats(problem, _ptr(out_viol), _ptr(out_merit), _ptr(out_iters), _ptr(out_stat)))
+
+
+def comet_eval_check(problem) -> int:
+    """The last evaluator launch's device flag (0 nothing, 1 malformed order,
+    2 a bounded wait gave up); raises CometError (COMET_ERR_TIMEOUT) on 2."""
+    flag = ctypes.c_int32(0)
+    st = lib().comet_eval_check(problem, ctypes.byref(flag))
+    if st != 0:
+        _check(st)
+    return int(flag.value)
+
+
+def comet_debug_stall_staging(problem, on: bool):
+    _check(lib().comet_debug_stall_staging(problem, int(bool(on))))
 
 
 def comet_eval_modes_timed(problem, timing: dict, mode_seqs, n, warm_starts, max_iters, out_cost, out_traj,

@@ -326,6 +326,7 @@ comet_status launch_eval_device(comet_problem* p, const comet_mode_seq* d_seqs, 
     a.queue = p->d_queue;
     a.bad_input = p->d_bad;
     a.unroll = p->unroll;
+    a.stall_staging = p->stall_staging;
     a.sp = make_params(p->opts, max_iters);
     for (const comet_instance_desc& d : p->inst) a.sp.free_motion |= d.task == COMET_TASK_PUSHER_SLIDER && d.n_modes == 13;
     if (p->task == COMET_TASK_BIMANUAL)
@@ -558,8 +559,29 @@ comet_status comet_eval_modes_budget(comet_problem* p, const comet_mode_seq* seq
     if (!dev_status)
         CUDA_TRY(cudaMemcpyAsync(out_status, d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s), "copy status");
     if (!dev_traj) CUDA_TRY(cudaMemcpyAsync(out_traj, d_traj, traj_bytes, cudaMemcpyDeviceToHost, s), "copy traj");
-    if (!(dev_seqs && dev_warm && dev_cost && dev_status && dev_traj))
+    if (!(dev_seqs && dev_warm && dev_cost && dev_status && dev_traj)) {
         CUDA_TRY(cudaStreamSynchronize(s), "synchronise");
+        int flag = 0;
+        CUDA_TRY(cudaMemcpy(&flag, p->d_bad, sizeof(int), cudaMemcpyDeviceToHost), "read the device flag");
+        if (flag == 2) return fail(COMET_ERR_TIMEOUT, "a bounded device wait ran out (warm-start staging)");
+    }
+    return COMET_OK;
+}
+
+comet_status comet_eval_check(comet_problem* p, int32_t* out_flag) {
+    if (!p) return fail(COMET_ERR_INVALID_ARG, "problem is NULL");
+    CUDA_TRY(cudaSetDevice(p->device), "cudaSetDevice");
+    CUDA_TRY(cudaStreamSynchronize(p->stream), "synchronise");
+    int flag = 0;
+    CUDA_TRY(cudaMemcpy(&flag, p->d_bad, sizeof(int), cudaMemcpyDeviceToHost), "read the device flag");
+    if (out_flag) *out_flag = flag;
+    if (flag == 2) return fail(COMET_ERR_TIMEOUT, "a bounded device wait ran out (warm-start staging)");
+    return COMET_OK;
+}
+
+comet_status comet_debug_stall_staging(comet_problem* p, int32_t on) {
+    if (!p) return fail(COMET_ERR_INVALID_ARG, "problem is NULL");
+    p->stall_staging = on ? 1 : 0;
     return COMET_OK;
 }
 

@@ -74,6 +74,8 @@ struct EvalArgs {
     unsigned int* queue;     // work counter (next TO index)
     int* bad_input;          // set when a malformed order is met
     int unroll;              // stages per trip of the stage loops (1 or 2)
+    int stall_staging;       // test hook: warm-start staging copies are not issued, so
+                             // the bounded wait on them runs out (never in a release call)
     SolverParams sp;
 };
 

@@ -1468,7 +1468,7 @@ __global__ void __launch_bounds__(128, 3) eval_kernel(EvalArgs A) {
                          ((src & 15) >> 2);
             const int h_end = bulk ? (int)((a0 - src) >> 2) : nrec, t_begin = bulk ? (int)((a1 - src) >> 2) : nrec;
             __syncwarp();
-            if (bulk && lane == 0)
+            if (bulk && lane == 0 && !A.stall_staging)
                 ek_bulk_copy(ek_smem_u32(stg) + (uint32_t)(a0 - src), reinterpret_cast<const void*>(a0),
                              (uint32_t)(a1 - a0), wbar);
             for (int j = lane; j < h_end; j += 32) stg[j] = warm[j];

@@ -23,6 +23,7 @@ struct comet_problem {
     int warps_per_block = 4;
     int blocks_per_sm = 0;
     int unroll = 1;  // stages per trip of the evaluator's stage loops
+    int stall_staging = 0;  // test hook of comet_debug_stall_staging
     float* d_ws = nullptr;
     int64_t ws_warps = 0;
     // per-warp workspace of the timing-optimisation kernel

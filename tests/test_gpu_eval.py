@@ -338,6 +338,37 @@ def test_mixed_workload_full_launch_sampled(P):
     assert not PA.certify_different(T, insts, si, list(modes), lens, Ns, g, rep)
 
 
+def test_bounded_wait_gives_up_and_reports_timeout(P):
+    # failure detection without a fault: with the test hook on, the
+    # warm-start staging copy is not issued, so the bounded wait on its
+    # barrier runs out (nothing completes it, no copy is in flight); the TO
+    # is flagged, the launch reports COMET_ERR_TIMEOUT, and the context stays
+    # usable: the same problem then solves the same order from the same
+    # warm start
+    import time
+
+    prob = P.Problem([W.push_l2_instance(0)])
+    d = torch.from_numpy(P.pack_mode_seqs([(0, 3)]).view(np.uint8).reshape(1, P.MODE_SEQ_BYTES)).cuda()
+    base = prob.eval(d, want_traj=True)
+    warm = base["traj"].clone()
+    assert P.comet_eval_check(prob.handle) == 0
+    P.comet_debug_stall_staging(prob.handle, True)
+    t0 = time.time()
+    r = prob.eval(d, warm=warm)
+    with pytest.raises(P.CometError, match="status 4"):
+        P.comet_eval_check(prob.handle)
+    dt = time.time() - t0
+    print(f"the stalled launch ended after {dt:.1f} s")
+    assert int(r["status"][0]) == P.TO_NONFINITE and np.isnan(float(r["cost"][0]))
+    assert dt < 20.0
+    P.comet_debug_stall_staging(prob.handle, False)
+    r2 = prob.eval(d, warm=warm)
+    assert P.comet_eval_check(prob.handle) == 0
+    assert int(r2["status"][0]) == P.TO_CONVERGED
+    assert float(r2["cost"][0]) == pytest.approx(float(base["cost"][0]), rel=1e-4)
+    prob.close()
+
+
 def test_warm_start_at_oracle_solution(P):
     inst = W.push_l2_instance(4)
     seqs = W.all_sequences(12, 2)[::13]
