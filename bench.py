@@ -316,7 +316,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * P.MODE_SEQ_BYTES),
-                "d2h_bytes_per_step": int(n * (4 + 4 + 4))},
+                "d2h_bytes_per_step": int(n * (4 + 4 + 4) + 4)},  # cost, status, v_hat; the device flag
         # per step: the longest-first ordering (hist, scan, scatter kernels;
         # the problem holds orders of up to 4 segments) and the evaluator
         "gpu_launches": 4 * args.steps,
