@@ -97,6 +97,18 @@ comet_status comet_proposal_set_params(comet_proposal* q, const float* flat);
  * step into host or device buffers of n_params floats.  Synchronous. */
 comet_status comet_proposal_get_params(comet_proposal* q, float* flat, float* grad);
 
+/* Checkpoint and resume (an addition of this library).  save writes the
+ * parameters, both AdamW moments and the step count to the file at `path`
+ * (a 48-byte header -- magic "COMETPR1", version 1, in_dim, width, out_dim,
+ * the task layout, n_params, the step count -- then 3 x n_params floats,
+ * little-endian); load reads such a file into a proposal of the same layout
+ * (in_dim, width, out_dim, task), so that training continues exactly where
+ * it stopped.  The training set is not part of the file.  Both synchronous;
+ * COMET_ERR_INVALID_ARG if the file cannot be opened, written or read, is not
+ * a checkpoint, or holds another layout (the proposal is then unchanged). */
+comet_status comet_proposal_save(comet_proposal* q, const char* path);
+comet_status comet_proposal_load(comet_proposal* q, const char* path);
+
 /* Features of n orders (host or device seqs) into out_x [n][in_dim] BF16
  * bit patterns (device).  Orders of another instance index than the
  * problem's are an error (host) or zero rows (device). */

@@ -134,6 +134,7 @@ EXPORTS = (
     # include/comet_proposal.h
     "comet_default_proposal_desc", "comet_default_adamw_opts", "comet_proposal_create", "comet_proposal_destroy",
     "comet_proposal_dims", "comet_proposal_set_params", "comet_proposal_get_params", "comet_proposal_features",
+    "comet_proposal_save", "comet_proposal_load",
     "comet_proposal_forward", "comet_proposal_train_batch", "comet_proposal_add_samples",
     "comet_proposal_dataset_size", "comet_proposal_dataset_rows", "comet_proposal_train", "comet_proposal_predict", "comet_proposal_prune",
     "comet_gemm_bf16", "comet_plan_learned",
@@ -204,6 +205,8 @@ def lib(build_if_missing: bool = False):
                                               ctypes.POINTER(i64)]
             L.comet_proposal_set_params.argtypes = [vp, vp]
             L.comet_proposal_get_params.argtypes = [vp, vp, vp]
+            L.comet_proposal_save.argtypes = [vp, ctypes.c_char_p]
+            L.comet_proposal_load.argtypes = [vp, ctypes.c_char_p]
             L.comet_proposal_features.argtypes = [vp, vp, i64, vp]
             L.comet_proposal_forward.argtypes = [vp, vp, i64, vp]
             L.comet_proposal_train_batch.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(AdamWOpts),
@@ -714,6 +717,16 @@ def comet_proposal_set_params(q, flat):
 
 def comet_proposal_get_params(q, flat, grad=None):
     _check(lib().comet_proposal_get_params(q, _ptr(flat), _ptr(grad)))
+
+
+def comet_proposal_save(q, path):
+    """Parameters, AdamW moments and step count to a checkpoint file."""
+    _check(lib().comet_proposal_save(q, os.fsencode(path)))
+
+
+def comet_proposal_load(q, path):
+    """Resume from a checkpoint file of the same network layout."""
+    _check(lib().comet_proposal_load(q, os.fsencode(path)))
 
 
 def comet_proposal_features(q, seqs, n, out_x):

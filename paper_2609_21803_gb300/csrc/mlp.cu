@@ -892,6 +892,71 @@ comet_status comet_proposal_set_params(comet_proposal* q, const float* flat) {
     return COMET_OK;
 }
 
+// checkpoint file: this header, then the parameters, the two AdamW moments
+// (n_params floats each, little-endian IEEE single)
+struct ProposalCkpt {
+    char magic[8];
+    int32_t version, in_dim, width, out_dim, bim, reserved;
+    int64_t n_params, step;
+};
+constexpr char kCkptMagic[8] = {'C', 'O', 'M', 'E', 'T', 'P', 'R', '1'};
+
+comet_status comet_proposal_save(comet_proposal* q, const char* path) {
+    if (!q || !path) return qfail(COMET_ERR_INVALID_ARG, "proposal and path are required");
+    cudaStream_t s = q->p->stream;
+    const size_t n = (size_t)q->n_params;
+    std::vector<float> buf(3 * n);
+    ProposalCkpt h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+    h.version = 1;
+    h.in_dim = q->in_dim;
+    h.width = q->width;
+    h.out_dim = q->out_dim;
+    h.bim = q->bim;
+    h.n_params = q->n_params;
+    QTRY(cudaMemcpyAsync(buf.data(), q->master, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy params");
+    QTRY(cudaMemcpyAsync(buf.data() + n, q->m1, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy moments");
+    QTRY(cudaMemcpyAsync(buf.data() + 2 * n, q->m2, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy moments");
+    QTRY(cudaMemcpyAsync(&h.step, q->d_step, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "copy step count");
+    QTRY(cudaStreamSynchronize(s), "synchronise");
+    FILE* f = fopen(path, "wb");
+    if (!f) return qfail(COMET_ERR_INVALID_ARG, "checkpoint: cannot open the file for writing");
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    if (fclose(f) != 0 || !ok) return qfail(COMET_ERR_INVALID_ARG, "checkpoint: write failed");
+    return COMET_OK;
+}
+
+comet_status comet_proposal_load(comet_proposal* q, const char* path) {
+    if (!q || !path) return qfail(COMET_ERR_INVALID_ARG, "proposal and path are required");
+    FILE* f = fopen(path, "rb");
+    if (!f) return qfail(COMET_ERR_INVALID_ARG, "checkpoint: cannot open the file");
+    ProposalCkpt h;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0 || h.version != 1) {
+        fclose(f);
+        return qfail(COMET_ERR_INVALID_ARG, "checkpoint: not a proposal checkpoint");
+    }
+    if (h.in_dim != q->in_dim || h.width != q->width || h.out_dim != q->out_dim || h.bim != q->bim ||
+        h.n_params != q->n_params || h.step < 0) {
+        fclose(f);
+        return qfail(COMET_ERR_INVALID_ARG, "checkpoint: the network's layout differs from this proposal's");
+    }
+    const size_t n = (size_t)q->n_params;
+    std::vector<float> buf(3 * n);
+    const bool ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return qfail(COMET_ERR_INVALID_ARG, "checkpoint: the file is truncated");
+    cudaStream_t s = q->p->stream;
+    QTRY(cudaMemcpyAsync(q->master, buf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy params");
+    QTRY(cudaMemcpyAsync(q->m1, buf.data() + n, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy moments");
+    QTRY(cudaMemcpyAsync(q->m2, buf.data() + 2 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy moments");
+    QTRY(cudaMemcpyAsync(q->d_step, &h.step, sizeof(int64_t), cudaMemcpyHostToDevice, s), "copy step count");
+    quantize_kernel<<<grid_for(q->n_params), 256, 0, s>>>(q->master, q->n_params, layer_tab(q));
+    QTRY(cudaGetLastError(), "quantize");
+    QTRY(cudaStreamSynchronize(s), "synchronise");
+    return COMET_OK;
+}
+
 comet_status comet_proposal_get_params(comet_proposal* q, float* flat, float* grad) {
     if (!q) return qfail(COMET_ERR_INVALID_ARG, "proposal is NULL");
     cudaStream_t s = q->p->stream;

@@ -356,3 +356,62 @@ def test_fused_forward_at_pruning_size(P):
     assert np.all(np.isfinite(y))
     P.comet_proposal_destroy(q)
     prob.close()
+
+
+def test_checkpoint_resumes_training_exactly(P, tmp_path):
+    # two proposals over the same training set: the second loads the first's
+    # checkpoint after some training steps, and both then continue with the
+    # same batches; parameters, moments and step count were all restored, so
+    # the two stay together up to the order of the training step's atomic
+    # sums (about 1e-6 relative), far below what restarting the optimiser
+    # moves (asserted last)
+    prob, insts = _problem(P)
+    rng = np.random.default_rng(7)
+    n = 600
+    seqs = [tuple(int(m) for m in rng.integers(0, 12, rng.integers(1, 5))) for _ in range(n)]
+    idx = rng.integers(0, 2, n).astype(np.int32)
+    packed = P.pack_mode_seqs(seqs, idx)
+    stride = prob.stride
+    cost = rng.uniform(0.01, 2.0, n).astype(np.float32)
+    viol = (rng.uniform(0, 1, n) ** 4 * 1e-3).astype(np.float32)
+    status = rng.choice([0, 0, 0, 1, 2], n).astype(np.int32)
+    traj = rng.normal(size=(n, stride)).astype(np.float32)
+    qa = P.comet_proposal_create(prob.handle, {"dataset_cap": n})
+    qb = P.comet_proposal_create(prob.handle, {"dataset_cap": n})
+    for q in (qa, qb):
+        P.comet_proposal_add_samples(q, packed, n, cost, viol, status, traj)
+    P.comet_proposal_train(qa, 40, 256, {"lr": 1e-3}, seed=1)
+    path = str(tmp_path / "proposal.ckpt")
+    P.comet_proposal_save(qa, path)
+    P.comet_proposal_load(qb, path)
+    _, _, _, npar = P.comet_proposal_dims(qa)
+    a, b = np.zeros(npar, np.float32), np.zeros(npar, np.float32)
+    P.comet_proposal_get_params(qa, a)
+    P.comet_proposal_get_params(qb, b)
+    np.testing.assert_array_equal(a, b)
+    la = P.comet_proposal_train(qa, 25, 256, {"lr": 1e-3}, seed=2)
+    lb = P.comet_proposal_train(qb, 25, 256, {"lr": 1e-3}, seed=2)
+    np.testing.assert_allclose(lb, la, rtol=1e-5)
+    P.comet_proposal_get_params(qa, a)
+    P.comet_proposal_get_params(qb, b)
+    np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6)
+    # a proposal whose moments were reset takes a different step
+    qc = P.comet_proposal_create(prob.handle, {"dataset_cap": n})
+    P.comet_proposal_add_samples(qc, packed, n, cost, viol, status, traj)
+    P.comet_proposal_load(qc, path)
+    P.comet_proposal_get_params(qc, b)
+    P.comet_proposal_set_params(qc, b)   # same weights, optimiser reset
+    lc = P.comet_proposal_train(qc, 25, 256, {"lr": 1e-3}, seed=2)
+    assert np.max(np.abs(lc - la) / np.abs(la)) > 1e-3
+    # files that are not checkpoints of this layout are refused
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint" * 8)
+    with pytest.raises(P.CometError):
+        P.comet_proposal_load(qb, str(bad))
+    raw = open(path, "rb").read()
+    (tmp_path / "short.ckpt").write_bytes(raw[: len(raw) // 2])
+    with pytest.raises(P.CometError):
+        P.comet_proposal_load(qb, str(tmp_path / "short.ckpt"))
+    for q in (qa, qb, qc):
+        P.comet_proposal_destroy(q)
+    prob.close()
