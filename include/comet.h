@@ -296,6 +296,20 @@ comet_status comet_frontier_next(comet_frontier* f, const comet_mode_seq** seqs,
  * return its size in *n; BUDGET if cap is too small; synchronises. */
 comet_status comet_frontier_copy_next(comet_frontier* f, comet_mode_seq* out, int64_t cap, int64_t* n);
 
+/* Checkpoint and resume of a frontier (an addition of this library): save
+ * writes V (its mode codes and M_hat merits) and the pending batch F_{s+1}
+ * to the file at `path` (a 56-byte header -- magic "COMETFV1", version 1,
+ * instance, alphabet size, L_max, edit radius, grammar, capacity, |V|,
+ * |F_{s+1}| -- then |V| u64 codes, |V| f32 merits and |F_{s+1}|
+ * comet_mode_seq records, little-endian); load reads such a file into a
+ * frontier of the same instance, alphabet, L_max and neighbourhood rule
+ * with room for it, replacing its contents and rebuilding the hash set, so
+ * that expansion continues as if never interrupted.  Both synchronous;
+ * COMET_ERR_INVALID_ARG if the file cannot be opened, written or read, is
+ * not a frontier checkpoint, or does not fit this frontier. */
+comet_status comet_frontier_save(comet_frontier* f, const char* path);
+comet_status comet_frontier_load(comet_frontier* f, const char* path);
+
 /* |V| and the device-side error flags (bit 0 malformed order, bit 1 value 2
  * capacity exceeded); synchronises. */
 comet_status comet_frontier_size(comet_frontier* f, int64_t* n_evaluated, int32_t* error_flags);

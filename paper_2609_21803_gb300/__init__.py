@@ -130,6 +130,7 @@ EXPORTS = (
     "comet_last_error", "comet_eval_modes_noalloc", "comet_fp32_fma_peak", "comet_fp32_fma_peak_threads",
     "comet_frontier_create", "comet_frontier_destroy", "comet_frontier_add", "comet_expand",
     "comet_frontier_next", "comet_frontier_size", "comet_frontier_best", "comet_frontier_copy_next",
+    "comet_frontier_save", "comet_frontier_load",
     "comet_default_plan_opts", "comet_plan",
     # include/comet_proposal.h
     "comet_default_proposal_desc", "comet_default_adamw_opts", "comet_proposal_create", "comet_proposal_destroy",
@@ -190,6 +191,8 @@ def lib(build_if_missing: bool = False):
             L.comet_frontier_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
             L.comet_frontier_copy_next.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
             L.comet_frontier_best.argtypes = [vp, i32, vp, vp]
+            L.comet_frontier_save.argtypes = [vp, ctypes.c_char_p]
+            L.comet_frontier_load.argtypes = [vp, ctypes.c_char_p]
             L.comet_default_plan_opts.argtypes = [ctypes.POINTER(PlanOpts)]
             L.comet_plan.argtypes = [vp, i32, vp, i64, ctypes.POINTER(PlanOpts), ctypes.POINTER(PlanResult), vp]
             L.comet_mode_code.argtypes = [ctypes.POINTER(ModeSeq), i32]
@@ -431,6 +434,16 @@ def comet_frontier_size(frontier):
     e = ctypes.c_int32()
     _check(lib().comet_frontier_size(frontier, ctypes.byref(n), ctypes.byref(e)))
     return n.value, e.value
+
+
+def comet_frontier_save(frontier, path):
+    """V's codes and merits and the pending batch to a checkpoint file."""
+    _check(lib().comet_frontier_save(frontier, os.fsencode(path)))
+
+
+def comet_frontier_load(frontier, path):
+    """Resume a frontier of the same instance and rule from a checkpoint."""
+    _check(lib().comet_frontier_load(frontier, os.fsencode(path)))
 
 
 def comet_frontier_best(frontier, k: int):

@@ -362,6 +362,21 @@ __global__ void compact_kernel(FrontierDev F, int64_t total, int batch, int64_t 
 
 size_t topk_smem_bytes() { return sizeof(TopKey) * kChunk; }
 
+// V's codes back into the (cleared) hash set after a checkpoint restored
+// codes[0..n) and merit[0..n)
+__global__ void restore_kernel(FrontierDev F, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        set_insert(F.set, F.set_mask, F.codes[i]);
+}
+
+cudaError_t launch_frontier_restore(const FrontierDev& F, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 4096);
+    restore_kernel<<<blocks, threads, 0, s>>>(F, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_frontier_add(const FrontierDev& F, const comet_mode_seq* seqs, int64_t n, const int64_t* d_n,
                                 const float* cost, const float* viol, float eps_feas, float merit_mu, cudaStream_t s) {
     const int64_t work = d_n ? F.batch_cap : n;

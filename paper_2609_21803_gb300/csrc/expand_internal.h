@@ -57,6 +57,7 @@ constexpr int kPushFree = 12;  // free motion in the 13-mode pushing alphabet
 
 size_t topk_smem_bytes();
 cudaError_t prepare_expand();
+cudaError_t launch_frontier_restore(const FrontierDev& F, int64_t n, cudaStream_t s);
 cudaError_t launch_frontier_add(const FrontierDev& F, const comet_mode_seq* seqs, int64_t n, const int64_t* d_n,
                                 const float* cost, const float* viol, float eps_feas, float merit_mu, cudaStream_t s);
 const TopKey* launch_topk(const FrontierDev& F, int k, cudaStream_t s, cudaError_t* err);

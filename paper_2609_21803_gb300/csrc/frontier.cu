@@ -155,6 +155,102 @@ comet_status comet_frontier_create_ex(comet_problem* p, int32_t instance, int64_
     return COMET_OK;
 }
 
+// checkpoint file: this header, then V's codes (u64) and merits (f32), then
+// the pending batch (comet_mode_seq records)
+struct FrontierCkpt {
+    char magic[8];
+    int32_t version, instance, n_modes, lmax, radius, grammar;
+    int64_t capacity, n_evaluated, n_next;
+};
+constexpr char kFrontierMagic[8] = {'C', 'O', 'M', 'E', 'T', 'F', 'V', '1'};
+
+comet_status comet_frontier_save(comet_frontier* f, const char* path) {
+    if (!f || !path) return ffail(COMET_ERR_INVALID_ARG, "frontier and path are required");
+    const comet::FrontierDev& F = f->d;
+    cudaStream_t s = f->p->stream;
+    unsigned long long nv = 0;
+    int64_t nn = 0;
+    cudaError_t e = cudaMemcpyAsync(&nv, F.nV, sizeof(nv), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, F.n_next, sizeof(nn), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fcuda(e, "checkpoint: read the sizes");
+    const int64_t n = (int64_t)std::min<unsigned long long>(nv, (unsigned long long)F.capacity);
+    nn = std::max<int64_t>(0, std::min<int64_t>(nn, f->batch));
+    std::vector<unsigned long long> codes(n);
+    std::vector<float> merit(n);
+    std::vector<comet_mode_seq> next(nn);
+    if (n) e = cudaMemcpyAsync(codes.data(), F.codes, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(merit.data(), F.merit, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nn)
+        e = cudaMemcpyAsync(next.data(), F.next, sizeof(comet_mode_seq) * nn, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fcuda(e, "checkpoint: read the frontier");
+    FrontierCkpt h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kFrontierMagic, sizeof(h.magic));
+    h.version = 1;
+    h.instance = F.instance;
+    h.n_modes = F.n_modes;
+    h.lmax = F.lmax;
+    h.radius = F.radius;
+    h.grammar = F.grammar;
+    h.capacity = F.capacity;
+    h.n_evaluated = n;
+    h.n_next = nn;
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: cannot open the file for writing");
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+    ok = ok && (n == 0 || (fwrite(codes.data(), sizeof(unsigned long long), n, fp) == (size_t)n &&
+                           fwrite(merit.data(), sizeof(float), n, fp) == (size_t)n));
+    ok = ok && (nn == 0 || fwrite(next.data(), sizeof(comet_mode_seq), nn, fp) == (size_t)nn);
+    if (fclose(fp) != 0 || !ok) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: write failed");
+    return COMET_OK;
+}
+
+comet_status comet_frontier_load(comet_frontier* f, const char* path) {
+    if (!f || !path) return ffail(COMET_ERR_INVALID_ARG, "frontier and path are required");
+    comet::FrontierDev& F = f->d;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: cannot open the file");
+    FrontierCkpt h;
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, kFrontierMagic, sizeof(h.magic)) != 0 || h.version != 1) {
+        fclose(fp);
+        return ffail(COMET_ERR_INVALID_ARG, "checkpoint: not a frontier checkpoint");
+    }
+    if (h.instance != F.instance || h.n_modes != F.n_modes || h.lmax != F.lmax || h.radius != F.radius ||
+        h.grammar != F.grammar || h.n_evaluated < 0 || h.n_evaluated > F.capacity || h.n_next < 0 ||
+        h.n_next > f->batch) {
+        fclose(fp);
+        return ffail(COMET_ERR_INVALID_ARG, "checkpoint: another instance, alphabet, rule or a larger frontier");
+    }
+    const int64_t n = h.n_evaluated, nn = h.n_next;
+    std::vector<unsigned long long> codes(n);
+    std::vector<float> merit(n);
+    std::vector<comet_mode_seq> next(nn);
+    bool ok = n == 0 || (fread(codes.data(), sizeof(unsigned long long), n, fp) == (size_t)n &&
+                         fread(merit.data(), sizeof(float), n, fp) == (size_t)n);
+    ok = ok && (nn == 0 || fread(next.data(), sizeof(comet_mode_seq), nn, fp) == (size_t)nn);
+    fclose(fp);
+    if (!ok) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: the file is truncated");
+    for (int64_t i = 0; i < n; ++i)
+        if (codes[i] == 0) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: an invalid mode code");
+    cudaStream_t s = f->p->stream;
+    const unsigned long long nv = (unsigned long long)n;
+    cudaError_t e = cudaMemsetAsync(F.set, 0, sizeof(unsigned long long) * (F.set_mask + 1), s);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(F.codes, codes.data(), sizeof(unsigned long long) * n,
+                                                   cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(F.merit, merit.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nn)
+        e = cudaMemcpyAsync(F.next, next.data(), sizeof(comet_mode_seq) * nn, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F.nV, &nv, sizeof(nv), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F.n_next, &h.n_next, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(F.error, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = comet::launch_frontier_restore(F, n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fcuda(e, "checkpoint: restore the frontier");
+    return COMET_OK;
+}
+
 comet_status comet_frontier_destroy(comet_frontier* f) {
     if (!f) return COMET_OK;
     if (f->p && f->p->stream) cudaStreamSynchronize(f->p->stream); else cudaDeviceSynchronize();

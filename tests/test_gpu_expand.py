@@ -195,3 +195,57 @@ def test_uniform_sampler_matches_oracle(P, grammar):
         assert all(int(r["instance"]) == 0 for r in rec)
         assert got == S.sample_orders(seed, 100, 3000, inst["n_modes"], inst["max_segments"], grammar)
     prob.close()
+
+
+def test_frontier_checkpoint_resumes_the_rounds(P, tmp_path):
+    # Algorithm 1's rounds with a synthetic merit, interrupted after two
+    # rounds: the frontier saved there and loaded into a new frontier walks
+    # the same remaining rounds as the uninterrupted one (same batches, same
+    # best orders); mismatched frontiers and foreign files are refused
+    prob, inst = _problem(P, 4)
+    M = 12
+    target = (3, 8, 1, 10)
+
+    def merit_of(batch):
+        return [np.float32(sum(a != b for a, b in zip(s + (-1,) * 4, target)) + 0.01 * len(s)) for s in batch]
+
+    def rounds(f, frontier, n):
+        seen = []
+        for _ in range(n):
+            _add(P, f, frontier, merit_of(frontier))
+            P.comet_expand(prob.handle, f, 16)
+            frontier = _next(P, f)
+            seen.append(frontier)
+        return frontier, seen
+
+    seeds = [(m,) for m in range(M)]
+    fa = P.comet_frontier_create(prob.handle, 0, 20000, 200, 16)
+    mid, _ = rounds(fa, seeds, 2)
+    path = str(tmp_path / "frontier.ckpt")
+    P.comet_frontier_save(fa, path)
+    fb = P.comet_frontier_create(prob.handle, 0, 20000, 200, 16)
+    P.comet_frontier_load(fb, path)
+    assert P.comet_frontier_size(fb)[0] == P.comet_frontier_size(fa)[0]
+    assert _next(P, fb) == mid
+    ca, ma = P.comet_frontier_best(fa, 16)
+    cb, mb = P.comet_frontier_best(fb, 16)
+    np.testing.assert_array_equal(ca, cb)
+    np.testing.assert_array_equal(ma, mb)
+    _, seen_a = rounds(fa, mid, 3)
+    _, seen_b = rounds(fb, mid, 3)
+    assert seen_a == seen_b
+    np.testing.assert_array_equal(P.comet_frontier_best(fa, 16)[0], P.comet_frontier_best(fb, 16)[0])
+    # another neighbourhood rule, a smaller frontier, a foreign file
+    fr = P.comet_frontier_create(prob.handle, 0, 20000, 200, 16, radius=2)
+    with pytest.raises(P.CometError):
+        P.comet_frontier_load(fr, path)
+    fs = P.comet_frontier_create(prob.handle, 0, 100, 50, 16)
+    with pytest.raises(P.CometError):
+        P.comet_frontier_load(fs, path)
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"\0" * 200)
+    with pytest.raises(P.CometError):
+        P.comet_frontier_load(fb, str(bad))
+    for f in (fa, fb, fr, fs):
+        P.comet_frontier_destroy(f)
+    prob.close()
