@@ -1208,7 +1208,7 @@ __device__ BCert bcertify(BCtx& C, float beta_f) {
     return ct;
 }
 
-__global__ void __launch_bounds__(kBimThreads, 3) bimanual_kernel(EvalArgs A) {
+__global__ void __launch_bounds__(kBimThreads, 4) bimanual_kernel(EvalArgs A) {
     extern __shared__ float bsm[];
     BCtx C;
     C.tid = threadIdx.x;
