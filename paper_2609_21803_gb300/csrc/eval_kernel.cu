@@ -13,11 +13,13 @@
 //      complementarity, the local AL model over (u_k, x_{k+1}, x_k) and the
 //      elimination of the u_k block (independent of the value function, so
 //      it is taken off the sequential path);
-//   B  backward sweep k = N-1 .. 0 over S_k = H_k + rho I + beta A_k^T A_k
-//      (Sec. III-C "Fixed-workspace local solves"): only the 4 x_{k+1}
-//      columns are eliminated on the sequential path (Cholesky without
-//      pivoting, a failed pivot raises damping), producing V_k and the gains;
-//   C  forward pass dw_k = G_k [dx_k; 1];
+//   B  the state steps dx_0 .. dx_N from the block-tridiagonal system left
+//      after phase A (S_k = H_k + rho I + beta A_k^T A_k, Sec. III-C
+//      "Fixed-workspace local solves"): the same block Cholesky without
+//      pivoting as the backward sweep, taken in a lane-parallel order
+//      (lanes fold their stages, a shuffle tree joins them, a root solve,
+//      back-substitution); a failed pivot raises damping;
+//   C  stage-parallel control steps du_k from the u-block factors and dx;
 //   D  parallel trial-step merits: lane = (trial alpha, stage group), alpha
 //      in {0, 1, 1/2, ..., 1/64}, Armijo on the largest passing alpha;
 //   E  compensated update z += alpha dz and multiplier / penalty updates.
