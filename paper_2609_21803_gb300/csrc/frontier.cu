@@ -234,6 +234,11 @@ comet_status comet_frontier_load(comet_frontier* f, const char* path) {
     if (!ok) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: the file is truncated");
     for (int64_t i = 0; i < n; ++i)
         if (codes[i] == 0) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: an invalid mode code");
+    for (int64_t i = 0; i < nn; ++i) {
+        bool bad = next[i].instance != F.instance || next[i].len < 1 || next[i].len > F.lmax;
+        for (int j = 0; !bad && j < next[i].len; ++j) bad = next[i].modes[j] >= F.n_modes;
+        if (bad) return ffail(COMET_ERR_INVALID_ARG, "checkpoint: a pending order outside this frontier's alphabet");
+    }
     cudaStream_t s = f->p->stream;
     const unsigned long long nv = (unsigned long long)n;
     cudaError_t e = cudaMemsetAsync(F.set, 0, sizeof(unsigned long long) * (F.set_mask + 1), s);

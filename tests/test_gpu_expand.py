@@ -246,6 +246,17 @@ def test_frontier_checkpoint_resumes_the_rounds(P, tmp_path):
     bad.write_bytes(b"\0" * 200)
     with pytest.raises(P.CometError):
         P.comet_frontier_load(fb, str(bad))
+    # a truncated file, and a pending order with a mode outside the alphabet
+    # (the last 40-byte record's first mode: int32 instance, u8 len, 3 pad
+    # bytes, then u16 modes)
+    raw = bytearray(open(path, "rb").read())
+    bad.write_bytes(bytes(raw[:-10]))
+    with pytest.raises(P.CometError):
+        P.comet_frontier_load(fb, str(bad))
+    raw[len(raw) - 40 + 8: len(raw) - 40 + 10] = (M).to_bytes(2, "little")
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(P.CometError):
+        P.comet_frontier_load(fb, str(bad))
     for f in (fa, fb, fr, fs):
         P.comet_frontier_destroy(f)
     prob.close()
