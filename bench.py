@@ -53,10 +53,10 @@ FLOP_PER_STAGE_ITER = 1989.2
 # under each of the timing leg's bounds
 TIMING_FLOP_PER_STAGE_ITER = {"slack": 3362.3, "binding": 3555.3}
 # DRAM bytes (read + write) of one evaluator launch over the 20,736 orders,
-# from the ncu capture of the current kernel on the 4,096-order case (8.42 MB
-# read, 1.033 GB written: spills and stage records written back from L2;
+# from the ncu capture of the current kernel on the 4,096-order case (9.37 MB
+# read, 51.1 MB written: stage records and spills leaving L2;
 # profiles/eval_kernel_push_l4.md), scaled by the TOs processed
-EVAL_TRAFFIC_BYTES = (9.287168e6 + 37.679872e6) * 20736 / 4096
+EVAL_TRAFFIC_BYTES = (9.374208e6 + 51.054592e6) * 20736 / 4096
 # nominal FP32 FMA rate at the maximum clock (152 SMs x 128 lanes x 2 flop x
 # 2070 MHz), context only: the roofline's peak is measured at run time by the
 # library's FMA microbenchmark (comet_fp32_fma_peak)
