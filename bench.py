@@ -186,11 +186,24 @@ def oracle_rate(insts, seconds_target: float = 12.0, max_n: int = 20736):
     return conv / dt, n / dt, n, cores, dt
 
 
+WORKLOAD = ("push_l4 full enumeration: 20,736 orders (4 segments x 12 modes) x N=80 intervals per step, one seeded "
+            "instance per step, cold start")
+
+
 def run_reference(args):
     rank, world, _ = rank_env()
     if rank != 0:
         return
+    import oracle
+
     insts = instances()
+    # untimed warm-up steps: a short oracle batch each (pages the library and
+    # the thread pool in)
+    cores = os.cpu_count() or 1
+    seqs = W.all_sequences(12, SEG)
+    for _ in range(args.warmup):
+        oracle.solve_batch([insts[0]], np.zeros(cores, np.int32), seqs[:cores], np.full(cores, SEG, np.int32),
+                           nthreads=cores)
     t_all = 0.0
     conv_all = 0
     for s in range(args.steps):
@@ -202,8 +215,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "push_l4 enumeration (4 segments x 12 modes, N=80), oracle sample",
-                                         "instances": N_INSTANCES, "orders_per_instance": 20736},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "instances": N_INSTANCES, "orders_per_step": 20736,
+                                         "parallelism": f"replicas x{world}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {n} orders of instance 0 per step, FP64 C oracle, one TO per thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -310,9 +323,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "push_l4 full enumeration: 20,736 orders (4 segments x 12 modes) x N=80 intervals "
-                               "per step, one seeded instance per step, cold start",
-                   "instances": N_INSTANCES, "orders_per_step": n, "l2": "flushed (256 MB write) between steps",
+        "config": {"workload": WORKLOAD, "instances": N_INSTANCES, "orders_per_step": n, "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * P.MODE_SEQ_BYTES),
